@@ -1,0 +1,566 @@
+/*
+ * prrtc_oracle.c -- plain, slow FP64 CPU oracle of the pRRTC hot path.
+ *
+ * TEST INFRASTRUCTURE: loaded only by the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg.  Shares no code with the CUDA path.  Every
+ * step below is written as the definition it implements, in binary64, with no
+ * blocking, fusion or reordering beyond what that definition states.
+ * Interface and paper citations: prrtc_oracle.h.
+ */
+#include "prrtc_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+/* ------------------------------------------------------------------ Philox */
+/* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11): each round multiplies counter words 0
+ * and 2 by two fixed odd constants, swaps the halves and xors in the key;
+ * the key is bumped by the two Weyl constants between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* Word w of the stream for (problem, it): block w/4 of Philox with counter
+ * {problem, it, w/4, 0}. */
+static uint32_t sample_word(uint64_t seed, uint32_t problem, uint32_t it, int w) {
+  uint32_t ctr[4] = {problem, it, (uint32_t)(w / 4), 0u};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  return out[w % 4];
+}
+
+/* A 32-bit word mapped to [0,1) with 24 bits: (w >> 8) * 2^-24. */
+static double unit24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+/* RANDOM_CONFIG of Alg. 1 (Halton in the paper, Philox here). */
+int orc_sample(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it,
+               double goal_bias, double* q) {
+  double u0 = unit24(sample_word(seed, problem, it, 0));
+  if (u0 < goal_bias) return 1;
+  for (int j = 0; j < r->dof; ++j) {
+    double u = unit24(sample_word(seed, problem, it, j + 1));
+    q[j] = r->lower[j] + u * (r->upper[j] - r->lower[j]);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------- forward kinematics */
+static void mat4_identity(double M[16]) {
+  memset(M, 0, 16 * sizeof(double));
+  M[0] = M[5] = M[10] = M[15] = 1.0;
+}
+
+static void mat4_mul(const double A[16], const double B[16], double C[16]) {
+  double T[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += A[4 * i + k] * B[4 * k + j];
+      T[4 * i + j] = s;
+    }
+  memcpy(C, T, sizeof(T));
+}
+
+static void mat4_translation(double x, double y, double z, double M[16]) {
+  mat4_identity(M);
+  M[3] = x;
+  M[7] = y;
+  M[11] = z;
+}
+
+/* Joint transform J_i(q): rotation about a local axis or translation along it. */
+static void joint_transform(int32_t type, double q, double M[16]) {
+  mat4_identity(M);
+  double c = cos(q), s = sin(q);
+  if (type == ORC_REV_Z) {
+    M[0] = c;  M[1] = -s;
+    M[4] = s;  M[5] = c;
+  } else if (type == ORC_REV_Y) {
+    M[0] = c;  M[2] = s;
+    M[8] = -s; M[10] = c;
+  } else if (type == ORC_REV_X) {
+    M[5] = c;  M[6] = -s;
+    M[9] = s;  M[10] = c;
+  } else if (type == ORC_PRISM_X) {
+    M[3] = q;
+  } else if (type == ORC_PRISM_Y) {
+    M[7] = q;
+  } else {
+    M[11] = q;
+  }
+}
+
+/* Frame i = T_parent * J_i(q_i) * Trans(0, 0, L_i); sphere centre = T_f * [off, 1]. */
+void orc_fk(const orc_robot* r, const double* q, double* centres, double* frames) {
+  int d = r->dof;
+  double* T = (double*)malloc((size_t)d * 16 * sizeof(double));
+  for (int i = 0; i < d; ++i) {
+    double P[16], J[16], L[16], tmp[16];
+    int par = r->joint_parent[i];
+    if (par < 0)
+      mat4_translation(r->joint_base[3 * i], r->joint_base[3 * i + 1], r->joint_base[3 * i + 2], P);
+    else
+      memcpy(P, T + 16 * par, sizeof(P));
+    joint_transform(r->joint_type[i], q[i], J);
+    mat4_translation(0.0, 0.0, r->link_length[i], L);
+    mat4_mul(P, J, tmp);
+    mat4_mul(tmp, L, T + 16 * i);
+  }
+  for (int s = 0; s < r->n_spheres; ++s) {
+    const double* F = T + 16 * r->sphere_frame[s];
+    const double* o = r->sphere_offset + 3 * s;
+    for (int k = 0; k < 3; ++k)
+      centres[3 * s + k] = F[4 * k] * o[0] + F[4 * k + 1] * o[1] + F[4 * k + 2] * o[2] + F[4 * k + 3];
+  }
+  if (frames) memcpy(frames, T, (size_t)d * 16 * sizeof(double));
+  free(T);
+}
+
+/* ------------------------------------------------------- signed distances */
+double orc_sd_box(const double* b, const double p[3]) {
+  const double* c = b;
+  const double* h = b + 3;
+  const double* R = b + 6; /* world = R * local + c, row-major */
+  double v[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+  double excess[3];
+  for (int k = 0; k < 3; ++k) {
+    double local = R[0 * 3 + k] * v[0] + R[1 * 3 + k] * v[1] + R[2 * 3 + k] * v[2];
+    excess[k] = fabs(local) - h[k];
+  }
+  double outside = sqrt(fmax(excess[0], 0.0) * fmax(excess[0], 0.0) +
+                        fmax(excess[1], 0.0) * fmax(excess[1], 0.0) +
+                        fmax(excess[2], 0.0) * fmax(excess[2], 0.0));
+  double inside = fmin(fmax(excess[0], fmax(excess[1], excess[2])), 0.0);
+  return outside + inside;
+}
+
+double orc_sd_cyl(const double* cy, const double p[3]) {
+  const double* c = cy;
+  const double* a = cy + 3;
+  double radius = cy[6], half = cy[7];
+  double v[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+  double z = v[0] * a[0] + v[1] * a[1] + v[2] * a[2];
+  double w[3] = {v[0] - z * a[0], v[1] - z * a[1], v[2] - z * a[2]};
+  double rho = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double dr = rho - radius;
+  double dz = fabs(z) - half;
+  if (dr <= 0.0 && dz <= 0.0) return fmax(dr, dz);
+  double er = fmax(dr, 0.0), ez = fmax(dz, 0.0);
+  return sqrt(er * er + ez * ez);
+}
+
+double orc_sd_sph(const double* s, const double p[3]) {
+  double v[3] = {p[0] - s[0], p[1] - s[1], p[2] - s[2]};
+  return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) - s[3];
+}
+
+/* ------------------------------------------------------------ clearance */
+double orc_clearance(const orc_robot* r, const orc_env* e, const double* q,
+                     double* env_c, double* self_c) {
+  int S = r->n_spheres;
+  double* C = (double*)malloc((size_t)(S > 0 ? S : 1) * 3 * sizeof(double));
+  orc_fk(r, q, C, NULL);
+  double ce = DBL_MAX, cs = DBL_MAX;
+  for (int s = 0; s < S; ++s) {
+    const double* p = C + 3 * s;
+    double rs = r->sphere_radius[s];
+    for (int o = 0; o < e->n_box; ++o) ce = fmin(ce, orc_sd_box(e->box + 15 * o, p) - rs);
+    for (int o = 0; o < e->n_cyl; ++o) ce = fmin(ce, orc_sd_cyl(e->cyl + 8 * o, p) - rs);
+    for (int o = 0; o < e->n_sph; ++o) ce = fmin(ce, orc_sd_sph(e->sph + 4 * o, p) - rs);
+  }
+  for (int k = 0; k < r->n_pairs; ++k) {
+    int i = r->pairs[2 * k], j = r->pairs[2 * k + 1];
+    double dx = C[3 * i] - C[3 * j], dy = C[3 * i + 1] - C[3 * j + 1], dz = C[3 * i + 2] - C[3 * j + 2];
+    cs = fmin(cs, sqrt(dx * dx + dy * dy + dz * dz) - r->sphere_radius[i] - r->sphere_radius[j]);
+  }
+  free(C);
+  if (env_c) *env_c = ce;
+  if (self_c) *self_c = cs;
+  return fmin(ce, cs);
+}
+
+void orc_check_states(const orc_robot* r, const orc_env* e, const double* Q, int32_t n,
+                      uint8_t* free_out, double* clearance_out) {
+  for (int32_t i = 0; i < n; ++i) {
+    double c = orc_clearance(r, e, Q + (size_t)i * r->dof, NULL, NULL);
+    if (free_out) free_out[i] = (uint8_t)(c >= 0.0);
+    if (clearance_out) clearance_out[i] = c;
+  }
+}
+
+/* ------------------------------------------------------------- planner */
+typedef struct tree {
+  double* q;      /* [cap*d] */
+  int32_t* parent;
+  int32_t n, cap, d;
+} tree;
+
+static int tree_add(tree* t, const double* q, int32_t parent) {
+  if (t->n >= t->cap) return -1;
+  memcpy(t->q + (size_t)t->n * t->d, q, (size_t)t->d * sizeof(double));
+  t->parent[t->n] = parent;
+  return t->n++;
+}
+
+static double dist2(const double* a, const double* b, int d) {
+  double s = 0.0;
+  for (int j = 0; j < d; ++j) s += (a[j] - b[j]) * (a[j] - b[j]);
+  return s;
+}
+
+typedef struct plan_ctx {
+  const orc_robot* r;
+  const orc_env* e;
+  const orc_params* p;
+  orc_result* res;
+  int32_t it;
+  double* scratch; /* d doubles */
+} plan_ctx;
+
+static void note_amb(plan_ctx* c, int kind) {
+  if (c->res->first_amb_iter < 0) {
+    c->res->first_amb_iter = c->it;
+    c->res->first_amb_kind = kind;
+  }
+}
+
+/* ceil(x), noting an ambiguity when x lies next to an integer.  `exact` marks
+ * arguments that are the same in every precision (delta / resolution of a
+ * clamped step), which cannot flip. */
+static int32_t ceil_checked(plan_ctx* c, double x, int exact) {
+  double nearest = floor(x + 0.5);
+  if (!exact && x > 0.0 && fabs(x - nearest) <= c->p->amb_rel * fmax(1.0, x)) note_amb(c, ORC_AMB_CEIL);
+  return (int32_t)ceil(x);
+}
+
+/* NEAREST_NEIGHBOR (Sec. III-C): argmin of squared L2 distance, lowest index
+ * on ties; a near tie is noted as ambiguous. */
+static int32_t nearest(plan_ctx* c, const tree* t, const double* q) {
+  int32_t best = -1;
+  double bd = DBL_MAX, second = DBL_MAX;
+  for (int32_t i = 0; i < t->n; ++i) {
+    double dd = dist2(t->q + (size_t)i * t->d, q, t->d);
+    if (dd < bd) {
+      second = bd;
+      bd = dd;
+      best = i;
+    } else if (dd < second) {
+      second = dd;
+    }
+  }
+  if (t->n > 1 && second - bd <= c->p->amb_rel * bd + 1e-12) note_amb(c, ORC_AMB_NN_TIE);
+  return best;
+}
+
+/* Check the n_states interpolated states a + (k/n)(b - a), k = 1..n (Alg. 2,
+ * with the endpoint b included and a excluded).  Returns 1 when all are free. */
+static int check_edge(plan_ctx* c, const double* a, const double* b, int32_t n_states) {
+  int d = c->r->dof;
+  double* s = c->scratch;
+  int marginal = 0;
+  c->res->edges_checked++;
+  c->res->edge_states += n_states;
+  int valid = 1;
+  for (int32_t k = 1; k <= n_states; ++k) {
+    double t = (double)k / (double)n_states;
+    for (int j = 0; j < d; ++j) s[j] = (k == n_states) ? b[j] : a[j] + t * (b[j] - a[j]);
+    double cl = orc_clearance(c->r, c->e, s, NULL, NULL);
+    c->res->states_checked++;
+    if (fabs(cl) <= c->p->amb_band) marginal = 1;
+    if (cl < 0.0) valid = 0;
+    if (cl < -c->p->amb_band) {
+      marginal = 0; /* robustly invalid whatever the marginal states do */
+      break;
+    }
+  }
+  if (marginal) note_amb(c, ORC_AMB_CLEARANCE);
+  return valid;
+}
+
+static int32_t chain_to_root(const tree* t, int32_t node, int32_t* out, int32_t cap) {
+  int32_t n = 0;
+  while (node >= 0) {
+    if (n < cap) out[n] = node;
+    n++;
+    node = t->parent[node];
+  }
+  return n;
+}
+
+/* PATH(T_a, T_b): root(T_a) .. join_a, then join_b .. root(T_b); the two join
+ * nodes hold the same configuration, so one copy is dropped. */
+static void build_path(plan_ctx* c, const tree* A, const tree* B, int32_t ja, int32_t jb) {
+  orc_result* res = c->res;
+  int d = c->r->dof;
+  int32_t ca_cap = A->n, cb_cap = B->n;
+  int32_t* ca = (int32_t*)malloc((size_t)(ca_cap > 0 ? ca_cap : 1) * sizeof(int32_t));
+  int32_t* cb = (int32_t*)malloc((size_t)(cb_cap > 0 ? cb_cap : 1) * sizeof(int32_t));
+  int32_t na = chain_to_root(A, ja, ca, ca_cap);
+  int32_t nb = chain_to_root(B, jb, cb, cb_cap);
+  int32_t total = na + nb - 1;
+  res->path_n = total;
+  res->cost = 0.0;
+  const double* prev = NULL;
+  int32_t w = 0;
+  for (int32_t k = na - 1; k >= 0; --k) { /* root(T_a) .. join_a */
+    const double* q = A->q + (size_t)ca[k] * d;
+    if (prev) res->cost += sqrt(dist2(prev, q, d));
+    if (res->path && w < c->p->path_capacity) memcpy(res->path + (size_t)w * d, q, (size_t)d * sizeof(double));
+    w++;
+    prev = q;
+  }
+  for (int32_t k = 1; k < nb; ++k) { /* skip join_b (same configuration as join_a) */
+    const double* q = B->q + (size_t)cb[k] * d;
+    res->cost += sqrt(dist2(prev, q, d));
+    if (res->path && w < c->p->path_capacity) memcpy(res->path + (size_t)w * d, q, (size_t)d * sizeof(double));
+    w++;
+    prev = q;
+  }
+  res->status = (total > c->p->path_capacity) ? ORC_PATH_OVERFLOW : ORC_SOLVED;
+  free(ca);
+  free(cb);
+}
+
+int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
+                 const double* q_goal, const orc_params* p, orc_result* res) {
+  int d = r->dof;
+  res->status = ORC_NO_SOLUTION;
+  res->iterations = 0;
+  res->n_a = res->n_b = 0;
+  res->join_a = res->join_b = -1;
+  res->path_n = 0;
+  res->first_amb_iter = -1;
+  res->first_amb_kind = ORC_AMB_NONE;
+  res->cost = 0.0;
+  res->edges_checked = res->states_checked = res->edge_states = 0;
+  if (d <= 0 || p->tree_capacity < 1 || p->range <= 0.0 || p->resolution <= 0.0) {
+    res->status = ORC_BAD_INPUT;
+    return res->status;
+  }
+  for (int i = 0; i < d; ++i)
+    if (r->joint_parent[i] >= i || r->joint_type[i] < 0 || r->joint_type[i] > ORC_REV_X) {
+      res->status = ORC_BAD_INPUT;
+      return res->status;
+    }
+
+  /* Alg. 1: reject a start or goal in collision up front. */
+  if (orc_clearance(r, e, q_start, NULL, NULL) < 0.0) {
+    res->status = ORC_START_IN_COLLISION;
+    return res->status;
+  }
+  if (orc_clearance(r, e, q_goal, NULL, NULL) < 0.0) {
+    res->status = ORC_GOAL_IN_COLLISION;
+    return res->status;
+  }
+
+  size_t cap = (size_t)p->tree_capacity;
+  tree A = {res->nodes_a, res->parent_a, 0, p->tree_capacity, d};
+  tree B = {res->nodes_b, res->parent_b, 0, p->tree_capacity, d};
+  int own_a = 0, own_b = 0;
+  if (!A.q) { A.q = (double*)malloc(cap * d * sizeof(double)); A.parent = (int32_t*)malloc(cap * sizeof(int32_t)); own_a = 1; }
+  if (!B.q) { B.q = (double*)malloc(cap * d * sizeof(double)); B.parent = (int32_t*)malloc(cap * sizeof(int32_t)); own_b = 1; }
+
+  double* c_rand = (double*)malloc((size_t)d * sizeof(double));
+  double* c_new = (double*)malloc((size_t)d * sizeof(double));
+  double* c_ext = (double*)malloc((size_t)d * sizeof(double));
+  double* c_tgt = (double*)malloc((size_t)d * sizeof(double));
+  double* scratch = (double*)malloc((size_t)d * sizeof(double));
+  plan_ctx ctx = {r, e, p, res, 0, scratch};
+
+  /* Alg. 1 lines 1-2: T_a <- {c_start}, T_b <- {c_goal}; roots have parent -1. */
+  tree_add(&A, q_start, -1);
+  tree_add(&B, q_goal, -1);
+
+  const double delta = p->range, resol = p->resolution;
+  for (int32_t it = 0; it < p->max_iters; ++it) {
+    ctx.it = it;
+    res->iterations = it + 1;
+    /* line 3: T_s = smaller tree, T_o = larger; ties extend T_a. */
+    int s_is_a = (A.n <= B.n);
+    tree* Ts = s_is_a ? &A : &B;
+    tree* To = s_is_a ? &B : &A;
+    /* line 4: RANDOM_CONFIG, with goal bias toward the opposite root. */
+    if (orc_sample(r, p->seed, p->problem, (uint32_t)it, p->goal_bias, c_rand))
+      memcpy(c_rand, To->q, (size_t)d * sizeof(double));
+    /* line 5: NEAREST_NEIGHBOR in T_s. */
+    int32_t nn = nearest(&ctx, Ts, c_rand);
+    const double* c_nn = Ts->q + (size_t)nn * d;
+    /* Alg. 2 line 2: INTERPOLATE -- step from c_nn toward c_rand by at most delta. */
+    double dist = sqrt(dist2(c_rand, c_nn, d));
+    if (dist <= 0.0) continue; /* no motion: nothing to add */
+    if (fabs(dist - delta) <= p->amb_rel * delta) note_amb(&ctx, ORC_AMB_STEER);
+    double len;
+    int clamped = (dist > delta);
+    if (clamped) {
+      for (int j = 0; j < d; ++j) c_new[j] = c_nn[j] + (c_rand[j] - c_nn[j]) * (delta / dist);
+      len = delta;
+    } else {
+      memcpy(c_new, c_rand, (size_t)d * sizeof(double));
+      len = dist;
+    }
+    /* Alg. 2 lines 3-5: N_cc = ceil(len / resolution) states, all must be free. */
+    int32_t n_states = ceil_checked(&ctx, len / resol, clamped);
+    if (!check_edge(&ctx, c_nn, c_new, n_states)) continue;
+    /* line 7: add c_new to T_s. */
+    int32_t idx_new = tree_add(Ts, c_new, nn);
+    if (idx_new < 0) continue;
+    /* line 8: nearest node of T_o to c_new. */
+    int32_t nno = nearest(&ctx, To, c_new);
+    memcpy(c_tgt, To->q + (size_t)nno * d, (size_t)d * sizeof(double));
+    /* lines 9-15: greedy connect in n_ext = ceil(D / delta) steps of length
+     * delta along (c_tgt - c_new)/D; the last step lands on c_tgt. */
+    double D = sqrt(dist2(c_tgt, c_new, d));
+    int32_t n_ext = (D > 0.0) ? ceil_checked(&ctx, D / delta, 0) : 0;
+    int32_t prev = idx_new;
+    int connected = 1;
+    for (int32_t i = 1; i <= n_ext; ++i) {
+      double step_len;
+      if (i < n_ext) {
+        double f = (double)i * delta / D;
+        for (int j = 0; j < d; ++j) c_ext[j] = c_new[j] + f * (c_tgt[j] - c_new[j]);
+        step_len = delta;
+      } else {
+        memcpy(c_ext, c_tgt, (size_t)d * sizeof(double));
+        step_len = D - (double)(n_ext - 1) * delta;
+      }
+      int32_t ns = ceil_checked(&ctx, step_len / resol, i < n_ext);
+      if (ns < 1) ns = 1;
+      const double* from = Ts->q + (size_t)prev * d;
+      if (!check_edge(&ctx, from, c_ext, ns)) {
+        connected = 0;
+        break;
+      }
+      int32_t added = tree_add(Ts, c_ext, prev);
+      if (added < 0) {
+        connected = 0;
+        break;
+      }
+      prev = added;
+    }
+    if (connected) {
+      /* line 16: PATH -- the last node of T_s coincides with node nno of T_o. */
+      int32_t ja = s_is_a ? prev : nno;
+      int32_t jb = s_is_a ? nno : prev;
+      res->join_a = ja;
+      res->join_b = jb;
+      res->n_a = A.n;
+      res->n_b = B.n;
+      build_path(&ctx, &A, &B, ja, jb);
+      goto done;
+    }
+  }
+  res->n_a = A.n;
+  res->n_b = B.n;
+  res->status = ORC_NO_SOLUTION;
+done:
+  free(c_rand);
+  free(c_new);
+  free(c_ext);
+  free(c_tgt);
+  free(scratch);
+  if (own_a) { free(A.q); free(A.parent); }
+  if (own_b) { free(B.q); free(B.parent); }
+  return res->status;
+}
+
+int32_t orc_revalidate(const orc_robot* r, const orc_env* e, const double* path,
+                       int32_t n, double res, double* min_clearance) {
+  int d = r->dof;
+  double mc = DBL_MAX;
+  int32_t bad = 0;
+  double* s = (double*)malloc((size_t)d * sizeof(double));
+  if (n > 0) mc = fmin(mc, orc_clearance(r, e, path, NULL, NULL));
+  for (int32_t k = 0; k + 1 < n; ++k) {
+    const double* a = path + (size_t)k * d;
+    const double* b = path + (size_t)(k + 1) * d;
+    double len = sqrt(dist2(a, b, d));
+    int32_t m = (int32_t)ceil(len / res);
+    if (m < 1) m = 1;
+    int seg_bad = 0;
+    for (int32_t j = 1; j <= m; ++j) {
+      double t = (double)j / (double)m;
+      for (int i = 0; i < d; ++i) s[i] = a[i] + t * (b[i] - a[i]);
+      double c = orc_clearance(r, e, s, NULL, NULL);
+      mc = fmin(mc, c);
+      if (c < 0.0) seg_bad = 1;
+    }
+    bad += seg_bad;
+  }
+  free(s);
+  if (min_clearance) *min_clearance = mc;
+  return bad;
+}
+
+/* ------------------------------------------------------------- batch */
+typedef struct batch_ctx {
+  orc_problem* problems;
+  int32_t n;
+  int32_t next;
+  pthread_mutex_t lock;
+} batch_ctx;
+
+static double now_seconds(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+static void* batch_worker(void* arg) {
+  batch_ctx* b = (batch_ctx*)arg;
+  for (;;) {
+    pthread_mutex_lock(&b->lock);
+    int32_t i = b->next++;
+    pthread_mutex_unlock(&b->lock);
+    if (i >= b->n) break;
+    orc_problem* pr = &b->problems[i];
+    double t0 = now_seconds();
+    orc_plan(pr->robot, pr->env, pr->q_start, pr->q_goal, &pr->params, pr->result);
+    pr->seconds = now_seconds() - t0;
+  }
+  return NULL;
+}
+
+void orc_plan_batch(orc_problem* problems, int32_t n, int32_t threads) {
+  batch_ctx b;
+  b.problems = problems;
+  b.n = n;
+  b.next = 0;
+  pthread_mutex_init(&b.lock, NULL);
+  if (threads < 1) threads = 1;
+  pthread_t* th = (pthread_t*)malloc((size_t)threads * sizeof(pthread_t));
+  for (int32_t t = 0; t < threads; ++t) pthread_create(&th[t], NULL, batch_worker, &b);
+  for (int32_t t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+  free(th);
+  pthread_mutex_destroy(&b.lock);
+}

@@ -1,0 +1,171 @@
+/*
+ * prrtc_oracle.h -- plain, slow FP64 CPU oracle of the pRRTC hot path.
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header
+ * or table with the CUDA path (paper_2503_06757_gb300/csrc), and the product
+ * path never calls it.
+ *
+ * What it computes (pRRTC, Huang et al. 2025):
+ *   - Alg. 1 (pRRTC top level) executed serially: balanced tree choice,
+ *     sampling, nearest neighbour, pEXTEND, insertion, greedy connect, PATH.
+ *   - Alg. 2 (pEXTEND): steer by at most delta, then check the interpolated
+ *     states of the edge at the fixed collision-checking resolution.
+ *   - Sec. III-A: collision checking of a sphere model against cuboids,
+ *     capped cylinders and spheres, plus self-collision between sphere pairs.
+ *   - Philox4x32-10 (Salmon et al., SC'11) for the sampler (the paper samples
+ *     with Halton sequences; the counter-based generator replaces them).
+ * Every floating-point step is in IEEE binary64.
+ *
+ * Parity-pinned functions (see tests/test_oracle_pins.py):
+ *   orc_philox4x32_10  - published known-answer vectors of Random123.
+ *   orc_fk             - closed-form tip positions of 1-, 2- and 3-link chains.
+ *   orc_sd_box/cyl/sph - brute-force surface/volume sampling on tiny inputs.
+ *   orc_plan           - tree invariants, obstacle-free and walled-off special
+ *                        cases, grid-BFS reachability of a point robot.
+ */
+#ifndef PRRTC_ORACLE_H
+#define PRRTC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_REV_Z = 0, ORC_REV_Y = 1, ORC_PRISM_Z = 2, ORC_PRISM_X = 3, ORC_PRISM_Y = 4, ORC_REV_X = 5 };
+
+enum {
+  ORC_SOLVED = 0,
+  ORC_START_IN_COLLISION = 1,
+  ORC_GOAL_IN_COLLISION = 2,
+  ORC_NO_SOLUTION = 3,
+  ORC_PATH_OVERFLOW = 4,
+  ORC_BAD_INPUT = -1
+};
+
+/* Ambiguity kinds recorded by the planner: decisions whose outcome could flip
+ * under FP32 rounding (the device path) and so end an exact comparison. */
+enum {
+  ORC_AMB_NONE = 0,
+  ORC_AMB_CLEARANCE = 1, /* a checked state had |clearance| <= band       */
+  ORC_AMB_NN_TIE = 2,    /* best and second-best squared distances close  */
+  ORC_AMB_CEIL = 3,      /* a ceil() argument lay next to an integer      */
+  ORC_AMB_STEER = 4      /* sample distance next to the range delta        */
+};
+
+typedef struct orc_robot {
+  int32_t dof;
+  const int32_t* joint_type;   /* [dof]  ORC_REV_* / ORC_PRISM_* (local axis)  */
+  const int32_t* joint_parent; /* [dof]  parent joint, -1 = world             */
+  const double* joint_base;    /* [dof*3] world offset of world-parented joints */
+  const double* link_length;   /* [dof]  translation along local z after J_i  */
+  const double* lower;         /* [dof]  joint limits                          */
+  const double* upper;         /* [dof]                                        */
+  int32_t n_spheres;
+  const int32_t* sphere_frame; /* [S]    frame (joint) carrying the sphere     */
+  const double* sphere_offset; /* [S*3]  centre in frame coordinates           */
+  const double* sphere_radius; /* [S]                                          */
+  int32_t n_pairs;
+  const int32_t* pairs;        /* [P*2]  sphere pairs tested for self-collision */
+} orc_robot;
+
+typedef struct orc_env {
+  int32_t n_box;
+  const double* box;   /* [n_box*15]: centre(3) half(3) R(9, row-major, world = R*local + c) */
+  int32_t n_cyl;
+  const double* cyl;   /* [n_cyl*8]: centre(3) unit axis(3) radius half_length */
+  int32_t n_sph;
+  const double* sph;   /* [n_sph*4]: centre(3) radius */
+} orc_env;
+
+typedef struct orc_params {
+  double range;          /* delta: extension range (configuration-space L2)  */
+  double resolution;     /* collision-checking resolution along an edge      */
+  double goal_bias;      /* probability of sampling the opposite tree's root */
+  double amb_band;       /* clearance band treated as ambiguous (1e-5 m)     */
+  double amb_rel;        /* relative gap that makes an NN / ceil decision ambiguous */
+  uint64_t seed;         /* Philox key                                       */
+  uint32_t problem;      /* Philox counter word 0                            */
+  int32_t max_iters;     /* global budget of Alg. 1 bodies                    */
+  int32_t tree_capacity; /* nodes per tree; an insertion into a full tree fails */
+  int32_t path_capacity; /* rows of the caller's path buffer                 */
+} orc_params;
+
+typedef struct orc_result {
+  int32_t status;
+  int32_t iterations;          /* Alg. 1 bodies executed (it + 1 at success)    */
+  int32_t n_a, n_b;            /* tree sizes                                   */
+  int32_t join_a, join_b;      /* joined nodes (indices into T_a, T_b)         */
+  int32_t path_n;              /* waypoints written to path                    */
+  int32_t first_amb_iter;      /* first iteration with an ambiguous decision, -1 none */
+  int32_t first_amb_kind;
+  int32_t pad_;
+  double cost;                 /* sum of L2 segment lengths                    */
+  int64_t edges_checked;       /* edges whose states were examined            */
+  int64_t states_checked;      /* states examined (stop at the first collision) */
+  int64_t edge_states;         /* sum over checked edges of their state count   */
+  /* caller-owned buffers (nullable): trees and path */
+  double* nodes_a;             /* [tree_capacity*dof] */
+  int32_t* parent_a;           /* [tree_capacity]     */
+  double* nodes_b;
+  int32_t* parent_b;
+  double* path;                /* [path_capacity*dof] */
+} orc_result;
+
+/* Philox4x32-10 block: out = Philox(ctr, key).  Salmon et al. SC'11. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Sample of Alg. 1 (RANDOM_CONFIG) for iteration `it`: returns 1 when the
+ * goal-bias branch fires (the caller substitutes the opposite root), else 0
+ * and writes a uniform configuration inside the joint limits to q. */
+int orc_sample(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it,
+               double goal_bias, double* q);
+
+/* Forward kinematics by 4x4 homogeneous products.  centres: [S*3];
+ * frames (nullable): [dof*16] row-major world transforms. */
+void orc_fk(const orc_robot* r, const double* q, double* centres, double* frames);
+
+/* Signed distances from a point to one obstacle (negative inside). */
+double orc_sd_box(const double* box15, const double p[3]);
+double orc_sd_cyl(const double* cyl8, const double p[3]);
+double orc_sd_sph(const double* sph4, const double p[3]);
+
+/* Clearance of one configuration: min over (sphere, obstacle) of sd - r and
+ * over self pairs of |ci - cj| - ri - rj.  The state is in collision iff the
+ * clearance is negative.  env_c / self_c (nullable) receive the two parts. */
+double orc_clearance(const orc_robot* r, const orc_env* e, const double* q,
+                     double* env_c, double* self_c);
+
+/* Verdicts for n states (row-major [n*dof]); free[i] = clearance >= 0. */
+void orc_check_states(const orc_robot* r, const orc_env* e, const double* Q, int32_t n,
+                      uint8_t* free_out, double* clearance_out);
+
+/* Serial pRRTC (Alg. 1 with Alg. 2).  Returns res->status. */
+int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
+                 const double* q_goal, const orc_params* p, orc_result* res);
+
+/* Re-check every segment of a path at resolution `res`: each segment of
+ * length l is split into ceil(l/res) steps and all states after the first
+ * waypoint are tested.  Returns the number of segments with a colliding state;
+ * *min_clearance receives the smallest clearance seen. */
+int32_t orc_revalidate(const orc_robot* r, const orc_env* e, const double* path,
+                       int32_t n, double res, double* min_clearance);
+
+/* Batch of independent plans on `threads` POSIX threads (one problem at a
+ * time per thread).  Arrays are indexed by problem. */
+typedef struct orc_problem {
+  const orc_robot* robot;
+  const orc_env* env;
+  const double* q_start;
+  const double* q_goal;
+  orc_params params;
+  orc_result* result;
+  double seconds;              /* wall time of this plan (output) */
+} orc_problem;
+
+void orc_plan_batch(orc_problem* problems, int32_t n, int32_t threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
