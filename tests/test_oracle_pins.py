@@ -443,3 +443,30 @@ def test_plan_batch_matches_single():
     for pb, r in zip(pbs, rs):
         one = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=2)
         assert one["cost"] == r["cost"] and one["iterations"] == r["iterations"]
+
+
+@pytest.mark.parametrize("D", [0.7, 2.3, 3.61, 5.05])
+def test_plan_straight_line_state_counts(D):
+    """Free space with goal bias 1: the first extension moves delta toward the goal,
+    then the connect covers D - delta in ceil((D - delta)/delta) steps.  Every edge of
+    length l is checked at ceil(l / res) states, endpoint included, so the counts
+    are fixed in closed form."""
+    rb = H.no_self(W.arm7())
+    s = np.zeros(7)
+    u = np.array([1.0, -2.0, 0.5, 0.0, 1.5, -1.0, 0.25])
+    u /= np.linalg.norm(u)
+    g = s + D * u
+    delta, res = 1.0, 1.0 / 32
+    r = O.plan(rb, H.empty_scene(), s, g, seed=1, goal_bias=1.0, range=delta, resolution=res)
+    assert r["status"] == 0 and r["iterations"] == 1
+    if D <= delta:
+        edges, states = 1, int(np.ceil(D / res))
+    else:
+        rest = D - delta
+        n_ext = int(np.ceil(rest / delta))
+        last = rest - (n_ext - 1) * delta
+        edges = 1 + n_ext
+        states = int(round(delta / res)) * n_ext + int(np.ceil(last / res))
+    assert r["edges_checked"] == edges
+    assert r["edge_states"] == states
+    assert r["states_checked"] == states
