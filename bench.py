@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the pRRTC hot path on GB300 (one JSON line on stdout).
+
+Step = one batched planning launch (prrtc_plan_batch) over the 200-problem
+cubby-shelf workload: a synthetic 7-DoF arm, 3x3 shelf of 0.3 m cells plus
+clutter (30 cuboids, 10 capped cylinders, 10 spheres), goals inside cubbies,
+edge resolution 1/32, range 1.0, 5% goal bias, at most 50k iterations per
+problem.  All inputs are seeded and synthetic (stand-ins for the paper's
+MotionBenchMaker scenes, which are not available here).
+
+Reported:
+  value      edge states checked per second over the device time of the
+             setup + planner kernels (CUDA events on the launching stream).
+  e2e        the same metric over the wall time of the whole C-ABI call with
+             host buffers (descriptor upload and result download included).
+  ttfs       time to first solution per problem (device %globaltimer from
+             launch start), p50/p95/p99; plus single-problem TTFS through
+             prrtc_plan (host wall clock, environment resident).
+  roofline   the planner kernel's counted arithmetic against the issue-rate
+             bound of the SMs (128 lane-instructions / clock / SM).
+  cpu_baseline  the FP64 oracle on the host cores (bounded sample).
+
+`--impl reference` times the oracle alone on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p50/p95 time-to-first-solution & edge states checked/s; learned vs plain, 1 GB300"
+UNIT = "edge states/s"
+WORKLOAD = "shelf-200: 200 cubby-shelf problems, 7-DoF arm (28 spheres), 50 obstacles each, one launch"
+
+# Counted arithmetic per test (lane-level instructions of the test as written:
+# FADD/FMUL/FFMA/FMNMX/FSETP, MUFU counted once).
+OPS = dict(centre=9, aabb=13, obb=22, cyl=24, sph=9, pair=7, joint=17)
+
+
+def percentiles(v, ps=(50, 95, 99)):
+    if not len(v):
+        return {f"p{p}": None for p in ps}
+    return {f"p{p}": float(np.percentile(v, p)) for p in ps}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+
+def gpu_accept_factory(P):
+    """Start/goal acceptance through the device collision checker."""
+    cache = {}
+
+    def accept(robot, scene, Q):
+        key = (robot.name, id(scene))
+        if key not in cache:
+            cache.clear()
+            cache[key] = (P.make_robot(robot), P.make_env(scene))
+        rb, ev = cache[key]
+        valid, sph = P.prrtc_check_states(rb, ev, Q, want_spheres=True)
+        ee = np.zeros((len(Q), len(robot.ee_frames), 3))
+        for k, f in enumerate(robot.ee_frames):
+            idx = np.nonzero(robot.sphere_frame == f)[0]
+            z = robot.sphere_offset[idx, 2]
+            order = idx[np.argsort(z)]
+            a, b = order[-2], order[-1]          # two outermost spheres on the link axis
+            za, zb = robot.sphere_offset[a, 2], robot.sphere_offset[b, 2]
+            ca, cb = sph[:, a, :3].astype(np.float64), sph[:, b, :3].astype(np.float64)
+            ee[:, k] = cb + (cb - ca) * ((0.0 - zb) / (zb - za))   # frame origin at offset 0
+        return valid, ee
+
+    return accept
+
+
+def shelf_problems(accept, count=200, seed0=1000):
+    from paper_2503_06757_gb300 import workload as W
+    return W.problem_set("shelf", count, seed0, accept)
+
+
+def c1_problem(accept):
+    from paper_2503_06757_gb300 import workload as W
+    return W.problem_set("c1", 1, 1, accept)[0]
+
+
+def op_count(path, env_counts, dof, dpad):
+    a, o, c, s = env_counts
+    per_sphere = OPS["centre"] + OPS["aabb"] * a + OPS["obb"] * o + OPS["cyl"] * c + OPS["sph"] * s
+    return (path["sphere_tests"] * per_sphere + path["pair_tests"] * OPS["pair"] +
+            path["fk_states"] * OPS["joint"] * dof + path["nn_nodes"] * (2 * dpad + 1))
+
+
+# ------------------------------------------------------------------ CPU baseline
+
+def oracle_sample(problems, budget_s=12.0, threads=None):
+    """The oracle as it stands on the host cores: whole problems, in chunks of
+    `threads`, until the time budget is used."""
+    from oracle import oracle as O
+    threads = threads or os.cpu_count() or 1
+    done, states, wall, solved, costs = 0, 0, 0.0, 0, []
+    while done < len(problems) and wall < budget_s:
+        chunk = problems[done:done + threads]
+        t = time.perf_counter()
+        rs = O.plan_batch(chunk, threads=threads, seed=1, problem_ids=list(range(done, done + len(chunk))),
+                          range=1.0, resolution=float(np.float32(1 / 32)), goal_bias=float(np.float32(0.05)))
+        wall += time.perf_counter() - t
+        done += len(chunk)
+        for r in rs:
+            states += r["edge_states"]
+            solved += r["status"] == 0
+            if r["status"] == 0:
+                costs.append(r["cost"])
+    return dict(value=states / wall if wall > 0 else None, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"first {done} of {len(problems)} shelf problems, 1 Philox key, one problem per thread",
+                problems=done, seconds=wall, success_rate=solved / max(done, 1),
+                mean_cost=float(np.mean(costs)) if costs else None)
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    # the oracle builds its own start/goal acceptance
+    probs = shelf_problems(O.accept, count=args.problems)
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(probs, budget_s=budget / 4)
+    vals, secs = [], []
+    last = None
+    for _ in range(args.steps):
+        r = oracle_sample(probs, budget_s=budget)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+        last = r
+    value = float(np.mean(vals))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * float(np.mean(secs)), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, problems=args.problems, sample="bounded per step"),
+                cpu_baseline=dict(last, value=value),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        # the library keeps its own CUDA runtime state: give each rank one visible GPU
+        os.environ["CUDA_VISIBLE_DEVICES"] = str(local)
+    import torch
+    from paper_2503_06757_gb300 import build as B
+    B.build()
+    from paper_2503_06757_gb300 import prrtc as P
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.init()
+    dev_props = torch.cuda.get_device_properties(0)
+    sms = dev_props.multi_processor_count
+
+    accept = gpu_accept_factory(P)
+    probs = shelf_problems(accept, count=args.problems, seed0=1000 + 10000 * rank)
+    robots, envs, items, counts = {}, [], [], []
+    for k, pb in enumerate(probs):
+        if pb.robot.name not in robots:
+            robots[pb.robot.name] = P.make_robot(pb.robot)
+        rb = robots[pb.robot.name]
+        ev = P.make_env(pb.scene)
+        envs.append(ev)
+        info = rb.info()
+        counts.append((ev.info(), pb.robot.dof, info["dpad"]))
+        items.append((rb, ev, pb.q_start, pb.q_goal, 1, rank * args.problems + k))
+    prm = P.params()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        P.prrtc_plan_batch(items, prm)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    dev_ms, wall_s, edge_states, ops, launches, h2d, d2h = 0.0, 0.0, 0, 0, 0, 0, 0
+    kernel_ms = 0.0
+    ttfs, solved, costs = [], 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = P.prrtc_plan_batch(items, prm)
+        wall_s += time.perf_counter() - t
+        st = P.prrtc_last_launch_stats()
+        dev_ms += st["kernel_ms"] + st["setup_ms"]
+        kernel_ms += st["kernel_ms"]
+        launches += st["kernels"]
+        h2d += st["h2d_bytes"]
+        d2h += st["d2h_bytes"]
+        for r, (ec, dof, dpad) in zip(res, counts):
+            edge_states += r["edge_states"]
+            ops += op_count(r, ec, dof, dpad)
+            if r["status"] == P.SOLVED:
+                solved += 1
+                ttfs.append(r["solve_time_us"])
+                costs.append(r["cost"])
+    torch.cuda.synchronize()
+    plan_grid = dict(blocks=st["grid"], threads=st["block_threads"], smem=st["smem_bytes"])
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+
+    total_states = edge_states
+    device_s = dev_ms * 1e-3
+    if dist:
+        t = torch.tensor([device_s, wall_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        device_s, wall_s = float(t[0]), float(t[1])
+        n = torch.tensor([total_states], dtype=torch.float64, device="cuda")
+        dist.all_reduce(n)
+        total_states = float(n[0])
+    value = total_states / device_s
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gops = sms * 128 * sm_max * 1e-3
+    achieved_gops = ops / (kernel_ms * 1e-3) * 1e-9
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # single-problem TTFS through prrtc_plan (host wall clock, env resident)
+        c1 = c1_problem(accept)
+        rb1, ev1 = P.make_robot(c1.robot), P.make_env(c1.scene)
+        for key in range(1, 4):
+            P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, P.params(seed=key))
+        tt, ok = [], 0
+        for key in range(1, 101):
+            t = time.perf_counter()
+            r = P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, P.params(seed=key))
+            tt.append((time.perf_counter() - t) * 1e3)
+            ok += r["status"] == P.SOLVED
+        extra["ttfs_single_c1_ms"] = dict(percentiles(tt), success_rate=ok / 100, keys=100,
+                                          workload="c1: 7-DoF arm, 8 random cuboids, one problem, keys 1..100")
+        # collision-check microbenchmark: collision-free shelf states, every test runs
+        pb = probs[0]
+        rb, ev = robots[pb.robot.name], envs[0]
+        from paper_2503_06757_gb300 import workload as W
+        Q = W.candidates(pb.robot, 7, 3, 1 << 21).astype(np.float32)
+        F = Q[P.prrtc_check_states(rb, ev, Q)][: 1 << 20]
+        for _ in range(3):
+            P.prrtc_check_states(rb, ev, F)
+        ms = []
+        for _ in range(5):
+            flush.zero_()
+            torch.cuda.synchronize()
+            P.prrtc_check_states(rb, ev, F)
+            ms.append(P.prrtc_last_launch_stats()["kernel_ms"])
+        st = P.prrtc_last_launch_stats()
+        ec = ev.info()
+        per_sphere = OPS["centre"] + OPS["aabb"] * ec[0] + OPS["obb"] * ec[1] + OPS["cyl"] * ec[2] + OPS["sph"] * ec[3]
+        cc_ops = st["sphere_tests"] * per_sphere + st["pair_tests"] * OPS["pair"] + st["fk_states"] * OPS["joint"] * 7
+        kms = float(np.median(ms))
+        extra["roofline_cc_microbench"] = dict(
+            bound="alu", achieved=cc_ops / (kms * 1e-3) * 1e-9, peak=peak_gops, unit="Gop/s",
+            frac=cc_ops / (kms * 1e-3) * 1e-9 / peak_gops, states=int(len(F)), kernel_ms=kms,
+            states_per_s=len(F) / (kms * 1e-3), ops_per_state=cc_ops / len(F))
+        extra["cpu_baseline"] = oracle_sample(probs, budget_s=args.cpu_budget)
+
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=dev_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic",
+        config=dict(workload=WORKLOAD, problems=args.problems, problems_per_gpu=args.problems,
+                    l2="flushed between steps (256 MiB write)", mode="async", range=1.0, resolution=1 / 32,
+                    goal_bias=0.05, max_iters=50000, grid=plan_grid, parallelism=f"problems sharded over {world} GPU(s)"),
+        ttfs_us=dict(percentiles(ttfs), note="device time from launch start to each problem's solution"),
+        success_rate=solved / (len(items) * args.steps), mean_cost=float(np.mean(costs)) if costs else None,
+        roofline=dict(bound="alu", achieved=achieved_gops, peak=peak_gops, unit="Gop/s",
+                      frac=achieved_gops / peak_gops, traffic=None,
+                      note="planner kernel: counted FP32/ALU instructions of FK, collision tests and NN scans "
+                           "per launch / kernel time; peak = SMs x 128 lanes x max SM clock (issue bound)"),
+        e2e=dict(value=total_states / wall_s, unit=UNIT, h2d_bytes_per_step=h2d // args.steps,
+                 d2h_bytes_per_step=d2h // args.steps),
+        gpu_launches=launches, clocks=clk, learned=None,
+    )
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--problems", type=int, default=200)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,269 @@
+/*
+ * prrtc.h -- C ABI of the GB300-native pRRTC planner (libprrtc.so).
+ *
+ * pRRTC (Huang, Jadhav, Plancher, Kingston, "pRRTC: GPU-Parallel RRT-Connect
+ * for Fast, Consistent, and Low-Cost Motion Planning", arXiv 2503.06757):
+ * RRT-Connect whose iterations run concurrently against two shared trees on
+ * the GPU (Sec. III, Alg. 1), with every interpolated state of a candidate
+ * edge collision-checked in parallel (Alg. 2, Sec. III-A) and a parallel
+ * nearest-neighbour scan (Sec. III-C).
+ *
+ * Conventions for every entry point:
+ *   - Return value: PRRTC_OK (0) on success, a negative PRRTC_ERR_* code on
+ *     failure.  Planning outcomes (no solution, start in collision, ...) are
+ *     positive status codes reported per problem, never as errors.  No C++
+ *     exception crosses this boundary.
+ *   - Handles (prrtc_env, prrtc_robot) are opaque, owned by the library and
+ *     released by the matching *_destroy call.  Their geometry lives in device
+ *     memory of the CUDA device that was current when they were created.
+ *   - Pointers without a "_device" suffix are host pointers; the library
+ *     copies what it needs before returning and keeps no reference.
+ *   - Floating-point inputs are IEEE binary32; configurations are row-major
+ *     [n x dof] arrays of joint values (radians / metres).
+ *   - Thread safety: calls on different handles may run from different host
+ *     threads; each planning call serialises on the library's stream for the
+ *     current device, so an env update issued between two calls applies
+ *     exactly between them.
+ *   - There is no CPU fallback: without a usable CUDA device every call
+ *     returns PRRTC_ERR_NO_DEVICE.
+ */
+#ifndef PRRTC_H
+#define PRRTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define PRRTC_OK 0
+#define PRRTC_ERR_INVALID_ARG (-1)   /* a pointer, size or descriptor is invalid      */
+#define PRRTC_ERR_OOM (-2)           /* device or host allocation failed              */
+#define PRRTC_ERR_CUDA (-3)          /* a CUDA runtime call failed                    */
+#define PRRTC_ERR_TIMEOUT (-4)       /* a bounded device-side wait gave up            */
+#define PRRTC_ERR_DEVICE_INDEX (-5)  /* a device-side bounds check fired              */
+#define PRRTC_ERR_NO_DEVICE (-6)     /* no CUDA device is available                   */
+#define PRRTC_ERR_UNSUPPORTED (-7)   /* a feature outside the compiled limits         */
+
+/* per-problem planning outcomes (prrtc_path.status, out_status[]) */
+#define PRRTC_SOLVED 0
+#define PRRTC_START_IN_COLLISION 1
+#define PRRTC_GOAL_IN_COLLISION 2
+#define PRRTC_NO_SOLUTION 3          /* iteration budget spent (Alg. 1 "return Failed") */
+#define PRRTC_PATH_OVERFLOW 4        /* solved, but the path exceeded path_capacity    */
+#define PRRTC_TIME_LIMIT 5           /* wall-clock budget spent on the device          */
+
+/* compiled limits */
+#define PRRTC_MAX_DOF 16
+#define PRRTC_MAX_SPHERES 128        /* spheres per robot as given (before merging)    */
+#define PRRTC_MAX_PAIRS 4096         /* self-collision sphere pairs as given           */
+#define PRRTC_MAX_OBSTACLES 1024
+
+/* ------------------------------------------------------------ geometry */
+#define PRRTC_OBS_BOX 0       /* cuboid: centre, half extents, rotation                 */
+#define PRRTC_OBS_CYLINDER 1  /* solid cylinder with flat caps: centre, axis, radius, half length */
+#define PRRTC_OBS_SPHERE 2    /* centre, radius                                          */
+
+/* One obstacle primitive (Sec. III-A: environments of primitive geometry).
+ *   box:      centre, half[0..2] = half extents, rot = row-major rotation
+ *             (world = rot * local + centre); identity rot = axis-aligned.
+ *   cylinder: centre, axis = unit axis direction, half[0] = radius,
+ *             half[1] = half length.
+ *   sphere:   centre, half[0] = radius.
+ * A robot sphere of radius r collides with a primitive iff the squared
+ * distance from its centre to the primitive is < r^2 (touching is free). */
+typedef struct prrtc_obstacle {
+  int32_t type;
+  float center[3];
+  float half[3];
+  float axis[3];
+  float rot[9];
+} prrtc_obstacle;
+
+#define PRRTC_JOINT_REV_Z 0
+#define PRRTC_JOINT_REV_Y 1
+#define PRRTC_JOINT_PRISM_Z 2
+#define PRRTC_JOINT_PRISM_X 3
+#define PRRTC_JOINT_PRISM_Y 4
+#define PRRTC_JOINT_REV_X 5
+
+/* Sphere model of a robot (Sec. III-A, bounding spheres per link).
+ * Frame i = T_parent(i) * J_i(q_i) * Trans(0, 0, link_length[i]), where J_i
+ * rotates about / translates along a local axis (PRRTC_JOINT_*), and
+ * T_parent = Trans(joint_base[3i..3i+2]) when joint_parent[i] == -1.
+ * joint_parent[i] must be -1 or i-1 (one or more serial chains).
+ * Sphere s has centre T_{sphere_frame[s]} * [sphere_offset[3s..3s+2], 1] and
+ * radius sphere_radius[s].  self_pairs lists sphere index pairs checked for
+ * self-collision (collide iff |ci - cj|^2 < (ri + rj)^2).  Joint values are
+ * sampled uniformly in [lower, upper]. */
+typedef struct prrtc_robot_desc {
+  int32_t dof;
+  const int32_t* joint_type;    /* [dof] */
+  const int32_t* joint_parent;  /* [dof] */
+  const float* joint_base;      /* [dof*3] */
+  const float* link_length;     /* [dof] */
+  const float* lower;           /* [dof] */
+  const float* upper;           /* [dof] */
+  int32_t n_spheres;
+  const int32_t* sphere_frame;  /* [n_spheres] */
+  const float* sphere_offset;   /* [n_spheres*3] */
+  const float* sphere_radius;   /* [n_spheres] */
+  int32_t n_pairs;
+  const int32_t* self_pairs;    /* [n_pairs*2] */
+} prrtc_robot_desc;
+
+typedef struct prrtc_env prrtc_env;
+typedef struct prrtc_robot prrtc_robot;
+
+/* ------------------------------------------------------------ parameters */
+#define PRRTC_MODE_ASYNC 0   /* blocks x warps run Alg. 1 iterations concurrently (Sec. III) */
+#define PRRTC_MODE_SERIAL 1  /* one warp runs the iterations in order: the serial Alg. 1   */
+
+typedef struct prrtc_params {
+  float range;            /* delta: extension range in configuration space (L2)        */
+  float resolution;       /* collision-checking resolution: an edge of length l is
+                             checked at ceil(l / resolution) states (Alg. 2, N_cc)    */
+  float goal_bias;        /* probability of sampling the opposite tree's root          */
+  int32_t max_iters;      /* budget of Alg. 1 iterations per problem, shared by all workers */
+  int32_t tree_capacity;  /* nodes per tree per problem                                */
+  int32_t path_capacity;  /* waypoints per returned path                               */
+  int32_t mode;           /* PRRTC_MODE_*                                              */
+  int32_t blocks;         /* grid size of the planner launch; 0 = one wave of resident blocks */
+  int32_t warps_per_block;/* worker warps per block; 0 = 4                             */
+  int32_t reserved0;
+  uint64_t seed;          /* Philox key used by prrtc_plan                             */
+  double time_limit_s;    /* device-side wall-clock budget per launch; 0 = none        */
+  int32_t reserved[8];
+} prrtc_params;
+
+/* Fills the defaults: range 1.0, resolution 1/32, goal bias 0.05, 50000
+ * iterations, 65536 nodes per tree, 16384 waypoints, async mode, seed 1. */
+void prrtc_params_default(prrtc_params* p);
+
+/* ------------------------------------------------------------ results */
+typedef struct prrtc_path {
+  int32_t status;          /* PRRTC_SOLVED or another planning outcome                    */
+  int32_t n;               /* waypoints in q                                              */
+  int32_t dof;
+  int32_t iterations;      /* Alg. 1 iterations started for this problem                  */
+  float* q;                /* [n*dof] host memory owned by the library; prrtc_path_free   */
+  double cost;             /* sum of L2 segment lengths (Table I "arclength")             */
+  int32_t nodes_a;         /* start-tree size                                             */
+  int32_t nodes_b;         /* goal-tree size                                              */
+  int64_t edges_checked;   /* edges whose states were tested                              */
+  int64_t edge_states;     /* sum over tested edges of their state count                  */
+  double solve_time_us;    /* device time from launch start to this problem's solution    */
+  int64_t sphere_tests;    /* lane-level sphere passes over the obstacle set              */
+  int64_t pair_tests;      /* lane-level self-collision pair tests                        */
+  int64_t fk_states;       /* lane-level forward-kinematics evaluations                   */
+  int64_t nn_nodes;        /* tree rows scanned by nearest-neighbour queries              */
+} prrtc_path;
+
+void prrtc_path_free(prrtc_path* path);
+
+/* Work counters and timing of the most recent planning launch on the current
+ * device (for throughput and roofline accounting). */
+typedef struct prrtc_launch_stats {
+  double kernel_ms;          /* planner kernel, CUDA events on the library stream    */
+  double setup_ms;           /* arena reset + root insertion kernel                   */
+  int64_t edges_checked;
+  int64_t edge_states;       /* states of all tested edges                            */
+  int64_t sphere_tests;      /* lane-level sphere passes over the environment         */
+  int64_t env_tests;         /* lane-level sphere-primitive tests                     */
+  int64_t pair_tests;        /* lane-level self-collision pair tests                  */
+  int64_t fk_states;         /* lane-level forward-kinematics evaluations              */
+  int64_t nn_nodes;          /* tree nodes scanned by nearest-neighbour queries        */
+  int64_t iterations;        /* Alg. 1 iterations across all problems                  */
+  int32_t grid;              /* blocks launched                                        */
+  int32_t block_threads;
+  int32_t smem_bytes;
+  int32_t problems;
+  int64_t h2d_bytes;         /* host -> device bytes copied by the call                */
+  int64_t d2h_bytes;         /* device -> host bytes copied by the call                */
+  int32_t kernels;           /* kernels the call launched                              */
+  int32_t reserved_;
+} prrtc_launch_stats;
+
+int prrtc_last_launch_stats(prrtc_launch_stats* out);
+
+/* Copy tree `tree` (0 = start tree T_a, 1 = goal tree T_b) of problem
+ * `problem` of the most recent planning launch on the current device:
+ * rows [min(size, cap) * dof] into nodes, parent indices into parents (-1 for
+ * the root), *out_n = rows available.  Buffers are host memory of `cap` rows;
+ * either may be null.  For tests and diagnostics (tree invariants, lockstep
+ * comparison with a serial reference). */
+int prrtc_debug_tree(int32_t problem, int32_t tree, float* nodes, int32_t* parents, int32_t cap, int32_t* out_n);
+
+/* ------------------------------------------------------------ entry points */
+const char* prrtc_status_string(int code);
+const char* prrtc_version(void);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* prrtc_last_error(void);
+
+/* Upload an obstacle set (Sec. III-A; obstacles cached in GPU memory).
+ * n may be 0.  Returns PRRTC_ERR_INVALID_ARG for an unknown type, a
+ * non-positive size or n > PRRTC_MAX_OBSTACLES. */
+int prrtc_env_create(const prrtc_obstacle* obstacles, int32_t n, prrtc_env** out);
+
+/* Replace obstacles ids[k] (indices in creation order) by obstacles[k]; each
+ * keeps its type.  Stream-ordered: applies between planning calls. */
+int prrtc_env_update(prrtc_env* env, const int32_t* ids, const prrtc_obstacle* obstacles, int32_t n);
+
+void prrtc_env_destroy(prrtc_env* env);
+
+/* Upload a robot sphere model.  Coincident spheres of equal radius on the same
+ * frame are merged (the verdicts do not change); self pairs are re-indexed. */
+int prrtc_robot_create(const prrtc_robot_desc* desc, prrtc_robot** out);
+void prrtc_robot_destroy(prrtc_robot* robot);
+
+/* Sizes after merging: DoF, distinct spheres, distinct self pairs and the
+ * tree row stride in floats (any pointer may be null). */
+int prrtc_robot_info(const prrtc_robot* robot, int32_t* dof, int32_t* n_spheres, int32_t* n_pairs, int32_t* dpad);
+
+/* counts4 = {axis-aligned boxes, oriented boxes, cylinders, spheres}. */
+int prrtc_env_info(const prrtc_env* env, int32_t* counts4);
+
+/* Collision verdicts of n configurations (Sec. III-A): FK of the sphere model,
+ * sphere-vs-primitive and self-collision tests.  q: host [n*dof];
+ * out_valid: host [n], 1 = collision-free; out_spheres (nullable): host
+ * [n*n_spheres*4], world centre xyz and radius of every sphere in the order
+ * given to prrtc_robot_create. */
+int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const float* q, int32_t n,
+                       uint8_t* out_valid, float* out_spheres);
+
+/* As prrtc_check_states with device pointers, enqueued on `stream`
+ * (cudaStream_t, 0 = legacy default stream); returns without synchronising. */
+int prrtc_check_states_device(const prrtc_robot* robot, const prrtc_env* env, const float* q_device,
+                              int32_t n, uint8_t* valid_device, float* spheres_device, void* stream);
+
+/* Solve one planning problem (Alg. 1) on the device; blocks until done.
+ * out_path receives the path (host memory, free with prrtc_path_free). */
+int prrtc_plan(const prrtc_robot* robot, const prrtc_env* env, const float* q_start,
+               const float* q_goal, const prrtc_params* params, prrtc_path* out_path);
+
+/* One planning problem of a batch. */
+typedef struct prrtc_problem {
+  const prrtc_robot* robot;
+  const prrtc_env* env;
+  const float* q_start;   /* host [robot dof] */
+  const float* q_goal;    /* host [robot dof] */
+  uint64_t seed;          /* Philox key of this problem                  */
+  uint32_t problem_id;    /* Philox counter word 0 of this problem        */
+  int32_t reserved;
+} prrtc_problem;
+
+/* Solve n independent problems in one persistent launch: blocks take
+ * problems from a device work queue and move to unsolved ones as problems
+ * finish.  out_paths [n] and out_status [n] (nullable) receive per-problem
+ * results.  Robots of different DoF and environments of different sizes may
+ * be mixed. */
+int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params,
+                     prrtc_path* out_paths, int32_t* out_status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

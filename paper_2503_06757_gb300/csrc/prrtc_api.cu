@@ -1,0 +1,846 @@
+// prrtc_api.cu -- host runtime of libprrtc: handles, device arenas, launch
+// sequencing and the extern "C" entry points declared in include/prrtc.h.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "prrtc.h"
+#include "prrtc_launch.h"
+
+using namespace prrtc;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_last_error;
+
+static int fail(int code, const std::string& msg) {
+  t_last_error = msg;
+  return code;
+}
+
+static int cuda_fail(const char* what, cudaError_t e) {
+  t_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return PRRTC_ERR_CUDA;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(#call, e_); \
+  } while (0)
+
+// ------------------------------------------------------------------ handles
+struct prrtc_env {
+  int device = -1;
+  float4* d_data = nullptr;
+  std::vector<float4> h_data;
+  int n_aabb = 0, n_obb = 0, n_cyl = 0, n_sph = 0;
+  std::vector<int> kind;    // per obstacle id: 0 aabb, 1 obb, 2 cylinder, 3 sphere
+  std::vector<int> offset;  // per obstacle id: first float4 in the blob
+  EnvView view() const {
+    EnvView v;
+    v.data = d_data;
+    v.n_aabb = n_aabb;
+    v.n_obb = n_obb;
+    v.n_cyl = n_cyl;
+    v.n_sph = n_sph;
+    return v;
+  }
+};
+
+struct prrtc_robot {
+  int device = -1;
+  RobotDev* d = nullptr;
+  RobotDev* h = nullptr;
+};
+
+// ------------------------------------------------------------------ per-device context
+namespace {
+
+struct DeviceCtx {
+  bool ready = false;
+  int device = -1;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  // planner arenas
+  int slots = 0, cap = 0, path_cap = 0;
+  float* nodes = nullptr;
+  int* parents = nullptr;
+  float* paths = nullptr;
+  int* path_idx = nullptr;
+  ProblemDesc* d_desc = nullptr;
+  ProblemState* d_state = nullptr;
+  PlanGlobals* d_glob = nullptr;
+  ProblemDesc* h_desc = nullptr;
+  ProblemState* h_state = nullptr;
+  PlanGlobals* h_glob = nullptr;
+  int* d_offsets = nullptr;
+  int* h_offsets = nullptr;
+  float* d_packed = nullptr;
+  float* h_packed = nullptr;
+  size_t packed_cap = 0;
+  // check_states scratch
+  float* d_q = nullptr;
+  uint8_t* d_valid = nullptr;
+  float* d_spheres = nullptr;
+  size_t q_cap = 0, valid_cap = 0, spheres_cap = 0;
+  unsigned long long* d_counters = nullptr;
+  int* d_error = nullptr;
+  cudaEvent_t ev[4] = {};
+  prrtc_launch_stats last{};
+};
+
+DeviceCtx g_ctx[64];
+std::mutex g_init_mu;
+
+int current_ctx(DeviceCtx** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  int count = 0;
+  if (e != cudaSuccess || cudaGetDeviceCount(&count) != cudaSuccess || count < 1)
+    return fail(PRRTC_ERR_NO_DEVICE, "no CUDA device available");
+  if (dev < 0 || dev >= 64) return fail(PRRTC_ERR_NO_DEVICE, "device index out of range");
+  DeviceCtx* c = &g_ctx[dev];
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (!c->ready) {
+    c->device = dev;
+    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    for (auto& ev : c->ev) CK(cudaEventCreate(&ev));
+    CK(cudaMalloc(&c->d_counters, 8 * sizeof(unsigned long long)));
+    CK(cudaMalloc(&c->d_error, sizeof(int)));
+    CK(cudaMallocHost(&c->h_glob, sizeof(PlanGlobals)));
+    CK(cudaMalloc(&c->d_glob, sizeof(PlanGlobals)));
+    c->ready = true;
+  }
+  *out = c;
+  return PRRTC_OK;
+}
+
+template <class T>
+int grow_device(T** p, size_t* cap, size_t need) {
+  if (*cap >= need && *p) return PRRTC_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  size_t n = std::max<size_t>(need, 1);
+  if (cudaMalloc(p, n * sizeof(T)) != cudaSuccess) return fail(PRRTC_ERR_OOM, "device allocation failed");
+  *cap = n;
+  return PRRTC_OK;
+}
+
+void free_arenas(DeviceCtx* c) {
+  cudaFree(c->nodes);
+  cudaFree(c->parents);
+  cudaFree(c->paths);
+  cudaFree(c->path_idx);
+  cudaFree(c->d_desc);
+  cudaFree(c->d_state);
+  cudaFree(c->d_offsets);
+  cudaFreeHost(c->h_desc);
+  cudaFreeHost(c->h_state);
+  cudaFreeHost(c->h_offsets);
+  c->nodes = nullptr;
+  c->parents = nullptr;
+  c->paths = nullptr;
+  c->path_idx = nullptr;
+  c->d_desc = nullptr;
+  c->d_state = nullptr;
+  c->d_offsets = nullptr;
+  c->h_desc = nullptr;
+  c->h_state = nullptr;
+  c->h_offsets = nullptr;
+  c->slots = c->cap = c->path_cap = 0;
+}
+
+// Tree arenas: slot p, tree t occupies cap rows of kMaxDof floats (the row
+// stride used is the problem's dpad, so any DoF fits).
+int ensure_arenas(DeviceCtx* c, int slots, int cap, int path_cap) {
+  if (c->slots >= slots && c->cap >= cap && c->path_cap >= path_cap) return PRRTC_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  slots = std::max(slots, c->slots);
+  cap = std::max(cap, c->cap);
+  path_cap = std::max(path_cap, c->path_cap);
+  free_arenas(c);
+  const size_t rows = (size_t)slots * 2 * cap;
+  bool ok = cudaMalloc(&c->nodes, rows * kMaxDof * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->parents, rows * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->paths, (size_t)slots * path_cap * kMaxDof * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->path_idx, (size_t)slots * path_cap * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->d_desc, (size_t)slots * sizeof(ProblemDesc)) == cudaSuccess &&
+            cudaMalloc(&c->d_state, (size_t)slots * sizeof(ProblemState)) == cudaSuccess &&
+            cudaMalloc(&c->d_offsets, (size_t)(slots + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&c->h_desc, (size_t)slots * sizeof(ProblemDesc)) == cudaSuccess &&
+            cudaMallocHost(&c->h_state, (size_t)slots * sizeof(ProblemState)) == cudaSuccess &&
+            cudaMallocHost(&c->h_offsets, (size_t)(slots + 1) * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_arenas(c);
+    return fail(PRRTC_ERR_OOM, "planner arena allocation failed");
+  }
+  CK(cudaMemsetAsync(c->nodes, 0xFF, rows * kMaxDof * sizeof(float), c->stream));   // NaN rows
+  CK(cudaMemsetAsync(c->parents, 0xFF, rows * sizeof(int), c->stream));             // unset parents
+  CK(cudaMemsetAsync(c->d_state, 0, (size_t)slots * sizeof(ProblemState), c->stream));
+  c->slots = slots;
+  c->cap = cap;
+  c->path_cap = path_cap;
+  return PRRTC_OK;
+}
+
+bool finite_all(const float* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+int validate_params(const prrtc_params* p) {
+  if (!p) return fail(PRRTC_ERR_INVALID_ARG, "params is null");
+  if (!(p->range > 0.f) || !std::isfinite(p->range)) return fail(PRRTC_ERR_INVALID_ARG, "range must be > 0");
+  if (!(p->resolution > 0.f) || !std::isfinite(p->resolution))
+    return fail(PRRTC_ERR_INVALID_ARG, "resolution must be > 0");
+  if (!(p->goal_bias >= 0.f && p->goal_bias <= 1.f)) return fail(PRRTC_ERR_INVALID_ARG, "goal_bias must be in [0,1]");
+  if (p->max_iters < 1) return fail(PRRTC_ERR_INVALID_ARG, "max_iters must be >= 1");
+  if (p->tree_capacity < 2) return fail(PRRTC_ERR_INVALID_ARG, "tree_capacity must be >= 2");
+  if (p->tree_capacity > (1 << 26)) return fail(PRRTC_ERR_INVALID_ARG, "tree_capacity too large");
+  if (p->path_capacity < 2) return fail(PRRTC_ERR_INVALID_ARG, "path_capacity must be >= 2");
+  if (p->mode != PRRTC_MODE_ASYNC && p->mode != PRRTC_MODE_SERIAL) return fail(PRRTC_ERR_INVALID_ARG, "unknown mode");
+  if (p->blocks < 0 || p->warps_per_block < 0 || p->warps_per_block > 16)
+    return fail(PRRTC_ERR_INVALID_ARG, "blocks / warps_per_block out of range");
+  if (p->time_limit_s < 0.0) return fail(PRRTC_ERR_INVALID_ARG, "time_limit_s must be >= 0");
+  const double ratio = (double)p->range / (double)p->resolution;
+  if (ratio > 4096.0) return fail(PRRTC_ERR_INVALID_ARG, "range / resolution too large");
+  return PRRTC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* prrtc_version(void) { return "prrtc-gb300 0.1 (sm_103a)"; }
+
+const char* prrtc_last_error(void) { return t_last_error.c_str(); }
+
+const char* prrtc_status_string(int code) {
+  switch (code) {
+    case PRRTC_OK: return "ok / solved";
+    case PRRTC_ERR_INVALID_ARG: return "invalid argument";
+    case PRRTC_ERR_OOM: return "out of memory";
+    case PRRTC_ERR_CUDA: return "CUDA error";
+    case PRRTC_ERR_TIMEOUT: return "device wait timed out";
+    case PRRTC_ERR_DEVICE_INDEX: return "device bounds check failed";
+    case PRRTC_ERR_NO_DEVICE: return "no CUDA device";
+    case PRRTC_ERR_UNSUPPORTED: return "unsupported (exceeds compiled limits)";
+    case PRRTC_START_IN_COLLISION: return "start in collision";
+    case PRRTC_GOAL_IN_COLLISION: return "goal in collision";
+    case PRRTC_NO_SOLUTION: return "no solution within the iteration budget";
+    case PRRTC_PATH_OVERFLOW: return "path longer than path_capacity";
+    case PRRTC_TIME_LIMIT: return "time limit reached";
+    default: return "unknown status";
+  }
+}
+
+void prrtc_params_default(prrtc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->range = 1.0f;
+  p->resolution = 1.0f / 32.0f;
+  p->goal_bias = 0.05f;
+  p->max_iters = 50000;
+  p->tree_capacity = 1 << 16;
+  p->path_capacity = 1 << 14;
+  p->mode = PRRTC_MODE_ASYNC;
+  p->blocks = 0;
+  p->warps_per_block = 0;
+  p->seed = 1;
+  p->time_limit_s = 0.0;
+}
+
+void prrtc_path_free(prrtc_path* path) {
+  if (!path) return;
+  std::free(path->q);
+  path->q = nullptr;
+  path->n = 0;
+}
+
+int prrtc_last_launch_stats(prrtc_launch_stats* out) {
+  if (!out) return fail(PRRTC_ERR_INVALID_ARG, "out is null");
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->last;
+  return PRRTC_OK;
+}
+
+// -------------------------------------------------------------- environment
+static int pack_obstacle(const prrtc_obstacle& o, int* kind, float4* out) {
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(o.center[k]) || !std::isfinite(o.half[k]) || !std::isfinite(o.axis[k])) return -1;
+  for (int k = 0; k < 9; ++k)
+    if (!std::isfinite(o.rot[k])) return -1;
+  const float* c = o.center;
+  if (o.type == PRRTC_OBS_BOX) {
+    if (!(o.half[0] > 0.f && o.half[1] > 0.f && o.half[2] > 0.f)) return -1;
+    bool identity = true;
+    for (int i = 0; i < 9; ++i) identity &= (o.rot[i] == ((i % 4 == 0) ? 1.f : 0.f));
+    out[0] = make_float4(c[0], c[1], c[2], 0.f);
+    out[1] = make_float4(o.half[0], o.half[1], o.half[2], 0.f);
+    if (identity) {
+      *kind = 0;
+      return 2;
+    }
+    // rows of R^T (columns of R): local_k = <column k of R, p - c>
+    for (int k = 0; k < 3; ++k) out[2 + k] = make_float4(o.rot[0 * 3 + k], o.rot[1 * 3 + k], o.rot[2 * 3 + k], 0.f);
+    *kind = 1;
+    return 5;
+  }
+  if (o.type == PRRTC_OBS_CYLINDER) {
+    const double n = std::sqrt((double)o.axis[0] * o.axis[0] + (double)o.axis[1] * o.axis[1] +
+                               (double)o.axis[2] * o.axis[2]);
+    if (!(o.half[0] > 0.f && o.half[1] > 0.f) || std::fabs(n - 1.0) > 1e-3) return -1;
+    out[0] = make_float4(c[0], c[1], c[2], o.half[0]);
+    out[1] = make_float4(o.axis[0], o.axis[1], o.axis[2], o.half[1]);
+    *kind = 2;
+    return 2;
+  }
+  if (o.type == PRRTC_OBS_SPHERE) {
+    if (!(o.half[0] > 0.f)) return -1;
+    out[0] = make_float4(c[0], c[1], c[2], o.half[0]);
+    *kind = 3;
+    return 1;
+  }
+  return -1;
+}
+
+int prrtc_env_create(const prrtc_obstacle* obstacles, int32_t n, prrtc_env** out) {
+  if (!out) return fail(PRRTC_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (n < 0 || n > PRRTC_MAX_OBSTACLES || (n > 0 && !obstacles))
+    return fail(PRRTC_ERR_INVALID_ARG, "bad obstacle count or null obstacles");
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  std::vector<int> kinds(n);
+  std::vector<std::vector<float4>> packed(n);
+  int cnt[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    float4 tmp[5];
+    int kind = 0;
+    const int m = pack_obstacle(obstacles[i], &kind, tmp);
+    if (m < 0) return fail(PRRTC_ERR_INVALID_ARG, "invalid obstacle " + std::to_string(i));
+    kinds[i] = kind;
+    packed[i].assign(tmp, tmp + m);
+    cnt[kind]++;
+  }
+  prrtc_env* e = new prrtc_env();
+  e->device = c->device;
+  e->n_aabb = cnt[0];
+  e->n_obb = cnt[1];
+  e->n_cyl = cnt[2];
+  e->n_sph = cnt[3];
+  const int width[4] = {2, 5, 2, 1};
+  int base[4];
+  base[0] = 0;
+  for (int k = 1; k < 4; ++k) base[k] = base[k - 1] + cnt[k - 1] * width[k - 1];
+  const int total = base[3] + cnt[3] * width[3];
+  e->h_data.assign(std::max(total, 1), make_float4(0.f, 0.f, 0.f, 0.f));
+  e->kind.resize(n);
+  e->offset.resize(n);
+  int fill[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    const int k = kinds[i];
+    const int off = base[k] + fill[k] * width[k];
+    fill[k]++;
+    e->kind[i] = k;
+    e->offset[i] = off;
+    std::copy(packed[i].begin(), packed[i].end(), e->h_data.begin() + off);
+  }
+  if (cudaMalloc(&e->d_data, e->h_data.size() * sizeof(float4)) != cudaSuccess) {
+    cudaGetLastError();
+    delete e;
+    return fail(PRRTC_ERR_OOM, "env allocation failed");
+  }
+  cudaError_t ce = cudaMemcpy(e->d_data, e->h_data.data(), e->h_data.size() * sizeof(float4), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(e->d_data);
+    delete e;
+    return cuda_fail("env upload", ce);
+  }
+  *out = e;
+  return PRRTC_OK;
+}
+
+int prrtc_env_update(prrtc_env* env, const int32_t* ids, const prrtc_obstacle* obstacles, int32_t n) {
+  if (!env || n < 0 || (n > 0 && (!ids || !obstacles))) return fail(PRRTC_ERR_INVALID_ARG, "bad env update");
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  if (c->device != env->device) return fail(PRRTC_ERR_INVALID_ARG, "env belongs to another device");
+  std::lock_guard<std::mutex> lk(c->mu);
+  int lo = INT_MAX, hi = -1;
+  for (int k = 0; k < n; ++k) {
+    const int id = ids[k];
+    if (id < 0 || id >= (int)env->kind.size()) return fail(PRRTC_ERR_INVALID_ARG, "obstacle id out of range");
+    float4 tmp[5];
+    int kind = 0;
+    const int m = pack_obstacle(obstacles[k], &kind, tmp);
+    if (m < 0 || kind != env->kind[id]) return fail(PRRTC_ERR_INVALID_ARG, "update changes an obstacle's kind");
+    std::copy(tmp, tmp + m, env->h_data.begin() + env->offset[id]);
+    lo = std::min(lo, env->offset[id]);
+    hi = std::max(hi, env->offset[id] + m);
+  }
+  if (hi < 0) return PRRTC_OK;
+  // Stream-ordered upload: lands between the planning launches around it.
+  CK(cudaMemcpyAsync(env->d_data + lo, env->h_data.data() + lo, (size_t)(hi - lo) * sizeof(float4),
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PRRTC_OK;
+}
+
+void prrtc_env_destroy(prrtc_env* env) {
+  if (!env) return;
+  cudaFree(env->d_data);
+  delete env;
+}
+
+// -------------------------------------------------------------- robot
+int prrtc_robot_create(const prrtc_robot_desc* d, prrtc_robot** out) {
+  if (!out) return fail(PRRTC_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (!d) return fail(PRRTC_ERR_INVALID_ARG, "desc is null");
+  if (d->dof < 1 || d->dof > PRRTC_MAX_DOF) return fail(PRRTC_ERR_INVALID_ARG, "dof out of range");
+  if (!d->joint_type || !d->joint_parent || !d->joint_base || !d->link_length || !d->lower || !d->upper)
+    return fail(PRRTC_ERR_INVALID_ARG, "null joint table");
+  if (d->n_spheres < 0 || d->n_spheres > PRRTC_MAX_SPHERES || (d->n_spheres > 0 && (!d->sphere_frame ||
+      !d->sphere_offset || !d->sphere_radius)))
+    return fail(PRRTC_ERR_INVALID_ARG, "bad sphere table");
+  if (d->n_pairs < 0 || d->n_pairs > PRRTC_MAX_PAIRS || (d->n_pairs > 0 && !d->self_pairs))
+    return fail(PRRTC_ERR_INVALID_ARG, "bad pair table");
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  const int dof = d->dof;
+  for (int i = 0; i < dof; ++i) {
+    if (d->joint_type[i] < 0 || d->joint_type[i] > 5) return fail(PRRTC_ERR_INVALID_ARG, "unknown joint type");
+    if (d->joint_parent[i] != -1 && d->joint_parent[i] != i - 1)
+      return fail(PRRTC_ERR_UNSUPPORTED, "joint_parent must be -1 or i-1 (serial chains)");
+    if (!std::isfinite(d->lower[i]) || !std::isfinite(d->upper[i]) || d->lower[i] > d->upper[i])
+      return fail(PRRTC_ERR_INVALID_ARG, "bad joint limits");
+  }
+  if (!finite_all(d->joint_base, 3 * dof) || !finite_all(d->link_length, dof))
+    return fail(PRRTC_ERR_INVALID_ARG, "non-finite joint table");
+  // merge coincident equal-radius spheres of one frame; keep them grouped by frame
+  std::vector<int> raw_to(d->n_spheres, -1);
+  std::vector<std::tuple<int, float, float, float, float>> distinct;
+  for (int f = 0; f < dof; ++f) {
+    for (int s = 0; s < d->n_spheres; ++s) {
+      const int fr = d->sphere_frame[s];
+      if (fr < 0 || fr >= dof) return fail(PRRTC_ERR_INVALID_ARG, "sphere frame out of range");
+      if (fr != f) continue;
+      const float* o = d->sphere_offset + 3 * s;
+      const float r = d->sphere_radius[s];
+      if (!(r > 0.f) || !finite_all(o, 3) || !std::isfinite(r)) return fail(PRRTC_ERR_INVALID_ARG, "bad sphere");
+      auto key = std::make_tuple(f, o[0], o[1], o[2], r);
+      int idx = -1;
+      for (size_t k = 0; k < distinct.size(); ++k)
+        if (distinct[k] == key) idx = (int)k;
+      if (idx < 0) {
+        idx = (int)distinct.size();
+        distinct.push_back(key);
+      }
+      raw_to[s] = idx;
+    }
+  }
+  if ((int)distinct.size() > kMaxDistinctSpheres) return fail(PRRTC_ERR_UNSUPPORTED, "too many distinct spheres");
+  std::vector<std::pair<int, int>> pairs;
+  for (int k = 0; k < d->n_pairs; ++k) {
+    const int a = d->self_pairs[2 * k], b = d->self_pairs[2 * k + 1];
+    if (a < 0 || b < 0 || a >= d->n_spheres || b >= d->n_spheres) return fail(PRRTC_ERR_INVALID_ARG, "pair index");
+    int x = raw_to[a], y = raw_to[b];
+    if (x > y) std::swap(x, y);
+    pairs.emplace_back(x, y);
+  }
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  if ((int)pairs.size() > kMaxDistinctPairs) return fail(PRRTC_ERR_UNSUPPORTED, "too many distinct pairs");
+
+  RobotDev* h = (RobotDev*)std::calloc(1, sizeof(RobotDev));
+  if (!h) return fail(PRRTC_ERR_OOM, "host allocation failed");
+  RobotHeader& H = h->h;
+  H.dof = dof;
+  H.dpad = std::max(4, (dof + 3) & ~3);
+  H.n_spheres = (int)distinct.size();
+  H.n_pairs = (int)pairs.size();
+  H.n_raw = d->n_spheres;
+  for (int i = 0; i < dof; ++i) {
+    H.jtype[i] = d->joint_type[i];
+    H.jparent[i] = d->joint_parent[i];
+    H.jlen[i] = d->link_length[i];
+    H.lo[i] = d->lower[i];
+    H.span[i] = d->upper[i] - d->lower[i];
+    H.jbase[i] = make_float4(d->joint_base[3 * i], d->joint_base[3 * i + 1], d->joint_base[3 * i + 2], 0.f);
+  }
+  int s = 0;
+  for (int f = 0; f <= dof; ++f) {
+    while (s < (int)distinct.size() && std::get<0>(distinct[s]) < f) ++s;
+    H.sph_begin[f] = s;
+  }
+  H.sph_begin[dof] = (int)distinct.size();
+  for (int f = dof + 1; f <= kMaxDof; ++f) H.sph_begin[f] = (int)distinct.size();
+  for (size_t k = 0; k < distinct.size(); ++k)
+    H.sph[k] = make_float4(std::get<1>(distinct[k]), std::get<2>(distinct[k]), std::get<3>(distinct[k]),
+                           std::get<4>(distinct[k]));
+  for (size_t k = 0; k < pairs.size(); ++k) {
+    h->pair[k] = (uint32_t)pairs[k].first | ((uint32_t)pairs[k].second << 16);
+    const float rr = H.sph[pairs[k].first].w + H.sph[pairs[k].second].w;
+    h->thr[k] = rr * rr;
+  }
+  for (int r = 0; r < d->n_spheres; ++r) h->raw_to_distinct[r] = (int16_t)raw_to[r];
+
+  prrtc_robot* rb = new prrtc_robot();
+  rb->device = c->device;
+  rb->h = h;
+  if (cudaMalloc(&rb->d, sizeof(RobotDev)) != cudaSuccess) {
+    cudaGetLastError();
+    std::free(h);
+    delete rb;
+    return fail(PRRTC_ERR_OOM, "robot allocation failed");
+  }
+  cudaError_t ce = cudaMemcpy(rb->d, h, sizeof(RobotDev), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(rb->d);
+    std::free(h);
+    delete rb;
+    return cuda_fail("robot upload", ce);
+  }
+  *out = rb;
+  return PRRTC_OK;
+}
+
+void prrtc_robot_destroy(prrtc_robot* robot) {
+  if (!robot) return;
+  cudaFree(robot->d);
+  std::free(robot->h);
+  delete robot;
+}
+
+// Extra introspection used by tests and the benchmark.
+int prrtc_robot_info(const prrtc_robot* robot, int32_t* dof, int32_t* n_spheres, int32_t* n_pairs, int32_t* dpad) {
+  if (!robot) return fail(PRRTC_ERR_INVALID_ARG, "robot is null");
+  if (dof) *dof = robot->h->h.dof;
+  if (n_spheres) *n_spheres = robot->h->h.n_spheres;
+  if (n_pairs) *n_pairs = robot->h->h.n_pairs;
+  if (dpad) *dpad = robot->h->h.dpad;
+  return PRRTC_OK;
+}
+
+int prrtc_env_info(const prrtc_env* env, int32_t* counts4) {
+  if (!env || !counts4) return fail(PRRTC_ERR_INVALID_ARG, "null argument");
+  counts4[0] = env->n_aabb;
+  counts4[1] = env->n_obb;
+  counts4[2] = env->n_cyl;
+  counts4[3] = env->n_sph;
+  return PRRTC_OK;
+}
+
+// -------------------------------------------------------------- collision checking
+int prrtc_check_states_device(const prrtc_robot* robot, const prrtc_env* env, const float* q_device, int32_t n,
+                              uint8_t* valid_device, float* spheres_device, void* stream) {
+  if (!robot || !env || n < 0 || (n > 0 && (!q_device || !valid_device)))
+    return fail(PRRTC_ERR_INVALID_ARG, "bad check_states arguments");
+  if (n == 0) return PRRTC_OK;
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  if (robot->device != c->device || env->device != c->device)
+    return fail(PRRTC_ERR_INVALID_ARG, "handle belongs to another device");
+  cudaError_t e = launch_check_states(robot->d, robot->h->h, env->view(), q_device, n, valid_device, spheres_device,
+                                      c->d_counters, c->d_error, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail("check_states launch", e);
+  return PRRTC_OK;
+}
+
+int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const float* q, int32_t n, uint8_t* out_valid,
+                       float* out_spheres) {
+  if (!robot || !env || n < 0 || (n > 0 && (!q || !out_valid)))
+    return fail(PRRTC_ERR_INVALID_ARG, "bad check_states arguments");
+  if (n == 0) return PRRTC_OK;
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  if (robot->device != c->device || env->device != c->device)
+    return fail(PRRTC_ERR_INVALID_ARG, "handle belongs to another device");
+  std::lock_guard<std::mutex> lk(c->mu);
+  const int dof = robot->h->h.dof, n_raw = robot->h->h.n_raw;
+  if ((rc = grow_device(&c->d_q, &c->q_cap, (size_t)n * dof))) return rc;
+  if ((rc = grow_device(&c->d_valid, &c->valid_cap, (size_t)n))) return rc;
+  if (out_spheres && (rc = grow_device(&c->d_spheres, &c->spheres_cap, (size_t)n * n_raw * 4))) return rc;
+  CK(cudaMemcpyAsync(c->d_q, q, (size_t)n * dof * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->d_counters, 0, 8 * sizeof(unsigned long long), c->stream));
+  CK(cudaMemsetAsync(c->d_error, 0, sizeof(int), c->stream));
+  CK(cudaEventRecord(c->ev[0], c->stream));
+  cudaError_t e = launch_check_states(robot->d, robot->h->h, env->view(), c->d_q, n, c->d_valid,
+                                      out_spheres ? c->d_spheres : nullptr, c->d_counters, c->d_error, c->stream);
+  if (e != cudaSuccess) return cuda_fail("check_states launch", e);
+  CK(cudaEventRecord(c->ev[1], c->stream));
+  CK(cudaMemcpyAsync(out_valid, c->d_valid, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+  if (out_spheres)
+    CK(cudaMemcpyAsync(out_spheres, c->d_spheres, (size_t)n * n_raw * 4 * sizeof(float), cudaMemcpyDeviceToHost,
+                       c->stream));
+  unsigned long long cnt[3] = {0, 0, 0};
+  int err = 0;
+  CK(cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&err, c->d_error, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+  c->last = prrtc_launch_stats{};
+  c->last.kernel_ms = ms;
+  c->last.sphere_tests = (int64_t)cnt[0];
+  c->last.pair_tests = (int64_t)cnt[1];
+  c->last.fk_states = (int64_t)cnt[2];
+  c->last.problems = 0;
+  c->last.kernels = 1;
+  c->last.h2d_bytes = (int64_t)n * dof * (int64_t)sizeof(float);
+  c->last.d2h_bytes = (int64_t)n + (out_spheres ? (int64_t)n * n_raw * 4 * (int64_t)sizeof(float) : 0);
+  if (err) return fail(err, "device-side wait gave up in check_states");
+  return PRRTC_OK;
+}
+
+// -------------------------------------------------------------- planning
+int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params, prrtc_path* out_paths,
+                     int32_t* out_status) {
+  if (!problems || n < 1) return fail(PRRTC_ERR_INVALID_ARG, "no problems");
+  int rc = validate_params(params);
+  if (rc) return rc;
+  DeviceCtx* c = nullptr;
+  rc = current_ctx(&c);
+  if (rc) return rc;
+  for (int p = 0; p < n; ++p) {
+    const prrtc_problem& pb = problems[p];
+    if (!pb.robot || !pb.env || !pb.q_start || !pb.q_goal)
+      return fail(PRRTC_ERR_INVALID_ARG, "problem " + std::to_string(p) + " has a null field");
+    if (pb.robot->device != c->device || pb.env->device != c->device)
+      return fail(PRRTC_ERR_INVALID_ARG, "handle belongs to another device");
+    const int dof = pb.robot->h->h.dof;
+    if (!finite_all(pb.q_start, dof) || !finite_all(pb.q_goal, dof))
+      return fail(PRRTC_ERR_INVALID_ARG, "non-finite start or goal");
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((rc = ensure_arenas(c, n, params->tree_capacity, params->path_capacity))) return rc;
+
+  int max_spheres = 1, max_pairs = 0, max_env = 0;
+  for (int p = 0; p < n; ++p) {
+    const prrtc_problem& pb = problems[p];
+    const RobotHeader& H = pb.robot->h->h;
+    ProblemDesc& D = c->h_desc[p];
+    std::memset(&D, 0, sizeof(D));
+    D.robot = pb.robot->d;
+    D.env = pb.env->view();
+    const size_t tree_stride = (size_t)c->cap * kMaxDof;
+    D.nodes[0] = c->nodes + ((size_t)p * 2 + 0) * tree_stride;
+    D.nodes[1] = c->nodes + ((size_t)p * 2 + 1) * tree_stride;
+    D.parent[0] = c->parents + ((size_t)p * 2 + 0) * c->cap;
+    D.parent[1] = c->parents + ((size_t)p * 2 + 1) * c->cap;
+    D.path = c->paths + (size_t)p * c->path_cap * kMaxDof;
+    D.path_idx = c->path_idx + (size_t)p * c->path_cap;
+    D.cap = params->tree_capacity;
+    D.dpad = H.dpad;
+    D.dof = H.dof;
+    D.n_spheres = H.n_spheres;
+    D.n_pairs = H.n_pairs;
+    D.key_lo = (uint32_t)(pb.seed & 0xffffffffu);
+    D.key_hi = (uint32_t)(pb.seed >> 32);
+    D.pid = pb.problem_id;
+    for (int j = 0; j < H.dof; ++j) {
+      D.q_start[j] = pb.q_start[j];
+      D.q_goal[j] = pb.q_goal[j];
+    }
+    max_spheres = std::max(max_spheres, H.n_spheres);
+    max_pairs = std::max(max_pairs, H.n_pairs);
+    max_env = std::max(max_env, D.env.n_float4());
+  }
+  PlanGlobals& G = *c->h_glob;
+  std::memset(&G, 0, sizeof(G));
+  G.n_problems = n;
+  G.mode = params->mode;
+  G.max_iters = params->max_iters;
+  G.n_full = (int)std::ceil((double)params->range / (double)params->resolution);
+  if (G.n_full < 1) G.n_full = 1;
+  G.range = params->range;
+  G.resolution = params->resolution;
+  G.bias_thr = (uint32_t)std::ceil((double)params->goal_bias * 16777216.0);
+  G.path_cap = params->path_capacity;
+  G.t0 = ULLONG_MAX;
+  G.time_limit_ns = (unsigned long long)(params->time_limit_s * 1e9);
+  G.cursor = 0;
+  G.error = 0;
+
+  const PlanLaunch cfg = plan_launch_config(n, params->mode, params->blocks, params->warps_per_block, max_spheres,
+                                            max_pairs, max_env, c->sms);
+  if (cfg.smem > 227 * 1024) return fail(PRRTC_ERR_UNSUPPORTED, "robot + environment exceed shared memory");
+
+  CK(cudaMemcpyAsync(c->d_desc, c->h_desc, (size_t)n * sizeof(ProblemDesc), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_glob, c->h_glob, sizeof(PlanGlobals), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaEventRecord(c->ev[0], c->stream));
+  cudaError_t e = launch_setup(c->d_desc, c->d_state, n, max_spheres, max_pairs, max_env, c->stream);
+  if (e != cudaSuccess) return cuda_fail("setup launch", e);
+  CK(cudaEventRecord(c->ev[1], c->stream));
+  e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, c->stream);
+  if (e != cudaSuccess) return cuda_fail("plan launch", e);
+  CK(cudaEventRecord(c->ev[2], c->stream));
+  e = launch_record_usage(c->d_desc, c->d_state, n, c->stream);
+  if (e != cudaSuccess) return cuda_fail("usage launch", e);
+  CK(cudaMemcpyAsync(c->h_state, c->d_state, (size_t)n * sizeof(ProblemState), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(PlanGlobals), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+
+  // per-problem outcome and packed path offsets
+  std::vector<int> status(n);
+  int total = 0;
+  c->h_offsets[0] = 0;
+  for (int p = 0; p < n; ++p) {
+    const ProblemState& S = c->h_state[p];
+    int st;
+    if (S.pre_status) st = S.pre_status;
+    else if (S.solved) st = (S.path_status == PRRTC_SOLVED || S.path_status == PRRTC_PATH_OVERFLOW) ? S.path_status
+                                                                                                     : PRRTC_ERR_TIMEOUT;
+    else if (S.timed_out) st = PRRTC_TIME_LIMIT;
+    else st = PRRTC_NO_SOLUTION;
+    status[p] = st;
+    const int rows = (st == PRRTC_SOLVED) ? S.path_n : 0;
+    total += rows * c->h_desc[p].dof;
+    c->h_offsets[p + 1] = total;
+  }
+  if (total > 0) {
+    if ((size_t)total > c->packed_cap) {
+      cudaFree(c->d_packed);
+      cudaFreeHost(c->h_packed);
+      c->d_packed = nullptr;
+      c->h_packed = nullptr;
+      c->packed_cap = 0;
+      if (cudaMalloc(&c->d_packed, (size_t)total * sizeof(float)) != cudaSuccess ||
+          cudaMallocHost(&c->h_packed, (size_t)total * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PRRTC_ERR_OOM, "path buffer allocation failed");
+      }
+      c->packed_cap = (size_t)total;
+    }
+    CK(cudaMemcpyAsync(c->d_offsets, c->h_offsets, (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    e = launch_gather_paths(c->d_desc, c->d_offsets, n, c->d_packed, c->stream);
+    if (e != cudaSuccess) return cuda_fail("gather launch", e);
+    CK(cudaMemcpyAsync(c->h_packed, c->d_packed, (size_t)total * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+
+  float setup_ms = 0.f, plan_ms = 0.f;
+  cudaEventElapsedTime(&setup_ms, c->ev[0], c->ev[1]);
+  cudaEventElapsedTime(&plan_ms, c->ev[1], c->ev[2]);
+  prrtc_launch_stats L{};
+  L.kernel_ms = plan_ms;
+  L.setup_ms = setup_ms;
+  L.grid = cfg.grid;
+  L.block_threads = cfg.warps * 32;
+  L.smem_bytes = cfg.smem;
+  L.problems = n;
+  L.h2d_bytes = (int64_t)n * (int64_t)sizeof(ProblemDesc) + (int64_t)sizeof(PlanGlobals) +
+                (total > 0 ? (int64_t)(n + 1) * (int64_t)sizeof(int) : 0);
+  L.d2h_bytes = (int64_t)n * (int64_t)sizeof(ProblemState) + (int64_t)sizeof(PlanGlobals) +
+                (int64_t)total * (int64_t)sizeof(float);
+  L.kernels = 3 + (total > 0 ? 1 : 0);
+  const unsigned long long t0 = c->h_glob->t0;
+  for (int p = 0; p < n; ++p) {
+    const ProblemState& S = c->h_state[p];
+    L.edges_checked += (int64_t)S.edges;
+    L.edge_states += (int64_t)S.edge_states;
+    L.sphere_tests += (int64_t)S.sphere_tests;
+    L.pair_tests += (int64_t)S.pair_tests;
+    L.fk_states += (int64_t)S.fk_states;
+    L.nn_nodes += (int64_t)S.nn_nodes;
+    L.iterations += (int64_t)S.iterations;
+    if (out_status) out_status[p] = status[p];
+    if (out_paths) {
+      prrtc_path& P = out_paths[p];
+      std::memset(&P, 0, sizeof(P));
+      const int dof = c->h_desc[p].dof;
+      P.status = status[p];
+      P.dof = dof;
+      P.iterations = std::min(S.iter, params->max_iters);
+      P.nodes_a = std::min(S.count[0], params->tree_capacity);
+      P.nodes_b = std::min(S.count[1], params->tree_capacity);
+      P.edges_checked = (int64_t)S.edges;
+      P.edge_states = (int64_t)S.edge_states;
+      P.solve_time_us = (S.solved && S.t_solve >= t0) ? (double)(S.t_solve - t0) * 1e-3 : -1.0;
+      P.sphere_tests = (int64_t)S.sphere_tests;
+      P.pair_tests = (int64_t)S.pair_tests;
+      P.fk_states = (int64_t)S.fk_states;
+      P.nn_nodes = (int64_t)S.nn_nodes;
+      if (status[p] == PRRTC_SOLVED) {
+        P.n = S.path_n;
+        P.cost = S.cost;
+        P.q = (float*)std::malloc((size_t)S.path_n * dof * sizeof(float));
+        if (!P.q) return fail(PRRTC_ERR_OOM, "host path allocation failed");
+        std::memcpy(P.q, c->h_packed + c->h_offsets[p], (size_t)S.path_n * dof * sizeof(float));
+      } else if (status[p] == PRRTC_PATH_OVERFLOW) {
+        P.n = S.path_n;
+        P.cost = S.cost;
+      }
+    }
+  }
+  c->last = L;
+  if (c->h_glob->error) return fail(c->h_glob->error, "device-side wait gave up in the planner");
+  return PRRTC_OK;
+}
+
+int prrtc_debug_tree(int32_t problem, int32_t tree, float* nodes, int32_t* parents, int32_t cap, int32_t* out_n) {
+  if (tree < 0 || tree > 1 || cap < 0 || !out_n) return fail(PRRTC_ERR_INVALID_ARG, "bad debug_tree arguments");
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (problem < 0 || problem >= c->last.problems || !c->h_desc)
+    return fail(PRRTC_ERR_INVALID_ARG, "problem not in the last launch");
+  const ProblemDesc& D = c->h_desc[problem];
+  const ProblemState& S = c->h_state[problem];
+  const int rows = std::min(S.count[tree], D.cap);
+  *out_n = rows;
+  const int m = std::min(rows, cap);
+  if (m <= 0) return PRRTC_OK;
+  if (nodes) {
+    std::vector<float> buf((size_t)m * D.dpad);
+    CK(cudaMemcpy(buf.data(), D.nodes[tree], buf.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < m; ++r)
+      for (int j = 0; j < D.dof; ++j) nodes[(size_t)r * D.dof + j] = buf[(size_t)r * D.dpad + j];
+  }
+  if (parents) {
+    CK(cudaMemcpy(parents, D.parent[tree], (size_t)m * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < m; ++r)
+      if (parents[r] == kRootParent) parents[r] = -1;
+  }
+  return PRRTC_OK;
+}
+
+int prrtc_plan(const prrtc_robot* robot, const prrtc_env* env, const float* q_start, const float* q_goal,
+               const prrtc_params* params, prrtc_path* out_path) {
+  if (!out_path) return fail(PRRTC_ERR_INVALID_ARG, "out_path is null");
+  prrtc_problem pb;
+  std::memset(&pb, 0, sizeof(pb));
+  pb.robot = robot;
+  pb.env = env;
+  pb.q_start = q_start;
+  pb.q_goal = q_goal;
+  pb.seed = params ? params->seed : 1;
+  pb.problem_id = 0;
+  return prrtc_plan_batch(&pb, 1, params, out_path, nullptr);
+}
+
+}  // extern "C"

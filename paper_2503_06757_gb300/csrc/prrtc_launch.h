@@ -1,0 +1,103 @@
+// prrtc_launch.h -- descriptors shared by the host runtime and the planner
+// kernels, and the kernel launchers each .cu file exports.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "prrtc_device.cuh"
+
+namespace prrtc {
+
+constexpr int kRootParent = -2;    // parent of a tree root
+constexpr int kUnsetParent = -1;   // parent slot not written yet (0xFF fill)
+
+// Launch-wide parameters and bookkeeping (one per planning launch).
+struct PlanGlobals {
+  int n_problems;
+  int mode;              // 0 async, 1 serial
+  int max_iters;
+  int n_full;            // ceil(range / resolution): states of a full-length step
+  float range;
+  float resolution;
+  uint32_t bias_thr;     // goal bias as a threshold on the top 24 bits of a Philox word
+  int path_cap;
+  unsigned long long t0;             // launch start (min over blocks, %globaltimer ns)
+  unsigned long long time_limit_ns;  // 0 = none
+  int cursor;            // work-queue ticket counter
+  int error;             // device-side error code (PRRTC_ERR_*), 0 = none
+  int error_info;
+  int pad_;
+};
+
+// Per-problem inputs (uploaded every call).
+struct ProblemDesc {
+  const RobotDev* robot;
+  EnvView env;
+  float* nodes[2];       // [cap * dpad] per tree, rows NaN until written
+  int* parent[2];        // [cap] per tree
+  float* path;           // [path_cap * dof]
+  int* path_idx;         // [path_cap] scratch of (tree << 30 | node)
+  int cap;
+  int dpad;
+  int dof;
+  int n_spheres;         // distinct spheres (staging size)
+  int n_pairs;
+  uint32_t key_lo, key_hi;
+  uint32_t pid;
+  float q_start[kMaxDof];
+  float q_goal[kMaxDof];
+};
+
+// Per-problem device state.  The setup kernel resets everything but the
+// arena bookkeeping (used[]), which tells it which rows to clear next time.
+struct ProblemState {
+  int iter;              // Alg. 1 iteration tickets handed out
+  int count[2];          // tree sizes (may exceed cap after failed insertions)
+  int solved;
+  int done;
+  int timed_out;
+  int pre_status;        // start / goal in collision
+  int s_tree;            // tree extended by the winning iteration
+  int join_s, join_o;
+  int path_n;
+  int path_status;
+  double cost;
+  unsigned long long t_solve;
+  unsigned long long edges, edge_states, sphere_tests, pair_tests, fk_states, nn_nodes, iterations, insert_fail;
+  // arena bookkeeping, preserved across launches
+  int used_rows[2];
+  int used_dpad;
+  int pad_;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& host_header, EnvView env, const float* q,
+                                int n, uint8_t* valid, float* spheres, unsigned long long* counters, int* error,
+                                cudaStream_t stream);
+
+cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
+                         int max_env_f4, cudaStream_t stream);
+
+struct PlanLaunch {
+  int grid;
+  int warps;
+  int smem;
+  int robot_bytes;
+  int env_bytes;
+  int stage_bytes;
+};
+
+PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, int max_spheres, int max_pairs,
+                              int max_env_f4, int sm_count);
+
+cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
+                        cudaStream_t stream);
+
+// Clear-list bookkeeping after a plan: rows each tree used, for the next setup.
+cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, int n, cudaStream_t stream);
+
+// Copy every problem's path into one packed buffer; offsets[p]..offsets[p+1]
+// is problem p's float range (n + 1 entries, device memory).
+cudaError_t launch_gather_paths(const ProblemDesc* desc, const int* offsets, int n, float* out, cudaStream_t stream);
+
+}  // namespace prrtc

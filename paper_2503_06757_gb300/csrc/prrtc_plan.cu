@@ -1,0 +1,684 @@
+// prrtc_plan.cu -- the pRRTC expansion loop on the device (Alg. 1 with
+// Alg. 2), batched over many problems in one persistent launch.
+//
+// Layout (GB300-first):
+//   * A block stages one problem's robot tables and obstacle set in shared
+//     memory (TMA bulk copies) and runs `warps` independent workers on it.  A
+//     worker is one warp executing Alg. 1 iterations: the paper's block-level
+//     parallel iterations (Sec. III) map to warps, its thread-level NN and CC
+//     to lanes.
+//   * Blocks take problems from a device work queue (an atomic ticket) and,
+//     when their problem is solved or out of budget, move to the next unsolved
+//     one, so hard problems soak up the blocks freed by easy ones.
+//   * Both trees of a problem live in global memory (L2-resident at these
+//     sizes).  Rows start as NaN; a worker reserves a row with one atomicAdd,
+//     writes the parent, fences, then the coordinates.  Readers scan with L2
+//     loads and skip rows whose distance is NaN, so a row is used only once
+//     all its coordinates are final (each word changes NaN -> value once).
+//   * Serial mode runs one worker per problem; it performs exactly the
+//     iterations of the serial Alg. 1 in order.
+#include <cfloat>
+#include <climits>
+
+#include "prrtc.h"
+#include "prrtc_launch.h"
+
+namespace prrtc {
+
+namespace {
+
+static_assert(sizeof(RobotHeader) % 16 == 0, "robot header must stay 16-byte aligned for TMA");
+static_assert(offsetof(RobotDev, pair) % 16 == 0 && offsetof(RobotDev, thr) % 16 == 0, "TMA alignment");
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+struct Local {
+  unsigned long long edges = 0, edge_states = 0, nn_nodes = 0, iterations = 0, insert_fail = 0;
+  WorkCount wc;
+};
+
+struct Ctx {
+  const PlanGlobals* g;
+  const ProblemDesc* D;
+  ProblemState* S;
+  const RobotHeader* R;
+  const uint32_t* pair;
+  const float* thr;
+  const float4* env;
+  float* stage;
+  int lane;
+};
+
+// NEAREST_NEIGHBOR (Sec. III-C): each lane scans a strided slice of the
+// tree, then a butterfly reduction over the warp; ties go to the lowest index.
+template <int DP>
+__device__ __forceinline__ int nearest(const float* __restrict__ nodes, int n, const float (&q)[DP], int lane,
+                                       Local& lc) {
+  float best = FLT_MAX;
+  int bi = INT_MAX;
+  int i = lane;
+  for (; i + 32 < n; i += 64) {
+    const float4* r0 = reinterpret_cast<const float4*>(nodes + (size_t)i * DP);
+    const float4* r1 = reinterpret_cast<const float4*>(nodes + (size_t)(i + 32) * DP);
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < DP / 4; ++k) {
+      const float4 a = __ldcg(r0 + k), b = __ldcg(r1 + k);
+      float t;
+      t = q[4 * k + 0] - a.x; d0 = fmaf(t, t, d0);
+      t = q[4 * k + 1] - a.y; d0 = fmaf(t, t, d0);
+      t = q[4 * k + 2] - a.z; d0 = fmaf(t, t, d0);
+      t = q[4 * k + 3] - a.w; d0 = fmaf(t, t, d0);
+      t = q[4 * k + 0] - b.x; d1 = fmaf(t, t, d1);
+      t = q[4 * k + 1] - b.y; d1 = fmaf(t, t, d1);
+      t = q[4 * k + 2] - b.z; d1 = fmaf(t, t, d1);
+      t = q[4 * k + 3] - b.w; d1 = fmaf(t, t, d1);
+    }
+    if (d0 < best) { best = d0; bi = i; }
+    if (d1 < best) { best = d1; bi = i + 32; }
+  }
+  if (i < n) {
+    const float4* r0 = reinterpret_cast<const float4*>(nodes + (size_t)i * DP);
+    float d0 = 0.f;
+#pragma unroll
+    for (int k = 0; k < DP / 4; ++k) {
+      const float4 a = __ldcg(r0 + k);
+      float t;
+      t = q[4 * k + 0] - a.x; d0 = fmaf(t, t, d0);
+      t = q[4 * k + 1] - a.y; d0 = fmaf(t, t, d0);
+      t = q[4 * k + 2] - a.z; d0 = fmaf(t, t, d0);
+      t = q[4 * k + 3] - a.w; d0 = fmaf(t, t, d0);
+    }
+    if (d0 < best) { best = d0; bi = i; }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const float ob = __shfl_xor_sync(kFull, best, off);
+    const int oi = __shfl_xor_sync(kFull, bi, off);
+    if (ob < best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (lane == 0) lc.nn_nodes += (unsigned long long)n;
+  return bi;
+}
+
+template <int DP>
+__device__ __forceinline__ void load_row(const float* __restrict__ nodes, int idx, float (&v)[DP]) {
+  const float4* r = reinterpret_cast<const float4*>(nodes + (size_t)idx * DP);
+#pragma unroll
+  for (int k = 0; k < DP / 4; ++k) {
+    const float4 a = __ldcg(r + k);
+    v[4 * k + 0] = a.x;
+    v[4 * k + 1] = a.y;
+    v[4 * k + 2] = a.z;
+    v[4 * k + 3] = a.w;
+  }
+}
+
+// Alg. 2 lines 3-5: the N states a + (k/N)(b - a), k = 1..N, one per lane
+// (several passes if N > 32); false at the first colliding state.
+template <int DP>
+__device__ __forceinline__ bool edge_free(const Ctx& c, const float (&a)[DP], const float (&b)[DP], int N, Local& lc) {
+  lc.edges++;
+  lc.edge_states += (unsigned long long)N;
+  const float fN = (float)N;
+  for (int base = 0; base < N; base += 32) {
+    const int k = base + c.lane + 1;
+    const bool active = k <= N;
+    const int kk = active ? k : N;
+    const float t = __fdiv_rn((float)kk, fN);
+    float q[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) q[j] = (kk == N) ? b[j] : fmaf(t, b[j] - a[j], a[j]);
+    if (state_collides<DP, true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
+                                 c.D->env.n_sph, c.stage, q, active, c.lane, lc.wc))
+      return false;
+  }
+  return true;
+}
+
+// Append a row to tree t; returns its index or -1 when the tree is full.
+template <int DP>
+__device__ __forceinline__ int insert(const Ctx& c, int t, const float (&q)[DP], int parent, Local& lc) {
+  int idx = 0;
+  if (c.lane == 0) idx = atomicAdd(&c.S->count[t], 1);
+  idx = __shfl_sync(kFull, idx, 0);
+  if (idx >= c.D->cap) {
+    if (c.lane == 0) lc.insert_fail++;
+    return -1;
+  }
+  if (c.lane == 0) {
+    __stcg(c.D->parent[t] + idx, parent);
+    __threadfence();
+  }
+  __syncwarp();
+  float v = 0.f;
+#pragma unroll
+  for (int j = 0; j < DP; ++j)
+    if (c.lane == j) v = q[j];
+  if (c.lane < DP) __stcg(c.D->nodes[t] + (size_t)idx * DP + c.lane, v);
+  __syncwarp();
+  return idx;
+}
+
+// Parent of a node, waiting (bounded) for a row still being written.
+__device__ __forceinline__ int parent_of(const int* par, int node, int* err) {
+  int p = ld_volatile(par + node);
+  for (int spin = 0; p == kUnsetParent && spin < (1 << 20); ++spin) p = ld_volatile(par + node);
+  if (p == kUnsetParent) *err = 1;
+  return p;
+}
+
+// PATH(T_a, T_b) by the winning warp: root(T_a) .. join .. root(T_b).  The two
+// join rows hold the same configuration; the copy in T_b is dropped when T_a
+// was extended and vice versa, so the path lists each waypoint once.
+template <int DP>
+__device__ void extract_path(const Ctx& c, int s, int js, int jo) {
+  const ProblemDesc* D = c.D;
+  const int o = 1 - s;
+  int err = 0;
+  int ns = 0, no = 0;
+  if (c.lane == 0) {
+    for (int x = js; x >= 0 && ns <= D->cap; x = parent_of(D->parent[s], x, &err)) ns++;
+    for (int x = jo; x >= 0 && no <= D->cap; x = parent_of(D->parent[o], x, &err)) no++;
+  }
+  ns = __shfl_sync(kFull, ns, 0);
+  no = __shfl_sync(kFull, no, 0);
+  err = __shfl_sync(kFull, err, 0);
+  const int K = ns + no - 1;
+  if (c.lane == 0) c.S->path_n = K;
+  if (err || ns > D->cap || no > D->cap) {
+    if (c.lane == 0) c.S->path_status = PRRTC_ERR_TIMEOUT;
+    return;
+  }
+  if (K > c.g->path_cap) {
+    if (c.lane == 0) c.S->path_status = PRRTC_PATH_OVERFLOW;
+    return;
+  }
+  // the T_a-side chain (root first) then the T_b-side chain without its join row
+  const int a_tree = 0;
+  const int a_join = (s == 0) ? js : jo;
+  const int b_join = (s == 0) ? jo : js;
+  const int na = (s == 0) ? ns : no;
+  if (c.lane == 0) {
+    // both walks are bounded by the chain lengths counted above
+    int pos = na - 1;
+    for (int x = a_join; x >= 0 && pos >= 0; x = parent_of(D->parent[a_tree], x, &err)) D->path_idx[pos--] = x;
+    pos = na;
+    for (int x = parent_of(D->parent[1], b_join, &err); x >= 0 && pos < K; x = parent_of(D->parent[1], x, &err))
+      D->path_idx[pos++] = (1 << 30) | x;
+    __threadfence_block();
+  }
+  __syncwarp();
+  const int dof = D->dof;
+  double seg = 0.0;
+  for (int r = c.lane; r < K; r += 32) {
+    const int code = D->path_idx[r];
+    const int t = code >> 30, x = code & ((1 << 30) - 1);
+    float v[DP];
+    load_row<DP>(D->nodes[t], x, v);
+#pragma unroll
+    for (int j = 0; j < DP; ++j)
+      if (j < dof) D->path[(size_t)r * dof + j] = v[j];
+    if (r > 0) {
+      const int pc = D->path_idx[r - 1];
+      float w[DP];
+      load_row<DP>(D->nodes[pc >> 30], pc & ((1 << 30) - 1), w);
+      double s2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < DP; ++j) {
+        const double d = (double)v[j] - (double)w[j];
+        s2 += d * d;
+      }
+      seg += sqrt(s2);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) seg += __shfl_xor_sync(kFull, seg, off);
+  if (c.lane == 0) {
+    c.S->cost = seg;
+    c.S->path_status = err ? PRRTC_ERR_TIMEOUT : PRRTC_SOLVED;
+  }
+}
+
+// Alg. 1 iterations of one worker warp on one problem until it is solved,
+// out of budget or out of time.
+template <int DP>
+__device__ void worker(const Ctx& c, Local& lc) {
+  const PlanGlobals* g = c.g;
+  const ProblemDesc* D = c.D;
+  ProblemState* S = c.S;
+  const RobotHeader* R = c.R;
+  const int lane = c.lane;
+  const int dof = D->dof;
+  const int cap = D->cap;
+  const float range = g->range;
+  const float res = g->resolution;
+  const int n_full = g->n_full;
+  const uint2 key = make_uint2(D->key_lo, D->key_hi);
+  for (;;) {
+    int stop = 0, it = 0;
+    if (lane == 0) {
+      stop = ld_volatile(&S->done) | ld_volatile(&S->solved);
+      if (!stop) it = atomicAdd(&S->iter, 1);
+    }
+    stop = __shfl_sync(kFull, stop, 0);
+    if (stop) break;
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= g->max_iters) {
+      if (lane == 0) atomicExch(&S->done, 1);
+      break;
+    }
+    if (g->time_limit_ns && globaltimer_ns() - g->t0 > g->time_limit_ns) {
+      if (lane == 0) {
+        S->timed_out = 1;
+        atomicExch(&S->done, 1);
+      }
+      break;
+    }
+    lc.iterations++;
+
+    // Alg. 1 line 3: extend the smaller tree (ties: T_a).
+    const int na = min(ld_relaxed(&S->count[0]), cap);
+    const int nb = min(ld_relaxed(&S->count[1]), cap);
+    const int s = (na <= nb) ? 0 : 1;
+    const int o = 1 - s;
+    const int n_s = s ? nb : na;
+
+    // line 4: RANDOM_CONFIG -- Philox words w_0..w_dof of counter {pid, it, blk, 0};
+    // lane l holds word l (lanes 0..19 evaluate blocks 0..4).
+    uint32_t w = 0;
+    if (lane < 20) {
+      const uint4 r = philox4x32_10(make_uint4(D->pid, (uint32_t)it, (uint32_t)(lane >> 2), 0u), key);
+      const int k = lane & 3;
+      w = (k == 0) ? r.x : (k == 1) ? r.y : (k == 2) ? r.z : r.w;
+    }
+    const uint32_t w0 = __shfl_sync(kFull, w, 0);
+    float crand[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+      const uint32_t wj = __shfl_sync(kFull, w, j + 1);
+      crand[j] = (j < dof) ? fmaf(u24(wj), R->span[j], R->lo[j]) : 0.f;
+    }
+    if ((w0 >> 8) < g->bias_thr) load_row<DP>(D->nodes[o], 0, crand);  // goal bias: root of T_o
+
+    // line 5: nearest node of T_s.
+    const int nn = nearest<DP>(D->nodes[s], n_s, crand, lane, lc);
+    float cnn[DP];
+    load_row<DP>(D->nodes[s], nn, cnn);
+
+    // Alg. 2: steer from c_nn toward c_rand by at most delta, check the edge.
+    float d2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+      const float t = crand[j] - cnn[j];
+      d2 = fmaf(t, t, d2);
+    }
+    if (!(d2 > 0.f)) continue;
+    const float dist = __fsqrt_rn(d2);
+    float cnew[DP];
+    int N;
+    if (dist > range) {
+      const float f = __fdiv_rn(range, dist);
+#pragma unroll
+      for (int j = 0; j < DP; ++j) cnew[j] = fmaf(crand[j] - cnn[j], f, cnn[j]);
+      N = n_full;
+    } else {
+#pragma unroll
+      for (int j = 0; j < DP; ++j) cnew[j] = crand[j];
+      N = (int)ceilf(__fdiv_rn(dist, res));
+    }
+    if (N < 1) N = 1;
+    if (!edge_free<DP>(c, cnn, cnew, N, lc)) continue;
+
+    // line 7: add c_new to T_s.
+    const int idx = insert<DP>(c, s, cnew, nn, lc);
+    if (idx < 0) continue;
+
+    // line 8: nearest node of T_o to c_new; lines 9-15: greedy connect.
+    const int n_o = min(ld_relaxed(&S->count[o]), cap);
+    const int nno = nearest<DP>(D->nodes[o], n_o, cnew, lane, lc);
+    float ct[DP];
+    load_row<DP>(D->nodes[o], nno, ct);
+    float D2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+      const float t = ct[j] - cnew[j];
+      D2 = fmaf(t, t, D2);
+    }
+    const float Dd = __fsqrt_rn(D2);
+    const int n_ext = (Dd > 0.f) ? (int)ceilf(__fdiv_rn(Dd, range)) : 0;
+    int prev = idx;
+    float prevq[DP];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) prevq[j] = cnew[j];
+    bool connected = true;
+    for (int i = 1; i <= n_ext; ++i) {
+      int solved = 0;
+      if (lane == 0) solved = ld_volatile(&S->solved);
+      if (__shfl_sync(kFull, solved, 0)) {
+        connected = false;
+        break;
+      }
+      float ext[DP];
+      int Ni;
+      if (i < n_ext) {
+        const float f = __fdiv_rn((float)i * range, Dd);
+#pragma unroll
+        for (int j = 0; j < DP; ++j) ext[j] = fmaf(f, ct[j] - cnew[j], cnew[j]);
+        Ni = n_full;
+      } else {
+#pragma unroll
+        for (int j = 0; j < DP; ++j) ext[j] = ct[j];
+        const float len = Dd - (float)(n_ext - 1) * range;
+        Ni = (int)ceilf(__fdiv_rn(len, res));
+        if (Ni < 1) Ni = 1;
+      }
+      if (!edge_free<DP>(c, prevq, ext, Ni, lc)) {
+        connected = false;
+        break;
+      }
+      const int a = insert<DP>(c, s, ext, prev, lc);
+      if (a < 0) {
+        connected = false;
+        break;
+      }
+      prev = a;
+#pragma unroll
+      for (int j = 0; j < DP; ++j) prevq[j] = ext[j];
+    }
+    if (!connected) continue;
+
+    // line 16: the trees meet -- the first worker to claim the problem writes PATH.
+    int won = 0;
+    if (lane == 0) won = (atomicCAS(&S->solved, 0, 1) == 0);
+    won = __shfl_sync(kFull, won, 0);
+    if (won) {
+      if (lane == 0) {
+        S->t_solve = globaltimer_ns();
+        S->s_tree = s;
+        S->join_s = prev;
+        S->join_o = nno;
+      }
+      extract_path<DP>(c, s, prev, nno);
+      __threadfence();
+      if (lane == 0) atomicExch(&S->done, 1);
+    }
+    break;
+  }
+}
+
+__device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
+  const int P = g->n_problems;
+  const int t = atomicAdd(&g->cursor, 1);
+  if (g->mode == PRRTC_MODE_SERIAL) return t < P ? t : -1;
+  for (int k = 0; k < P; ++k) {
+    const int p = (t + k) % P;
+    if (!ld_volatile(&states[p].done)) return p;
+  }
+  return -1;
+}
+
+__global__ void plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
+                            ProblemState* __restrict__ states, int robot_bytes, int env_bytes, int stage_bytes_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_prob;
+  __shared__ int s_ok;
+  __shared__ const RobotDev* s_robot;
+  __shared__ const float4* s_env;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) {
+    atomicMin(&g->t0, globaltimer_ns());
+    mbar_init(&bar, 1);
+    s_robot = nullptr;
+    s_env = nullptr;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  Local lc;
+  for (;;) {
+    if (threadIdx.x == 0) s_prob = pick_problem(g, states);
+    __syncthreads();
+    const int p = s_prob;
+    if (p < 0) break;
+    const ProblemDesc* D = descs + p;
+    const int np_pad = (D->n_pairs + 3) & ~3;
+    RobotHeader* R = reinterpret_cast<RobotHeader*>(smem);
+    uint32_t* pair = reinterpret_cast<uint32_t*>(smem + sizeof(RobotHeader));
+    float* thr = reinterpret_cast<float*>(pair + np_pad);
+    float4* senv = reinterpret_cast<float4*>(smem + robot_bytes);
+    const int env_f4 = D->env.n_float4();
+    // Stage robot and environment unless the block already holds them.
+    const bool restage = (s_robot != D->robot) || (s_env != D->env.data);
+    __syncthreads();
+    if (restage) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        const uint32_t bytes = (uint32_t)sizeof(RobotHeader) + 8u * (uint32_t)np_pad + 16u * (uint32_t)env_f4;
+        mbar_arrive_expect_tx(&bar, bytes);
+        bulk_g2s(R, &D->robot->h, sizeof(RobotHeader), &bar);
+        if (np_pad) {
+          bulk_g2s(pair, D->robot->pair, 4u * np_pad, &bar);
+          bulk_g2s(thr, D->robot->thr, 4u * np_pad, &bar);
+        }
+        if (env_f4) bulk_g2s(senv, D->env.data, 16u * env_f4, &bar);
+      }
+      if (threadIdx.x == 0) {
+        s_ok = mbar_wait(&bar, phase, 1u << 26) ? 1 : 0;
+        if (!s_ok) atomicExch(&g->error, PRRTC_ERR_TIMEOUT);
+        s_robot = D->robot;
+        s_env = D->env.data;
+      }
+      phase ^= 1u;
+      __syncthreads();
+      if (!s_ok) break;  // block-uniform: every thread leaves the same way
+    }
+    Ctx c;
+    c.g = g;
+    c.D = D;
+    c.S = states + p;
+    c.R = R;
+    c.pair = pair;
+    c.thr = thr;
+    c.env = senv;
+    c.stage = reinterpret_cast<float*>(smem + robot_bytes + env_bytes) + warp * (stage_bytes_warp / 4);
+    c.lane = lane;
+    switch (D->dpad) {
+      case 4: worker<4>(c, lc); break;
+      case 8: worker<8>(c, lc); break;
+      case 12: worker<12>(c, lc); break;
+      default: worker<16>(c, lc); break;
+    }
+    // flush this warp's counters into the problem
+    unsigned long long v[8] = {lc.edges, lc.edge_states, lc.wc.sphere_tests, lc.wc.pair_tests,
+                               lc.wc.fk_states, lc.nn_nodes, lc.iterations, lc.insert_fail};
+#pragma unroll
+    for (int k = 2; k < 5; ++k)
+#pragma unroll
+      for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], off);
+    if (lane == 0) {
+      ProblemState* S = states + p;
+      atomicAdd(&S->edges, v[0]);
+      atomicAdd(&S->edge_states, v[1]);
+      atomicAdd(&S->sphere_tests, v[2]);
+      atomicAdd(&S->pair_tests, v[3]);
+      atomicAdd(&S->fk_states, v[4]);
+      atomicAdd(&S->nn_nodes, v[5]);
+      atomicAdd(&S->iterations, v[6]);
+      atomicAdd(&S->insert_fail, v[7]);
+    }
+    lc = Local();
+    __syncthreads();
+  }
+}
+
+// One block per problem: clear the rows the previous launch wrote (back to
+// NaN / unset parent), insert the roots, reset the counters, and reject a
+// start or goal in collision (Alg. 1 lines 1-2).
+template <int DP>
+__device__ void check_endpoints(const ProblemDesc* D, ProblemState* S, float* stage, const float4* env_global) {
+  const int lane = threadIdx.x & 31;
+  const RobotHeader* R = &D->robot->h;
+  float q[DP];
+#pragma unroll
+  for (int j = 0; j < DP; ++j) q[j] = (j < D->dof) ? (lane == 0 ? D->q_start[j] : D->q_goal[j]) : 0.f;
+  WorkCount wc;
+  const bool hit = state_collides<DP, false>(R, D->robot->pair, D->robot->thr, env_global, D->env.n_aabb,
+                                             D->env.n_obb, D->env.n_cyl, D->env.n_sph, stage, q, lane < 2, lane, wc);
+  const unsigned m = __ballot_sync(kFull, hit);
+  if (lane == 0) {
+    if (m & 1u) S->pre_status = PRRTC_START_IN_COLLISION;
+    else if (m & 2u) S->pre_status = PRRTC_GOAL_IN_COLLISION;
+    if (m & 3u) S->done = 1;
+  }
+}
+
+__global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ProblemDesc* D = descs + blockIdx.x;
+  ProblemState* S = states + blockIdx.x;
+  const int dpad = D->dpad;
+  for (int t = 0; t < 2; ++t) {
+    const int rows = S->used_rows[t];
+    const size_t nf = (size_t)rows * S->used_dpad;
+    const uint32_t nan_bits = 0xffffffffu;
+    uint32_t* nodes = reinterpret_cast<uint32_t*>(D->nodes[t]);
+    for (size_t k = threadIdx.x; k < nf; k += blockDim.x) nodes[k] = nan_bits;
+    for (int k = threadIdx.x; k < rows; k += blockDim.x) D->parent[t][k] = kUnsetParent;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int j = threadIdx.x;
+    if (j < dpad) {
+      D->nodes[0][j] = (j < D->dof) ? D->q_start[j] : 0.f;
+      D->nodes[1][j] = (j < D->dof) ? D->q_goal[j] : 0.f;
+    }
+    if (j == 0) {
+      D->parent[0][0] = kRootParent;
+      D->parent[1][0] = kRootParent;
+      S->iter = 0;
+      S->count[0] = 1;
+      S->count[1] = 1;
+      S->solved = 0;
+      S->done = 0;
+      S->timed_out = 0;
+      S->pre_status = 0;
+      S->s_tree = -1;
+      S->join_s = S->join_o = -1;
+      S->path_n = 0;
+      S->path_status = -100;
+      S->cost = 0.0;
+      S->t_solve = 0;
+      S->edges = S->edge_states = S->sphere_tests = S->pair_tests = 0;
+      S->fk_states = S->nn_nodes = S->iterations = S->insert_fail = 0;
+    }
+    __syncwarp();
+    float* stage = reinterpret_cast<float*>(smem);
+    switch (dpad) {
+      case 4: check_endpoints<4>(D, S, stage, D->env.data); break;
+      case 8: check_endpoints<8>(D, S, stage, D->env.data); break;
+      case 12: check_endpoints<12>(D, S, stage, D->env.data); break;
+      default: check_endpoints<16>(D, S, stage, D->env.data); break;
+    }
+  }
+}
+
+// After the plan: record which rows were written so the next setup clears them.
+__global__ void record_usage_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const ProblemDesc* D = descs + p;
+  ProblemState* S = states + p;
+  S->used_rows[0] = min(S->count[0], D->cap);
+  S->used_rows[1] = min(S->count[1], D->cap);
+  S->used_dpad = D->dpad;
+}
+
+__global__ void gather_paths_kernel(const ProblemDesc* __restrict__ descs, const int* __restrict__ offsets, int n,
+                                    float* __restrict__ out) {
+  const int p = blockIdx.x;
+  if (p >= n) return;
+  const int begin = offsets[p], count = offsets[p + 1] - begin;
+  const float* src = descs[p].path;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) out[(size_t)begin + k] = src[k];
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
+                         int max_env_f4, cudaStream_t stream) {
+  (void)max_pairs;
+  (void)max_env_f4;
+  if (n <= 0) return cudaSuccess;
+  const int smem = stage_bytes(max_spheres);
+  cudaError_t e = cudaFuncSetAttribute(setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  setup_kernel<<<n, 256, smem, stream>>>(desc, state);
+  return cudaGetLastError();
+}
+
+PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, int max_spheres, int max_pairs,
+                              int max_env_f4, int sm_count) {
+  PlanLaunch c{};
+  c.warps = (mode == PRRTC_MODE_SERIAL) ? 1 : (warps > 0 ? warps : 4);
+  if (c.warps > 16) c.warps = 16;
+  c.robot_bytes = robot_smem_bytes((max_pairs + 3) & ~3);
+  c.env_bytes = max_env_f4 * 16;
+  c.stage_bytes = stage_bytes(max_spheres);
+  c.smem = c.robot_bytes + c.env_bytes + c.warps * c.stage_bytes;
+  int per_sm = 0;
+  cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel, c.warps * 32, c.smem);
+  if (per_sm < 1) per_sm = 1;
+  int resident = per_sm * sm_count;
+  if (blocks > 0) {
+    c.grid = blocks;
+  } else if (mode == PRRTC_MODE_SERIAL) {
+    c.grid = n_problems < resident ? n_problems : resident;
+  } else if (n_problems == 1) {
+    // one problem: 256 concurrent workers (the paper's saturation point, Sec. IV-C)
+    c.grid = 256 / c.warps;
+    if (c.grid > resident) c.grid = resident;
+  } else {
+    c.grid = resident;
+  }
+  if (c.grid < 1) c.grid = 1;
+  return c;
+}
+
+cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
+                        cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg.smem);
+  if (e != cudaSuccess) return e;
+  plan_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
+                                                              cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, int n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  record_usage_kernel<<<(n + 127) / 128, 128, 0, stream>>>(desc, state, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_paths(const ProblemDesc* desc, const int* offsets, int n, float* out, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  gather_paths_kernel<<<n, 128, 0, stream>>>(desc, offsets, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace prrtc

@@ -1,0 +1,362 @@
+"""Python binding of libprrtc (include/prrtc.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; all planning and
+collision-checking work runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library has not been built, or no CUDA device is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workload as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libprrtc.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_INDEX, ERR_NO_DEVICE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+SOLVED, START_IN_COLLISION, GOAL_IN_COLLISION, NO_SOLUTION, PATH_OVERFLOW, TIME_LIMIT = 0, 1, 2, 3, 4, 5
+MODE_ASYNC, MODE_SERIAL = 0, 1
+OBS_BOX, OBS_CYLINDER, OBS_SPHERE = 0, 1, 2
+
+_f = C.POINTER(C.c_float)
+_i = C.POINTER(C.c_int32)
+
+
+class prrtc_obstacle(C.Structure):
+    _fields_ = [("type", C.c_int32), ("center", C.c_float * 3), ("half", C.c_float * 3),
+                ("axis", C.c_float * 3), ("rot", C.c_float * 9)]
+
+
+class prrtc_robot_desc(C.Structure):
+    _fields_ = [("dof", C.c_int32), ("joint_type", _i), ("joint_parent", _i), ("joint_base", _f),
+                ("link_length", _f), ("lower", _f), ("upper", _f), ("n_spheres", C.c_int32),
+                ("sphere_frame", _i), ("sphere_offset", _f), ("sphere_radius", _f),
+                ("n_pairs", C.c_int32), ("self_pairs", _i)]
+
+
+class prrtc_params(C.Structure):
+    _fields_ = [("range", C.c_float), ("resolution", C.c_float), ("goal_bias", C.c_float),
+                ("max_iters", C.c_int32), ("tree_capacity", C.c_int32), ("path_capacity", C.c_int32),
+                ("mode", C.c_int32), ("blocks", C.c_int32), ("warps_per_block", C.c_int32),
+                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("time_limit_s", C.c_double),
+                ("reserved", C.c_int32 * 8)]
+
+
+class prrtc_path(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("dof", C.c_int32), ("iterations", C.c_int32),
+                ("q", _f), ("cost", C.c_double), ("nodes_a", C.c_int32), ("nodes_b", C.c_int32),
+                ("edges_checked", C.c_int64), ("edge_states", C.c_int64), ("solve_time_us", C.c_double),
+                ("sphere_tests", C.c_int64), ("pair_tests", C.c_int64), ("fk_states", C.c_int64),
+                ("nn_nodes", C.c_int64)]
+
+
+class prrtc_launch_stats(C.Structure):
+    _fields_ = [("kernel_ms", C.c_double), ("setup_ms", C.c_double), ("edges_checked", C.c_int64),
+                ("edge_states", C.c_int64), ("sphere_tests", C.c_int64), ("env_tests", C.c_int64),
+                ("pair_tests", C.c_int64), ("fk_states", C.c_int64), ("nn_nodes", C.c_int64),
+                ("iterations", C.c_int64), ("grid", C.c_int32), ("block_threads", C.c_int32),
+                ("smem_bytes", C.c_int32), ("problems", C.c_int32), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("reserved_", C.c_int32)]
+
+
+class prrtc_problem(C.Structure):
+    _fields_ = [("robot", C.c_void_p), ("env", C.c_void_p), ("q_start", _f), ("q_goal", _f),
+                ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("reserved", C.c_int32)]
+
+
+EXPORTS = [
+    "prrtc_params_default", "prrtc_path_free", "prrtc_last_launch_stats", "prrtc_status_string",
+    "prrtc_version", "prrtc_last_error", "prrtc_env_create", "prrtc_env_update", "prrtc_env_destroy",
+    "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
+    "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
+]
+
+_lib = None
+
+
+class PrrtcError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code}): {last_error()}")
+
+
+def lib():
+    """Load the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libprrtc is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    L.prrtc_status_string.restype = C.c_char_p
+    L.prrtc_version.restype = C.c_char_p
+    L.prrtc_last_error.restype = C.c_char_p
+    L.prrtc_env_create.argtypes = [C.POINTER(prrtc_obstacle), C.c_int32, C.POINTER(C.c_void_p)]
+    L.prrtc_env_update.argtypes = [C.c_void_p, _i, C.POINTER(prrtc_obstacle), C.c_int32]
+    L.prrtc_env_destroy.argtypes = [C.c_void_p]
+    L.prrtc_robot_create.argtypes = [C.POINTER(prrtc_robot_desc), C.POINTER(C.c_void_p)]
+    L.prrtc_robot_destroy.argtypes = [C.c_void_p]
+    L.prrtc_robot_info.argtypes = [C.c_void_p, _i, _i, _i, _i]
+    L.prrtc_env_info.argtypes = [C.c_void_p, _i]
+    L.prrtc_check_states.argtypes = [C.c_void_p, C.c_void_p, _f, C.c_int32, C.POINTER(C.c_uint8), _f]
+    L.prrtc_check_states_device.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]
+    L.prrtc_plan.argtypes = [C.c_void_p, C.c_void_p, _f, _f, C.POINTER(prrtc_params), C.POINTER(prrtc_path)]
+    L.prrtc_plan_batch.argtypes = [C.POINTER(prrtc_problem), C.c_int32, C.POINTER(prrtc_params),
+                                   C.POINTER(prrtc_path), _i]
+    L.prrtc_path_free.argtypes = [C.POINTER(prrtc_path)]
+    L.prrtc_params_default.argtypes = [C.POINTER(prrtc_params)]
+    L.prrtc_last_launch_stats.argtypes = [C.POINTER(prrtc_launch_stats)]
+    L.prrtc_debug_tree.argtypes = [C.c_int32, C.c_int32, _f, _i, C.c_int32, _i]
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().prrtc_status_string(int(code)).decode()
+
+
+def last_error() -> str:
+    return lib().prrtc_last_error().decode()
+
+
+def version() -> str:
+    return lib().prrtc_version().decode()
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise PrrtcError(rc, what)
+
+
+def _fa(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_f)
+
+
+def _ia(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_i)
+
+
+# ------------------------------------------------------------------ handles
+
+class Env:
+    """Device-resident obstacle set (prrtc_env_create / _update / _destroy)."""
+
+    def __init__(self, obstacles):
+        self._lib = lib()
+        arr = (prrtc_obstacle * max(1, len(obstacles)))(*obstacles)
+        h = C.c_void_p()
+        _check(self._lib.prrtc_env_create(arr, len(obstacles), C.byref(h)), "prrtc_env_create")
+        self.handle = h
+        self.n = len(obstacles)
+
+    def update(self, ids, obstacles):
+        ids_a, ids_p = _ia(ids)
+        arr = (prrtc_obstacle * max(1, len(obstacles)))(*obstacles)
+        _check(self._lib.prrtc_env_update(self.handle, ids_p, arr, len(obstacles)), "prrtc_env_update")
+
+    def info(self):
+        out = (C.c_int32 * 4)()
+        _check(self._lib.prrtc_env_info(self.handle, out), "prrtc_env_info")
+        return tuple(out)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.prrtc_env_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Robot:
+    """Device-resident sphere model (prrtc_robot_create / _destroy)."""
+
+    def __init__(self, rb: W.Robot):
+        self._lib = lib()
+        keep = []
+
+        def f(a):
+            a, p = _fa(a)
+            keep.append(a)
+            return p
+
+        def i(a):
+            a, p = _ia(a)
+            keep.append(a)
+            return p
+
+        desc = prrtc_robot_desc(
+            dof=rb.dof, joint_type=i(rb.joint_type), joint_parent=i(rb.joint_parent),
+            joint_base=f(rb.joint_base.reshape(-1)), link_length=f(rb.link_length), lower=f(rb.lower),
+            upper=f(rb.upper), n_spheres=rb.n_spheres, sphere_frame=i(rb.sphere_frame),
+            sphere_offset=f(rb.sphere_offset.reshape(-1)), sphere_radius=f(rb.sphere_radius),
+            n_pairs=int(rb.self_pairs.shape[0]),
+            self_pairs=i(rb.self_pairs.reshape(-1) if rb.self_pairs.size else np.zeros(2, np.int32)))
+        h = C.c_void_p()
+        _check(self._lib.prrtc_robot_create(C.byref(desc), C.byref(h)), "prrtc_robot_create")
+        self.handle = h
+        self.dof = rb.dof
+        self.n_raw = rb.n_spheres
+        self.model = rb
+
+    def info(self):
+        v = [C.c_int32() for _ in range(4)]
+        _check(self._lib.prrtc_robot_info(self.handle, *[C.byref(x) for x in v]), "prrtc_robot_info")
+        return dict(dof=v[0].value, n_spheres=v[1].value, n_pairs=v[2].value, dpad=v[3].value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.prrtc_robot_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def obstacles_from_scene(scene: W.Scene):
+    obs = []
+    for b in scene.boxes:
+        o = prrtc_obstacle(type=OBS_BOX)
+        o.center[:] = [float(x) for x in b[0:3]]
+        o.half[:] = [float(x) for x in b[3:6]]
+        o.rot[:] = [float(x) for x in b[6:15]]
+        obs.append(o)
+    for c in scene.cylinders:
+        o = prrtc_obstacle(type=OBS_CYLINDER)
+        o.center[:] = [float(x) for x in c[0:3]]
+        o.axis[:] = [float(x) for x in c[3:6]]
+        o.half[:] = [float(c[6]), float(c[7]), 0.0]
+        obs.append(o)
+    for s in scene.spheres:
+        o = prrtc_obstacle(type=OBS_SPHERE)
+        o.center[:] = [float(x) for x in s[0:3]]
+        o.half[:] = [float(s[3]), 0.0, 0.0]
+        obs.append(o)
+    return obs
+
+
+def make_env(scene: W.Scene) -> Env:
+    return Env(obstacles_from_scene(scene))
+
+
+def make_robot(rb: W.Robot) -> Robot:
+    return Robot(rb)
+
+
+# ------------------------------------------------------------------ calls
+
+def prrtc_params_default() -> prrtc_params:
+    p = prrtc_params()
+    lib().prrtc_params_default(C.byref(p))
+    return p
+
+
+def params(**kw) -> prrtc_params:
+    p = prrtc_params_default()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def prrtc_check_states(robot: Robot, env: Env, Q, want_spheres: bool = False):
+    """Verdicts (True = collision-free) and, optionally, [n, S, 4] sphere centres+radii."""
+    Q, qp = _fa(np.asarray(Q).reshape(-1, robot.dof))
+    n = Q.shape[0]
+    valid = np.zeros(n, dtype=np.uint8)
+    sph = np.zeros((n, robot.n_raw, 4), dtype=np.float32) if want_spheres else None
+    _check(lib().prrtc_check_states(robot.handle, env.handle, qp, n, valid.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                    sph.ctypes.data_as(_f) if want_spheres else None), "prrtc_check_states")
+    return (valid.astype(bool), sph) if want_spheres else valid.astype(bool)
+
+
+def prrtc_check_states_device(robot: Robot, env: Env, q_ptr: int, n: int, valid_ptr: int, spheres_ptr: int = 0,
+                              stream: int = 0):
+    """Device-pointer form (e.g. torch tensors' data_ptr(), stream.cuda_stream)."""
+    _check(lib().prrtc_check_states_device(robot.handle, env.handle, C.c_void_p(q_ptr), n, C.c_void_p(valid_ptr),
+                                           C.c_void_p(spheres_ptr or None), C.c_void_p(stream or None)),
+           "prrtc_check_states_device")
+
+
+def _path_dict(p: prrtc_path):
+    d = dict(status=int(p.status), n=int(p.n), dof=int(p.dof), iterations=int(p.iterations), cost=float(p.cost),
+             nodes_a=int(p.nodes_a), nodes_b=int(p.nodes_b), edges_checked=int(p.edges_checked),
+             edge_states=int(p.edge_states), solve_time_us=float(p.solve_time_us),
+             sphere_tests=int(p.sphere_tests), pair_tests=int(p.pair_tests), fk_states=int(p.fk_states),
+             nn_nodes=int(p.nn_nodes))
+    if p.q and p.n > 0:
+        d["path"] = np.ctypeslib.as_array(p.q, shape=(p.n * p.dof,)).reshape(p.n, p.dof).copy()
+    else:
+        d["path"] = np.zeros((0, p.dof), np.float32)
+    return d
+
+
+def prrtc_plan(robot: Robot, env: Env, q_start, q_goal, prm: prrtc_params | None = None):
+    prm = prm or prrtc_params_default()
+    s, sp = _fa(q_start)
+    g, gp = _fa(q_goal)
+    out = prrtc_path()
+    _check(lib().prrtc_plan(robot.handle, env.handle, sp, gp, C.byref(prm), C.byref(out)), "prrtc_plan")
+    try:
+        return _path_dict(out)
+    finally:
+        lib().prrtc_path_free(C.byref(out))
+
+
+def prrtc_plan_batch(problems, prm: prrtc_params | None = None):
+    """problems: sequence of (Robot, Env, q_start, q_goal, seed, problem_id)."""
+    prm = prm or prrtc_params_default()
+    n = len(problems)
+    arr = (prrtc_problem * n)()
+    keep = []
+    for k, (rb, ev, qs, qg, seed, pid) in enumerate(problems):
+        s, sp = _fa(qs)
+        g, gp = _fa(qg)
+        keep += [s, g]
+        arr[k].robot = rb.handle
+        arr[k].env = ev.handle
+        arr[k].q_start = sp
+        arr[k].q_goal = gp
+        arr[k].seed = int(seed)
+        arr[k].problem_id = int(pid)
+    paths = (prrtc_path * n)()
+    status = (C.c_int32 * n)()
+    _check(lib().prrtc_plan_batch(arr, n, C.byref(prm), paths, status), "prrtc_plan_batch")
+    out = []
+    for k in range(n):
+        out.append(_path_dict(paths[k]))
+        lib().prrtc_path_free(C.byref(paths[k]))
+    return out
+
+
+def prrtc_last_launch_stats():
+    s = prrtc_launch_stats()
+    _check(lib().prrtc_last_launch_stats(C.byref(s)), "prrtc_last_launch_stats")
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def prrtc_debug_tree(problem: int, tree: int, dof: int):
+    """Rows and parents (root: -1) of one tree of the last planning launch."""
+    n = C.c_int32()
+    _check(lib().prrtc_debug_tree(problem, tree, None, None, 0, C.byref(n)), "prrtc_debug_tree")
+    m = n.value
+    nodes = np.zeros((max(m, 1), dof), np.float32)
+    par = np.zeros(max(m, 1), np.int32)
+    _check(lib().prrtc_debug_tree(problem, tree, nodes.ctypes.data_as(_f), par.ctypes.data_as(_i), m, C.byref(n)),
+           "prrtc_debug_tree")
+    return nodes[:m], par[:m]

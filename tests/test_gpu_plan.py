@@ -1,0 +1,235 @@
+"""Parity of the CUDA planner (prrtc_plan / prrtc_plan_batch) with the FP64 oracle.
+
+* Serial mode runs Alg. 1 in iteration order on one warp; it must build the
+  same trees and return the same path as the serial oracle wherever the
+  oracle met no ambiguous decision (a clearance inside 1e-5 m, a near tie in
+  the nearest-neighbour scan, a ceil() argument next to an integer).
+* Async mode (many warps over shared trees, Sec. III) is nondeterministic:
+  every returned path must start at q_start, end at q_goal, take steps of at
+  most delta and pass the oracle's re-check at 4x finer resolution; every tree
+  edge must be collision-free at the planning resolution.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_06757_gb300 import prrtc as P
+from paper_2503_06757_gb300 import workload as W
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+F32 = lambda x: float(np.float32(x))
+RANGE, RES, BIAS = 1.0, F32(1 / 32), F32(0.05)
+BAND = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2503_06757_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def c1_problems():
+    return W.problem_set("c1", 6, 1, O.accept)
+
+
+def gpu_plan(pb, seed, **kw):
+    rb, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
+    prm = P.params(seed=seed, **kw)
+    return P.prrtc_plan(rb, ev, pb.q_start, pb.q_goal, prm)
+
+
+def oracle_plan(pb, seed, **kw):
+    kw.setdefault("range", RANGE)
+    kw.setdefault("resolution", RES)
+    kw.setdefault("goal_bias", BIAS)
+    return O.plan(pb.robot, pb.scene, pb.q_start.astype(np.float32).astype(np.float64),
+                  pb.q_goal.astype(np.float32).astype(np.float64), seed=seed, want_trees=True, **kw)
+
+
+def assert_path_valid(pb, r, delta=RANGE, res=RES):
+    P_ = r["path"].astype(np.float64)
+    assert r["status"] == P.SOLVED
+    np.testing.assert_array_equal(r["path"][0], pb.q_start.astype(np.float32))
+    np.testing.assert_array_equal(r["path"][-1], pb.q_goal.astype(np.float32))
+    seg = np.linalg.norm(np.diff(P_, axis=0), axis=1)
+    assert np.all(seg <= delta * (1 + 1e-5)), seg.max()
+    assert abs(r["cost"] - seg.sum()) <= 1e-4 * max(1.0, seg.sum())
+    bad, mc = O.revalidate(pb.robot, pb.scene, P_, res / 4)
+    return bad, mc
+
+
+# ------------------------------------------------------------------ serial lockstep parity
+
+@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("seed", [1, 2])
+def test_serial_mode_matches_oracle(c1_problems, k, seed):
+    pb = c1_problems[k]
+    g = gpu_plan(pb, seed, mode=P.MODE_SERIAL, tree_capacity=1 << 14)
+    o = oracle_plan(pb, seed, tree_capacity=1 << 14)
+    amb = o["first_amb_iter"]
+    if amb != -1 and amb < o["iterations"]:
+        pytest.skip(f"oracle met an ambiguous decision at iteration {amb} (kind {o['first_amb_kind']})")
+    assert g["status"] == o["status"] == 0
+    assert g["iterations"] == o["iterations"]
+    assert (g["nodes_a"], g["nodes_b"]) == (o["n_a"], o["n_b"])
+    for t, (nodes, par) in enumerate(((o["nodes_a"], o["parent_a"]), (o["nodes_b"], o["parent_b"]))):
+        gn, gp = P.prrtc_debug_tree(0, t, pb.robot.dof)
+        np.testing.assert_array_equal(gp, par)
+        np.testing.assert_allclose(gn, nodes, atol=1e-4)
+    np.testing.assert_allclose(g["path"], o["path"], atol=1e-4)
+    assert abs(g["cost"] - o["cost"]) <= 1e-4 * o["cost"]
+    assert g["edges_checked"] == o["edges_checked"]
+    assert g["edge_states"] == o["edge_states"]
+
+
+def test_serial_mode_unambiguous_cases_exist(c1_problems):
+    """The lockstep comparison above must not be vacuous."""
+    clean = 0
+    for pb in c1_problems:
+        for seed in (1, 2):
+            o = oracle_plan(pb, seed, tree_capacity=1 << 14)
+            clean += o["first_amb_iter"] == -1 or o["first_amb_iter"] >= o["iterations"]
+    assert clean >= 6
+
+
+def test_serial_batch_equals_serial_alone(c1_problems):
+    """Each problem's result is the same alone and in a batch (serial mode: bitwise)."""
+    probs = [(P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 3, k)
+             for k, pb in enumerate(c1_problems)]
+    prm = P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14)
+    batch = P.prrtc_plan_batch(probs, prm)
+    for k, pr in enumerate(probs):
+        alone = P.prrtc_plan_batch([pr], prm)[0]
+        assert alone["status"] == batch[k]["status"]
+        np.testing.assert_array_equal(alone["path"], batch[k]["path"])
+        assert alone["iterations"] == batch[k]["iterations"]
+
+
+# ------------------------------------------------------------------ async mode
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_async_paths_revalidate(c1_problems, seed):
+    for pb in c1_problems:
+        r = gpu_plan(pb, seed)
+        bad, mc = assert_path_valid(pb, r)
+        assert bad == 0 or mc > -1e-3, (bad, mc)
+
+
+def test_async_tree_invariants(c1_problems):
+    pb = c1_problems[0]
+    r = gpu_plan(pb, 7, goal_bias=0.0, max_iters=400)  # no goal bias: trees grow before they meet
+    rng = np.random.default_rng(0)
+    for t, root in ((0, pb.q_start), (1, pb.q_goal)):
+        nodes, par = P.prrtc_debug_tree(0, t, pb.robot.dof)
+        assert np.all(np.isfinite(nodes))
+        np.testing.assert_array_equal(nodes[0], root.astype(np.float32))
+        assert par[0] == -1
+        assert np.all(par[1:] >= 0) and np.all(par[1:] < np.arange(1, len(par)))
+        L = np.linalg.norm(nodes[1:] - nodes[par[1:]], axis=1)
+        assert np.all(L <= RANGE * (1 + 1e-5))
+        for i in rng.choice(np.arange(1, len(par)), min(60, len(par) - 1), replace=False):
+            a, b = nodes[par[i]].astype(np.float64), nodes[i].astype(np.float64)
+            m = max(1, int(np.ceil(np.float32(np.linalg.norm(b - a)) / np.float32(RES))))
+            Q = np.array([a + (k / m) * (b - a) for k in range(1, m + 1)])
+            _, cl = O.check_states(pb.robot, pb.scene, Q)
+            assert np.all(cl >= -BAND), (t, i, cl.min())
+    assert r["status"] in (P.SOLVED, P.NO_SOLUTION)
+
+
+def test_async_success_matches_oracle_on_c1_keys(c1_problems):
+    pb = c1_problems[1]
+    g_ok = o_ok = 0
+    for seed in range(1, 21):
+        g_ok += gpu_plan(pb, seed)["status"] == P.SOLVED
+        o_ok += oracle_plan(pb, seed)["status"] == 0
+    assert g_ok == o_ok == 20
+
+
+# ------------------------------------------------------------------ special cases
+
+def test_free_space_solves_immediately():
+    robot = H.no_self(W.arm7())
+    rb, ev = P.make_robot(robot), P.make_env(H.empty_scene())
+    s = np.zeros(7, np.float32)
+    g = np.full(7, 0.5, np.float32)
+    r = P.prrtc_plan(rb, ev, s, g, P.params(goal_bias=1.0, mode=P.MODE_SERIAL))
+    assert r["status"] == P.SOLVED and r["iterations"] == 1
+    assert abs(r["cost"] - np.linalg.norm(g - s)) < 1e-5
+
+
+def test_start_goal_in_collision():
+    robot = W.arm7()
+    sc = H.scene(boxes=[H.aabb([0, 0, 1.13], [0.1, 0.1, 0.1])])
+    rb, ev = P.make_robot(robot), P.make_env(sc)
+    q0 = np.zeros(7, np.float32)
+    q1 = np.zeros(7, np.float32)
+    q1[1] = 1.5
+    assert P.prrtc_plan(rb, ev, q0, q1)["status"] == P.START_IN_COLLISION
+    assert P.prrtc_plan(rb, ev, q1, q0)["status"] == P.GOAL_IN_COLLISION
+
+
+@pytest.mark.parametrize("mode", [P.MODE_SERIAL, P.MODE_ASYNC])
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+def test_maze_reachability(mode, seed):
+    n, cell = 6, 0.2
+    sc, edges = H.maze(seed, n=n, cell=cell)
+    robot = H.point_robot()
+    s = np.array([0.1, 0.1], np.float32)
+    g = np.array([(n - 0.5) * cell, (n - 0.5) * cell], np.float32)
+    reach = H.maze_reachable(edges, n, (0, 0), (n - 1, n - 1))
+    rb, ev = P.make_robot(robot), P.make_env(sc)
+    r = P.prrtc_plan(rb, ev, s, g, P.params(seed=seed, range=F32(0.2), resolution=F32(0.01), max_iters=4000,
+                                            mode=mode))
+    assert (r["status"] == P.SOLVED) == reach, (seed, reach, r["status"])
+    if reach:
+        pb = W.Problem(robot, sc, s.astype(np.float64), g.astype(np.float64), seed)
+        bad, _ = assert_path_valid(pb, r, delta=F32(0.2), res=F32(0.01))
+        assert bad == 0
+
+
+def test_walled_off_goal_no_solution():
+    n, cell = 6, 0.2
+    sc, _ = H.maze(9, n=n, cell=cell, open_frac=1.0, enclose=(n - 1, n - 1))
+    rb, ev = P.make_robot(H.point_robot()), P.make_env(sc)
+    r = P.prrtc_plan(rb, ev, np.array([0.1, 0.1], np.float32), np.array([1.1, 1.1], np.float32),
+                     P.params(range=F32(0.2), resolution=F32(0.01), max_iters=1500))
+    assert r["status"] == P.NO_SOLUTION and r["iterations"] == 1500
+
+
+def test_budget_and_capacity_edges(c1_problems):
+    pb = c1_problems[2]
+    r = gpu_plan(pb, 1, max_iters=1, goal_bias=0.0)
+    assert r["iterations"] == 1 and r["status"] in (P.SOLVED, P.NO_SOLUTION)
+    r = gpu_plan(pb, 1, tree_capacity=2)
+    assert r["nodes_a"] <= 2 and r["nodes_b"] <= 2
+    r = gpu_plan(pb, 1, path_capacity=2)
+    assert r["status"] in (P.PATH_OVERFLOW, P.SOLVED)
+    if r["status"] == P.PATH_OVERFLOW:
+        assert r["n"] > 2
+
+
+def test_invalid_params_rejected(c1_problems):
+    pb = c1_problems[0]
+    for bad in (dict(range=0.0), dict(resolution=-1.0), dict(goal_bias=2.0), dict(max_iters=0), dict(mode=7)):
+        with pytest.raises(P.PrrtcError) as e:
+            gpu_plan(pb, 1, **bad)
+        assert e.value.code == P.ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------------ batches
+
+def test_mixed_dof_batch_one_launch():
+    probs = W.problem_set("mixed", 9, 2000, O.accept)
+    items = [(P.make_robot(p.robot), P.make_env(p.scene), p.q_start, p.q_goal, 5, k) for k, p in enumerate(probs)]
+    res = P.prrtc_plan_batch(items, P.params(max_iters=20000))
+    st = P.prrtc_last_launch_stats()
+    assert st["problems"] == 9
+    for p, r in zip(probs, res):
+        assert r["status"] in (P.SOLVED, P.NO_SOLUTION)
+        if r["status"] == P.SOLVED:
+            bad, mc = assert_path_valid(p, r)
+            assert bad == 0 or mc > -1e-3
+    assert sum(r["status"] == P.SOLVED for r in res) >= 6
