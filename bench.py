@@ -62,55 +62,75 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """SM clock, power and clock-event reasons read through NVML (read-only)
+    every ~1 ms during the timed region; falls back to nvidia-smi."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, period_s=0.001):
         self.index = index
-        self.proc = None
-        self.lines = []
+        self.period = period_s
+        self.samples = []
+        self.running = False
+        self.nvml = None
+        try:
+            import ctypes
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                raise OSError("no handle")
+            self.nvml, self.h, self.ct = nv, h, ctypes
+            mx = ctypes.c_uint()
+            nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+            self.max_mhz = float(mx.value)
+            self.reason_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except Exception:
+            self.nvml = None
+
+    def _loop(self):
+        ct, nv, h = self.ct, self.nvml, self.h
+        clk, rs, pw = ct.c_uint(), ct.c_ulonglong(), ct.c_uint()
+        while self.running:
+            nv.nvmlDeviceGetClockInfo(h, 1, ct.byref(clk))
+            self.reason_fn(h, ct.byref(rs))
+            nv.nvmlDeviceGetPowerUsage(h, ct.byref(pw))
+            self.samples.append((clk.value, rs.value, pw.value))
+            time.sleep(self.period)
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+        if self.nvml is None:
+            return
+        self.running = True
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
 
     def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
+        if self.nvml is None:
+            return self._smi_once()
+        self.running = False
+        self.t.join()
+        sm = [c for c, _, _ in self.samples]
+        reasons = set()
+        for _, r, _ in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvml",
+                "power_w_max": max(p for _, _, p in self.samples) / 1000.0 if self.samples else None}
+
+    def _smi_once(self):
         try:
-            self.proc.wait(timeout=5)
+            out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm", "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=20).stdout.split(",")
+            return {"sm_mhz": float(out[0]), "sm_max_mhz": float(out[1]), "reasons": [], "samples": 1,
+                    "source": "nvidia-smi (after the run)"}
         except Exception:
-            self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
-            parts = [p.strip() for p in l.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for k, nm in enumerate(names):
-                if parts[5 + k].lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock query unavailable"], "samples": 0}
 
 
 # ------------------------------------------------------------------ workload
@@ -251,11 +271,12 @@ def run_ours(args):
         P.prrtc_plan_batch(items, prm)
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(0)
     clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     dev_ms, wall_s, edge_states, ops, launches, h2d, d2h = 0.0, 0.0, 0, 0, 0, 0, 0
     kernel_ms = 0.0
     ttfs, solved, costs = [], 0, []
@@ -279,6 +300,7 @@ def run_ours(args):
                 ttfs.append(r["solve_time_us"])
                 costs.append(r["cost"])
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     plan_grid = dict(blocks=st["grid"], threads=st["block_threads"], smem=st["smem_bytes"])
     if dist:
         dist.barrier()
