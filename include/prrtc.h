@@ -263,6 +263,37 @@ typedef struct prrtc_problem {
 int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params,
                      prrtc_path* out_paths, int32_t* out_status);
 
+/* ------------------------------------------------------------ planning without allocation */
+/* The paper has no counterpart of this entry point; it exists for callers
+ * that must not allocate device memory while they plan -- a real-time control
+ * thread that cannot block in an allocator, an application whose framework
+ * owns all device memory through its own pool or budget, or code running
+ * while another component captures the stream into a CUDA graph.
+ *
+ * prrtc_plan_noalloc solves one problem like prrtc_plan but keeps the trees,
+ * the planner state and the path in one fixed, file-scope device array of
+ * about 0.8 MiB, resident on every GPU that loads the library until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Robot and env handles are created beforehand with the usual
+ * calls (those do allocate).
+ *   params->tree_capacity and params->path_capacity must be <=
+ *   PRRTC_NOALLOC_MAX_ROWS, else PRRTC_ERR_INVALID_ARG (nothing runs).
+ *   path_out: host buffer of path_rows * dof floats owned by the caller; a
+ *   path longer than path_rows is reported as PRRTC_PATH_OVERFLOW.
+ *   info_out: host struct filled like prrtc_plan's path; its q points at
+ *   path_out (nothing to free).  prrtc_last_error() is not updated.
+ *   stream: cudaStream_t the kernels run on (0 = legacy default stream); the
+ *   call returns after the stream has completed them.
+ * The first call on a device resolves the array's address and marks every
+ * tree row unwritten; make that first call before any stream capture.  Every
+ * call shares the one array and leaves its contents for the next; calls that
+ * overlap on the GPU (other threads or streams) race on it and must be
+ * serialised by the caller. */
+#define PRRTC_NOALLOC_MAX_ROWS 4096
+int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env, const float* q_start,
+                       const float* q_goal, const prrtc_params* params, float* path_out,
+                       int32_t path_rows, prrtc_path* info_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -543,6 +543,18 @@ int prrtc_robot_info(const prrtc_robot* robot, int32_t* dof, int32_t* n_spheres,
   return PRRTC_OK;
 }
 
+// Device-side views of two handles, for entry points compiled in other files
+// (not part of the public header).  Allocates nothing.
+int prrtc_internal_views(const prrtc_robot* robot, const prrtc_env* env, const void** robot_dev,
+                         const void** robot_header, EnvView* env_view, int* device) {
+  if (!robot || !env || !robot->h || robot->device != env->device) return PRRTC_ERR_INVALID_ARG;
+  *robot_dev = robot->d;
+  *robot_header = &robot->h->h;
+  *env_view = env->view();
+  *device = robot->device;
+  return PRRTC_OK;
+}
+
 int prrtc_env_info(const prrtc_env* env, int32_t* counts4) {
   if (!env || !counts4) return fail(PRRTC_ERR_INVALID_ARG, "null argument");
   counts4[0] = env->n_aabb;

@@ -74,6 +74,7 @@ EXPORTS = [
     "prrtc_version", "prrtc_last_error", "prrtc_env_create", "prrtc_env_update", "prrtc_env_destroy",
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
     "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
+    "prrtc_plan_noalloc",
 ]
 
 _lib = None
@@ -113,6 +114,8 @@ def lib():
     L.prrtc_params_default.argtypes = [C.POINTER(prrtc_params)]
     L.prrtc_last_launch_stats.argtypes = [C.POINTER(prrtc_launch_stats)]
     L.prrtc_debug_tree.argtypes = [C.c_int32, C.c_int32, _f, _i, C.c_int32, _i]
+    L.prrtc_plan_noalloc.argtypes = [C.c_void_p, C.c_void_p, _f, _f, C.POINTER(prrtc_params), _f, C.c_int32,
+                                     C.POINTER(prrtc_path), C.c_void_p]
     _lib = L
     return L
 
@@ -360,3 +363,22 @@ def prrtc_debug_tree(problem: int, tree: int, dof: int):
     _check(lib().prrtc_debug_tree(problem, tree, nodes.ctypes.data_as(_f), par.ctypes.data_as(_i), m, C.byref(n)),
            "prrtc_debug_tree")
     return nodes[:m], par[:m]
+
+
+def prrtc_plan_noalloc(robot: Robot, env: Env, q_start, q_goal, prm: prrtc_params | None = None, path_rows: int = 4096,
+                       stream: int = 0):
+    """Plan one problem without any device allocation (fixed static scratch).
+
+    The caller owns the host path buffer; returns the same dict as prrtc_plan.
+    Raises PrrtcError with the C status code on failure."""
+    prm = prm or prrtc_params_default()
+    s, sp = _fa(q_start)
+    g, gp = _fa(q_goal)
+    buf = np.zeros((max(path_rows, 1), robot.dof), np.float32)
+    info = prrtc_path()
+    rc = lib().prrtc_plan_noalloc(robot.handle, env.handle, sp, gp, C.byref(prm), buf.ctypes.data_as(_f), path_rows,
+                                  C.byref(info), C.c_void_p(stream or None))
+    if rc != OK:
+        raise PrrtcError(rc, "prrtc_plan_noalloc")
+    d = _path_dict(info)  # copies the rows out of buf
+    return d
