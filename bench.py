@@ -47,6 +47,28 @@ WORKLOAD = "shelf-200: 200 cubby-shelf problems, 7-DoF arm (28 spheres), 50 obst
 OPS = dict(centre=9, aabb=13, obb=22, cyl=24, sph=9, pair=7, joint=17)
 
 
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ["prrtc_device.cuh", "prrtc_launch.h", "prrtc_plan.cu"]:
+        h.update(f.encode())
+        with open(os.path.join(ROOT, "paper_2503_06757_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(problems):
+    """DRAM bytes per planner launch from the committed ncu summary, scaled by
+    problems, or None when the kernel source changed since the capture."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "plan_kernel_shelf64_full.md")).read()
+        src = text.split("kernel_source:")[1].split()[0]
+        per = float(text.split("dram_bytes_per_problem:")[1].split()[0])
+    except Exception:
+        return None
+    return per * problems if src == kernel_source_hash() else None
+
+
 def percentiles(v, ps=(50, 95, 99)):
     if not len(v):
         return {f"p{p}": None for p in ps}
@@ -371,7 +393,7 @@ def run_ours(args):
         ttfs_us=dict(percentiles(ttfs), note="device time from launch start to each problem's solution"),
         success_rate=solved / (len(items) * args.steps), mean_cost=float(np.mean(costs)) if costs else None,
         roofline=dict(bound="alu", achieved=achieved_gops, peak=peak_gops, unit="Gop/s",
-                      frac=achieved_gops / peak_gops, traffic=None,
+                      frac=achieved_gops / peak_gops, traffic=profiled_traffic(args.problems),
                       note="planner kernel: counted FP32/ALU instructions of FK, collision tests and NN scans "
                            "per launch / kernel time; peak = SMs x 128 lanes x max SM clock (issue bound)"),
         e2e=dict(value=total_states / wall_s, unit=UNIT, h2d_bytes_per_step=h2d // args.steps,

@@ -13,7 +13,8 @@ namespace {
 
 constexpr int kCheckWarps = 4;
 
-template <int DP>
+constexpr int kQStageFloats = kMaxDof * 32;  // per warp: [joint][lane]
+
 __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const RobotDev* __restrict__ robot, EnvView env,
                                                                         const float* __restrict__ q, int n,
                                                                         uint8_t* __restrict__ valid,
@@ -22,13 +23,14 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
                                                                         int* __restrict__ error, int np_pad) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_ok;
   const int robot_bytes = robot_smem_bytes(np_pad);
   RobotHeader* R = reinterpret_cast<RobotHeader*>(smem);
   uint32_t* pair = reinterpret_cast<uint32_t*>(smem + sizeof(RobotHeader));
   float* thr = reinterpret_cast<float*>(pair + np_pad);
   const int env_f4 = env.n_float4();
   float4* senv = reinterpret_cast<float4*>(smem + robot_bytes);
-  float* stage_all = reinterpret_cast<float*>(smem + robot_bytes + env_f4 * 16);
+  float* warp_all = reinterpret_cast<float*>(smem + robot_bytes + env_f4 * 16);
 
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -40,9 +42,6 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
       bulk_g2s(thr, robot->thr, 4u * np_pad, &bar);
     }
     if (env_f4) bulk_g2s(senv, env.data, 16u * env_f4, &bar);
-  }
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
     s_ok = mbar_wait(&bar, 0, 1u << 26) ? 1 : 0;
     if (!s_ok) atomicExch(error, PRRTC_ERR_TIMEOUT);
   }
@@ -52,19 +51,19 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int dof = R->dof;
   const int n_raw = R->n_raw;
-  float* stage = stage_all + warp * R->n_spheres * 96;
+  float* qst = warp_all + warp * (kQStageFloats + R->n_spheres * 96);
+  float* stage = qst + kQStageFloats;
   const int gw = blockIdx.x * kCheckWarps + warp;
   const int nw = gridDim.x * kCheckWarps;
   WorkCount wc;
+  const LaneQ qs{qst, lane};
   for (int base = gw * 32; base < n; base += nw * 32) {
     const int idx = base + lane;
     const bool active = idx < n;
     const size_t src = (size_t)(active ? idx : n - 1) * dof;
-    float qv[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) qv[j] = (j < dof) ? q[src + j] : 0.f;
-    const bool hit = state_collides<DP, false>(R, pair, thr, senv, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph, stage,
-                                               qv, active, lane, wc);
+    for (int j = 0; j < dof; ++j) qst[j * 32 + lane] = q[src + j];
+    const bool hit = state_collides<false>(R, pair, thr, senv, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph, stage,
+                                           qs, active, lane, wc);
     if (active) {
       valid[idx] = hit ? 0 : 1;
       if (spheres) {
@@ -92,25 +91,6 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
   }
 }
 
-template <int DP>
-cudaError_t launch_dp(const RobotDev* robot, int n_spheres, int np_pad, EnvView env, const float* q, int n,
-                      uint8_t* valid, float* spheres, unsigned long long* counters, int* error, cudaStream_t stream) {
-  const int smem = robot_smem_bytes(np_pad) + env.n_float4() * 16 + kCheckWarps * stage_bytes(n_spheres);
-  cudaError_t e = cudaFuncSetAttribute(check_states_kernel<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, check_states_kernel<DP>, kCheckWarps * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const long long want = ((long long)n + kCheckWarps * 32 - 1) / (kCheckWarps * 32);
-  const int grid = (int)(want < (long long)sms * per_sm ? (want > 0 ? want : 1) : (long long)sms * per_sm);
-  check_states_kernel<DP><<<grid, kCheckWarps * 32, smem, stream>>>(robot, env, q, n, valid, spheres, counters, error,
-                                                                    np_pad);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& h, EnvView env, const float* q, int n,
@@ -118,13 +98,21 @@ cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& h, Env
                                 cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int np_pad = (h.n_pairs + 3) & ~3;
-  switch (h.dpad) {
-    case 4: return launch_dp<4>(robot, h.n_spheres, np_pad, env, q, n, valid, spheres, counters, error, stream);
-    case 8: return launch_dp<8>(robot, h.n_spheres, np_pad, env, q, n, valid, spheres, counters, error, stream);
-    case 12: return launch_dp<12>(robot, h.n_spheres, np_pad, env, q, n, valid, spheres, counters, error, stream);
-    case 16: return launch_dp<16>(robot, h.n_spheres, np_pad, env, q, n, valid, spheres, counters, error, stream);
-    default: return cudaErrorInvalidValue;
-  }
+  const int smem = robot_smem_bytes(np_pad) + env.n_float4() * 16 +
+                   kCheckWarps * (kQStageFloats * (int)sizeof(float) + stage_bytes(h.n_spheres));
+  cudaError_t e = cudaFuncSetAttribute(check_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, check_states_kernel, kCheckWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long want = ((long long)n + kCheckWarps * 32 - 1) / (kCheckWarps * 32);
+  const int grid = (int)(want < (long long)sms * per_sm ? (want > 0 ? want : 1) : (long long)sms * per_sm);
+  check_states_kernel<<<grid, kCheckWarps * 32, smem, stream>>>(robot, env, q, n, valid, spheres, counters, error,
+                                                               np_pad);
+  return cudaGetLastError();
 }
 
 }  // namespace prrtc

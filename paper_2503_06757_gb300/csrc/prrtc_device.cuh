@@ -28,7 +28,7 @@ enum JointType : int { kRevZ = 0, kRevY = 1, kPrismZ = 2, kPrismX = 3, kPrismY =
 // meets each frame's spheres right after placing the frame.
 struct RobotHeader {
   int dof;
-  int dpad;            // tree row stride in floats: dof + 1 rounded up to 4 (>= 4)
+  int dpad;            // tree row stride in floats: dof rounded up to a multiple of 4
   int n_spheres;       // distinct spheres
   int n_pairs;         // distinct self-collision pairs
   int n_raw;           // spheres as given
@@ -140,16 +140,34 @@ __device__ __forceinline__ bool sphere_hits_env(float cx, float cy, float cz, fl
 }
 
 // ------------------------------------------------------------------ FK + CC
+// Joint-value sources for state_collides: lane-private values staged in
+// shared memory ([joint][lane]) or a point on a warp-uniform edge a -> b
+// (both held in shared memory) at parameter t, exactly b at the endpoint.
+struct LaneQ {
+  const float* q;  // [kMaxDof][32]
+  int lane;
+  __device__ __forceinline__ float operator()(int i) const { return q[i * 32 + lane]; }
+};
+
+struct EdgeQ {
+  const float* a;
+  const float* b;
+  float t;
+  bool end;
+  __device__ __forceinline__ float operator()(int i) const { return end ? b[i] : fmaf(t, b[i] - a[i], a[i]); }
+};
+
 // Collision test of one configuration per lane.  `stage` is this warp's
 // [n_spheres][3][32] shared-memory buffer of sphere centres.  With kWarpVote
 // the whole warp returns true as soon as any active lane collides (the edge
 // verdict), otherwise each lane returns its own verdict and the warp runs to
-// completion.  q holds DP joint values (entries >= dof unused).
-template <int DP, bool kWarpVote>
+// completion.  The joint loop is a runtime loop so that the obstacle loops
+// exist once in the code.
+template <bool kWarpVote, class QS>
 __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R, const uint32_t* __restrict__ pair,
                                                const float* __restrict__ thr, const float4* __restrict__ env,
                                                int n_aabb, int n_obb, int n_cyl, int n_sph, float* __restrict__ stage,
-                                               const float (&q)[DP], bool active, int lane, WorkCount& wc) {
+                                               const QS& qs, bool active, int lane, WorkCount& wc) {
   const int dof = R->dof;
   float ax = 1.f, ay = 0.f, az = 0.f;  // rotation column 0 (local x in world)
   float bx = 0.f, by = 1.f, bz = 0.f;  // column 1
@@ -157,9 +175,8 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
   float px = 0.f, py = 0.f, pz = 0.f;
   bool hit = false;
   wc.fk_states += active;
-#pragma unroll
-  for (int i = 0; i < DP; ++i) {
-    if (i >= dof) break;
+#pragma unroll 1
+  for (int i = 0; i < dof; ++i) {
     if (R->jparent[i] < 0) {
       ax = 1.f; ay = 0.f; az = 0.f;
       bx = 0.f; by = 1.f; bz = 0.f;
@@ -168,7 +185,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       px = b.x; py = b.y; pz = b.z;
     }
     const int ty = R->jtype[i];
-    const float qi = q[i];
+    const float qi = qs(i);
     if (ty == kRevZ || ty == kRevY || ty == kRevX) {
       float s, c;
       sincosf(qi, &s, &c);

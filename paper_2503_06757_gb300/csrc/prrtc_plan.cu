@@ -45,6 +45,14 @@ struct Local {
   WorkCount wc;
 };
 
+// Warp-uniform vectors of one worker, in shared memory; lane j owns element j.
+struct WarpVecs {
+  float* rnd;   // sample c_rand
+  float* a;     // edge start
+  float* b;     // edge end
+};
+constexpr int kWarpVecFloats = 3 * kMaxDof;
+
 struct Ctx {
   const PlanGlobals* g;
   const ProblemDesc* D;
@@ -54,48 +62,68 @@ struct Ctx {
   const float* thr;
   const float4* env;
   float* stage;
+  WarpVecs v;
   int lane;
 };
 
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
+  return x;
+}
+
+// Element `lane` of row `idx` (0 for lanes past the row width).
+__device__ __forceinline__ float row_elem(const float* __restrict__ nodes, int idx, int dpad, int lane) {
+  return lane < dpad ? __ldcg(nodes + (size_t)idx * dpad + lane) : 0.f;
+}
+
 // NEAREST_NEIGHBOR (Sec. III-C): each lane scans a strided slice of the
 // tree, then a butterfly reduction over the warp; ties go to the lowest index.
-template <int DP>
-__device__ __forceinline__ int nearest(const float* __restrict__ nodes, int n, const float (&q)[DP], int lane,
-                                       Local& lc) {
+// Rows are dpad floats (4, 8, 12 or 16) read as float4 from L2.
+__device__ __noinline__ int nearest(const float* __restrict__ nodes, int n, int dpad, const float* __restrict__ qv,
+                                    int lane, unsigned long long* nn_nodes) {
+  float q[kMaxDof];
+#pragma unroll
+  for (int j = 0; j < kMaxDof; ++j) q[j] = (j < dpad) ? qv[j] : 0.f;
+  const int nq = dpad >> 2;
   float best = FLT_MAX;
   int bi = INT_MAX;
   int i = lane;
   for (; i + 32 < n; i += 64) {
-    const float4* r0 = reinterpret_cast<const float4*>(nodes + (size_t)i * DP);
-    const float4* r1 = reinterpret_cast<const float4*>(nodes + (size_t)(i + 32) * DP);
+    const float4* r0 = reinterpret_cast<const float4*>(nodes + (size_t)i * dpad);
+    const float4* r1 = reinterpret_cast<const float4*>(nodes + (size_t)(i + 32) * dpad);
     float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-    for (int k = 0; k < DP / 4; ++k) {
-      const float4 a = __ldcg(r0 + k), b = __ldcg(r1 + k);
-      float t;
-      t = q[4 * k + 0] - a.x; d0 = fmaf(t, t, d0);
-      t = q[4 * k + 1] - a.y; d0 = fmaf(t, t, d0);
-      t = q[4 * k + 2] - a.z; d0 = fmaf(t, t, d0);
-      t = q[4 * k + 3] - a.w; d0 = fmaf(t, t, d0);
-      t = q[4 * k + 0] - b.x; d1 = fmaf(t, t, d1);
-      t = q[4 * k + 1] - b.y; d1 = fmaf(t, t, d1);
-      t = q[4 * k + 2] - b.z; d1 = fmaf(t, t, d1);
-      t = q[4 * k + 3] - b.w; d1 = fmaf(t, t, d1);
+    for (int k = 0; k < kMaxDof / 4; ++k) {
+      if (k < nq) {
+        const float4 a = __ldcg(r0 + k), b = __ldcg(r1 + k);
+        float t;
+        t = q[4 * k + 0] - a.x; d0 = fmaf(t, t, d0);
+        t = q[4 * k + 1] - a.y; d0 = fmaf(t, t, d0);
+        t = q[4 * k + 2] - a.z; d0 = fmaf(t, t, d0);
+        t = q[4 * k + 3] - a.w; d0 = fmaf(t, t, d0);
+        t = q[4 * k + 0] - b.x; d1 = fmaf(t, t, d1);
+        t = q[4 * k + 1] - b.y; d1 = fmaf(t, t, d1);
+        t = q[4 * k + 2] - b.z; d1 = fmaf(t, t, d1);
+        t = q[4 * k + 3] - b.w; d1 = fmaf(t, t, d1);
+      }
     }
     if (d0 < best) { best = d0; bi = i; }
     if (d1 < best) { best = d1; bi = i + 32; }
   }
   if (i < n) {
-    const float4* r0 = reinterpret_cast<const float4*>(nodes + (size_t)i * DP);
+    const float4* r0 = reinterpret_cast<const float4*>(nodes + (size_t)i * dpad);
     float d0 = 0.f;
 #pragma unroll
-    for (int k = 0; k < DP / 4; ++k) {
-      const float4 a = __ldcg(r0 + k);
-      float t;
-      t = q[4 * k + 0] - a.x; d0 = fmaf(t, t, d0);
-      t = q[4 * k + 1] - a.y; d0 = fmaf(t, t, d0);
-      t = q[4 * k + 2] - a.z; d0 = fmaf(t, t, d0);
-      t = q[4 * k + 3] - a.w; d0 = fmaf(t, t, d0);
+    for (int k = 0; k < kMaxDof / 4; ++k) {
+      if (k < nq) {
+        const float4 a = __ldcg(r0 + k);
+        float t;
+        t = q[4 * k + 0] - a.x; d0 = fmaf(t, t, d0);
+        t = q[4 * k + 1] - a.y; d0 = fmaf(t, t, d0);
+        t = q[4 * k + 2] - a.z; d0 = fmaf(t, t, d0);
+        t = q[4 * k + 3] - a.w; d0 = fmaf(t, t, d0);
+      }
     }
     if (d0 < best) { best = d0; bi = i; }
   }
@@ -108,27 +136,14 @@ __device__ __forceinline__ int nearest(const float* __restrict__ nodes, int n, c
       bi = oi;
     }
   }
-  if (lane == 0) lc.nn_nodes += (unsigned long long)n;
+  if (lane == 0) *nn_nodes += (unsigned long long)n;
   return bi;
 }
 
-template <int DP>
-__device__ __forceinline__ void load_row(const float* __restrict__ nodes, int idx, float (&v)[DP]) {
-  const float4* r = reinterpret_cast<const float4*>(nodes + (size_t)idx * DP);
-#pragma unroll
-  for (int k = 0; k < DP / 4; ++k) {
-    const float4 a = __ldcg(r + k);
-    v[4 * k + 0] = a.x;
-    v[4 * k + 1] = a.y;
-    v[4 * k + 2] = a.z;
-    v[4 * k + 3] = a.w;
-  }
-}
-
-// Alg. 2 lines 3-5: the N states a + (k/N)(b - a), k = 1..N, one per lane
-// (several passes if N > 32); false at the first colliding state.
-template <int DP>
-__device__ __forceinline__ bool edge_free(const Ctx& c, const float (&a)[DP], const float (&b)[DP], int N, Local& lc) {
+// Alg. 2 lines 3-5: the N states a + (k/N)(b - a), k = 1..N, of the edge held
+// in c.v.a / c.v.b, one per lane (several passes if N > 32); false at the
+// first colliding state.
+__device__ __forceinline__ bool edge_free(const Ctx& c, int N, Local& lc) {
   lc.edges++;
   lc.edge_states += (unsigned long long)N;
   const float fN = (float)N;
@@ -136,20 +151,17 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, const float (&a)[DP], co
     const int k = base + c.lane + 1;
     const bool active = k <= N;
     const int kk = active ? k : N;
-    const float t = __fdiv_rn((float)kk, fN);
-    float q[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) q[j] = (kk == N) ? b[j] : fmaf(t, b[j] - a[j], a[j]);
-    if (state_collides<DP, true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
-                                 c.D->env.n_sph, c.stage, q, active, c.lane, lc.wc))
+    const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N};
+    if (state_collides<true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
+                             c.D->env.n_sph, c.stage, qs, active, c.lane, lc.wc))
       return false;
   }
   return true;
 }
 
-// Append a row to tree t; returns its index or -1 when the tree is full.
-template <int DP>
-__device__ __forceinline__ int insert(const Ctx& c, int t, const float (&q)[DP], int parent, Local& lc) {
+// Append the row held by lane j's `val` (element j) to tree t; returns its
+// index or -1 when the tree is full.
+__device__ __forceinline__ int insert(const Ctx& c, int t, float val, int parent, Local& lc) {
   int idx = 0;
   if (c.lane == 0) idx = atomicAdd(&c.S->count[t], 1);
   idx = __shfl_sync(kFull, idx, 0);
@@ -162,11 +174,7 @@ __device__ __forceinline__ int insert(const Ctx& c, int t, const float (&q)[DP],
     __threadfence();
   }
   __syncwarp();
-  float v = 0.f;
-#pragma unroll
-  for (int j = 0; j < DP; ++j)
-    if (c.lane == j) v = q[j];
-  if (c.lane < DP) __stcg(c.D->nodes[t] + (size_t)idx * DP + c.lane, v);
+  if (c.lane < c.D->dpad) __stcg(c.D->nodes[t] + (size_t)idx * c.D->dpad + c.lane, val);
   __syncwarp();
   return idx;
 }
@@ -182,7 +190,6 @@ __device__ __forceinline__ int parent_of(const int* par, int node, int* err) {
 // PATH(T_a, T_b) by the winning warp: root(T_a) .. join .. root(T_b).  The two
 // join rows hold the same configuration; the copy in T_b is dropped when T_a
 // was extended and vice versa, so the path lists each waypoint once.
-template <int DP>
 __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   const ProblemDesc* D = c.D;
   const int o = 1 - s;
@@ -206,38 +213,31 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
     return;
   }
   // the T_a-side chain (root first) then the T_b-side chain without its join row
-  const int a_tree = 0;
   const int a_join = (s == 0) ? js : jo;
   const int b_join = (s == 0) ? jo : js;
   const int na = (s == 0) ? ns : no;
   if (c.lane == 0) {
     // both walks are bounded by the chain lengths counted above
     int pos = na - 1;
-    for (int x = a_join; x >= 0 && pos >= 0; x = parent_of(D->parent[a_tree], x, &err)) D->path_idx[pos--] = x;
+    for (int x = a_join; x >= 0 && pos >= 0; x = parent_of(D->parent[0], x, &err)) D->path_idx[pos--] = x;
     pos = na;
     for (int x = parent_of(D->parent[1], b_join, &err); x >= 0 && pos < K; x = parent_of(D->parent[1], x, &err))
       D->path_idx[pos++] = (1 << 30) | x;
     __threadfence_block();
   }
   __syncwarp();
-  const int dof = D->dof;
+  const int dof = D->dof, dpad = D->dpad;
   double seg = 0.0;
   for (int r = c.lane; r < K; r += 32) {
     const int code = D->path_idx[r];
-    const int t = code >> 30, x = code & ((1 << 30) - 1);
-    float v[DP];
-    load_row<DP>(D->nodes[t], x, v);
-#pragma unroll
-    for (int j = 0; j < DP; ++j)
-      if (j < dof) D->path[(size_t)r * dof + j] = v[j];
+    const float* row = D->nodes[code >> 30] + (size_t)(code & ((1 << 30) - 1)) * dpad;
+    for (int j = 0; j < dof; ++j) D->path[(size_t)r * dof + j] = __ldcg(row + j);
     if (r > 0) {
       const int pc = D->path_idx[r - 1];
-      float w[DP];
-      load_row<DP>(D->nodes[pc >> 30], pc & ((1 << 30) - 1), w);
+      const float* prow = D->nodes[pc >> 30] + (size_t)(pc & ((1 << 30) - 1)) * dpad;
       double s2 = 0.0;
-#pragma unroll
-      for (int j = 0; j < DP; ++j) {
-        const double d = (double)v[j] - (double)w[j];
+      for (int j = 0; j < dof; ++j) {
+        const double d = (double)__ldcg(row + j) - (double)__ldcg(prow + j);
         s2 += d * d;
       }
       seg += sqrt(s2);
@@ -252,20 +252,20 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
 }
 
 // Alg. 1 iterations of one worker warp on one problem until it is solved,
-// out of budget or out of time.
-template <int DP>
+// out of budget or out of time.  Lane j holds element j of every vector.
 __device__ void worker(const Ctx& c, Local& lc) {
   const PlanGlobals* g = c.g;
   const ProblemDesc* D = c.D;
   ProblemState* S = c.S;
   const RobotHeader* R = c.R;
   const int lane = c.lane;
-  const int dof = D->dof;
+  const int dof = D->dof, dpad = D->dpad;
   const int cap = D->cap;
   const float range = g->range;
   const float res = g->resolution;
   const int n_full = g->n_full;
   const uint2 key = make_uint2(D->key_lo, D->key_hi);
+  const bool mine = lane < dpad;
   for (;;) {
     int stop = 0, it = 0;
     if (lane == 0) {
@@ -304,98 +304,84 @@ __device__ void worker(const Ctx& c, Local& lc) {
       w = (k == 0) ? r.x : (k == 1) ? r.y : (k == 2) ? r.z : r.w;
     }
     const uint32_t w0 = __shfl_sync(kFull, w, 0);
-    float crand[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) {
-      const uint32_t wj = __shfl_sync(kFull, w, j + 1);
-      crand[j] = (j < dof) ? fmaf(u24(wj), R->span[j], R->lo[j]) : 0.f;
-    }
-    if ((w0 >> 8) < g->bias_thr) load_row<DP>(D->nodes[o], 0, crand);  // goal bias: root of T_o
+    const uint32_t wj = __shfl_sync(kFull, w, (lane + 1) & 31);
+    float crand = (lane < dof) ? fmaf(u24(wj), R->span[lane], R->lo[lane]) : 0.f;
+    if ((w0 >> 8) < g->bias_thr) crand = row_elem(D->nodes[o], 0, dpad, lane);  // goal bias: root of T_o
+    if (mine) c.v.rnd[lane] = crand;
+    __syncwarp();
 
     // line 5: nearest node of T_s.
-    const int nn = nearest<DP>(D->nodes[s], n_s, crand, lane, lc);
-    float cnn[DP];
-    load_row<DP>(D->nodes[s], nn, cnn);
+    const int nn = nearest(D->nodes[s], n_s, dpad, c.v.rnd, lane, &lc.nn_nodes);
+    const float cnn = row_elem(D->nodes[s], nn, dpad, lane);
 
-    // Alg. 2: steer from c_nn toward c_rand by at most delta, check the edge.
-    float d2 = 0.f;
-#pragma unroll
-    for (int j = 0; j < DP; ++j) {
-      const float t = crand[j] - cnn[j];
-      d2 = fmaf(t, t, d2);
-    }
+    // Alg. 2: steer from c_nn toward c_rand by at most delta.
+    const float diff = crand - cnn;
+    const float d2 = warp_sum(diff * diff);
     if (!(d2 > 0.f)) continue;
     const float dist = __fsqrt_rn(d2);
-    float cnew[DP];
+    float cnew;
     int N;
     if (dist > range) {
-      const float f = __fdiv_rn(range, dist);
-#pragma unroll
-      for (int j = 0; j < DP; ++j) cnew[j] = fmaf(crand[j] - cnn[j], f, cnn[j]);
+      cnew = fmaf(diff, __fdiv_rn(range, dist), cnn);
       N = n_full;
     } else {
-#pragma unroll
-      for (int j = 0; j < DP; ++j) cnew[j] = crand[j];
+      cnew = crand;
       N = (int)ceilf(__fdiv_rn(dist, res));
     }
     if (N < 1) N = 1;
-    if (!edge_free<DP>(c, cnn, cnew, N, lc)) continue;
-
-    // line 7: add c_new to T_s.
-    const int idx = insert<DP>(c, s, cnew, nn, lc);
-    if (idx < 0) continue;
-
-    // line 8: nearest node of T_o to c_new; lines 9-15: greedy connect.
-    const int n_o = min(ld_relaxed(&S->count[o]), cap);
-    const int nno = nearest<DP>(D->nodes[o], n_o, cnew, lane, lc);
-    float ct[DP];
-    load_row<DP>(D->nodes[o], nno, ct);
-    float D2 = 0.f;
-#pragma unroll
-    for (int j = 0; j < DP; ++j) {
-      const float t = ct[j] - cnew[j];
-      D2 = fmaf(t, t, D2);
+    if (mine) {
+      c.v.a[lane] = cnn;
+      c.v.b[lane] = cnew;
     }
-    const float Dd = __fsqrt_rn(D2);
-    const int n_ext = (Dd > 0.f) ? (int)ceilf(__fdiv_rn(Dd, range)) : 0;
-    int prev = idx;
-    float prevq[DP];
-#pragma unroll
-    for (int j = 0; j < DP; ++j) prevq[j] = cnew[j];
-    bool connected = true;
-    for (int i = 1; i <= n_ext; ++i) {
-      int solved = 0;
-      if (lane == 0) solved = ld_volatile(&S->solved);
-      if (__shfl_sync(kFull, solved, 0)) {
-        connected = false;
+    __syncwarp();
+
+    // Phase 0 checks and adds c_new (Alg. 1 lines 5-7); phase i >= 1 is the
+    // i-th greedy connect step toward c_nno (lines 9-15).  One edge check
+    // site serves both.
+    int prev = nn;        // row the current edge starts from (tree s)
+    int nno = -1, n_ext = 0;
+    float ct = 0.f, Dd = 0.f;
+    float bval = cnew;    // element `lane` of the edge end
+    bool connected = false;
+    for (int phase = 0;; ++phase) {
+      if (phase > 0) {
+        int solved = 0;
+        if (lane == 0) solved = ld_volatile(&S->solved);
+        if (__shfl_sync(kFull, solved, 0)) break;
+      }
+      if (!edge_free(c, N, lc)) break;
+      const int added = insert(c, s, bval, prev, lc);
+      if (added < 0) break;
+      prev = added;
+      if (phase == 0) {
+        // line 8: nearest node of T_o to c_new, and the connect length.
+        const int n_o = min(ld_relaxed(&S->count[o]), cap);
+        nno = nearest(D->nodes[o], n_o, dpad, c.v.b, lane, &lc.nn_nodes);
+        ct = row_elem(D->nodes[o], nno, dpad, lane);
+        const float dd = ct - cnew;
+        Dd = __fsqrt_rn(warp_sum(dd * dd));
+        n_ext = (Dd > 0.f) ? (int)ceilf(__fdiv_rn(Dd, range)) : 0;
+      }
+      if (phase == n_ext) {
+        connected = true;
         break;
       }
-      float ext[DP];
-      int Ni;
+      // next connect step: from the row just added toward c_new + (i delta / D)(c_nno - c_new)
+      const int i = phase + 1;
       if (i < n_ext) {
-        const float f = __fdiv_rn((float)i * range, Dd);
-#pragma unroll
-        for (int j = 0; j < DP; ++j) ext[j] = fmaf(f, ct[j] - cnew[j], cnew[j]);
-        Ni = n_full;
+        bval = fmaf(__fdiv_rn((float)i * range, Dd), ct - cnew, cnew);
+        N = n_full;
       } else {
-#pragma unroll
-        for (int j = 0; j < DP; ++j) ext[j] = ct[j];
+        bval = ct;
         const float len = Dd - (float)(n_ext - 1) * range;
-        Ni = (int)ceilf(__fdiv_rn(len, res));
-        if (Ni < 1) Ni = 1;
+        N = (int)ceilf(__fdiv_rn(len, res));
+        if (N < 1) N = 1;
       }
-      if (!edge_free<DP>(c, prevq, ext, Ni, lc)) {
-        connected = false;
-        break;
+      if (mine) {
+        c.v.a[lane] = c.v.b[lane];
+        c.v.b[lane] = bval;
       }
-      const int a = insert<DP>(c, s, ext, prev, lc);
-      if (a < 0) {
-        connected = false;
-        break;
-      }
-      prev = a;
-#pragma unroll
-      for (int j = 0; j < DP; ++j) prevq[j] = ext[j];
+      __syncwarp();
     }
     if (!connected) continue;
 
@@ -410,7 +396,7 @@ __device__ void worker(const Ctx& c, Local& lc) {
         S->join_s = prev;
         S->join_o = nno;
       }
-      extract_path<DP>(c, s, prev, nno);
+      extract_path(c, s, prev, nno);
       __threadfence();
       if (lane == 0) atomicExch(&S->done, 1);
     }
@@ -430,7 +416,7 @@ __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
 }
 
 __global__ void plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
-                            ProblemState* __restrict__ states, int robot_bytes, int env_bytes, int stage_bytes_warp) {
+                            ProblemState* __restrict__ states, int robot_bytes, int env_bytes, int warp_floats) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_prob;
@@ -493,14 +479,13 @@ __global__ void plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __re
     c.pair = pair;
     c.thr = thr;
     c.env = senv;
-    c.stage = reinterpret_cast<float*>(smem + robot_bytes + env_bytes) + warp * (stage_bytes_warp / 4);
+    float* warp_area = reinterpret_cast<float*>(smem + robot_bytes + env_bytes) + warp * (warp_floats);
+    c.v.rnd = warp_area;
+    c.v.a = warp_area + kMaxDof;
+    c.v.b = warp_area + 2 * kMaxDof;
+    c.stage = warp_area + kWarpVecFloats;
     c.lane = lane;
-    switch (D->dpad) {
-      case 4: worker<4>(c, lc); break;
-      case 8: worker<8>(c, lc); break;
-      case 12: worker<12>(c, lc); break;
-      default: worker<16>(c, lc); break;
-    }
+    worker(c, lc);
     // flush this warp's counters into the problem
     unsigned long long v[8] = {lc.edges, lc.edge_states, lc.wc.sphere_tests, lc.wc.pair_tests,
                                lc.wc.fk_states, lc.nn_nodes, lc.iterations, lc.insert_fail};
@@ -527,16 +512,20 @@ __global__ void plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __re
 // One block per problem: clear the rows the previous launch wrote (back to
 // NaN / unset parent), insert the roots, reset the counters, and reject a
 // start or goal in collision (Alg. 1 lines 1-2).
-template <int DP>
-__device__ void check_endpoints(const ProblemDesc* D, ProblemState* S, float* stage, const float4* env_global) {
+struct EndpointQ {
+  const float* start;
+  const float* goal;
+  int lane;
+  __device__ __forceinline__ float operator()(int i) const { return lane == 0 ? start[i] : goal[i]; }
+};
+
+__device__ void check_endpoints(const ProblemDesc* D, ProblemState* S, float* stage) {
   const int lane = threadIdx.x & 31;
   const RobotHeader* R = &D->robot->h;
-  float q[DP];
-#pragma unroll
-  for (int j = 0; j < DP; ++j) q[j] = (j < D->dof) ? (lane == 0 ? D->q_start[j] : D->q_goal[j]) : 0.f;
   WorkCount wc;
-  const bool hit = state_collides<DP, false>(R, D->robot->pair, D->robot->thr, env_global, D->env.n_aabb,
-                                             D->env.n_obb, D->env.n_cyl, D->env.n_sph, stage, q, lane < 2, lane, wc);
+  const EndpointQ qs{D->q_start, D->q_goal, lane};
+  const bool hit = state_collides<false>(R, D->robot->pair, D->robot->thr, D->env.data, D->env.n_aabb, D->env.n_obb,
+                                         D->env.n_cyl, D->env.n_sph, stage, qs, lane < 2, lane, wc);
   const unsigned m = __ballot_sync(kFull, hit);
   if (lane == 0) {
     if (m & 1u) S->pre_status = PRRTC_START_IN_COLLISION;
@@ -586,12 +575,7 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
     }
     __syncwarp();
     float* stage = reinterpret_cast<float*>(smem);
-    switch (dpad) {
-      case 4: check_endpoints<4>(D, S, stage, D->env.data); break;
-      case 8: check_endpoints<8>(D, S, stage, D->env.data); break;
-      case 12: check_endpoints<12>(D, S, stage, D->env.data); break;
-      default: check_endpoints<16>(D, S, stage, D->env.data); break;
-    }
+    check_endpoints(D, S, stage);
   }
 }
 
@@ -636,7 +620,7 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
   if (c.warps > 16) c.warps = 16;
   c.robot_bytes = robot_smem_bytes((max_pairs + 3) & ~3);
   c.env_bytes = max_env_f4 * 16;
-  c.stage_bytes = stage_bytes(max_spheres);
+  c.stage_bytes = stage_bytes(max_spheres) + kWarpVecFloats * (int)sizeof(float);  // per warp
   c.smem = c.robot_bytes + c.env_bytes + c.warps * c.stage_bytes;
   int per_sm = 0;
   cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
@@ -663,7 +647,8 @@ cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemSt
   cudaError_t e = cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg.smem);
   if (e != cudaSuccess) return e;
   plan_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
-                                                              cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes);
+                                                              cfg.robot_bytes, cfg.env_bytes,
+                                                              cfg.stage_bytes / (int)sizeof(float));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaSuccess;
