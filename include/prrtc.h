@@ -263,6 +263,20 @@ typedef struct prrtc_problem {
 int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params,
                      prrtc_path* out_paths, int32_t* out_status);
 
+/* ------------------------------------------------------------ learned proposal: dense layers */
+/* BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor memory)
+ * for the dense layers of the learned sampling proposal:
+ *   C[M, N] = A[M, K] * B[N, K]^T (+ bias[N]) (then ReLU if relu != 0).
+ * A and B are row-major BF16 device arrays (K contiguous, 16-byte aligned);
+ * c32 (FP32, row stride N) and/or c16 (BF16, row stride N) receive C; either
+ * may be null but not both.  K and N must be multiples of 8
+ * (PRRTC_ERR_UNSUPPORTED otherwise).  Enqueued on `stream`; no
+ * synchronisation.  prrtc_gemm_error() returns and clears the error word of
+ * the kernels (a bounded device wait that gave up: PRRTC_ERR_TIMEOUT). */
+int prrtc_gemm_bf16(const void* a, const void* b, int32_t M, int32_t N, int32_t K, const float* bias,
+                    int32_t relu, float* c32, void* c16, void* stream);
+int prrtc_gemm_error(void);
+
 /* ------------------------------------------------------------ planning without allocation */
 /* The paper has no counterpart of this entry point; it exists for callers
  * that must not allocate device memory while they plan -- a real-time control

@@ -74,7 +74,7 @@ EXPORTS = [
     "prrtc_version", "prrtc_last_error", "prrtc_env_create", "prrtc_env_update", "prrtc_env_destroy",
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
     "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
-    "prrtc_plan_noalloc",
+    "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_error",
 ]
 
 _lib = None
@@ -114,6 +114,8 @@ def lib():
     L.prrtc_params_default.argtypes = [C.POINTER(prrtc_params)]
     L.prrtc_last_launch_stats.argtypes = [C.POINTER(prrtc_launch_stats)]
     L.prrtc_debug_tree.argtypes = [C.c_int32, C.c_int32, _f, _i, C.c_int32, _i]
+    L.prrtc_gemm_bf16.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]
     L.prrtc_plan_noalloc.argtypes = [C.c_void_p, C.c_void_p, _f, _f, C.POINTER(prrtc_params), _f, C.c_int32,
                                      C.POINTER(prrtc_path), C.c_void_p]
     _lib = L
@@ -382,3 +384,15 @@ def prrtc_plan_noalloc(robot: Robot, env: Env, q_start, q_goal, prm: prrtc_param
         raise PrrtcError(rc, "prrtc_plan_noalloc")
     d = _path_dict(info)  # copies the rows out of buf
     return d
+
+
+def prrtc_gemm_bf16(a_ptr: int, b_ptr: int, M: int, N: int, K: int, bias_ptr: int = 0, relu: bool = False,
+                    c32_ptr: int = 0, c16_ptr: int = 0, stream: int = 0):
+    """C[M,N] = A[M,K] B[N,K]^T (+bias, ReLU) on the tensor cores; device pointers."""
+    _check(lib().prrtc_gemm_bf16(C.c_void_p(a_ptr), C.c_void_p(b_ptr), M, N, K, C.c_void_p(bias_ptr or None),
+                                 int(bool(relu)), C.c_void_p(c32_ptr or None), C.c_void_p(c16_ptr or None),
+                                 C.c_void_p(stream or None)), "prrtc_gemm_bf16")
+
+
+def prrtc_gemm_error() -> int:
+    return int(lib().prrtc_gemm_error())
