@@ -47,7 +47,7 @@ class OrcParams(C.Structure):
         ("range", C.c_double), ("resolution", C.c_double), ("goal_bias", C.c_double),
         ("amb_band", C.c_double), ("amb_rel", C.c_double), ("seed", C.c_uint64),
         ("problem", C.c_uint32), ("max_iters", C.c_int32), ("tree_capacity", C.c_int32),
-        ("path_capacity", C.c_int32),
+        ("path_capacity", C.c_int32), ("gmm", _PD), ("learned_ratio", C.c_double),
     ]
 
 
@@ -106,6 +106,7 @@ def lib():
         _lib.orc_plan.restype = C.c_int32
         _lib.orc_revalidate.restype = C.c_int32
         _lib.orc_sample.restype = C.c_int
+        _lib.orc_sample_learned.restype = C.c_int
     return _lib
 
 
@@ -179,6 +180,26 @@ def sample(robot, seed, problem, it, goal_bias):
     return bool(g), q
 
 
+def sample_learned(robot, seed, problem, it, goal_bias, gmm, learned_ratio, amb_rel=1e-5):
+    r = make_robot(robot)
+    q = np.zeros(robot.dof)
+    g = np.ascontiguousarray(gmm, dtype=np.float64)
+    amb = C.c_int()
+    kind = lib().orc_sample_learned(C.byref(r), C.c_uint64(seed), C.c_uint32(problem), C.c_uint32(it),
+                                    C.c_double(goal_bias), g.ctypes.data_as(_PD), C.c_double(learned_ratio),
+                                    C.c_double(amb_rel), q.ctypes.data_as(_PD), C.byref(amb))
+    return int(kind), q, bool(amb.value)
+
+
+def occupancy(scene, origin=(-0.8, -0.8, 0.0), cell=0.1, n=16, radius=0.05):
+    e = make_env(scene)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    out = np.zeros(n * n * n, dtype=np.uint8)
+    lib().orc_occupancy(C.byref(e), o.ctypes.data_as(_PD), C.c_double(cell), C.c_int32(n), C.c_double(radius),
+                        out.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return out
+
+
 def fk(robot, q):
     r = make_robot(robot)
     q, qp = _d(q)
@@ -239,16 +260,25 @@ def accept(robot, scene, Q):
 # ------------------------------------------------------------------ planner
 
 DEFAULT_PARAMS = dict(range=1.0, resolution=1.0 / 32.0, goal_bias=0.05, amb_band=1e-5, amb_rel=1e-5,
-                      seed=1, problem=0, max_iters=50000, tree_capacity=1 << 16, path_capacity=1 << 14)
+                      seed=1, problem=0, max_iters=50000, tree_capacity=1 << 16, path_capacity=1 << 14,
+                      gmm=None, learned_ratio=0.5)
 
 
-def _params(**kw):
+def _params(keep=None, **kw):
     p = dict(DEFAULT_PARAMS)
     p.update(kw)
-    return OrcParams(range=p["range"], resolution=p["resolution"], goal_bias=p["goal_bias"],
-                     amb_band=p["amb_band"], amb_rel=p["amb_rel"], seed=int(p["seed"]),
-                     problem=int(p["problem"]), max_iters=int(p["max_iters"]),
-                     tree_capacity=int(p["tree_capacity"]), path_capacity=int(p["path_capacity"]))
+    prm = OrcParams(range=p["range"], resolution=p["resolution"], goal_bias=p["goal_bias"],
+                    amb_band=p["amb_band"], amb_rel=p["amb_rel"], seed=int(p["seed"]),
+                    problem=int(p["problem"]), max_iters=int(p["max_iters"]),
+                    tree_capacity=int(p["tree_capacity"]), path_capacity=int(p["path_capacity"]))
+    g = p.get("gmm")
+    if g is not None:
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        if keep is not None:
+            keep.append(g)
+        prm.gmm = g.ctypes.data_as(_PD)
+        prm.learned_ratio = float(p.get("learned_ratio", 0.5))
+    return prm
 
 
 def _result_dict(res, d, trees=None, path=None):
@@ -271,7 +301,8 @@ def _result_dict(res, d, trees=None, path=None):
 
 def plan(robot, scene, q_start, q_goal, want_trees=False, **kw):
     r, e = make_robot(robot), make_env(scene)
-    prm = _params(**kw)
+    keep = []
+    prm = _params(keep, **kw)
     d = robot.dof
     res = OrcResult()
     path = np.zeros((prm.path_capacity, d))
@@ -311,7 +342,7 @@ def plan_batch(problems, threads=None, **kw):
         r, e = make_robot(pb.robot), make_env(pb.scene)
         s, sp = _d(pb.q_start)
         g, gp = _d(pb.q_goal)
-        prm = _params(**kw)
+        prm = _params(keep, **kw)
         prm.seed = int(seeds[k]) if seeds is not None else int(kw.get("seed", pb.seed))
         prm.problem = int(pids[k]) if pids is not None else int(kw.get("problem", 0))
         res = OrcResult()

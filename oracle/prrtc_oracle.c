@@ -9,6 +9,10 @@
  */
 #include "prrtc_oracle.h"
 
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
 #include <float.h>
 #include <math.h>
 #include <pthread.h>
@@ -73,6 +77,75 @@ int orc_sample(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it,
     q[j] = r->lower[j] + u * (r->upper[j] - r->lower[j]);
   }
   return 0;
+}
+
+/* Learned proposal draw (BASELINE's mixture proposal; not in the paper).
+ * Words 20.. of the iteration's stream (Philox blocks 5-9): word 20 decides
+ * learned vs uniform, word 21 picks the component, then Box-Muller pairs
+ * (u1 from (w >> 8) + 1, so u1 is in (0, 1]) give standard normals. */
+int orc_sample_learned(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it, double goal_bias,
+                       const double* gmm, double learned_ratio, double amb_rel, double* q, int* amb) {
+  const int d = r->dof;
+  const int K = 8;
+  if (amb) *amb = 0;
+  double u0 = unit24(sample_word(seed, problem, it, 0));
+  if (u0 < goal_bias) return 1;
+  if (gmm && unit24(sample_word(seed, problem, it, 20)) < learned_ratio) {
+    const double* logits = gmm;
+    const double* mean = gmm + K;
+    const double* logsig = gmm + K + K * d;
+    double mx = logits[0];
+    for (int k = 1; k < K; ++k) mx = fmax(mx, logits[k]);
+    double pk[8], tot = 0.0;
+    for (int k = 0; k < K; ++k) {
+      pk[k] = exp(logits[k] - mx);
+      tot += pk[k];
+    }
+    double uk = unit24(sample_word(seed, problem, it, 21));
+    int comp = K - 1;
+    double cum = 0.0;
+    for (int k = 0; k < K; ++k) {
+      cum += pk[k] / tot;
+      if (amb && fabs(uk - cum) <= amb_rel) *amb = 1;
+      if (uk < cum) {
+        comp = k;
+        break;
+      }
+    }
+    for (int j = 0; j < d; ++j) {
+      int m = j / 2;
+      uint32_t wa = sample_word(seed, problem, it, 22 + 2 * m);
+      uint32_t wb = sample_word(seed, problem, it, 23 + 2 * m);
+      double u1 = (double)((wa >> 8) + 1u) * (1.0 / 16777216.0);
+      double u2 = (double)(wb >> 8) * (1.0 / 16777216.0);
+      double rad = sqrt(-2.0 * log(u1));
+      double z = (j % 2 == 0) ? rad * cos(2.0 * M_PI * u2) : rad * sin(2.0 * M_PI * u2);
+      double ls = fmin(fmax(logsig[comp * d + j], -5.0), 2.0);
+      double un = mean[comp * d + j] + exp(ls) * z;
+      double v = r->lower[j] + 0.5 * (un + 1.0) * (r->upper[j] - r->lower[j]);
+      q[j] = fmin(fmax(v, r->lower[j]), r->upper[j]);
+    }
+    return 2;
+  }
+  for (int j = 0; j < d; ++j) {
+    double u = unit24(sample_word(seed, problem, it, j + 1));
+    q[j] = r->lower[j] + u * (r->upper[j] - r->lower[j]);
+  }
+  return 0;
+}
+
+void orc_occupancy(const orc_env* e, const double origin[3], double cell, int32_t n, double radius,
+                   uint8_t* out) {
+  for (int32_t k = 0; k < n; ++k)
+    for (int32_t j = 0; j < n; ++j)
+      for (int32_t i = 0; i < n; ++i) {
+        double p[3] = {origin[0] + (i + 0.5) * cell, origin[1] + (j + 0.5) * cell, origin[2] + (k + 0.5) * cell};
+        double best = DBL_MAX;
+        for (int o = 0; o < e->n_box; ++o) best = fmin(best, orc_sd_box(e->box + 15 * o, p));
+        for (int o = 0; o < e->n_cyl; ++o) best = fmin(best, orc_sd_cyl(e->cyl + 8 * o, p));
+        for (int o = 0; o < e->n_sph; ++o) best = fmin(best, orc_sd_sph(e->sph + 4 * o, p));
+        out[i + n * j + n * n * k] = (uint8_t)(best < radius);
+      }
 }
 
 /* ------------------------------------------------------- forward kinematics */
@@ -410,9 +483,13 @@ int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
     int s_is_a = (A.n <= B.n);
     tree* Ts = s_is_a ? &A : &B;
     tree* To = s_is_a ? &B : &A;
-    /* line 4: RANDOM_CONFIG, with goal bias toward the opposite root. */
-    if (orc_sample(r, p->seed, p->problem, (uint32_t)it, p->goal_bias, c_rand))
-      memcpy(c_rand, To->q, (size_t)d * sizeof(double));
+    /* line 4: RANDOM_CONFIG, with goal bias toward the opposite root (and the
+     * learned proposal when one is given). */
+    int amb_k = 0;
+    int kind = orc_sample_learned(r, p->seed, p->problem, (uint32_t)it, p->goal_bias, p->gmm,
+                                  p->gmm ? p->learned_ratio : 0.0, p->amb_rel, c_rand, &amb_k);
+    if (amb_k) note_amb(&ctx, ORC_AMB_COMPONENT);
+    if (kind == 1) memcpy(c_rand, To->q, (size_t)d * sizeof(double));
     /* line 5: NEAREST_NEIGHBOR in T_s. */
     int32_t nn = nearest(&ctx, Ts, c_rand);
     const double* c_nn = Ts->q + (size_t)nn * d;

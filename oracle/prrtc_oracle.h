@@ -23,6 +23,9 @@
  *   orc_sd_box/cyl/sph - brute-force surface/volume sampling on tiny inputs.
  *   orc_plan           - tree invariants, obstacle-free and walled-off special
  *                        cases, grid-BFS reachability of a point robot.
+ *   orc_occupancy      - closed-form voxel sets of a sphere and a box.
+ *   orc_sample_learned - the mixture statistics of its draws (component
+ *                        frequencies, per-component mean and spread).
  */
 #ifndef PRRTC_ORACLE_H
 #define PRRTC_ORACLE_H
@@ -50,7 +53,8 @@ enum {
   ORC_AMB_CLEARANCE = 1, /* a checked state had |clearance| <= band       */
   ORC_AMB_NN_TIE = 2,    /* best and second-best squared distances close  */
   ORC_AMB_CEIL = 3,      /* a ceil() argument lay next to an integer      */
-  ORC_AMB_STEER = 4      /* sample distance next to the range delta        */
+  ORC_AMB_STEER = 4,     /* sample distance next to the range delta        */
+  ORC_AMB_COMPONENT = 5  /* mixture component draw next to a boundary      */
 };
 
 typedef struct orc_robot {
@@ -89,6 +93,11 @@ typedef struct orc_params {
   int32_t max_iters;     /* global budget of Alg. 1 bodies                    */
   int32_t tree_capacity; /* nodes per tree; an insertion into a full tree fails */
   int32_t path_capacity; /* rows of the caller's path buffer                 */
+  /* learned proposal (nullable): mixture of 8 diagonal Gaussians over joint
+   * values normalised to [-1, 1]; layout logits[8], mean[8*dof],
+   * log_sigma[8*dof] (clamped to [-5, 2] when used) */
+  const double* gmm;
+  double learned_ratio;  /* probability of drawing from the mixture (after goal bias) */
 } orc_params;
 
 typedef struct orc_result {
@@ -120,6 +129,19 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * and writes a uniform configuration inside the joint limits to q. */
 int orc_sample(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it,
                double goal_bias, double* q);
+
+/* Sample with the learned proposal enabled: goal bias first (returns 1),
+ * then with probability learned_ratio a draw from the mixture (returns 2),
+ * else uniform (returns 0).  *amb is set when the component choice fell next
+ * to a cumulative-probability boundary. */
+int orc_sample_learned(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it, double goal_bias,
+                       const double* gmm, double learned_ratio, double amb_rel, double* q, int* amb);
+
+/* Occupancy grid of an environment: voxel (i, j, k), index i + n*j + n*n*k,
+ * centre origin + (index + 0.5) * cell per axis, is occupied iff its centre
+ * lies closer than `radius` to some obstacle (signed distance < radius). */
+void orc_occupancy(const orc_env* e, const double origin[3], double cell, int32_t n, double radius,
+                   uint8_t* out);
 
 /* Forward kinematics by 4x4 homogeneous products.  centres: [S*3];
  * frames (nullable): [dof*16] row-major world transforms. */

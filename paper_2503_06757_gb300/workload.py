@@ -555,3 +555,39 @@ def problem_set(kind: str, count: int, seed0: int, accept, n_obstacles=None):
             out.append(Problem(robot, scene, pair[0], pair[1], seed, f"{kind}-{seed}"))
         seed += 1
     return out
+
+
+# --------------------------------------------------------------------------- learned proposal inputs
+
+PROPOSAL_IN = 16 ** 3 + 2 * 32      # occupancy voxels + padded start + padded goal
+PROPOSAL_HIDDEN = (1024, 512, 512)
+PROPOSAL_COMPONENTS = 8
+
+
+def proposal_head_pad(dof: int) -> int:
+    """Head width (8 logits + 8*dof means + 8*dof log-sigmas) rounded up to 128."""
+    return ((PROPOSAL_COMPONENTS * (1 + 2 * dof) + 127) // 128) * 128
+
+
+def proposal_init(dof: int, seed: int):
+    """Seeded He-normal initial weights (W [out, in], b [out]) of the proposal MLP,
+    binary32-exact; biases start at zero."""
+    dims = (PROPOSAL_IN,) + PROPOSAL_HIDDEN + (proposal_head_pad(dof),)
+    st = Stream(seed, 77)
+    params = []
+    for i in range(4):
+        fan_in, fan_out = dims[i], dims[i + 1]
+        scale = np.sqrt(2.0 / fan_in) if i < 3 else 0.1 * np.sqrt(1.0 / fan_in)
+        W = _f32(st.normal(fan_out * fan_in).reshape(fan_out, fan_in) * scale)
+        params.append((W, np.zeros(fan_out)))
+    return params
+
+
+def random_mixture(dof: int, seed: int, spread: float = 0.6):
+    """Seeded mixture parameters [logits(8) | means(8*dof) | log-sigmas(8*dof)]
+    over normalised joint values (inputs for sampler parity tests)."""
+    st = Stream(seed, 78)
+    logits = st.normal(PROPOSAL_COMPONENTS)
+    means = st.range(-spread, spread, PROPOSAL_COMPONENTS * dof)
+    logsig = st.range(-3.0, -1.0, PROPOSAL_COMPONENTS * dof)
+    return _f32(np.concatenate([logits, means, logsig]))

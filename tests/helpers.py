@@ -104,3 +104,12 @@ def maze_reachable(open_edges, n, a, b):
                 seen.add(y)
                 todo.append(y)
     return False
+
+
+def bf16_round(x):
+    """Round binary32 values to bfloat16 (nearest, ties to even), returned as float32."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    bits = a.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    bits = (bits + 0x7FFF + lsb) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).reshape(a.shape)
