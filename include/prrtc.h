@@ -132,7 +132,8 @@ typedef struct prrtc_params {
   int32_t mode;           /* PRRTC_MODE_*                                              */
   int32_t blocks;         /* grid size of the planner launch; 0 = one wave of resident blocks */
   int32_t warps_per_block;/* worker warps per block; 0 = 4                             */
-  int32_t reserved0;
+  float learned_ratio;    /* probability of drawing from a problem's learned mixture
+                             (after the goal bias); 0 = uniform sampling only         */
   uint64_t seed;          /* Philox key used by prrtc_plan                             */
   double time_limit_s;    /* device-side wall-clock budget per launch; 0 = none        */
   int32_t reserved[8];
@@ -253,6 +254,10 @@ typedef struct prrtc_problem {
   uint64_t seed;          /* Philox key of this problem                  */
   uint32_t problem_id;    /* Philox counter word 0 of this problem        */
   int32_t reserved;
+  /* nullable: sampling mixture of this problem, host [8 + 16*dof] floats:
+   * logits[8], means[8*dof], log-sigmas[8*dof] over joint values normalised
+   * to [-1, 1] (log-sigmas clamped to [-5, 2]); used with params->learned_ratio */
+  const float* gmm;
 } prrtc_problem;
 
 /* Solve n independent problems in one persistent launch: blocks take
@@ -276,6 +281,58 @@ int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_param
 int prrtc_gemm_bf16(const void* a, const void* b, int32_t M, int32_t N, int32_t K, const float* bias,
                     int32_t relu, float* c32, void* c16, void* stream);
 int prrtc_gemm_error(void);
+
+/* ------------------------------------------------------------ learned proposal */
+/* Not part of the paper (which samples uniformly): an MLP maps [start, goal,
+ * 16^3 occupancy grid of the 1.6 m workspace] to an 8-component diagonal
+ * Gaussian mixture over joint values normalised to [-1, 1].  Mixed with
+ * uniform sampling at params->learned_ratio, so planning stays
+ * probabilistically complete; the collision checker remains the judge.
+ * Layers 4160 -> 1024 -> 512 -> 512 -> 8(1 + 2 dof) (padded to 128), ReLU,
+ * BF16 weights and activations on the tensor cores, FP32 accumulation, FP32
+ * master weights and Adam moments.  Flat parameter layout:
+ * [W1 (1024 x 4160), b1, W2 (512 x 1024), b2, W3 (512 x 512), b3,
+ *  W4 (head x 512), b4], W row-major [out x in].  Input row:
+ * [occupancy (voxel i + 16 j + 256 k, centre (-0.8, -0.8, 0) + 0.1 (idx + 0.5),
+ *  occupied iff closer than 0.05 m to an obstacle) | 2 (q_start - lo)/(hi - lo) - 1
+ *  padded to 32 | same for q_goal].  All calls are synchronous. */
+typedef struct prrtc_proposal prrtc_proposal;
+
+/* params: host [n_params] FP32 initial parameters, or null for zeros. */
+int prrtc_proposal_create(int32_t dof, const float* lower, const float* upper, const float* params,
+                          prrtc_proposal** out);
+void prrtc_proposal_destroy(prrtc_proposal* proposal);
+int prrtc_proposal_info(const prrtc_proposal* proposal, int32_t* dof, int32_t* head, int64_t* n_params,
+                        int32_t* step);
+/* Copies the FP32 master parameters and/or the last computed gradients (host [n_params]). */
+int prrtc_proposal_get_params(const prrtc_proposal* proposal, float* params, float* grads);
+/* Raw head output for B inputs: occ host [B * 4096] (0/1), q_* host [B * dof];
+ * out host [B * head]. */
+int prrtc_proposal_forward(prrtc_proposal* proposal, const uint8_t* occ, const float* q_start,
+                           const float* q_goal, int32_t B, float* out);
+/* Mean mixture negative log-likelihood of target [B * dof] and its gradient
+ * (stored in the proposal, read with prrtc_proposal_get_params); no update. */
+int prrtc_proposal_grads(prrtc_proposal* proposal, const uint8_t* occ, const float* q_start,
+                         const float* q_goal, const float* target, int32_t B, float* loss);
+/* `steps` Adam steps (learning rate lr) on batches drawn without replacement
+ * from n_samples samples (seeded shuffle per epoch); sample i uses occupancy
+ * row scene_of[i] of occ [n_scenes * 4096].  losses (nullable) host [steps]. */
+int prrtc_proposal_train(prrtc_proposal* proposal, const uint8_t* occ, int32_t n_scenes, const int32_t* scene_of,
+                         const float* q_start, const float* q_goal, const float* target, int32_t n_samples,
+                         int32_t batch, int32_t steps, float lr, uint64_t seed, float* losses);
+/* Checkpoint: header (magic, version, dof, head, n_params, step, limits) then
+ * FP32 master parameters and Adam moments. */
+int prrtc_proposal_save(const prrtc_proposal* proposal, const char* path);
+int prrtc_proposal_load(const char* path, prrtc_proposal** out);
+/* Occupancy grid of an environment (host [4096]), computed on the device. */
+int prrtc_occupancy(const prrtc_env* env, uint8_t* out);
+
+/* prrtc_plan_batch with the learned proposal: for every problem whose
+ * proposals[p] is non-null (its DoF must match the robot's), the mixture is
+ * inferred on the device from the problem's environment, start and goal and
+ * used with params->learned_ratio.  proposals may be null (plain planning). */
+int prrtc_plan_batch_learned(const prrtc_problem* problems, prrtc_proposal* const* proposals, int32_t n,
+                             const prrtc_params* params, prrtc_path* out_paths, int32_t* out_status);
 
 /* ------------------------------------------------------------ planning without allocation */
 /* The paper has no counterpart of this entry point; it exists for callers

@@ -87,6 +87,9 @@ struct DeviceCtx {
   float* d_packed = nullptr;
   float* h_packed = nullptr;
   size_t packed_cap = 0;
+  float* d_gmm = nullptr;   // [slots][kGmmStride] learned mixtures
+  float* h_gmm = nullptr;
+  size_t gmm_cap = 0;
   // check_states scratch
   float* d_q = nullptr;
   uint8_t* d_valid = nullptr;
@@ -215,6 +218,8 @@ int validate_params(const prrtc_params* p) {
   if (p->blocks < 0 || p->warps_per_block < 0 || p->warps_per_block > 16)
     return fail(PRRTC_ERR_INVALID_ARG, "blocks / warps_per_block out of range");
   if (p->time_limit_s < 0.0) return fail(PRRTC_ERR_INVALID_ARG, "time_limit_s must be >= 0");
+  if (!(p->learned_ratio >= 0.f && p->learned_ratio <= 1.f))
+    return fail(PRRTC_ERR_INVALID_ARG, "learned_ratio must be in [0,1]");
   const double ratio = (double)p->range / (double)p->resolution;
   if (ratio > 4096.0) return fail(PRRTC_ERR_INVALID_ARG, "range / resolution too large");
   return PRRTC_OK;
@@ -555,6 +560,15 @@ int prrtc_internal_views(const prrtc_robot* robot, const prrtc_env* env, const v
   return PRRTC_OK;
 }
 
+int prrtc_internal_env_view(const prrtc_env* env, EnvView* view, int* device) {
+  if (!env) return PRRTC_ERR_INVALID_ARG;
+  *view = env->view();
+  *device = env->device;
+  return PRRTC_OK;
+}
+
+void prrtc_internal_set_error(const char* msg) { t_last_error = msg ? msg : ""; }
+
 int prrtc_env_info(const prrtc_env* env, int32_t* counts4) {
   if (!env || !counts4) return fail(PRRTC_ERR_INVALID_ARG, "null argument");
   counts4[0] = env->n_aabb;
@@ -629,8 +643,15 @@ int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const flo
 }
 
 // -------------------------------------------------------------- planning
-int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params, prrtc_path* out_paths,
-                     int32_t* out_status) {
+}  // extern "C"
+
+// Implemented in prrtc_mlp.cu.
+int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, const float* qs_host,
+                                     const float* qg_host, int B, float* const* gmm_rows, cudaStream_t stream);
+extern "C" int prrtc_proposal_info(const prrtc_proposal*, int32_t*, int32_t*, int64_t*, int32_t*);
+
+static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc_params* params,
+                           prrtc_proposal* const* proposals, prrtc_path* out_paths, int32_t* out_status) {
   if (!problems || n < 1) return fail(PRRTC_ERR_INVALID_ARG, "no problems");
   int rc = validate_params(params);
   if (rc) return rc;
@@ -649,6 +670,69 @@ int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_param
   }
   std::lock_guard<std::mutex> lk(c->mu);
   if ((rc = ensure_arenas(c, n, params->tree_capacity, params->path_capacity))) return rc;
+
+  // learned mixtures: given by the caller (host) or inferred on the device
+  bool any_gmm = false;
+  for (int p = 0; p < n; ++p) any_gmm |= (problems[p].gmm != nullptr) || (proposals && proposals[p]);
+  if (any_gmm && c->gmm_cap < (size_t)n) {
+    cudaFree(c->d_gmm);
+    cudaFreeHost(c->h_gmm);
+    c->d_gmm = nullptr;
+    c->h_gmm = nullptr;
+    c->gmm_cap = 0;
+    if (cudaMalloc(&c->d_gmm, (size_t)n * kGmmStride * sizeof(float)) != cudaSuccess ||
+        cudaMallocHost(&c->h_gmm, (size_t)n * kGmmStride * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PRRTC_ERR_OOM, "mixture buffer allocation failed");
+    }
+    c->gmm_cap = (size_t)n;
+  }
+  bool host_gmm = false;
+  for (int p = 0; p < n; ++p) {
+    const prrtc_problem& pb = problems[p];
+    if (!pb.gmm || (proposals && proposals[p])) continue;
+    const int dof = pb.robot->h->h.dof;
+    float* g = c->h_gmm + (size_t)p * kGmmStride;
+    std::memset(g, 0, kGmmStride * sizeof(float));
+    for (int k = 0; k < kMixK; ++k) {
+      g[k] = pb.gmm[k];
+      for (int j = 0; j < dof; ++j) {
+        g[kMixK + k * kMaxDof + j] = pb.gmm[kMixK + k * dof + j];
+        g[kMixK + kMixK * kMaxDof + k * kMaxDof + j] =
+            std::min(std::max(pb.gmm[kMixK + kMixK * dof + k * dof + j], -5.f), 2.f);
+      }
+    }
+    if (!finite_all(g, kGmmStride)) return fail(PRRTC_ERR_INVALID_ARG, "non-finite mixture");
+    host_gmm = true;
+  }
+  if (host_gmm)
+    CK(cudaMemcpyAsync(c->d_gmm, c->h_gmm, (size_t)n * kGmmStride * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if (proposals) {
+    // group problems by proposal; each group is one batched inference
+    std::vector<int> done(n, 0);
+    for (int p = 0; p < n; ++p) {
+      if (!proposals[p] || done[p]) continue;
+      prrtc_proposal* prop = proposals[p];
+      int pdof = 0;
+      prrtc_proposal_info(prop, &pdof, nullptr, nullptr, nullptr);
+      std::vector<EnvView> envs;
+      std::vector<float> qs, qg;
+      std::vector<float*> rows;
+      for (int r = p; r < n; ++r) {
+        if (proposals[r] != prop) continue;
+        const prrtc_problem& pb = problems[r];
+        if (pb.robot->h->h.dof != pdof) return fail(PRRTC_ERR_INVALID_ARG, "proposal DoF does not match the robot");
+        envs.push_back(pb.env->view());
+        qs.insert(qs.end(), pb.q_start, pb.q_start + pdof);
+        qg.insert(qg.end(), pb.q_goal, pb.q_goal + pdof);
+        rows.push_back(c->d_gmm + (size_t)r * kGmmStride);
+        done[r] = 1;
+      }
+      int rc2 = prrtc_internal_proposal_mixtures(prop, envs.data(), qs.data(), qg.data(), (int)envs.size(),
+                                                 rows.data(), c->stream);
+      if (rc2) return rc2;
+    }
+  }
 
   int max_spheres = 1, max_pairs = 0, max_env = 0;
   for (int p = 0; p < n; ++p) {
@@ -673,6 +757,7 @@ int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_param
     D.key_lo = (uint32_t)(pb.seed & 0xffffffffu);
     D.key_hi = (uint32_t)(pb.seed >> 32);
     D.pid = pb.problem_id;
+    D.gmm = (pb.gmm || (proposals && proposals[p])) ? c->d_gmm + (size_t)p * kGmmStride : nullptr;
     for (int j = 0; j < H.dof; ++j) {
       D.q_start[j] = pb.q_start[j];
       D.q_goal[j] = pb.q_goal[j];
@@ -691,6 +776,7 @@ int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_param
   G.range = params->range;
   G.resolution = params->resolution;
   G.bias_thr = (uint32_t)std::ceil((double)params->goal_bias * 16777216.0);
+  G.learned_thr = (uint32_t)std::ceil((double)params->learned_ratio * 16777216.0);
   G.path_cap = params->path_capacity;
   G.t0 = ULLONG_MAX;
   G.time_limit_ns = (unsigned long long)(params->time_limit_s * 1e9);
@@ -813,6 +899,18 @@ int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_param
   return PRRTC_OK;
 }
 
+extern "C" {
+
+int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params, prrtc_path* out_paths,
+                     int32_t* out_status) {
+  return plan_batch_impl(problems, n, params, nullptr, out_paths, out_status);
+}
+
+int prrtc_plan_batch_learned(const prrtc_problem* problems, prrtc_proposal* const* proposals, int32_t n,
+                             const prrtc_params* params, prrtc_path* out_paths, int32_t* out_status) {
+  return plan_batch_impl(problems, n, params, proposals, out_paths, out_status);
+}
+
 int prrtc_debug_tree(int32_t problem, int32_t tree, float* nodes, int32_t* parents, int32_t cap, int32_t* out_n) {
   if (tree < 0 || tree > 1 || cap < 0 || !out_n) return fail(PRRTC_ERR_INVALID_ARG, "bad debug_tree arguments");
   DeviceCtx* c = nullptr;
@@ -852,6 +950,7 @@ int prrtc_plan(const prrtc_robot* robot, const prrtc_env* env, const float* q_st
   pb.q_goal = q_goal;
   pb.seed = params ? params->seed : 1;
   pb.problem_id = 0;
+  pb.gmm = nullptr;
   return prrtc_plan_batch(&pb, 1, params, out_path, nullptr);
 }
 

@@ -9,6 +9,8 @@
 namespace prrtc {
 
 constexpr int kRootParent = -2;    // parent of a tree root
+constexpr int kMixK = 8;           // learned mixture components
+constexpr int kGmmStride = kMixK + 2 * kMixK * kMaxDof;  // logits | means [8][16] | log-sigmas [8][16]
 constexpr int kUnsetParent = -1;   // parent slot not written yet (0xFF fill)
 
 // Launch-wide parameters and bookkeeping (one per planning launch).
@@ -26,7 +28,7 @@ struct PlanGlobals {
   int cursor;            // work-queue ticket counter
   int error;             // device-side error code (PRRTC_ERR_*), 0 = none
   int error_info;
-  int pad_;
+  uint32_t learned_thr;  // learned-vs-uniform draw as a threshold on the top 24 bits of a Philox word
 };
 
 // Per-problem inputs (uploaded every call).
@@ -44,6 +46,7 @@ struct ProblemDesc {
   int n_pairs;
   uint32_t key_lo, key_hi;
   uint32_t pid;
+  const float* gmm;      // learned mixture (kGmmStride floats, device) or null
   float q_start[kMaxDof];
   float q_goal[kMaxDof];
 };
@@ -99,5 +102,10 @@ cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, in
 // Copy every problem's path into one packed buffer; offsets[p]..offsets[p+1]
 // is problem p's float range (n + 1 entries, device memory).
 cudaError_t launch_gather_paths(const ProblemDesc* desc, const int* offsets, int n, float* out, cudaStream_t stream);
+
+// Tensor-core GEMM (prrtc_gemm.cu): C[M,N] = A[M,K] B[N,K]^T (+bias, ReLU).
+int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32, int ldc32,
+              void* c16, int ldc16, cudaStream_t stream);
+int gemm_take_error();
 
 }  // namespace prrtc

@@ -1,0 +1,744 @@
+// prrtc_mlp.cu -- the learned sampling proposal on the device.
+//
+// A small MLP maps [occupancy 16^3 | start | goal] to an 8-component diagonal
+// Gaussian mixture over joint values normalised to [-1, 1].  Dense layers run
+// on the tensor cores (prrtc_gemm.cu: BF16 operands, FP32 accumulation);
+// everything else is elementwise or per-sample work:
+//   forward   x -> relu(W1 x + b1) -> relu(W2 .) -> relu(W3 .) -> W4 . + b4
+//   loss      mean mixture negative log-likelihood of target configurations
+//   backward  dW = dZ^T H, dH = dZ W (BF16 operands transposed explicitly),
+//             ReLU masks, bias column sums
+//   update    Adam on FP32 master weights, then BF16 copies (and transposes)
+// The proposal is an addition to pRRTC (the paper samples uniformly).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "prrtc.h"
+#include "prrtc_launch.h"
+
+using bf16 = __nv_bfloat16;
+
+namespace prrtc {
+namespace {
+
+constexpr int kGrid = 16, kVox = kGrid * kGrid * kGrid, kQPad = 32, kIn = kVox + 2 * kQPad, kK = 8;
+constexpr int kHid0 = 1024, kHid1 = 512, kHid2 = 512;
+constexpr float kOrigin[3] = {-0.8f, -0.8f, 0.0f};
+constexpr float kCell = 0.1f, kOccRadius = 0.05f;
+constexpr float kLogSigMin = -5.f, kLogSigMax = 2.f;
+
+int head_pad(int dof) { return ((kK * (1 + 2 * dof) + 127) / 128) * 128; }
+
+// ------------------------------------------------------------------ kernels
+// Voxel (i, j, k) -> index i + 16 j + 256 k is occupied iff its centre is
+// closer than 5 cm to an obstacle (a 5 cm sphere there would collide).
+__global__ void occupancy_kernel(EnvView env, uint8_t* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= kVox) return;
+  const int i = v % kGrid, j = (v / kGrid) % kGrid, k = v / (kGrid * kGrid);
+  const float px = kOrigin[0] + (i + 0.5f) * kCell;
+  const float py = kOrigin[1] + (j + 0.5f) * kCell;
+  const float pz = kOrigin[2] + (k + 0.5f) * kCell;
+  out[v] = sphere_hits_env(px, py, pz, kOccRadius, env.data, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph) ? 1 : 0;
+}
+
+// Occupancy grids of B environments (one grid per blockIdx.y).
+__global__ void occupancy_batch_kernel(const EnvView* __restrict__ envs, uint8_t* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= kVox) return;
+  const EnvView env = envs[blockIdx.y];
+  const int i = v % kGrid, j = (v / kGrid) % kGrid, k = v / (kGrid * kGrid);
+  const float px = kOrigin[0] + (i + 0.5f) * kCell;
+  const float py = kOrigin[1] + (j + 0.5f) * kCell;
+  const float pz = kOrigin[2] + (k + 0.5f) * kCell;
+  out[(size_t)blockIdx.y * kVox + v] =
+      sphere_hits_env(px, py, pz, kOccRadius, env.data, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph) ? 1 : 0;
+}
+
+// One feature row per sample (rows past B are zero): occupancy of the
+// sample's scene, then normalised start and goal, each zero-padded to 32.
+__global__ void features_kernel(const uint8_t* __restrict__ occ, const int* __restrict__ scene_of,
+                                const int* __restrict__ rows, const float* __restrict__ qs,
+                                const float* __restrict__ qg, const float* __restrict__ lo,
+                                const float* __restrict__ span, int B, int dof, bf16* __restrict__ x) {
+  const int b = blockIdx.x;
+  bf16* dst = x + (size_t)b * kIn;
+  if (b >= B) {
+    for (int c = threadIdx.x; c < kIn; c += blockDim.x) dst[c] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  const int r = rows ? rows[b] : b;
+  const int s = scene_of ? scene_of[r] : r;
+  const uint8_t* o = occ + (size_t)s * kVox;
+  for (int c = threadIdx.x; c < kIn; c += blockDim.x) {
+    float v;
+    if (c < kVox) {
+      v = o[c] ? 1.f : 0.f;
+    } else {
+      const int j = (c - kVox) % kQPad;
+      const float* q = (c < kVox + kQPad) ? qs : qg;
+      v = (j < dof) ? 2.f * (q[(size_t)r * dof + j] - lo[j]) / span[j] - 1.f : 0.f;
+    }
+    dst[c] = __float2bfloat16_rn(v);
+  }
+}
+
+// Mixture negative log-likelihood of each sample's target and its gradient
+// with respect to the head output (scaled by 1/B).  One warp per sample;
+// lane k < 8 owns component k.
+__global__ void mixture_loss_kernel(const float* __restrict__ out, int P, const float* __restrict__ target,
+                                    const int* __restrict__ rows, const float* __restrict__ lo,
+                                    const float* __restrict__ span, int B, int dof, float invB,
+                                    float* __restrict__ dout32, bf16* __restrict__ dout16,
+                                    float* __restrict__ loss_sum) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const int r = rows ? rows[warp] : warp;
+  const float* o = out + (size_t)warp * P;
+  const bool comp = lane < kK;
+  const int k = comp ? lane : 0;
+  const float logit = comp ? o[k] : -INFINITY;
+  float mx = logit;
+  for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, off));
+  float se = comp ? expf(logit - mx) : 0.f;
+  for (int off = 16; off; off >>= 1) se += __shfl_xor_sync(kFull, se, off);
+  const float logpi = logit - mx - logf(se);
+  float a = -INFINITY;
+  if (comp) {
+    a = logpi - 0.5f * dof * 1.8378770664093453f;  // log(2 pi)
+    for (int j = 0; j < dof; ++j) {
+      const float u = 2.f * (target[(size_t)r * dof + j] - lo[j]) / span[j] - 1.f;
+      const float ls = fminf(fmaxf(o[kK + kK * dof + k * dof + j], kLogSigMin), kLogSigMax);
+      const float z = (u - o[kK + k * dof + j]) * expf(-ls);
+      a += -0.5f * z * z - ls;
+    }
+  }
+  float am = a;
+  for (int off = 16; off; off >>= 1) am = fmaxf(am, __shfl_xor_sync(kFull, am, off));
+  float sa = comp ? expf(a - am) : 0.f;
+  for (int off = 16; off; off >>= 1) sa += __shfl_xor_sync(kFull, sa, off);
+  const float lse = am + logf(sa);
+  float* d32 = dout32 + (size_t)warp * P;
+  bf16* d16 = dout16 + (size_t)warp * P;
+  if (comp) {
+    const float gamma = expf(a - lse), pi = expf(logpi);
+    const float gl = (pi - gamma) * invB;
+    d32[k] = gl;
+    d16[k] = __float2bfloat16_rn(gl);
+    for (int j = 0; j < dof; ++j) {
+      const float u = 2.f * (target[(size_t)r * dof + j] - lo[j]) / span[j] - 1.f;
+      const float raw = o[kK + kK * dof + k * dof + j];
+      const float ls = fminf(fmaxf(raw, kLogSigMin), kLogSigMax);
+      const float isig = expf(-ls);
+      const float z = (u - o[kK + k * dof + j]) * isig;
+      const float gm = -gamma * z * isig * invB;
+      const float gs = (raw > kLogSigMin && raw < kLogSigMax) ? -gamma * (z * z - 1.f) * invB : 0.f;
+      d32[kK + k * dof + j] = gm;
+      d16[kK + k * dof + j] = __float2bfloat16_rn(gm);
+      d32[kK + kK * dof + k * dof + j] = gs;
+      d16[kK + kK * dof + k * dof + j] = __float2bfloat16_rn(gs);
+    }
+  }
+  if (lane == 0) atomicAdd(loss_sum, -lse * invB);
+}
+
+// dZ = dH * [H > 0] in FP32 and BF16.
+__global__ void relu_back_kernel(const float* __restrict__ dh, const bf16* __restrict__ h, size_t n,
+                                 float* __restrict__ dz32, bf16* __restrict__ dz16) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = (__bfloat162float(h[i]) > 0.f) ? dh[i] : 0.f;
+    dz32[i] = v;
+    dz16[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// out[c] = sum over rows of g[r, c].
+__global__ void colsum_kernel(const float* __restrict__ g, int rows, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int r = 0; r < rows; ++r) s += g[(size_t)r * cols + c];
+  out[c] = s;
+}
+
+// out[c, r] = in[r, c] (BF16, 32 x 32 tiles through shared memory).
+__global__ void transpose_kernel(const bf16* __restrict__ in, int rows, int cols, bf16* __restrict__ out) {
+  __shared__ bf16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) out[(size_t)c * rows + r] = tile[threadIdx.x][k];
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ in, size_t n, bf16* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// Adam with bias-corrected moments: c1 = 1/(1 - b1^t), c2 = 1/(1 - b2^t).
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+// Mixture parameters of each row's head output, in the planner's layout:
+// [logits(8) | mean (8 x 16) | log-sigma clamped (8 x 16)].
+__global__ void mixture_params_kernel(const float* __restrict__ out, int P, int B, int dof,
+                                      float* const* __restrict__ rows) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const float* o = out + (size_t)b * P;
+  float* g = rows[b];
+  for (int t = threadIdx.x; t < kK + 2 * kK * kMaxDof; t += blockDim.x) {
+    float v = 0.f;
+    if (t < kK) {
+      v = o[t];
+    } else if (t < kK + kK * kMaxDof) {
+      const int k = (t - kK) / kMaxDof, j = (t - kK) % kMaxDof;
+      v = (j < dof) ? o[kK + k * dof + j] : 0.f;
+    } else {
+      const int k = (t - kK - kK * kMaxDof) / kMaxDof, j = (t - kK - kK * kMaxDof) % kMaxDof;
+      v = (j < dof) ? fminf(fmaxf(o[kK + kK * dof + k * dof + j], kLogSigMin), kLogSigMax) : 0.f;
+    }
+    g[t] = v;
+  }
+}
+
+int blocks_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
+
+}  // namespace
+}  // namespace prrtc
+
+using namespace prrtc;
+
+// ------------------------------------------------------------------ handle
+struct prrtc_proposal {
+  int device = -1;
+  int dof = 0, P = 0;
+  int in_dim[4], out_dim[4];
+  size_t w_off[4], b_off[4], n_params = 0;
+  float* master = nullptr;
+  float* grad = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  bf16* w16[4] = {};
+  bf16* w16t[4] = {};
+  int step = 0;
+  float lo[kMaxDof], span[kMaxDof];
+  float* d_lims = nullptr;  // lo[16] | span[16]
+  cudaStream_t stream = nullptr;
+  // batch scratch
+  int cap = 0;
+  bf16 *x16 = nullptr, *xT = nullptr, *h16[3] = {}, *hT[3] = {}, *d16 = nullptr, *dT = nullptr, *z16[3] = {},
+       *zT[3] = {};
+  float *out32 = nullptr, *d32 = nullptr, *dh32 = nullptr, *z32[3] = {}, *loss = nullptr;
+  // sample data
+  uint8_t* occ = nullptr;
+  size_t occ_cap = 0;
+  float *qs = nullptr, *qg = nullptr, *tgt = nullptr;
+  int *scene_of = nullptr, *rows = nullptr;
+  size_t q_cap = 0, qg_cap = 0, tgt_cap = 0, scene_cap = 0, rows_cap = 0;
+  EnvView* envs = nullptr;
+  size_t envs_cap = 0;
+  float** gmm_rows = nullptr;
+  size_t gmm_rows_cap = 0;
+  cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+}  // namespace
+extern "C" void prrtc_internal_set_error(const char* msg);
+extern "C" int prrtc_internal_env_view(const prrtc_env* env, EnvView* view, int* device);
+namespace {
+
+int mlp_fail(int code, const char* msg) {
+  prrtc_internal_set_error(msg);
+  return code;
+}
+
+#define MCK(call)                                                           \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) return mlp_fail(PRRTC_ERR_CUDA, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+int grow(T** p, size_t* cap, size_t need) {
+  if (*p && *cap >= need) return PRRTC_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, std::max<size_t>(need, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return mlp_fail(PRRTC_ERR_OOM, "device allocation failed");
+  }
+  *cap = need;
+  return PRRTC_OK;
+}
+
+void free_scratch(prrtc_proposal* p) {
+  cudaFree(p->x16); cudaFree(p->xT); cudaFree(p->d16); cudaFree(p->dT);
+  cudaFree(p->out32); cudaFree(p->d32); cudaFree(p->dh32); cudaFree(p->loss);
+  for (int l = 0; l < 3; ++l) {
+    cudaFree(p->h16[l]); cudaFree(p->hT[l]); cudaFree(p->z16[l]); cudaFree(p->zT[l]); cudaFree(p->z32[l]);
+    p->h16[l] = p->hT[l] = p->z16[l] = p->zT[l] = nullptr;
+    p->z32[l] = nullptr;
+  }
+  p->x16 = p->xT = p->d16 = p->dT = nullptr;
+  p->out32 = p->d32 = p->dh32 = p->loss = nullptr;
+  p->cap = 0;
+}
+
+// Batch scratch for up to `rows` rows (a multiple of 8).
+int ensure_scratch(prrtc_proposal* p, int rows) {
+  if (p->cap >= rows) return PRRTC_OK;
+  free_scratch(p);
+  const int P = p->P;
+  const int hid[3] = {kHid0, kHid1, kHid2};
+  bool ok = cudaMalloc(&p->x16, (size_t)rows * kIn * 2) == cudaSuccess &&
+            cudaMalloc(&p->xT, (size_t)rows * kIn * 2) == cudaSuccess &&
+            cudaMalloc(&p->d16, (size_t)rows * P * 2) == cudaSuccess &&
+            cudaMalloc(&p->dT, (size_t)rows * P * 2) == cudaSuccess &&
+            cudaMalloc(&p->out32, (size_t)rows * P * 4) == cudaSuccess &&
+            cudaMalloc(&p->d32, (size_t)rows * P * 4) == cudaSuccess &&
+            cudaMalloc(&p->dh32, (size_t)rows * kHid0 * 4) == cudaSuccess &&
+            cudaMalloc(&p->loss, 4) == cudaSuccess;
+  for (int l = 0; l < 3 && ok; ++l)
+    ok = cudaMalloc(&p->h16[l], (size_t)rows * hid[l] * 2) == cudaSuccess &&
+         cudaMalloc(&p->hT[l], (size_t)rows * hid[l] * 2) == cudaSuccess &&
+         cudaMalloc(&p->z16[l], (size_t)rows * hid[l] * 2) == cudaSuccess &&
+         cudaMalloc(&p->zT[l], (size_t)rows * hid[l] * 2) == cudaSuccess &&
+         cudaMalloc(&p->z32[l], (size_t)rows * hid[l] * 4) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_scratch(p);
+    return mlp_fail(PRRTC_ERR_OOM, "scratch allocation failed");
+  }
+  p->cap = rows;
+  return PRRTC_OK;
+}
+
+int transpose(const bf16* in, int rows, int cols, bf16* out, cudaStream_t s) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  transpose_kernel<<<grid, block, 0, s>>>(in, rows, cols, out);
+  return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
+}
+
+// BF16 copies of the weights and their transposes from the FP32 masters.
+int refresh_weights(prrtc_proposal* p) {
+  for (int l = 0; l < 4; ++l) {
+    const size_t n = (size_t)p->out_dim[l] * p->in_dim[l];
+    to_bf16_kernel<<<blocks_for(n), 256, 0, p->stream>>>(p->master + p->w_off[l], n, p->w16[l]);
+    int rc = transpose(p->w16[l], p->out_dim[l], p->in_dim[l], p->w16t[l], p->stream);
+    if (rc) return rc;
+  }
+  return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
+}
+
+int gemm(const bf16* a, const bf16* b, int M, int N, int K, const float* bias, int relu, float* c32, bf16* c16,
+         cudaStream_t s) {
+  return gemm_bf16(a, b, M, N, K, bias, relu, c32, N, c16, N, s);
+}
+
+// Forward of `rows` feature rows already in x16; out32 receives the head.
+int forward_rows(prrtc_proposal* p, int rows) {
+  const cudaStream_t s = p->stream;
+  int rc;
+  const bf16* in = p->x16;
+  for (int l = 0; l < 3; ++l) {
+    if ((rc = gemm(in, p->w16[l], rows, p->out_dim[l], p->in_dim[l], p->master + p->b_off[l], 1, nullptr, p->h16[l],
+                   s)))
+      return rc;
+    in = p->h16[l];
+  }
+  return gemm(in, p->w16[3], rows, p->P, p->in_dim[3], p->master + p->b_off[3], 0, p->out32, nullptr, s);
+}
+
+// Gradients of the mean NLL for `B` samples (rows padded to `rows`) into p->grad.
+int backward_rows(prrtc_proposal* p, int B, int rows) {
+  const cudaStream_t s = p->stream;
+  const int P = p->P;
+  int rc;
+  // head: dW4 = dout^T h3, db4 = colsum(dout), dh3 = dout W4
+  if ((rc = transpose(p->d16, rows, P, p->dT, s))) return rc;
+  const bf16* hprev[4] = {p->x16, p->h16[0], p->h16[1], p->h16[2]};
+  bf16* hprevT[4] = {p->xT, p->hT[0], p->hT[1], p->hT[2]};
+  const bf16* dz16 = p->d16;
+  const bf16* dzT = p->dT;
+  const float* dz32 = p->d32;
+  for (int l = 3; l >= 0; --l) {
+    const int in = p->in_dim[l], out = p->out_dim[l];
+    if ((rc = transpose(hprev[l], rows, in, hprevT[l], s))) return rc;
+    // dW_l [out x in] = dZ^T [out x rows] * (H^T [in x rows])^T
+    if ((rc = gemm(dzT, hprevT[l], out, in, rows, nullptr, 0, p->grad + p->w_off[l], nullptr, s))) return rc;
+    colsum_kernel<<<(out + 127) / 128, 128, 0, s>>>(dz32, rows, out, p->grad + p->b_off[l]);
+    if (l == 0) break;
+    // dH_{l-1} [rows x in] = dZ [rows x out] * (W^T [in x out])^T
+    if ((rc = gemm(dz16, p->w16t[l], rows, in, out, nullptr, 0, p->dh32, nullptr, s))) return rc;
+    const size_t n = (size_t)rows * in;
+    relu_back_kernel<<<blocks_for(n), 256, 0, s>>>(p->dh32, p->h16[l - 1], n, p->z32[l - 1], p->z16[l - 1]);
+    if ((rc = transpose(p->z16[l - 1], rows, in, p->zT[l - 1], s))) return rc;
+    dz16 = p->z16[l - 1];
+    dzT = p->zT[l - 1];
+    dz32 = p->z32[l - 1];
+  }
+  (void)B;
+  return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
+}
+
+int upload_samples(prrtc_proposal* p, const uint8_t* occ, int n_occ, const float* qs, const float* qg,
+                   const float* tgt, int n) {
+  int rc;
+  if ((rc = grow(&p->occ, &p->occ_cap, (size_t)n_occ * kVox))) return rc;
+  if ((rc = grow(&p->qs, &p->q_cap, (size_t)n * p->dof))) return rc;
+  if ((rc = grow(&p->qg, &p->qg_cap, (size_t)n * p->dof))) return rc;
+  if (tgt && (rc = grow(&p->tgt, &p->tgt_cap, (size_t)n * p->dof))) return rc;
+  MCK(cudaMemcpyAsync(p->occ, occ, (size_t)n_occ * kVox, cudaMemcpyHostToDevice, p->stream));
+  MCK(cudaMemcpyAsync(p->qs, qs, (size_t)n * p->dof * 4, cudaMemcpyHostToDevice, p->stream));
+  MCK(cudaMemcpyAsync(p->qg, qg, (size_t)n * p->dof * 4, cudaMemcpyHostToDevice, p->stream));
+  if (tgt) MCK(cudaMemcpyAsync(p->tgt, tgt, (size_t)n * p->dof * 4, cudaMemcpyHostToDevice, p->stream));
+  return PRRTC_OK;
+}
+
+int check_gemm_error() {
+  const int e = gemm_take_error();
+  return e ? mlp_fail(e, "a tensor-core kernel wait gave up") : PRRTC_OK;
+}
+
+}  // namespace
+
+// Internal: the mixture parameters of `B` problems into device memory (the
+// planner's layout), one destination row pointer per problem; ordered before
+// later work on `stream`.  Used by prrtc_plan_batch_learned.
+int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, const float* qs_host,
+                                     const float* qg_host, int B, float* const* gmm_rows, cudaStream_t stream) {
+  if (!p || B <= 0) return PRRTC_ERR_INVALID_ARG;
+  const int rows = (B + 7) & ~7;
+  int rc;
+  if ((rc = ensure_scratch(p, rows))) return rc;
+  if ((rc = grow(&p->occ, &p->occ_cap, (size_t)B * kVox))) return rc;
+  if ((rc = grow(&p->qs, &p->q_cap, (size_t)B * p->dof))) return rc;
+  if ((rc = grow(&p->qg, &p->qg_cap, (size_t)B * p->dof))) return rc;
+  if ((rc = grow(&p->envs, &p->envs_cap, (size_t)B))) return rc;
+  if ((rc = grow(&p->gmm_rows, &p->gmm_rows_cap, (size_t)B))) return rc;
+  MCK(cudaMemcpyAsync(p->envs, envs, (size_t)B * sizeof(EnvView), cudaMemcpyHostToDevice, p->stream));
+  MCK(cudaMemcpyAsync(p->gmm_rows, gmm_rows, (size_t)B * sizeof(float*), cudaMemcpyHostToDevice, p->stream));
+  MCK(cudaMemcpyAsync(p->qs, qs_host, (size_t)B * p->dof * 4, cudaMemcpyHostToDevice, p->stream));
+  MCK(cudaMemcpyAsync(p->qg, qg_host, (size_t)B * p->dof * 4, cudaMemcpyHostToDevice, p->stream));
+  occupancy_batch_kernel<<<dim3((kVox + 255) / 256, B), 256, 0, p->stream>>>(p->envs, p->occ);
+  features_kernel<<<rows, 256, 0, p->stream>>>(p->occ, nullptr, nullptr, p->qs, p->qg, p->d_lims,
+                                               p->d_lims + kMaxDof, B, p->dof, p->x16);
+  if ((rc = forward_rows(p, rows))) return rc;
+  mixture_params_kernel<<<B, 128, 0, p->stream>>>(p->out32, p->P, B, p->dof, p->gmm_rows);
+  MCK(cudaGetLastError());
+  // the planner runs on another stream: order it after this work
+  MCK(cudaEventRecord(p->done, p->stream));
+  MCK(cudaStreamWaitEvent(stream, p->done, 0));
+  // host inputs above are pageable and were staged at enqueue; the host
+  // vectors may be released once this returns
+  return PRRTC_OK;
+}
+
+extern "C" {
+
+int prrtc_proposal_create(int32_t dof, const float* lower, const float* upper, const float* params,
+                          prrtc_proposal** out) {
+  if (!out || dof < 1 || dof > kMaxDof || !lower || !upper) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  *out = nullptr;
+  int dev = -1, count = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceCount(&count) != cudaSuccess || count < 1)
+    return mlp_fail(PRRTC_ERR_NO_DEVICE, "no CUDA device");
+  for (int j = 0; j < dof; ++j)
+    if (!(upper[j] > lower[j])) return mlp_fail(PRRTC_ERR_INVALID_ARG, "joint limits must have upper > lower");
+  prrtc_proposal* p = new prrtc_proposal();
+  p->device = dev;
+  p->dof = dof;
+  p->P = head_pad(dof);
+  const int dims[5] = {kIn, kHid0, kHid1, kHid2, p->P};
+  size_t off = 0;
+  for (int l = 0; l < 4; ++l) {
+    p->in_dim[l] = dims[l];
+    p->out_dim[l] = dims[l + 1];
+    p->w_off[l] = off;
+    off += (size_t)dims[l + 1] * dims[l];
+    p->b_off[l] = off;
+    off += dims[l + 1];
+  }
+  p->n_params = off;
+  for (int j = 0; j < kMaxDof; ++j) {
+    p->lo[j] = j < dof ? lower[j] : 0.f;
+    p->span[j] = j < dof ? upper[j] - lower[j] : 1.f;
+  }
+  bool ok = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) == cudaSuccess &&
+            cudaMalloc(&p->master, off * 4) == cudaSuccess && cudaMalloc(&p->grad, off * 4) == cudaSuccess &&
+            cudaMalloc(&p->m, off * 4) == cudaSuccess && cudaMalloc(&p->v, off * 4) == cudaSuccess &&
+            cudaMalloc(&p->d_lims, 2 * kMaxDof * 4) == cudaSuccess;
+  for (int l = 0; l < 4 && ok; ++l)
+    ok = cudaMalloc(&p->w16[l], (size_t)dims[l + 1] * dims[l] * 2) == cudaSuccess &&
+         cudaMalloc(&p->w16t[l], (size_t)dims[l + 1] * dims[l] * 2) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    prrtc_proposal_destroy(p);
+    return mlp_fail(PRRTC_ERR_OOM, "proposal allocation failed");
+  }
+  float lims[2 * kMaxDof];
+  std::memcpy(lims, p->lo, sizeof(p->lo));
+  std::memcpy(lims + kMaxDof, p->span, sizeof(p->span));
+  bool ok2 = cudaMemcpy(p->d_lims, lims, sizeof(lims), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemset(p->m, 0, off * 4) == cudaSuccess && cudaMemset(p->v, 0, off * 4) == cudaSuccess &&
+             cudaMemset(p->grad, 0, off * 4) == cudaSuccess &&
+             (params ? cudaMemcpy(p->master, params, off * 4, cudaMemcpyHostToDevice)
+                     : cudaMemset(p->master, 0, off * 4)) == cudaSuccess;
+  if (!ok2 || refresh_weights(p) != PRRTC_OK || cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    prrtc_proposal_destroy(p);
+    return mlp_fail(PRRTC_ERR_CUDA, "proposal initialisation failed");
+  }
+  *out = p;
+  return PRRTC_OK;
+}
+
+void prrtc_proposal_destroy(prrtc_proposal* p) {
+  if (!p) return;
+  free_scratch(p);
+  cudaFree(p->master); cudaFree(p->grad); cudaFree(p->m); cudaFree(p->v); cudaFree(p->d_lims);
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(p->w16[l]);
+    cudaFree(p->w16t[l]);
+  }
+  cudaFree(p->occ); cudaFree(p->qs); cudaFree(p->qg); cudaFree(p->tgt); cudaFree(p->scene_of); cudaFree(p->rows);
+  cudaFree(p->envs); cudaFree(p->gmm_rows);
+  if (p->done) cudaEventDestroy(p->done);
+  if (p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+int prrtc_proposal_info(const prrtc_proposal* p, int32_t* dof, int32_t* head, int64_t* n_params, int32_t* step) {
+  if (!p) return mlp_fail(PRRTC_ERR_INVALID_ARG, "null proposal");
+  if (dof) *dof = p->dof;
+  if (head) *head = p->P;
+  if (n_params) *n_params = (int64_t)p->n_params;
+  if (step) *step = p->step;
+  return PRRTC_OK;
+}
+
+int prrtc_proposal_get_params(const prrtc_proposal* p, float* params, float* grads) {
+  if (!p) return mlp_fail(PRRTC_ERR_INVALID_ARG, "null proposal");
+  if (params) MCK(cudaMemcpy(params, p->master, p->n_params * 4, cudaMemcpyDeviceToHost));
+  if (grads) MCK(cudaMemcpy(grads, p->grad, p->n_params * 4, cudaMemcpyDeviceToHost));
+  return PRRTC_OK;
+}
+
+int prrtc_proposal_forward(prrtc_proposal* p, const uint8_t* occ, const float* q_start, const float* q_goal,
+                           int32_t B, float* out) {
+  if (!p || !occ || !q_start || !q_goal || !out || B < 1) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  const int rows = (B + 7) & ~7;
+  int rc;
+  if ((rc = ensure_scratch(p, rows))) return rc;
+  if ((rc = upload_samples(p, occ, B, q_start, q_goal, nullptr, B))) return rc;
+  features_kernel<<<rows, 256, 0, p->stream>>>(p->occ, nullptr, nullptr, p->qs, p->qg, p->d_lims, p->d_lims + kMaxDof,
+                                               B, p->dof, p->x16);
+  if ((rc = forward_rows(p, rows))) return rc;
+  MCK(cudaMemcpyAsync(out, p->out32, (size_t)B * p->P * 4, cudaMemcpyDeviceToHost, p->stream));
+  MCK(cudaStreamSynchronize(p->stream));
+  return check_gemm_error();
+}
+
+// One step on a batch: gradients into the proposal (readable with
+// prrtc_proposal_get_params) and, when lr > 0, an Adam update.
+static int step_on_rows(prrtc_proposal* p, const int* scene_of, const int* rows_dev, int B, float lr,
+                        float* loss_host) {
+  const int rows = (B + 7) & ~7;
+  int rc;
+  const cudaStream_t s = p->stream;
+  features_kernel<<<rows, 256, 0, s>>>(p->occ, scene_of, rows_dev, p->qs, p->qg, p->d_lims, p->d_lims + kMaxDof, B,
+                                       p->dof, p->x16);
+  if ((rc = forward_rows(p, rows))) return rc;
+  MCK(cudaMemsetAsync(p->d32, 0, (size_t)rows * p->P * 4, s));
+  MCK(cudaMemsetAsync(p->d16, 0, (size_t)rows * p->P * 2, s));
+  MCK(cudaMemsetAsync(p->loss, 0, 4, s));
+  mixture_loss_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(p->out32, p->P, p->tgt, rows_dev, p->d_lims,
+                                                            p->d_lims + kMaxDof, B, p->dof, 1.f / (float)B, p->d32,
+                                                            p->d16, p->loss);
+  if ((rc = backward_rows(p, B, rows))) return rc;
+  if (lr > 0.f) {
+    p->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f / (1.f - std::pow(b1, (float)p->step)), c2 = 1.f / (1.f - std::pow(b2, (float)p->step));
+    adam_kernel<<<blocks_for(p->n_params), 256, 0, s>>>(p->master, p->grad, p->m, p->v, p->n_params, lr, b1, b2,
+                                                         1e-8f, c1, c2);
+    if ((rc = refresh_weights(p))) return rc;
+  }
+  if (loss_host) MCK(cudaMemcpyAsync(loss_host, p->loss, 4, cudaMemcpyDeviceToHost, s));
+  return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
+}
+
+static int step_on_rows_direct(prrtc_proposal* p, int B, float* loss) {
+  return step_on_rows(p, nullptr, nullptr, B, 0.f, loss);
+}
+
+int prrtc_proposal_grads(prrtc_proposal* p, const uint8_t* occ, const float* q_start, const float* q_goal,
+                         const float* target, int32_t B, float* loss) {
+  if (!p || !occ || !q_start || !q_goal || !target || B < 1) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  const int rows = (B + 7) & ~7;
+  int rc;
+  if ((rc = ensure_scratch(p, rows))) return rc;
+  if ((rc = upload_samples(p, occ, B, q_start, q_goal, target, B))) return rc;
+  if ((rc = step_on_rows_direct(p, B, loss))) return rc;
+  MCK(cudaStreamSynchronize(p->stream));
+  return check_gemm_error();
+}
+
+int prrtc_proposal_train(prrtc_proposal* p, const uint8_t* occ, int32_t n_scenes, const int32_t* scene_of,
+                         const float* q_start, const float* q_goal, const float* target, int32_t n_samples,
+                         int32_t batch, int32_t steps, float lr, uint64_t seed, float* losses) {
+  if (!p || !occ || n_scenes < 1 || !scene_of || !q_start || !q_goal || !target || n_samples < 1 || batch < 1 ||
+      steps < 0 || !(lr > 0.f))
+    return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  for (int i = 0; i < n_samples; ++i)
+    if (scene_of[i] < 0 || scene_of[i] >= n_scenes) return mlp_fail(PRRTC_ERR_INVALID_ARG, "scene index out of range");
+  const int B = std::min(batch, n_samples);
+  const int rows = (B + 7) & ~7;
+  int rc;
+  if ((rc = ensure_scratch(p, rows))) return rc;
+  if ((rc = upload_samples(p, occ, n_scenes, q_start, q_goal, target, n_samples))) return rc;
+  if ((rc = grow(&p->scene_of, &p->scene_cap, (size_t)n_samples))) return rc;
+  MCK(cudaMemcpyAsync(p->scene_of, scene_of, (size_t)n_samples * 4, cudaMemcpyHostToDevice, p->stream));
+  // sample order: a seeded permutation per epoch, consumed batch by batch
+  std::vector<int> order(n_samples);
+  std::mt19937_64 rng(seed);
+  std::vector<int> idx((size_t)steps * B);
+  size_t pos = order.size();
+  for (size_t k = 0; k < idx.size(); ++k) {
+    if (pos == order.size()) {
+      for (int i = 0; i < n_samples; ++i) order[i] = i;
+      std::shuffle(order.begin(), order.end(), rng);
+      pos = 0;
+    }
+    idx[k] = order[pos++];
+  }
+  if ((rc = grow(&p->rows, &p->rows_cap, std::max<size_t>(idx.size(), 1)))) return rc;
+  if (!idx.empty())
+    MCK(cudaMemcpyAsync(p->rows, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice, p->stream));
+  std::vector<float> host_loss(std::max(steps, 1));
+  for (int t = 0; t < steps; ++t)
+    if ((rc = step_on_rows(p, p->scene_of, p->rows + (size_t)t * B, B, lr, losses ? &host_loss[t] : nullptr)))
+      return rc;
+  MCK(cudaStreamSynchronize(p->stream));
+  if (losses)
+    for (int t = 0; t < steps; ++t) losses[t] = host_loss[t];
+  return check_gemm_error();
+}
+
+int prrtc_occupancy(const prrtc_env* env, uint8_t* out) {
+  if (!env || !out) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  EnvView ev{};
+  int dev = -1;
+  int rc = prrtc_internal_env_view(env, &ev, &dev);
+  if (rc) return rc;
+  uint8_t* d = nullptr;
+  MCK(cudaMalloc(&d, kVox));
+  occupancy_kernel<<<(kVox + 255) / 256, 256>>>(ev, d);
+  cudaError_t e = cudaMemcpy(out, d, kVox, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return mlp_fail(PRRTC_ERR_CUDA, cudaGetErrorString(e));
+  return PRRTC_OK;
+}
+
+// File: "PRRTCMLP" | version | dof | head | n_params | step | lo[16] | span[16]
+// | master | m | v  (FP32, little-endian).
+int prrtc_proposal_save(const prrtc_proposal* p, const char* path) {
+  if (!p || !path) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  std::vector<float> buf(p->n_params * 3);
+  MCK(cudaMemcpy(buf.data(), p->master, p->n_params * 4, cudaMemcpyDeviceToHost));
+  MCK(cudaMemcpy(buf.data() + p->n_params, p->m, p->n_params * 4, cudaMemcpyDeviceToHost));
+  MCK(cudaMemcpy(buf.data() + 2 * p->n_params, p->v, p->n_params * 4, cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return mlp_fail(PRRTC_ERR_INVALID_ARG, "cannot open file");
+  const char magic[8] = {'P', 'R', 'R', 'T', 'C', 'M', 'L', 'P'};
+  const int64_t hdr[5] = {1, p->dof, p->P, (int64_t)p->n_params, p->step};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, 8, 5, f) == 5 &&
+            std::fwrite(p->lo, 4, kMaxDof, f) == (size_t)kMaxDof && std::fwrite(p->span, 4, kMaxDof, f) == (size_t)kMaxDof &&
+            std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? PRRTC_OK : mlp_fail(PRRTC_ERR_INVALID_ARG, "write failed");
+}
+
+int prrtc_proposal_load(const char* path, prrtc_proposal** out) {
+  if (!path || !out) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return mlp_fail(PRRTC_ERR_INVALID_ARG, "cannot open file");
+  char magic[8];
+  int64_t hdr[5];
+  float lo[kMaxDof], span[kMaxDof];
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PRRTCMLP", 8) == 0 && std::fread(hdr, 8, 5, f) == 5 &&
+            hdr[0] == 1 && hdr[1] >= 1 && hdr[1] <= kMaxDof && std::fread(lo, 4, kMaxDof, f) == (size_t)kMaxDof &&
+            std::fread(span, 4, kMaxDof, f) == (size_t)kMaxDof;
+  if (!ok) {
+    std::fclose(f);
+    return mlp_fail(PRRTC_ERR_INVALID_ARG, "not a proposal file");
+  }
+  const int dof = (int)hdr[1];
+  float up[kMaxDof];
+  for (int j = 0; j < kMaxDof; ++j) up[j] = lo[j] + span[j];
+  prrtc_proposal* p = nullptr;
+  int rc = prrtc_proposal_create(dof, lo, up, nullptr, &p);
+  if (rc) {
+    std::fclose(f);
+    return rc;
+  }
+  if ((int64_t)p->n_params != hdr[3] || p->P != hdr[2]) {
+    std::fclose(f);
+    prrtc_proposal_destroy(p);
+    return mlp_fail(PRRTC_ERR_INVALID_ARG, "size mismatch");
+  }
+  std::vector<float> buf(p->n_params * 3);
+  ok = std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) {
+    prrtc_proposal_destroy(p);
+    return mlp_fail(PRRTC_ERR_INVALID_ARG, "truncated file");
+  }
+  std::memcpy(p->lo, lo, sizeof(lo));
+  std::memcpy(p->span, span, sizeof(span));
+  float lims[2 * kMaxDof];
+  std::memcpy(lims, lo, sizeof(lo));
+  std::memcpy(lims + kMaxDof, span, sizeof(span));
+  bool ok2 = cudaMemcpy(p->d_lims, lims, sizeof(lims), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->master, buf.data(), p->n_params * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->m, buf.data() + p->n_params, p->n_params * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->v, buf.data() + 2 * p->n_params, p->n_params * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+  p->step = (int)hdr[4];
+  if (!ok2 || refresh_weights(p) || cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    prrtc_proposal_destroy(p);
+    return mlp_fail(PRRTC_ERR_CUDA, "upload failed");
+  }
+  *out = p;
+  return PRRTC_OK;
+}
+
+}  // extern "C"

@@ -251,6 +251,49 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   }
 }
 
+// Draw from a learned mixture (element `lane` of the configuration): the
+// component from word 21 against the cumulative softmax of the logits, then
+// z_j from Box-Muller on words 22 + 2m, 23 + 2m (m = j / 2; words >= 32 come
+// from Philox blocks 8-9), u_j = mean + exp(log_sigma) z_j, mapped from [-1, 1]
+// to the joint limits and clamped to them.
+__device__ __forceinline__ float mixture_draw(const float* __restrict__ gmm, const RobotHeader* R, uint32_t pid,
+                                              uint32_t it, uint2 key, uint32_t w, int lane, int dof) {
+  uint32_t w2 = 0;
+  {
+    const uint4 ph = philox4x32_10(make_uint4(pid, it, 8u + (uint32_t)((lane >> 2) & 1), 0u), key);
+    w2 = ((lane & 3) == 0) ? ph.x : ((lane & 3) == 1) ? ph.y : ((lane & 3) == 2) ? ph.z : ph.w;
+  }
+  const float uk = u24(__shfl_sync(kFull, w, 21));
+  float mx = -INFINITY;
+#pragma unroll
+  for (int k = 0; k < kMixK; ++k) mx = fmaxf(mx, gmm[k]);
+  float tot = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMixK; ++k) tot += expf(gmm[k] - mx);
+  int comp = kMixK - 1;
+  float cum = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMixK; ++k) {
+    cum += expf(gmm[k] - mx) / tot;
+    if (uk < cum && comp == kMixK - 1 && k < kMixK - 1) comp = k;
+  }
+  const int m = lane >> 1;
+  const int ia = 22 + 2 * m, ib = 23 + 2 * m;
+  const uint32_t a_lo = __shfl_sync(kFull, w, ia & 31), a_hi = __shfl_sync(kFull, w2, (ia - 32) & 31);
+  const uint32_t b_lo = __shfl_sync(kFull, w, ib & 31), b_hi = __shfl_sync(kFull, w2, (ib - 32) & 31);
+  if (lane >= dof) return 0.f;
+  const uint32_t wa = ia < 32 ? a_lo : a_hi, wb = ib < 32 ? b_lo : b_hi;
+  const float u1 = (float)((wa >> 8) + 1u) * (1.0f / 16777216.0f);
+  const float u2 = (float)(wb >> 8) * (1.0f / 16777216.0f);
+  const float rad = sqrtf(-2.f * logf(u1));
+  float sn, cs;
+  sincospif(2.f * u2, &sn, &cs);
+  const float z = (lane & 1) ? rad * sn : rad * cs;
+  const float un = fmaf(expf(gmm[kMixK + kMixK * kMaxDof + comp * kMaxDof + lane]), z, gmm[kMixK + comp * kMaxDof + lane]);
+  const float lo = R->lo[lane], span = R->span[lane];
+  return fminf(fmaxf(fmaf(0.5f * (un + 1.f), span, lo), lo), lo + span);
+}
+
 // Alg. 1 iterations of one worker warp on one problem until it is solved,
 // out of budget or out of time.  Lane j holds element j of every vector.
 __device__ void worker(const Ctx& c, Local& lc) {
@@ -295,18 +338,23 @@ __device__ void worker(const Ctx& c, Local& lc) {
     const int o = 1 - s;
     const int n_s = s ? nb : na;
 
-    // line 4: RANDOM_CONFIG -- Philox words w_0..w_dof of counter {pid, it, blk, 0};
-    // lane l holds word l (lanes 0..19 evaluate blocks 0..4).
-    uint32_t w = 0;
-    if (lane < 20) {
-      const uint4 r = philox4x32_10(make_uint4(D->pid, (uint32_t)it, (uint32_t)(lane >> 2), 0u), key);
-      const int k = lane & 3;
-      w = (k == 0) ? r.x : (k == 1) ? r.y : (k == 2) ? r.z : r.w;
-    }
+    // line 4: RANDOM_CONFIG -- Philox words of counter {pid, it, blk, 0}:
+    // lane l holds word l (blocks 0..7).  Word 0 draws the goal bias, words
+    // 1..dof the uniform configuration; with a learned mixture, word 20 draws
+    // learned-vs-uniform, word 21 the component, words 22.. Box-Muller pairs.
+    const uint4 ph = philox4x32_10(make_uint4(D->pid, (uint32_t)it, (uint32_t)(lane >> 2), 0u), key);
+    const uint32_t w = ((lane & 3) == 0) ? ph.x : ((lane & 3) == 1) ? ph.y : ((lane & 3) == 2) ? ph.z : ph.w;
     const uint32_t w0 = __shfl_sync(kFull, w, 0);
     const uint32_t wj = __shfl_sync(kFull, w, (lane + 1) & 31);
-    float crand = (lane < dof) ? fmaf(u24(wj), R->span[lane], R->lo[lane]) : 0.f;
-    if ((w0 >> 8) < g->bias_thr) crand = row_elem(D->nodes[o], 0, dpad, lane);  // goal bias: root of T_o
+    const uint32_t wl = __shfl_sync(kFull, w, 20);
+    float crand;
+    if ((w0 >> 8) < g->bias_thr) {
+      crand = row_elem(D->nodes[o], 0, dpad, lane);  // goal bias: root of T_o
+    } else if (D->gmm && (wl >> 8) < g->learned_thr) {
+      crand = mixture_draw(D->gmm, R, D->pid, (uint32_t)it, key, w, lane, dof);
+    } else {
+      crand = (lane < dof) ? fmaf(u24(wj), R->span[lane], R->lo[lane]) : 0.f;
+    }
     if (mine) c.v.rnd[lane] = crand;
     __syncwarp();
 

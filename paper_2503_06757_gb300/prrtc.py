@@ -43,7 +43,7 @@ class prrtc_params(C.Structure):
     _fields_ = [("range", C.c_float), ("resolution", C.c_float), ("goal_bias", C.c_float),
                 ("max_iters", C.c_int32), ("tree_capacity", C.c_int32), ("path_capacity", C.c_int32),
                 ("mode", C.c_int32), ("blocks", C.c_int32), ("warps_per_block", C.c_int32),
-                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("time_limit_s", C.c_double),
+                ("learned_ratio", C.c_float), ("seed", C.c_uint64), ("time_limit_s", C.c_double),
                 ("reserved", C.c_int32 * 8)]
 
 
@@ -66,7 +66,7 @@ class prrtc_launch_stats(C.Structure):
 
 class prrtc_problem(C.Structure):
     _fields_ = [("robot", C.c_void_p), ("env", C.c_void_p), ("q_start", _f), ("q_goal", _f),
-                ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("reserved", C.c_int32)]
+                ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("reserved", C.c_int32), ("gmm", _f)]
 
 
 EXPORTS = [
@@ -75,6 +75,9 @@ EXPORTS = [
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
     "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
     "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_error",
+    "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
+    "prrtc_proposal_forward", "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
+    "prrtc_proposal_load", "prrtc_occupancy", "prrtc_plan_batch_learned",
 ]
 
 _lib = None
@@ -116,6 +119,20 @@ def lib():
     L.prrtc_debug_tree.argtypes = [C.c_int32, C.c_int32, _f, _i, C.c_int32, _i]
     L.prrtc_gemm_bf16.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
                                   C.c_void_p, C.c_void_p, C.c_void_p]
+    _u8 = C.POINTER(C.c_uint8)
+    L.prrtc_proposal_create.argtypes = [C.c_int32, _f, _f, _f, C.POINTER(C.c_void_p)]
+    L.prrtc_proposal_destroy.argtypes = [C.c_void_p]
+    L.prrtc_proposal_info.argtypes = [C.c_void_p, _i, _i, C.POINTER(C.c_int64), _i]
+    L.prrtc_proposal_get_params.argtypes = [C.c_void_p, _f, _f]
+    L.prrtc_proposal_forward.argtypes = [C.c_void_p, _u8, _f, _f, C.c_int32, _f]
+    L.prrtc_proposal_grads.argtypes = [C.c_void_p, _u8, _f, _f, _f, C.c_int32, _f]
+    L.prrtc_proposal_train.argtypes = [C.c_void_p, _u8, C.c_int32, _i, _f, _f, _f, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_float, C.c_uint64, _f]
+    L.prrtc_proposal_save.argtypes = [C.c_void_p, C.c_char_p]
+    L.prrtc_proposal_load.argtypes = [C.c_char_p, C.POINTER(C.c_void_p)]
+    L.prrtc_occupancy.argtypes = [C.c_void_p, _u8]
+    L.prrtc_plan_batch_learned.argtypes = [C.POINTER(prrtc_problem), C.POINTER(C.c_void_p), C.c_int32,
+                                           C.POINTER(prrtc_params), C.POINTER(prrtc_path), _i]
     L.prrtc_plan_noalloc.argtypes = [C.c_void_p, C.c_void_p, _f, _f, C.POINTER(prrtc_params), _f, C.c_int32,
                                      C.POINTER(prrtc_path), C.c_void_p]
     _lib = L
@@ -323,13 +340,12 @@ def prrtc_plan(robot: Robot, env: Env, q_start, q_goal, prm: prrtc_params | None
         lib().prrtc_path_free(C.byref(out))
 
 
-def prrtc_plan_batch(problems, prm: prrtc_params | None = None):
-    """problems: sequence of (Robot, Env, q_start, q_goal, seed, problem_id)."""
-    prm = prm or prrtc_params_default()
+def _problem_array(problems, keep):
     n = len(problems)
     arr = (prrtc_problem * n)()
-    keep = []
-    for k, (rb, ev, qs, qg, seed, pid) in enumerate(problems):
+    for k, item in enumerate(problems):
+        rb, ev, qs, qg, seed, pid = item[:6]
+        gmm = item[6] if len(item) > 6 else None
         s, sp = _fa(qs)
         g, gp = _fa(qg)
         keep += [s, g]
@@ -339,13 +355,138 @@ def prrtc_plan_batch(problems, prm: prrtc_params | None = None):
         arr[k].q_goal = gp
         arr[k].seed = int(seed)
         arr[k].problem_id = int(pid)
-    paths = (prrtc_path * n)()
-    status = (C.c_int32 * n)()
-    _check(lib().prrtc_plan_batch(arr, n, C.byref(prm), paths, status), "prrtc_plan_batch")
+        if gmm is not None:
+            m, mp = _fa(gmm)
+            keep.append(m)
+            arr[k].gmm = mp
+    return arr
+
+
+def _collect(paths, n):
     out = []
     for k in range(n):
         out.append(_path_dict(paths[k]))
         lib().prrtc_path_free(C.byref(paths[k]))
+    return out
+
+
+def prrtc_plan_batch(problems, prm: prrtc_params | None = None):
+    """problems: sequence of (Robot, Env, q_start, q_goal, seed, problem_id[, gmm])."""
+    prm = prm or prrtc_params_default()
+    keep = []
+    n = len(problems)
+    arr = _problem_array(problems, keep)
+    paths = (prrtc_path * n)()
+    status = (C.c_int32 * n)()
+    _check(lib().prrtc_plan_batch(arr, n, C.byref(prm), paths, status), "prrtc_plan_batch")
+    return _collect(paths, n)
+
+
+def prrtc_plan_batch_learned(problems, proposals, prm: prrtc_params | None = None):
+    """As prrtc_plan_batch, with proposals[p] (Proposal or None) inferring each mixture on the device."""
+    prm = prm or prrtc_params_default()
+    keep = []
+    n = len(problems)
+    arr = _problem_array(problems, keep)
+    props = (C.c_void_p * n)(*[(pp.handle.value if pp is not None else None) for pp in proposals])
+    paths = (prrtc_path * n)()
+    status = (C.c_int32 * n)()
+    _check(lib().prrtc_plan_batch_learned(arr, props, n, C.byref(prm), paths, status), "prrtc_plan_batch_learned")
+    return _collect(paths, n)
+
+
+class Proposal:
+    """Learned sampling proposal (prrtc_proposal_*)."""
+
+    def __init__(self, dof=None, lower=None, upper=None, params=None, handle=None):
+        self._lib = lib()
+        if handle is None:
+            lo, lp = _fa(lower)
+            hi, hp = _fa(upper)
+            pr, pp = _fa(params) if params is not None else (None, None)
+            h = C.c_void_p()
+            _check(self._lib.prrtc_proposal_create(int(dof), lp, hp, pp, C.byref(h)), "prrtc_proposal_create")
+            handle = h
+        self.handle = handle
+        d, hd, npar, st = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
+        _check(self._lib.prrtc_proposal_info(self.handle, C.byref(d), C.byref(hd), C.byref(npar), C.byref(st)),
+               "prrtc_proposal_info")
+        self.dof, self.head, self.n_params = d.value, hd.value, npar.value
+
+    @property
+    def step(self):
+        st = C.c_int32()
+        _check(self._lib.prrtc_proposal_info(self.handle, None, None, None, C.byref(st)), "prrtc_proposal_info")
+        return st.value
+
+    @classmethod
+    def load(cls, path):
+        h = C.c_void_p()
+        _check(lib().prrtc_proposal_load(str(path).encode(), C.byref(h)), "prrtc_proposal_load")
+        return cls(handle=h)
+
+    def save(self, path):
+        _check(self._lib.prrtc_proposal_save(self.handle, str(path).encode()), "prrtc_proposal_save")
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(self._lib.prrtc_proposal_get_params(self.handle, out.ctypes.data_as(_f), None), "get_params")
+        return out
+
+    def grads(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(self._lib.prrtc_proposal_get_params(self.handle, None, out.ctypes.data_as(_f)), "get_params")
+        return out
+
+    def forward(self, occ, q_start, q_goal):
+        occ = np.ascontiguousarray(occ, np.uint8).reshape(-1, 4096)
+        B = occ.shape[0]
+        s, sp = _fa(np.asarray(q_start).reshape(B, self.dof))
+        g, gp = _fa(np.asarray(q_goal).reshape(B, self.dof))
+        out = np.zeros((B, self.head), np.float32)
+        _check(self._lib.prrtc_proposal_forward(self.handle, occ.ctypes.data_as(C.POINTER(C.c_uint8)), sp, gp, B,
+                                                out.ctypes.data_as(_f)), "prrtc_proposal_forward")
+        return out
+
+    def loss_and_grads(self, occ, q_start, q_goal, target):
+        occ = np.ascontiguousarray(occ, np.uint8).reshape(-1, 4096)
+        B = occ.shape[0]
+        s, sp = _fa(np.asarray(q_start).reshape(B, self.dof))
+        g, gp = _fa(np.asarray(q_goal).reshape(B, self.dof))
+        t, tp = _fa(np.asarray(target).reshape(B, self.dof))
+        loss = C.c_float()
+        _check(self._lib.prrtc_proposal_grads(self.handle, occ.ctypes.data_as(C.POINTER(C.c_uint8)), sp, gp, tp, B,
+                                              C.byref(loss)), "prrtc_proposal_grads")
+        return float(loss.value), self.grads()
+
+    def train(self, occ, scene_of, q_start, q_goal, target, batch, steps, lr=1e-3, seed=1):
+        occ = np.ascontiguousarray(occ, np.uint8).reshape(-1, 4096)
+        so, sop = _ia(scene_of)
+        N = len(so)
+        s, sp = _fa(np.asarray(q_start).reshape(N, self.dof))
+        g, gp = _fa(np.asarray(q_goal).reshape(N, self.dof))
+        t, tp = _fa(np.asarray(target).reshape(N, self.dof))
+        losses = np.zeros(max(steps, 1), np.float32)
+        _check(self._lib.prrtc_proposal_train(self.handle, occ.ctypes.data_as(C.POINTER(C.c_uint8)), occ.shape[0], sop,
+                                              sp, gp, tp, N, int(batch), int(steps), float(lr), int(seed),
+                                              losses.ctypes.data_as(_f)), "prrtc_proposal_train")
+        return losses[:steps]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.prrtc_proposal_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prrtc_occupancy(env: Env):
+    out = np.zeros(4096, np.uint8)
+    _check(lib().prrtc_occupancy(env.handle, out.ctypes.data_as(C.POINTER(C.c_uint8))), "prrtc_occupancy")
     return out
 
 

@@ -1,0 +1,199 @@
+"""Parity of the learned proposal's CUDA path with the FP64 oracle.
+
+The device keeps BF16 weights and activations and accumulates in FP32, so its
+forward output and gradients differ from the FP64 oracle (which uses the FP32
+master weights exactly) by BF16 rounding: about 2^-9 per element, compounding
+over four layers.  The bounds below are relative L2 errors of 2^-5 (forward)
+and 2^-4 (gradients, which pass through the forward activations twice).
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from oracle import oracle as O
+from paper_2503_06757_gb300 import prrtc as P
+from paper_2503_06757_gb300 import workload as W
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 2.0 ** -5
+GRAD_TOL = 2.0 ** -4
+F32 = lambda x: float(np.float32(x))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2503_06757_gb300 import build
+    build.build()
+
+
+def flat(params):
+    return np.concatenate([np.concatenate([Wm.ravel(), b]) for Wm, b in params]).astype(np.float32)
+
+
+def unflat(v, d):
+    out, k = [], 0
+    for (o, i) in M.shapes(d):
+        Wm = v[k:k + o * i].reshape(o, i).astype(np.float64)
+        k += o * i
+        b = v[k:k + o].astype(np.float64)
+        k += o
+        out.append((Wm, b))
+    return out
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def make_batch(robot, B, seed):
+    st = W.Stream(seed, 3)
+    scenes = [W.scene_shelf(1000 + k) for k in range(3)]
+    occ = np.stack([O.occupancy(scenes[k % 3]) for k in range(B)])
+    u = st.uniform(3 * B * robot.dof).reshape(3, B, robot.dof)
+    qs, qg, tg = (robot.lower + u[i] * (robot.upper - robot.lower) for i in range(3))
+    return occ, qs.astype(np.float32), qg.astype(np.float32), tg.astype(np.float32)
+
+
+def init(d, seed):
+    params = W.proposal_init(d, seed)
+    st = W.Stream(seed, 4)
+    return [(Wm, (0.05 * st.normal(len(b))).astype(np.float32).astype(np.float64)) for Wm, b in params]
+
+
+def oracle_x(robot, occ, qs, qg):
+    us = M.normalise(qs.astype(np.float64), robot.lower, robot.upper)
+    ug = M.normalise(qg.astype(np.float64), robot.lower, robot.upper)
+    return M.features(occ, us, ug)
+
+
+@pytest.mark.parametrize("name,B", [("arm7", 37), ("dual14", 256)])
+def test_forward_matches_oracle(name, B):
+    rb = W.ROBOTS[name]()
+    params = init(rb.dof, 11)
+    prop = P.Proposal(rb.dof, rb.lower, rb.upper, flat(params))
+    occ, qs, qg, _ = make_batch(rb, B, 5)
+    got = prop.forward(occ, qs, qg)
+    ref, _ = M.forward(params, oracle_x(rb, occ, qs, qg))
+    assert got.shape == ref.shape
+    assert rel(got, ref) <= FWD_TOL, rel(got, ref)
+
+
+@pytest.mark.parametrize("name,B", [("arm7", 40), ("dual14", 130)])
+def test_gradients_match_oracle(name, B):
+    rb = W.ROBOTS[name]()
+    d = rb.dof
+    params = init(d, 12)
+    prop = P.Proposal(d, rb.lower, rb.upper, flat(params))
+    occ, qs, qg, tg = make_batch(rb, B, 6)
+    loss, g = prop.loss_and_grads(occ, qs, qg, tg)
+    x = oracle_x(rb, occ, qs, qg)
+    u = M.normalise(tg.astype(np.float64), rb.lower, rb.upper)
+    ref_loss, ref_grads = M.loss_and_grads(params, x, u, d)
+    assert abs(loss - ref_loss) <= 2 ** -6 * abs(ref_loss), (loss, ref_loss)
+    got = unflat(g, d)
+    for li in range(4):
+        for which in (0, 1):
+            a, b = got[li][which], ref_grads[li][which]
+            r = rel(a, b)
+            cos = float(np.sum(a * b) / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+            assert r <= GRAD_TOL and cos >= 0.995, (li, which, r, cos)
+
+
+def test_adam_step_direction_matches_oracle():
+    rb = W.arm7()
+    d = rb.dof
+    params = init(d, 13)
+    prop = P.Proposal(d, rb.lower, rb.upper, flat(params))
+    occ, qs, qg, tg = make_batch(rb, 64, 7)
+    before = prop.params().astype(np.float64)
+    prop.train(occ, np.arange(64), qs, qg, tg, batch=64, steps=1, lr=1e-3, seed=1)
+    delta = prop.params().astype(np.float64) - before
+    x = oracle_x(rb, occ, qs, qg)
+    u = M.normalise(tg.astype(np.float64), rb.lower, rb.upper)
+    _, grads = M.loss_and_grads(params, x, u, d)
+    new = M.adam(params, grads, M.adam_state(params), lr=1e-3)
+    ref_delta = flat(new).astype(np.float64) - flat(params).astype(np.float64)
+    g = flat(grads).astype(np.float64)
+    strong = np.abs(g) > 1e-3 * np.max(np.abs(g))
+    agree = np.mean(np.sign(delta[strong]) == np.sign(ref_delta[strong]))
+    assert agree >= 0.99, agree
+    # first Adam step moves every strong coordinate by ~lr
+    assert np.median(np.abs(delta[strong])) == pytest.approx(1e-3, rel=0.05)
+
+
+def test_training_lowers_the_loss_on_a_fixed_batch():
+    rb = W.arm7()
+    prop = P.Proposal(rb.dof, rb.lower, rb.upper, flat(init(rb.dof, 14)))
+    occ, qs, qg, tg = make_batch(rb, 64, 8)
+    losses = prop.train(occ, np.arange(64), qs, qg, tg, batch=64, steps=80, lr=1e-3, seed=2)
+    assert np.all(np.isfinite(losses))
+    assert losses[-10:].mean() < losses[:5].mean() - 1.0, (losses[:5], losses[-10:])
+    assert prop.step == 80
+
+
+def test_checkpoint_round_trip(tmp_path):
+    rb = W.dual14()
+    prop = P.Proposal(rb.dof, rb.lower, rb.upper, flat(init(rb.dof, 15)))
+    occ, qs, qg, tg = make_batch(rb, 16, 9)
+    prop.train(occ, np.arange(16), qs, qg, tg, batch=16, steps=3, lr=1e-3)
+    path = tmp_path / "p.bin"
+    prop.save(path)
+    q = P.Proposal.load(path)
+    assert q.step == 3 and q.dof == 14
+    np.testing.assert_array_equal(q.params(), prop.params())
+    np.testing.assert_array_equal(q.forward(occ, qs, qg), prop.forward(occ, qs, qg))
+
+
+def test_occupancy_matches_oracle():
+    for seed in (1000, 1001, 2005):
+        sc = W.scene_shelf(seed) if seed < 2000 else W.scene_mixed(seed, 90)
+        got = P.prrtc_occupancy(P.make_env(sc))
+        want = O.occupancy(sc)
+        bad = np.nonzero(got != want)[0]
+        # any disagreement must sit on the 5 cm threshold (ambiguity band)
+        for v in bad:
+            i, j, k = v % 16, (v // 16) % 16, v // 256
+            p = np.array([-0.8 + 0.1 * (i + 0.5), -0.8 + 0.1 * (j + 0.5), 0.1 * (k + 0.5)])
+            sd = min([O.sd_box(b, p) for b in sc.boxes] + [O.sd_cyl(c, p) for c in sc.cylinders] +
+                     [O.sd_sph(s, p) for s in sc.spheres])
+            assert abs(sd - M.OCC_RADIUS) <= 1e-5, (v, sd)
+        assert 0 < want.sum() < 4096
+
+
+@pytest.fixture(scope="module")
+def c1_problems():
+    return W.problem_set("c1", 4, 1, O.accept)
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_serial_planner_with_mixture_matches_oracle(c1_problems, k):
+    pb = c1_problems[k]
+    gmm = W.random_mixture(7, 100 + k)
+    rb, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
+    prm = P.params(seed=3, mode=P.MODE_SERIAL, tree_capacity=1 << 14, learned_ratio=0.5)
+    g = P.prrtc_plan_batch([(rb, ev, pb.q_start, pb.q_goal, 3, 0, gmm)], prm)[0]
+    o = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=3, want_trees=True, tree_capacity=1 << 14,
+               range=1.0, resolution=F32(1 / 32), goal_bias=F32(0.05), gmm=gmm.astype(np.float64),
+               learned_ratio=F32(0.5))
+    if o["first_amb_iter"] != -1 and o["first_amb_iter"] < o["iterations"]:
+        pytest.skip(f"ambiguous decision at iteration {o['first_amb_iter']}")
+    assert g["status"] == o["status"] == 0
+    assert g["iterations"] == o["iterations"]
+    assert (g["nodes_a"], g["nodes_b"]) == (o["n_a"], o["n_b"])
+    np.testing.assert_allclose(g["path"], o["path"], atol=1e-4)
+
+
+def test_learned_batch_plans_with_device_inference(c1_problems):
+    rb7 = W.arm7()
+    prop = P.Proposal(7, rb7.lower, rb7.upper, flat(init(7, 16)))
+    items, props = [], []
+    for k, pb in enumerate(c1_problems):
+        items.append((P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 9, k))
+        props.append(prop if k % 2 == 0 else None)
+    res = P.prrtc_plan_batch_learned(items, props, P.params(learned_ratio=0.5))
+    for pb, r in zip(c1_problems, res):
+        assert r["status"] == P.SOLVED
+        bad, mc = O.revalidate(pb.robot, pb.scene, r["path"].astype(np.float64), F32(1 / 32) / 4)
+        assert bad == 0 or mc > -1e-3
