@@ -225,6 +225,51 @@ def oracle_sample(problems, budget_s=12.0, threads=None):
                 mean_cost=float(np.mean(costs)) if costs else None)
 
 
+# ------------------------------------------------------------------ learned proposal and serving
+
+def learned_section(args, P):
+    """Train the proposal on plain-planner solution paths (shelf scenes, 7-DoF) and
+    compare learned (50% mixture / 50% uniform) with plain sampling on held-out scenes."""
+    from paper_2503_06757_gb300 import learned as L
+    from paper_2503_06757_gb300 import workload as W
+    rb = W.arm7()
+    ds = L.build_dataset(rb, args.learned_scenes, args.learned_pairs, 100000)
+    prop, losses, tt = L.train(rb, ds, steps=args.learned_steps, batch=512)
+    held = L.build_dataset(rb, 30, 10, 900000)
+    untrained = L.train(rb, ds, steps=0)[0]
+    train = dict(paths=ds.paths, problems=ds.problems, samples=int(len(ds.target)), data_seconds=ds.seconds,
+                 steps=args.learned_steps, batch=512, train_seconds=tt,
+                 loss_first=float(np.mean(losses[:10])), loss_last=float(np.mean(losses[-10:])),
+                 heldout_nll=L.held_out_nll(prop, held), heldout_nll_untrained=L.held_out_nll(untrained, held))
+    ev = L.evaluate(rb, args.learned_eval_scenes, 1, 9000, prop, ratio=0.5)
+    return dict(workload="cubby shelf, 7-DoF arm; held-out scenes 9000.. (one problem each), Philox keys 1..3",
+                ratio=0.5, train=train, eval=ev,
+                note="TTFS includes the on-device inference (occupancy, features, 4 tensor-core GEMMs) "
+                     "that precedes planning"), prop
+
+
+def serving_section(args, P, proposals):
+    from paper_2503_06757_gb300 import serving as S
+    scenes = S.build_scenes(30, 12, 3000)
+    prm = P.params(max_iters=20000, tree_capacity=1 << 13, path_capacity=1 << 12, learned_ratio=0.5)
+    server = P.Server(prm, slice_us=300)
+    mover = S.ObstacleMover(scenes)
+    mover.start()
+    out = dict(workload="30 resident scenes (7/8/14-DoF in turn, 40-120 obstacles + 5 spheres moving at "
+                        "0.5 m/s, updated at 30 Hz), Poisson arrivals; learned proposal on the 7-DoF queries",
+               slice_us=300, slots=server.stats()["slots"])
+    try:
+        for rate in (200, 1000):
+            out[f"rate_{rate}"] = S.run_rate(server, scenes, rate, args.serve_seconds, seed=rate, proposals=proposals)
+    finally:
+        mover.stop_flag.set()
+        mover.join()
+        out["obstacle_updates"] = mover.ticks
+        out["slices"] = server.stats()["slices"]
+        server.close()
+    return out
+
+
 # ------------------------------------------------------------------ arms
 
 def run_reference(args):
@@ -382,6 +427,11 @@ def run_ours(args):
             frac=cc_ops / (kms * 1e-3) * 1e-9 / peak_gops, states=int(len(F)), kernel_ms=kms,
             states_per_s=len(F) / (kms * 1e-3), ops_per_state=cc_ops / len(F))
         extra["cpu_baseline"] = oracle_sample(probs, budget_s=args.cpu_budget)
+        prop = None
+        if not args.no_learned:
+            extra["learned"], prop = learned_section(args, P)
+        if not args.no_serving:
+            extra["serving"] = serving_section(args, P, {"arm7": prop} if prop is not None else None)
 
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -398,7 +448,7 @@ def run_ours(args):
                            "per launch / kernel time; peak = SMs x 128 lanes x max SM clock (issue bound)"),
         e2e=dict(value=total_states / wall_s, unit=UNIT, h2d_bytes_per_step=h2d // args.steps,
                  d2h_bytes_per_step=d2h // args.steps),
-        gpu_launches=launches, clocks=clk, learned=None,
+        gpu_launches=launches, clocks=clk, learned=None, serving=None,
     )
     line.update(extra)
     if rank == 0:
@@ -417,6 +467,13 @@ def main():
     ap.add_argument("--problems", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--learned-scenes", type=int, default=300)
+    ap.add_argument("--learned-pairs", type=int, default=40)
+    ap.add_argument("--learned-steps", type=int, default=4000)
+    ap.add_argument("--learned-eval-scenes", type=int, default=500)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -185,6 +185,8 @@ typedef struct prrtc_launch_stats {
   int64_t d2h_bytes;         /* device -> host bytes copied by the call                */
   int32_t kernels;           /* kernels the call launched                              */
   int32_t reserved_;
+  double prep_ms;            /* from the call's first device work to the setup kernel:
+                                learned-mixture inference and descriptor upload         */
 } prrtc_launch_stats;
 
 int prrtc_last_launch_stats(prrtc_launch_stats* out);
@@ -333,6 +335,55 @@ int prrtc_occupancy(const prrtc_env* env, uint8_t* out);
  * used with params->learned_ratio.  proposals may be null (plain planning). */
 int prrtc_plan_batch_learned(const prrtc_problem* problems, prrtc_proposal* const* proposals, int32_t n,
                              const prrtc_params* params, prrtc_path* out_paths, int32_t* out_status);
+
+/* ------------------------------------------------------------ serving loop */
+/* Continuous-batching request loop (not part of the paper).  Queries are
+ * submitted from any thread; a server thread admits them into free device
+ * slots (their number follows memory_budget_bytes), snapshots each query's
+ * environment at admission (later prrtc_env_update calls affect only later
+ * admissions), infers learned mixtures on the device, and runs the planner
+ * in resumable time slices of slice_us device microseconds over every
+ * occupied slot: queries that arrive while others plan join the next slice
+ * and their work overlaps on the device.  Finished queries are returned by
+ * prrtc_server_poll.  In PRRTC_MODE_SERIAL a query's result does not depend
+ * on what else is in flight. */
+typedef struct prrtc_server prrtc_server;
+
+typedef struct prrtc_server_config {
+  int32_t max_slots;           /* 0 = as many as memory_budget_bytes allows           */
+  int32_t slice_us;            /* device time slice between admissions (>= 10)         */
+  int64_t memory_budget_bytes; /* device memory for query slots (trees, paths, env)    */
+  prrtc_params params;         /* planner parameters for every query                    */
+} prrtc_server_config;
+
+typedef struct prrtc_server_stats {
+  int32_t slots;
+  int32_t active;
+  int64_t submitted, admitted, completed, pending, slices;
+  double busy_s;               /* host time spent in server rounds                     */
+  double uptime_s;
+} prrtc_server_stats;
+
+/* Defaults: 2 GiB budget, 500 us slices, prrtc_params_default with 8192 nodes
+ * per tree and 4096 waypoints per path. */
+void prrtc_server_config_default(prrtc_server_config* config);
+int prrtc_server_create(const prrtc_server_config* config, prrtc_server** out);
+/* Queue a query (copied; the handles must outlive it).  proposal (nullable,
+ * DoF of the robot) turns on learned sampling with params.learned_ratio; a
+ * proposal must not be used by another call at the same time. */
+int prrtc_server_submit(prrtc_server* server, const prrtc_problem* problem, prrtc_proposal* proposal,
+                        uint64_t* ticket);
+/* Up to max finished queries, oldest first: paths (free q with
+ * prrtc_path_free), tickets, latency from submission to completion and time
+ * spent waiting for a slot (host clock, ms); any output array may be null. */
+int prrtc_server_poll(prrtc_server* server, int32_t max, prrtc_path* paths, uint64_t* tickets, double* latency_ms,
+                      double* queue_ms, int32_t* n_out);
+/* Block until at least `completed` queries have finished or timeout_s passes
+ * (PRRTC_ERR_TIMEOUT). */
+int prrtc_server_wait(prrtc_server* server, int64_t completed, double timeout_s);
+int prrtc_server_get_stats(prrtc_server* server, prrtc_server_stats* out);
+/* Stops the loop (after the current slice) and frees everything. */
+void prrtc_server_destroy(prrtc_server* server);
 
 /* ------------------------------------------------------------ planning without allocation */
 /* The paper has no counterpart of this entry point; it exists for callers

@@ -38,6 +38,7 @@ static int cuda_fail(const char* what, cudaError_t e) {
 
 // ------------------------------------------------------------------ handles
 struct prrtc_env {
+  std::mutex mu;            // guards h_data against concurrent updates and snapshots
   int device = -1;
   float4* d_data = nullptr;
   std::vector<float4> h_data;
@@ -391,6 +392,7 @@ int prrtc_env_update(prrtc_env* env, const int32_t* ids, const prrtc_obstacle* o
   if (rc) return rc;
   if (c->device != env->device) return fail(PRRTC_ERR_INVALID_ARG, "env belongs to another device");
   std::lock_guard<std::mutex> lk(c->mu);
+  std::lock_guard<std::mutex> lk_env(env->mu);
   int lo = INT_MAX, hi = -1;
   for (int k = 0; k < n; ++k) {
     const int id = ids[k];
@@ -408,6 +410,20 @@ int prrtc_env_update(prrtc_env* env, const int32_t* ids, const prrtc_obstacle* o
   CK(cudaMemcpyAsync(env->d_data + lo, env->h_data.data() + lo, (size_t)(hi - lo) * sizeof(float4),
                      cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  return PRRTC_OK;
+}
+
+// Consistent copy of an environment's current obstacle blob into device
+// memory `dst` (at most max_f4 float4) on `stream`; *view describes the copy.
+// The host mirror is read under the env's lock before this returns.
+int prrtc_internal_env_snapshot(prrtc_env* env, float4* dst, int max_f4, EnvView* view, cudaStream_t stream) {
+  if (!env || !dst || !view) return PRRTC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(env->mu);
+  const int n = env->view().n_float4();
+  if (n > max_f4) return PRRTC_ERR_UNSUPPORTED;
+  if (n > 0) CK(cudaMemcpyAsync(dst, env->h_data.data(), (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, stream));
+  *view = env->view();
+  view->data = dst;
   return PRRTC_OK;
 }
 
@@ -569,6 +585,15 @@ int prrtc_internal_env_view(const prrtc_env* env, EnvView* view, int* device) {
 
 void prrtc_internal_set_error(const char* msg) { t_last_error = msg ? msg : ""; }
 
+int prrtc_internal_robot_view(const prrtc_robot* robot, const RobotDev** dev, const RobotHeader** header,
+                              int* device) {
+  if (!robot) return PRRTC_ERR_INVALID_ARG;
+  *dev = robot->d;
+  *header = &robot->h->h;
+  *device = robot->device;
+  return PRRTC_OK;
+}
+
 int prrtc_env_info(const prrtc_env* env, int32_t* counts4) {
   if (!env || !counts4) return fail(PRRTC_ERR_INVALID_ARG, "null argument");
   counts4[0] = env->n_aabb;
@@ -671,6 +696,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   std::lock_guard<std::mutex> lk(c->mu);
   if ((rc = ensure_arenas(c, n, params->tree_capacity, params->path_capacity))) return rc;
 
+  CK(cudaEventRecord(c->ev[3], c->stream));
   // learned mixtures: given by the caller (host) or inferred on the device
   bool any_gmm = false;
   for (int p = 0; p < n; ++p) any_gmm |= (problems[p].gmm != nullptr) || (proposals && proposals[p]);
@@ -840,10 +866,12 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     CK(cudaStreamSynchronize(c->stream));
   }
 
-  float setup_ms = 0.f, plan_ms = 0.f;
+  float setup_ms = 0.f, plan_ms = 0.f, prep_ms = 0.f;
   cudaEventElapsedTime(&setup_ms, c->ev[0], c->ev[1]);
   cudaEventElapsedTime(&plan_ms, c->ev[1], c->ev[2]);
+  cudaEventElapsedTime(&prep_ms, c->ev[3], c->ev[0]);
   prrtc_launch_stats L{};
+  L.prep_ms = prep_ms;
   L.kernel_ms = plan_ms;
   L.setup_ms = setup_ms;
   L.grid = cfg.grid;

@@ -29,6 +29,9 @@ struct PlanGlobals {
   int error;             // device-side error code (PRRTC_ERR_*), 0 = none
   int error_info;
   uint32_t learned_thr;  // learned-vs-uniform draw as a threshold on the top 24 bits of a Philox word
+  const int* active;     // problems of this launch as indices into the descriptors (null: 0..n-1)
+  unsigned long long slice_ns;  // 0 = run problems to completion; else stop starting iterations
+                                // this long after the launch start (problems resume next launch)
 };
 
 // Per-problem inputs (uploaded every call).
@@ -78,8 +81,9 @@ cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& host_h
                                 int n, uint8_t* valid, float* spheres, unsigned long long* counters, int* error,
                                 cudaStream_t stream);
 
+// idx (nullable, device): the problems to set up, as indices into desc/state.
 cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
-                         int max_env_f4, cudaStream_t stream);
+                         int max_env_f4, cudaStream_t stream, const int* idx = nullptr);
 
 struct PlanLaunch {
   int grid;
@@ -97,7 +101,8 @@ cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemSt
                         cudaStream_t stream);
 
 // Clear-list bookkeeping after a plan: rows each tree used, for the next setup.
-cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, int n, cudaStream_t stream);
+cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, int n, cudaStream_t stream,
+                                const int* idx = nullptr);
 
 // Copy every problem's path into one packed buffer; offsets[p]..offsets[p+1]
 // is problem p's float range (n + 1 entries, device memory).

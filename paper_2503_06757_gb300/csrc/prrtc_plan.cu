@@ -40,6 +40,11 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 
 __device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
 
+// Time slice of a resumable launch spent?
+__device__ __forceinline__ bool slice_over(const PlanGlobals* g) {
+  return g->slice_ns && globaltimer_ns() - g->t0 > g->slice_ns;
+}
+
 struct Local {
   unsigned long long edges = 0, edge_states = 0, nn_nodes = 0, iterations = 0, insert_fail = 0;
   WorkCount wc;
@@ -312,7 +317,9 @@ __device__ void worker(const Ctx& c, Local& lc) {
   for (;;) {
     int stop = 0, it = 0;
     if (lane == 0) {
-      stop = ld_volatile(&S->done) | ld_volatile(&S->solved);
+      // a spent time slice stops the worker before it takes an iteration
+      // ticket; the problem resumes in the next launch of a resumable batch
+      stop = ld_volatile(&S->done) | ld_volatile(&S->solved) | (slice_over(g) ? 1 : 0);
       if (!stop) it = atomicAdd(&S->iter, 1);
     }
     stop = __shfl_sync(kFull, stop, 0);
@@ -454,10 +461,12 @@ __device__ void worker(const Ctx& c, Local& lc) {
 
 __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
   const int P = g->n_problems;
+  if (slice_over(g)) return -1;
   const int t = atomicAdd(&g->cursor, 1);
-  if (g->mode == PRRTC_MODE_SERIAL) return t < P ? t : -1;
+  if (g->mode == PRRTC_MODE_SERIAL) return t < P ? (g->active ? g->active[t] : t) : -1;
   for (int k = 0; k < P; ++k) {
-    const int p = (t + k) % P;
+    const int i = (t + k) % P;
+    const int p = g->active ? g->active[i] : i;
     if (!ld_volatile(&states[p].done)) return p;
   }
   return -1;
@@ -582,10 +591,12 @@ __device__ void check_endpoints(const ProblemDesc* D, ProblemState* S, float* st
   }
 }
 
-__global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states) {
+__global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states,
+                             const int* __restrict__ idx) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const ProblemDesc* D = descs + blockIdx.x;
-  ProblemState* S = states + blockIdx.x;
+  const int p = idx ? idx[blockIdx.x] : blockIdx.x;
+  const ProblemDesc* D = descs + p;
+  ProblemState* S = states + p;
   const int dpad = D->dpad;
   for (int t = 0; t < 2; ++t) {
     const int rows = S->used_rows[t];
@@ -628,9 +639,11 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
 }
 
 // After the plan: record which rows were written so the next setup clears them.
-__global__ void record_usage_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states, int n) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+__global__ void record_usage_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states, int n,
+                                    const int* __restrict__ idx) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int p = idx ? idx[t] : t;
   const ProblemDesc* D = descs + p;
   ProblemState* S = states + p;
   S->used_rows[0] = min(S->count[0], D->cap);
@@ -650,14 +663,14 @@ __global__ void gather_paths_kernel(const ProblemDesc* __restrict__ descs, const
 }  // namespace
 
 cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
-                         int max_env_f4, cudaStream_t stream) {
+                         int max_env_f4, cudaStream_t stream, const int* idx) {
   (void)max_pairs;
   (void)max_env_f4;
   if (n <= 0) return cudaSuccess;
   const int smem = stage_bytes(max_spheres);
   cudaError_t e = cudaFuncSetAttribute(setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  setup_kernel<<<n, 256, smem, stream>>>(desc, state);
+  setup_kernel<<<n, 256, smem, stream>>>(desc, state, idx);
   return cudaGetLastError();
 }
 
@@ -702,9 +715,10 @@ cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemSt
   return cudaSuccess;
 }
 
-cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, int n, cudaStream_t stream) {
+cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, int n, cudaStream_t stream,
+                                const int* idx) {
   if (n <= 0) return cudaSuccess;
-  record_usage_kernel<<<(n + 127) / 128, 128, 0, stream>>>(desc, state, n);
+  record_usage_kernel<<<(n + 127) / 128, 128, 0, stream>>>(desc, state, n, idx);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,19 @@ class prrtc_launch_stats(C.Structure):
                 ("pair_tests", C.c_int64), ("fk_states", C.c_int64), ("nn_nodes", C.c_int64),
                 ("iterations", C.c_int64), ("grid", C.c_int32), ("block_threads", C.c_int32),
                 ("smem_bytes", C.c_int32), ("problems", C.c_int32), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("reserved_", C.c_int32)]
+                ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("reserved_", C.c_int32),
+                ("prep_ms", C.c_double)]
+
+
+class prrtc_server_config(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("slice_us", C.c_int32), ("memory_budget_bytes", C.c_int64),
+                ("params", prrtc_params)]
+
+
+class prrtc_server_stats(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("active", C.c_int32), ("submitted", C.c_int64), ("admitted", C.c_int64),
+                ("completed", C.c_int64), ("pending", C.c_int64), ("slices", C.c_int64), ("busy_s", C.c_double),
+                ("uptime_s", C.c_double)]
 
 
 class prrtc_problem(C.Structure):
@@ -78,6 +90,8 @@ EXPORTS = [
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
     "prrtc_proposal_forward", "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
     "prrtc_proposal_load", "prrtc_occupancy", "prrtc_plan_batch_learned",
+    "prrtc_server_config_default", "prrtc_server_create", "prrtc_server_submit", "prrtc_server_poll",
+    "prrtc_server_wait", "prrtc_server_get_stats", "prrtc_server_destroy",
 ]
 
 _lib = None
@@ -133,6 +147,14 @@ def lib():
     L.prrtc_occupancy.argtypes = [C.c_void_p, _u8]
     L.prrtc_plan_batch_learned.argtypes = [C.POINTER(prrtc_problem), C.POINTER(C.c_void_p), C.c_int32,
                                            C.POINTER(prrtc_params), C.POINTER(prrtc_path), _i]
+    L.prrtc_server_config_default.argtypes = [C.POINTER(prrtc_server_config)]
+    L.prrtc_server_create.argtypes = [C.POINTER(prrtc_server_config), C.POINTER(C.c_void_p)]
+    L.prrtc_server_submit.argtypes = [C.c_void_p, C.POINTER(prrtc_problem), C.c_void_p, C.POINTER(C.c_uint64)]
+    L.prrtc_server_poll.argtypes = [C.c_void_p, C.c_int32, C.POINTER(prrtc_path), C.POINTER(C.c_uint64),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), _i]
+    L.prrtc_server_wait.argtypes = [C.c_void_p, C.c_int64, C.c_double]
+    L.prrtc_server_get_stats.argtypes = [C.c_void_p, C.POINTER(prrtc_server_stats)]
+    L.prrtc_server_destroy.argtypes = [C.c_void_p]
     L.prrtc_plan_noalloc.argtypes = [C.c_void_p, C.c_void_p, _f, _f, C.POINTER(prrtc_params), _f, C.c_int32,
                                      C.POINTER(prrtc_path), C.c_void_p]
     _lib = L
@@ -537,3 +559,66 @@ def prrtc_gemm_bf16(a_ptr: int, b_ptr: int, M: int, N: int, K: int, bias_ptr: in
 
 def prrtc_gemm_error() -> int:
     return int(lib().prrtc_gemm_error())
+
+
+class Server:
+    """Continuous-batching request loop (prrtc_server_*)."""
+
+    def __init__(self, params: prrtc_params | None = None, slice_us: int = 500, memory_budget_bytes: int = 2 << 30,
+                 max_slots: int = 0):
+        self._lib = lib()
+        cfg = prrtc_server_config()
+        self._lib.prrtc_server_config_default(C.byref(cfg))
+        if params is not None:
+            cfg.params = params
+        cfg.slice_us = int(slice_us)
+        cfg.memory_budget_bytes = int(memory_budget_bytes)
+        cfg.max_slots = int(max_slots)
+        h = C.c_void_p()
+        _check(self._lib.prrtc_server_create(C.byref(cfg), C.byref(h)), "prrtc_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, robot: Robot, env: Env, q_start, q_goal, seed=1, problem_id=0, proposal=None, gmm=None):
+        keep = []
+        arr = _problem_array([(robot, env, q_start, q_goal, seed, problem_id) + ((gmm,) if gmm is not None else ())],
+                             keep)
+        t = C.c_uint64()
+        _check(self._lib.prrtc_server_submit(self.handle, arr, proposal.handle if proposal is not None else None,
+                                             C.byref(t)), "prrtc_server_submit")
+        return int(t.value)
+
+    def poll(self, max_n: int = 4096):
+        paths = (prrtc_path * max_n)()
+        tickets = (C.c_uint64 * max_n)()
+        lat = (C.c_double * max_n)()
+        que = (C.c_double * max_n)()
+        n = C.c_int32()
+        _check(self._lib.prrtc_server_poll(self.handle, max_n, paths, tickets, lat, que, C.byref(n)),
+               "prrtc_server_poll")
+        out = []
+        for k in range(n.value):
+            d = _path_dict(paths[k])
+            lib().prrtc_path_free(C.byref(paths[k]))
+            d.update(ticket=int(tickets[k]), latency_ms=float(lat[k]), queue_ms=float(que[k]))
+            out.append(d)
+        return out
+
+    def wait(self, completed: int, timeout_s: float = 60.0):
+        _check(self._lib.prrtc_server_wait(self.handle, int(completed), float(timeout_s)), "prrtc_server_wait")
+
+    def stats(self):
+        st = prrtc_server_stats()
+        _check(self._lib.prrtc_server_get_stats(self.handle, C.byref(st)), "prrtc_server_get_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.prrtc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -440,13 +440,18 @@ class MovingSpheres:
     rate_hz: float = 30.0
 
     def positions(self, k: int) -> np.ndarray:
+        return self.positions_track(k)[k]
+
+    def positions_track(self, n: int) -> np.ndarray:
+        """Centres after 0..n ticks, shape [n + 1, spheres, 3]."""
         st = Stream(self.seed, 99)
         p = self.centres0.copy()
         dt = 1.0 / self.rate_hz
-        n = p.shape[0]
-        head = st.normal(3 * n).reshape(n, 3)
-        for _ in range(k):
-            head = head + 0.3 * st.normal(3 * n).reshape(n, 3)
+        m = p.shape[0]
+        head = st.normal(3 * m).reshape(m, 3)
+        out = [_f32(p)]
+        for _ in range(n):
+            head = head + 0.3 * st.normal(3 * m).reshape(m, 3)
             v = head / np.linalg.norm(head, axis=1, keepdims=True) * self.speed
             p = p + v * dt
             lo = WORKSPACE_LO + self.radii[:, None]
@@ -456,7 +461,8 @@ class MovingSpheres:
             p = np.where(over, 2 * hi - p, p)
             p = np.where(under, 2 * lo - p, p)
             head = np.where(over | under, -head, head)
-        return _f32(p)
+            out.append(_f32(p))
+        return np.stack(out)
 
 
 def moving_spheres(seed: int, n: int = 5, bases=((0.0, 0.0, 0.0),)) -> MovingSpheres:

@@ -42,6 +42,8 @@ STRUCTS = {
     "prrtc_path": P.prrtc_path,
     "prrtc_launch_stats": P.prrtc_launch_stats,
     "prrtc_problem": P.prrtc_problem,
+    "prrtc_server_config": P.prrtc_server_config,
+    "prrtc_server_stats": P.prrtc_server_stats,
 }
 
 
