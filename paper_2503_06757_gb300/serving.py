@@ -97,7 +97,7 @@ def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int
     order = rng.permutation(len(pool))
     t0 = time.perf_counter()
     t_next = t0
-    k = 0
+    k = drawn = skipped = 0
     before = server.stats()["completed"]
     while True:
         now = time.perf_counter()
@@ -106,9 +106,16 @@ def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int
         if now < t_next:
             time.sleep(min(t_next - now, 0.0005))
             continue
-        si, qi = pool[order[k % len(pool)]]
-        sc = scenes[si]
-        qs, qg = sc.queries[qi]
+        # like a client that re-reads its sensors, only submit endpoints that are
+        # free against the obstacles as currently published
+        for _ in range(len(pool)):
+            si, qi = pool[order[drawn % len(pool)]]
+            drawn += 1
+            sc = scenes[si]
+            qs, qg = sc.queries[qi]
+            if P.prrtc_check_states(sc.rb, sc.env, np.stack([qs, qg])).all():
+                break
+            skipped += 1
         prop = proposals.get(sc.robot.name) if proposals else None
         server.submit(sc.rb, sc.env, qs, qg, seed=seed + k, problem_id=k, proposal=prop)
         k += 1
@@ -131,4 +138,5 @@ def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int
                 throughput_qps=len(res) / wall if wall > 0 else None,
                 latency_ms=dict(p50=pct(lat, 50), p95=pct(lat, 95), p99=pct(lat, 99), mean=float(lat.mean()) if len(lat) else None),
                 queue_ms=dict(p50=pct(que, 50), p99=pct(que, 99)),
-                success_rate=len(ok) / max(len(res), 1), endpoint_in_collision=in_coll)
+                success_rate=len(ok) / max(len(res), 1), endpoint_in_collision=in_coll,
+                skipped_blocked_endpoints=skipped)
