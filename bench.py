@@ -332,6 +332,10 @@ def run_ours(args):
         counts.append((ev.info(), pb.robot.dof, info["dpad"]))
         items.append((rb, ev, pb.q_start, pb.q_goal, 1, rank * args.problems + k))
     prm = P.params()
+    tuned = None
+    if not args.no_autotune:
+        prm, tuned_ms = P.prrtc_autotune(items, prm, trials=2)
+        tuned = dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, mean_ms=tuned_ms)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
@@ -393,15 +397,21 @@ def run_ours(args):
         # single-problem TTFS through prrtc_plan (host wall clock, env resident)
         c1 = c1_problem(accept)
         rb1, ev1 = P.make_robot(c1.robot), P.make_env(c1.scene)
+        p1 = P.params()
+        if not args.no_autotune:
+            p1, _ = P.prrtc_autotune([(rb1, ev1, c1.q_start, c1.q_goal, 101, 0)], p1, trials=8)
         for key in range(1, 4):
-            P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, P.params(seed=key))
+            p1.seed = key
+            P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, p1)
         tt, ok = [], 0
         for key in range(1, 101):
+            p1.seed = key
             t = time.perf_counter()
-            r = P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, P.params(seed=key))
+            r = P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, p1)
             tt.append((time.perf_counter() - t) * 1e3)
             ok += r["status"] == P.SOLVED
         extra["ttfs_single_c1_ms"] = dict(percentiles(tt), success_rate=ok / 100, keys=100,
+                                          launch=dict(blocks=p1.blocks, warps_per_block=p1.warps_per_block),
                                           workload="c1: 7-DoF arm, 8 random cuboids, one problem, keys 1..100")
         # collision-check microbenchmark: collision-free shelf states, every test runs
         pb = probs[0]
@@ -439,7 +449,7 @@ def run_ours(args):
         data="synthetic",
         config=dict(workload=WORKLOAD, problems=args.problems, problems_per_gpu=args.problems,
                     l2="flushed between steps (256 MiB write)", mode="async", range=1.0, resolution=1 / 32,
-                    goal_bias=0.05, max_iters=50000, grid=plan_grid, parallelism=f"problems sharded over {world} GPU(s)"),
+                    goal_bias=0.05, max_iters=50000, grid=plan_grid, autotuned=tuned, parallelism=f"problems sharded over {world} GPU(s)"),
         ttfs_us=dict(percentiles(ttfs), note="device time from launch start to each problem's solution"),
         success_rate=solved / (len(items) * args.steps), mean_cost=float(np.mean(costs)) if costs else None,
         roofline=dict(bound="alu", achieved=achieved_gops, peak=peak_gops, unit="Gop/s",
@@ -468,6 +478,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--learned-scenes", type=int, default=300)
     ap.add_argument("--learned-pairs", type=int, default=40)

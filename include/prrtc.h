@@ -270,6 +270,15 @@ typedef struct prrtc_problem {
 int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params,
                      prrtc_path* out_paths, int32_t* out_status);
 
+/* Autotuner: plan the given problems `trials` times (seeds varied) under
+ * several grid sizes and warps-per-block, keep the fastest (device time of
+ * setup + planner kernels) in *best and remember it for this device: later
+ * calls whose params leave blocks and warps_per_block at 0 use it for the
+ * same row width, obstacle-count bucket (64 float4) and batch-size bucket
+ * (power of two).  *best_ms (nullable) receives its mean time. */
+int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params* params, int32_t trials,
+                   prrtc_params* best, double* best_ms);
+
 /* ------------------------------------------------------------ learned proposal: dense layers */
 /* BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor memory)
  * for the dense layers of the learned sampling proposal:

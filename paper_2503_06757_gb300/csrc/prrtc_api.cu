@@ -91,6 +91,17 @@ struct DeviceCtx {
   float* d_gmm = nullptr;   // [slots][kGmmStride] learned mixtures
   float* h_gmm = nullptr;
   size_t gmm_cap = 0;
+  // CUDA graph of the launch sequence, keyed by everything it bakes in
+  struct GraphKey {
+    int n, grid, warps, smem, robot_bytes, env_bytes, stage_bytes, max_spheres, max_pairs, max_env, gen, head;
+    bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+  };
+  GraphKey gkey{};
+  cudaGraphExec_t gexec = nullptr;
+  int arena_gen = 0;
+  float* h_path_head = nullptr;  // first kHeadRows path rows of a single-problem call
+  // autotuned (blocks, warps) per (row width, obstacle bucket, batch-size bucket, mode)
+  std::map<uint64_t, std::pair<int, int>> tuned;
   // check_states scratch
   float* d_q = nullptr;
   uint8_t* d_valid = nullptr;
@@ -101,6 +112,8 @@ struct DeviceCtx {
   cudaEvent_t ev[4] = {};
   prrtc_launch_stats last{};
 };
+
+constexpr int kHeadRows = 512;
 
 DeviceCtx g_ctx[64];
 std::mutex g_init_mu;
@@ -123,6 +136,7 @@ int current_ctx(DeviceCtx** out) {
     CK(cudaMalloc(&c->d_error, sizeof(int)));
     CK(cudaMallocHost(&c->h_glob, sizeof(PlanGlobals)));
     CK(cudaMalloc(&c->d_glob, sizeof(PlanGlobals)));
+    CK(cudaMallocHost(&c->h_path_head, (size_t)kHeadRows * kMaxDof * sizeof(float)));
     c->ready = true;
   }
   *out = c;
@@ -196,7 +210,14 @@ int ensure_arenas(DeviceCtx* c, int slots, int cap, int path_cap) {
   c->slots = slots;
   c->cap = cap;
   c->path_cap = path_cap;
+  c->arena_gen++;
   return PRRTC_OK;
+}
+
+uint64_t tune_key(int dpad, int env_f4, int n, int mode) {
+  int nb = 0;
+  while ((1 << nb) < n) ++nb;
+  return ((uint64_t)dpad << 48) | ((uint64_t)((env_f4 + 63) / 64) << 32) | ((uint64_t)nb << 8) | (uint64_t)mode;
 }
 
 bool finite_all(const float* v, int n) {
@@ -654,6 +675,7 @@ int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const flo
   CK(cudaStreamSynchronize(c->stream));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+  cudaGetLastError();
   c->last = prrtc_launch_stats{};
   c->last.kernel_ms = ms;
   c->last.sphere_tests = (int64_t)cnt[0];
@@ -809,23 +831,70 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   G.cursor = 0;
   G.error = 0;
 
-  const PlanLaunch cfg = plan_launch_config(n, params->mode, params->blocks, params->warps_per_block, max_spheres,
-                                            max_pairs, max_env, c->sms);
+  int blocks = params->blocks, warps = params->warps_per_block;
+  if (blocks == 0 && warps == 0) {
+    auto it = c->tuned.find(tune_key(c->h_desc[0].dpad, max_env, n, params->mode));
+    if (it != c->tuned.end()) {
+      blocks = it->second.first;
+      warps = it->second.second;
+    }
+  }
+  const PlanLaunch cfg = plan_launch_config(n, params->mode, blocks, warps, max_spheres, max_pairs, max_env, c->sms);
   if (cfg.smem > 227 * 1024) return fail(PRRTC_ERR_UNSUPPORTED, "robot + environment exceed shared memory");
+  const int head_rows = (n == 1) ? std::min(kHeadRows, params->path_capacity) : 0;
 
-  CK(cudaMemcpyAsync(c->d_desc, c->h_desc, (size_t)n * sizeof(ProblemDesc), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->d_glob, c->h_glob, sizeof(PlanGlobals), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaEventRecord(c->ev[0], c->stream));
-  cudaError_t e = launch_setup(c->d_desc, c->d_state, n, max_spheres, max_pairs, max_env, c->stream);
-  if (e != cudaSuccess) return cuda_fail("setup launch", e);
-  CK(cudaEventRecord(c->ev[1], c->stream));
-  e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, c->stream);
-  if (e != cudaSuccess) return cuda_fail("plan launch", e);
-  CK(cudaEventRecord(c->ev[2], c->stream));
-  e = launch_record_usage(c->d_desc, c->d_state, n, c->stream);
-  if (e != cudaSuccess) return cuda_fail("usage launch", e);
-  CK(cudaMemcpyAsync(c->h_state, c->d_state, (size_t)n * sizeof(ProblemState), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(PlanGlobals), cudaMemcpyDeviceToHost, c->stream));
+  // The launch sequence: descriptors in, setup, planner, bookkeeping, results
+  // out (and, for one problem, the head of its path).  Replayed as a CUDA graph
+  // while its shape stays the same.
+  // Timing events become external event nodes when the sequence is captured.
+  auto enqueue = [&](bool capturing) -> int {
+    const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(cudaMemcpyAsync(c->d_desc, c->h_desc, (size_t)n * sizeof(ProblemDesc), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_glob, c->h_glob, sizeof(PlanGlobals), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventRecordWithFlags(c->ev[0], c->stream, ev_flags));
+    cudaError_t e = launch_setup(c->d_desc, c->d_state, n, max_spheres, max_pairs, max_env, c->stream);
+    if (e != cudaSuccess) return cuda_fail("setup launch", e);
+    CK(cudaEventRecordWithFlags(c->ev[1], c->stream, ev_flags));
+    e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, c->stream);
+    if (e != cudaSuccess) return cuda_fail("plan launch", e);
+    CK(cudaEventRecordWithFlags(c->ev[2], c->stream, ev_flags));
+    e = launch_record_usage(c->d_desc, c->d_state, n, c->stream);
+    if (e != cudaSuccess) return cuda_fail("usage launch", e);
+    CK(cudaMemcpyAsync(c->h_state, c->d_state, (size_t)n * sizeof(ProblemState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(PlanGlobals), cudaMemcpyDeviceToHost, c->stream));
+    if (head_rows)
+      CK(cudaMemcpyAsync(c->h_path_head, c->paths, (size_t)head_rows * c->h_desc[0].dof * sizeof(float),
+                         cudaMemcpyDeviceToHost, c->stream));
+    return PRRTC_OK;
+  };
+  static const bool no_graph = std::getenv("PRRTC_NO_GRAPH") != nullptr;
+  if (no_graph || (proposals && any_gmm)) {
+    if ((rc = enqueue(false))) return rc;
+  } else {
+    const DeviceCtx::GraphKey key{n, cfg.grid, cfg.warps, cfg.smem, cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes,
+                                  max_spheres, max_pairs, max_env, c->arena_gen, head_rows * c->h_desc[0].dof};
+    if (!c->gexec || !(c->gkey == key)) {
+      if (c->gexec) cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+      const int rc2 = enqueue(true);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+      if (rc2) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc2;
+      }
+      if (ec != cudaSuccess) return cuda_fail("graph capture", ec);
+      const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail("graph instantiate", ei);
+      }
+      c->gkey = key;
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
 
   // per-problem outcome and packed path offsets
@@ -845,7 +914,23 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     total += rows * c->h_desc[p].dof;
     c->h_offsets[p + 1] = total;
   }
-  if (total > 0) {
+  const bool from_head = head_rows > 0 && status[0] == PRRTC_SOLVED && c->h_state[0].path_n <= head_rows;
+  if (from_head) {
+    if ((size_t)total > c->packed_cap) {
+      cudaFreeHost(c->h_packed);
+      cudaFree(c->d_packed);
+      c->d_packed = nullptr;
+      c->h_packed = nullptr;
+      c->packed_cap = 0;
+      if (cudaMallocHost(&c->h_packed, (size_t)std::max(total, 1) * sizeof(float)) != cudaSuccess ||
+          cudaMalloc(&c->d_packed, (size_t)std::max(total, 1) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PRRTC_ERR_OOM, "path buffer allocation failed");
+      }
+      c->packed_cap = (size_t)std::max(total, 1);
+    }
+    std::memcpy(c->h_packed, c->h_path_head, (size_t)total * sizeof(float));
+  } else if (total > 0) {
     if ((size_t)total > c->packed_cap) {
       cudaFree(c->d_packed);
       cudaFreeHost(c->h_packed);
@@ -860,7 +945,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       c->packed_cap = (size_t)total;
     }
     CK(cudaMemcpyAsync(c->d_offsets, c->h_offsets, (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    e = launch_gather_paths(c->d_desc, c->d_offsets, n, c->d_packed, c->stream);
+    const cudaError_t e = launch_gather_paths(c->d_desc, c->d_offsets, n, c->d_packed, c->stream);
     if (e != cudaSuccess) return cuda_fail("gather launch", e);
     CK(cudaMemcpyAsync(c->h_packed, c->d_packed, (size_t)total * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -870,6 +955,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   cudaEventElapsedTime(&setup_ms, c->ev[0], c->ev[1]);
   cudaEventElapsedTime(&plan_ms, c->ev[1], c->ev[2]);
   cudaEventElapsedTime(&prep_ms, c->ev[3], c->ev[0]);
+  cudaGetLastError();  // timing is best effort: leave no error behind for later calls
   prrtc_launch_stats L{};
   L.prep_ms = prep_ms;
   L.kernel_ms = plan_ms;
@@ -879,10 +965,10 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   L.smem_bytes = cfg.smem;
   L.problems = n;
   L.h2d_bytes = (int64_t)n * (int64_t)sizeof(ProblemDesc) + (int64_t)sizeof(PlanGlobals) +
-                (total > 0 ? (int64_t)(n + 1) * (int64_t)sizeof(int) : 0);
+                (total > 0 && !from_head ? (int64_t)(n + 1) * (int64_t)sizeof(int) : 0);
   L.d2h_bytes = (int64_t)n * (int64_t)sizeof(ProblemState) + (int64_t)sizeof(PlanGlobals) +
-                (int64_t)total * (int64_t)sizeof(float);
-  L.kernels = 3 + (total > 0 ? 1 : 0);
+                (from_head ? (int64_t)head_rows * c->h_desc[0].dof : (int64_t)total) * (int64_t)sizeof(float);
+  L.kernels = 3 + (total > 0 && !from_head ? 1 : 0);
   const unsigned long long t0 = c->h_glob->t0;
   for (int p = 0; p < n; ++p) {
     const ProblemState& S = c->h_state[p];
@@ -937,6 +1023,64 @@ int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_param
 int prrtc_plan_batch_learned(const prrtc_problem* problems, prrtc_proposal* const* proposals, int32_t n,
                              const prrtc_params* params, prrtc_path* out_paths, int32_t* out_status) {
   return plan_batch_impl(problems, n, params, proposals, out_paths, out_status);
+}
+
+int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params* params, int32_t trials,
+                   prrtc_params* best, double* best_ms) {
+  if (!problems || n < 1 || !params || trials < 1 || !best) return fail(PRRTC_ERR_INVALID_ARG, "bad autotune arguments");
+  int rc = validate_params(params);
+  if (rc) return rc;
+  DeviceCtx* c = nullptr;
+  if ((rc = current_ctx(&c))) return rc;
+  int resident = 0;
+  {
+    // one wave of resident blocks for 4 warps, the default grid of a batch
+    const RobotHeader& H = problems[0].robot->h->h;
+    int max_env = 0;
+    for (int p = 0; p < n; ++p) max_env = std::max(max_env, problems[p].env->view().n_float4());
+    resident = plan_launch_config(n, params->mode, 0, 4, H.n_spheres, H.n_pairs, max_env, c->sms).grid;
+    if (n == 1) resident = c->sms * 4;
+  }
+  std::vector<std::pair<int, int>> cands;
+  const int warp_opts[3] = {2, 4, 8};
+  for (int w : warp_opts) {
+    if (params->mode == PRRTC_MODE_SERIAL && w != 1) continue;
+    if (n == 1) {
+      for (int workers : {64, 128, 256, 512, 1024}) cands.emplace_back(std::max(1, workers / w), w);
+    } else {
+      const int full = std::max(1, resident * 4 / w);
+      cands.emplace_back(std::max(1, full / 2), w);
+      cands.emplace_back(full, w);
+    }
+  }
+  if (params->mode == PRRTC_MODE_SERIAL) cands.emplace_back(0, 1);
+  std::vector<prrtc_problem> pb(problems, problems + n);
+  double best_t = 1e30;
+  std::pair<int, int> best_c{0, 0};
+  for (auto cand : cands) {
+    prrtc_params q = *params;
+    q.blocks = cand.first;
+    q.warps_per_block = cand.second;
+    double tot = 0.0;
+    for (int t = 0; t < trials; ++t) {
+      for (int p = 0; p < n; ++p) pb[p].seed = problems[p].seed + 7919ull * (uint64_t)(t + 1);
+      if ((rc = plan_batch_impl(pb.data(), n, &q, nullptr, nullptr, nullptr))) return rc;
+      tot += c->last.kernel_ms + c->last.setup_ms;
+    }
+    if (tot / trials < best_t) {
+      best_t = tot / trials;
+      best_c = cand;
+    }
+  }
+  *best = *params;
+  best->blocks = best_c.first;
+  best->warps_per_block = best_c.second;
+  if (best_ms) *best_ms = best_t;
+  int max_env = 0;
+  for (int p = 0; p < n; ++p) max_env = std::max(max_env, problems[p].env->view().n_float4());
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->tuned[tune_key(problems[0].robot->h->h.dpad, max_env, n, params->mode)] = best_c;
+  return PRRTC_OK;
 }
 
 int prrtc_debug_tree(int32_t problem, int32_t tree, float* nodes, int32_t* parents, int32_t cap, int32_t* out_n) {

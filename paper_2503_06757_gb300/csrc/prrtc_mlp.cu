@@ -436,6 +436,7 @@ int check_gemm_error() {
 int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, const float* qs_host,
                                      const float* qg_host, int B, float* const* gmm_rows, cudaStream_t stream) {
   if (!p || B <= 0) return PRRTC_ERR_INVALID_ARG;
+  cudaGetLastError();
   const int rows = (B + 7) & ~7;
   int rc;
   if ((rc = ensure_scratch(p, rows))) return rc;
@@ -466,6 +467,7 @@ extern "C" {
 
 int prrtc_proposal_create(int32_t dof, const float* lower, const float* upper, const float* params,
                           prrtc_proposal** out) {
+  cudaGetLastError();  // start from a clean error state
   if (!out || dof < 1 || dof > kMaxDof || !lower || !upper) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
   *out = nullptr;
   int dev = -1, count = 0;
@@ -554,6 +556,7 @@ int prrtc_proposal_get_params(const prrtc_proposal* p, float* params, float* gra
 
 int prrtc_proposal_forward(prrtc_proposal* p, const uint8_t* occ, const float* q_start, const float* q_goal,
                            int32_t B, float* out) {
+  cudaGetLastError();  // start from a clean error state
   if (!p || !occ || !q_start || !q_goal || !out || B < 1) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
   const int rows = (B + 7) & ~7;
   int rc;
@@ -602,6 +605,7 @@ static int step_on_rows_direct(prrtc_proposal* p, int B, float* loss) {
 
 int prrtc_proposal_grads(prrtc_proposal* p, const uint8_t* occ, const float* q_start, const float* q_goal,
                          const float* target, int32_t B, float* loss) {
+  cudaGetLastError();  // start from a clean error state
   if (!p || !occ || !q_start || !q_goal || !target || B < 1) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
   const int rows = (B + 7) & ~7;
   int rc;
@@ -615,6 +619,7 @@ int prrtc_proposal_grads(prrtc_proposal* p, const uint8_t* occ, const float* q_s
 int prrtc_proposal_train(prrtc_proposal* p, const uint8_t* occ, int32_t n_scenes, const int32_t* scene_of,
                          const float* q_start, const float* q_goal, const float* target, int32_t n_samples,
                          int32_t batch, int32_t steps, float lr, uint64_t seed, float* losses) {
+  cudaGetLastError();  // start from a clean error state
   if (!p || !occ || n_scenes < 1 || !scene_of || !q_start || !q_goal || !target || n_samples < 1 || batch < 1 ||
       steps < 0 || !(lr > 0.f))
     return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");

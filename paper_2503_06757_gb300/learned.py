@@ -155,7 +155,7 @@ def evaluate(robot: W.Robot, n_scenes: int, pairs_per_scene: int, seed0: int, pr
     items = [(rb, envs[k], s, g, 0, i) for i, (k, s, g) in enumerate(probs)]
     out = {}
     for name in ("plain", "learned"):
-        ttfs, ok, iters, cost, dev_ms = [], 0, [], [], 0.0
+        ttfs, ok, iters, cost, dev_ms, prep_ms = [], 0, [], [], 0.0, 0.0
         for key in keys:
             its = [it[:4] + (key, it[5]) for it in items]
             if name == "plain":
@@ -167,6 +167,7 @@ def evaluate(robot: W.Robot, n_scenes: int, pairs_per_scene: int, seed0: int, pr
                 res = P.prrtc_plan_batch_learned(its, [prop] * len(its), prm)
             st = P.prrtc_last_launch_stats()
             dev_ms += st["kernel_ms"] + st["setup_ms"] + st["prep_ms"]
+            prep_ms += st["prep_ms"]
             for r in res:
                 if r["status"] == P.SOLVED:
                     ok += 1
@@ -179,5 +180,6 @@ def evaluate(robot: W.Robot, n_scenes: int, pairs_per_scene: int, seed0: int, pr
                          ttfs_us_p95=float(np.percentile(ttfs, 95)) if ttfs else None,
                          iterations_mean=float(np.mean(iters)) if iters else None,
                          cost_mean=float(np.mean(cost)) if cost else None, device_ms=dev_ms / len(keys),
+                         prep_ms=prep_ms / len(keys),
                          problems=len(items), keys=len(keys))
     return out

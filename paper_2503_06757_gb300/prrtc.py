@@ -91,7 +91,7 @@ EXPORTS = [
     "prrtc_proposal_forward", "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
     "prrtc_proposal_load", "prrtc_occupancy", "prrtc_plan_batch_learned",
     "prrtc_server_config_default", "prrtc_server_create", "prrtc_server_submit", "prrtc_server_poll",
-    "prrtc_server_wait", "prrtc_server_get_stats", "prrtc_server_destroy",
+    "prrtc_server_wait", "prrtc_server_get_stats", "prrtc_server_destroy", "prrtc_autotune",
 ]
 
 _lib = None
@@ -155,6 +155,8 @@ def lib():
     L.prrtc_server_wait.argtypes = [C.c_void_p, C.c_int64, C.c_double]
     L.prrtc_server_get_stats.argtypes = [C.c_void_p, C.POINTER(prrtc_server_stats)]
     L.prrtc_server_destroy.argtypes = [C.c_void_p]
+    L.prrtc_autotune.argtypes = [C.POINTER(prrtc_problem), C.c_int32, C.POINTER(prrtc_params), C.c_int32,
+                                 C.POINTER(prrtc_params), C.POINTER(C.c_double)]
     L.prrtc_plan_noalloc.argtypes = [C.c_void_p, C.c_void_p, _f, _f, C.POINTER(prrtc_params), _f, C.c_int32,
                                      C.POINTER(prrtc_path), C.c_void_p]
     _lib = L
@@ -622,3 +624,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def prrtc_autotune(problems, prm: prrtc_params | None = None, trials: int = 3):
+    """Fastest (blocks, warps_per_block) for these problems; remembered by the library."""
+    prm = prm or prrtc_params_default()
+    keep = []
+    n = len(problems)
+    arr = _problem_array(problems, keep)
+    best = prrtc_params()
+    ms = C.c_double()
+    _check(lib().prrtc_autotune(arr, n, C.byref(prm), int(trials), C.byref(best), C.byref(ms)), "prrtc_autotune")
+    return best, float(ms.value)
