@@ -30,36 +30,80 @@ namespace {
 
 constexpr int kGrid = 16, kVox = kGrid * kGrid * kGrid, kQPad = 32, kIn = kVox + 2 * kQPad, kK = 8;
 constexpr int kHid0 = 1024, kHid1 = 512, kHid2 = 512;
-constexpr float kOrigin[3] = {-0.8f, -0.8f, 0.0f};
 constexpr float kCell = 0.1f, kOccRadius = 0.05f;
 constexpr float kLogSigMin = -5.f, kLogSigMax = 2.f;
 
 int head_pad(int dof) { return ((kK * (1 + 2 * dof) + 127) / 128) * 128; }
 
 // ------------------------------------------------------------------ kernels
-// Voxel (i, j, k) -> index i + 16 j + 256 k is occupied iff its centre is
-// closer than 5 cm to an obstacle (a 5 cm sphere there would collide).
-__global__ void occupancy_kernel(EnvView env, uint8_t* __restrict__ out) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= kVox) return;
-  const int i = v % kGrid, j = (v / kGrid) % kGrid, k = v / (kGrid * kGrid);
-  const float px = kOrigin[0] + (i + 0.5f) * kCell;
-  const float py = kOrigin[1] + (j + 0.5f) * kCell;
-  const float pz = kOrigin[2] + (k + 0.5f) * kCell;
-  out[v] = sphere_hits_env(px, py, pz, kOccRadius, env.data, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph) ? 1 : 0;
+// Occupancy grids of B environments, scattered per obstacle: voxel
+// (i, j, k) -> index i + 16 j + 256 k is occupied iff its centre is closer
+// than 5 cm to an obstacle (a 5 cm sphere there would collide).  One warp per
+// obstacle visits only the voxels inside the obstacle's bounding box grown by
+// 5 cm and applies the exact primitive test; grids must start zeroed (all
+// writers store 1, so overlapping obstacles need no ordering).  blockIdx.y
+// selects the environment.
+__device__ __forceinline__ float grid_origin(int axis) { return axis < 2 ? -0.8f : 0.0f; }
+__device__ __forceinline__ int vox_lo(float x, int axis) {
+  return max(0, (int)floorf((x - grid_origin(axis)) / kCell - 0.5f));
+}
+__device__ __forceinline__ int vox_hi(float x, int axis) {
+  return min(kGrid - 1, (int)ceilf((x - grid_origin(axis)) / kCell - 0.5f));
 }
 
-// Occupancy grids of B environments (one grid per blockIdx.y).
-__global__ void occupancy_batch_kernel(const EnvView* __restrict__ envs, uint8_t* __restrict__ out) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= kVox) return;
+__global__ void occupancy_scatter_kernel(const EnvView* __restrict__ envs, uint8_t* __restrict__ out) {
   const EnvView env = envs[blockIdx.y];
-  const int i = v % kGrid, j = (v / kGrid) % kGrid, k = v / (kGrid * kGrid);
-  const float px = kOrigin[0] + (i + 0.5f) * kCell;
-  const float py = kOrigin[1] + (j + 0.5f) * kCell;
-  const float pz = kOrigin[2] + (k + 0.5f) * kCell;
-  out[(size_t)blockIdx.y * kVox + v] =
-      sphere_hits_env(px, py, pz, kOccRadius, env.data, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph) ? 1 : 0;
+  uint8_t* grid = out + (size_t)blockIdx.y * kVox;
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  const int n_obs = env.n_aabb + env.n_obb + env.n_cyl + env.n_sph;
+  for (int o = (int)(blockIdx.x * warps + (threadIdx.x >> 5)); o < n_obs; o += gridDim.x * warps) {
+    // locate obstacle o in the blob and bound it
+    EnvView one{};
+    float3 c, e;
+    const float m = kOccRadius;
+    if (o < env.n_aabb) {
+      one.data = env.data + 2 * o;
+      one.n_aabb = 1;
+      const float4 a = one.data[0], h = one.data[1];
+      c = make_float3(a.x, a.y, a.z);
+      e = make_float3(h.x + m, h.y + m, h.z + m);
+    } else if (o < env.n_aabb + env.n_obb) {
+      one.data = env.data + 2 * env.n_aabb + 5 * (o - env.n_aabb);
+      one.n_obb = 1;
+      const float4 a = one.data[0], h = one.data[1], r0 = one.data[2], r1 = one.data[3], r2 = one.data[4];
+      c = make_float3(a.x, a.y, a.z);
+      // world half extents of the rotated box: sum_j |R[k][j]| h_j (r_j = column j of R)
+      e = make_float3(fabsf(r0.x) * h.x + fabsf(r1.x) * h.y + fabsf(r2.x) * h.z + m,
+                      fabsf(r0.y) * h.x + fabsf(r1.y) * h.y + fabsf(r2.y) * h.z + m,
+                      fabsf(r0.z) * h.x + fabsf(r1.z) * h.y + fabsf(r2.z) * h.z + m);
+    } else if (o < env.n_aabb + env.n_obb + env.n_cyl) {
+      one.data = env.data + 2 * env.n_aabb + 5 * env.n_obb + 2 * (o - env.n_aabb - env.n_obb);
+      one.n_cyl = 1;
+      const float4 a = one.data[0], ax = one.data[1];
+      c = make_float3(a.x, a.y, a.z);
+      const float rb = sqrtf(a.w * a.w + ax.w * ax.w) + m;
+      e = make_float3(rb, rb, rb);
+    } else {
+      one.data = env.data + 2 * env.n_aabb + 5 * env.n_obb + 2 * env.n_cyl + (o - env.n_aabb - env.n_obb - env.n_cyl);
+      one.n_sph = 1;
+      const float4 a = one.data[0];
+      c = make_float3(a.x, a.y, a.z);
+      e = make_float3(a.w + m, a.w + m, a.w + m);
+    }
+    const int i0 = vox_lo(c.x - e.x, 0), i1 = vox_hi(c.x + e.x, 0);
+    const int j0 = vox_lo(c.y - e.y, 1), j1 = vox_hi(c.y + e.y, 1);
+    const int k0 = vox_lo(c.z - e.z, 2), k1 = vox_hi(c.z + e.z, 2);
+    if (i1 < i0 || j1 < j0 || k1 < k0) continue;
+    const int ni = i1 - i0 + 1, nj = j1 - j0 + 1, nk = k1 - k0 + 1;
+    for (int t = lane; t < ni * nj * nk; t += 32) {
+      const int i = i0 + t % ni, j = j0 + (t / ni) % nj, k = k0 + t / (ni * nj);
+      const float px = grid_origin(0) + (i + 0.5f) * kCell;
+      const float py = grid_origin(1) + (j + 0.5f) * kCell;
+      const float pz = grid_origin(2) + (k + 0.5f) * kCell;
+      if (sphere_hits_env(px, py, pz, kOccRadius, one.data, one.n_aabb, one.n_obb, one.n_cyl, one.n_sph))
+        grid[i + kGrid * j + kGrid * kGrid * k] = 1;
+    }
+  }
 }
 
 // One feature row per sample (rows past B are zero): occupancy of the
@@ -449,7 +493,8 @@ int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, con
   MCK(cudaMemcpyAsync(p->gmm_rows, gmm_rows, (size_t)B * sizeof(float*), cudaMemcpyHostToDevice, p->stream));
   MCK(cudaMemcpyAsync(p->qs, qs_host, (size_t)B * p->dof * 4, cudaMemcpyHostToDevice, p->stream));
   MCK(cudaMemcpyAsync(p->qg, qg_host, (size_t)B * p->dof * 4, cudaMemcpyHostToDevice, p->stream));
-  occupancy_batch_kernel<<<dim3((kVox + 255) / 256, B), 256, 0, p->stream>>>(p->envs, p->occ);
+  MCK(cudaMemsetAsync(p->occ, 0, (size_t)B * kVox, p->stream));
+  occupancy_scatter_kernel<<<dim3(4, B), 256, 0, p->stream>>>(p->envs, p->occ);
   features_kernel<<<rows, 256, 0, p->stream>>>(p->occ, nullptr, nullptr, p->qs, p->qg, p->d_lims,
                                                p->d_lims + kMaxDof, B, p->dof, p->x16);
   if ((rc = forward_rows(p, rows))) return rc;
@@ -665,10 +710,21 @@ int prrtc_occupancy(const prrtc_env* env, uint8_t* out) {
   int rc = prrtc_internal_env_view(env, &ev, &dev);
   if (rc) return rc;
   uint8_t* d = nullptr;
+  EnvView* dv = nullptr;
   MCK(cudaMalloc(&d, kVox));
-  occupancy_kernel<<<(kVox + 255) / 256, 256>>>(ev, d);
-  cudaError_t e = cudaMemcpy(out, d, kVox, cudaMemcpyDeviceToHost);
+  if (cudaMalloc(&dv, sizeof(EnvView)) != cudaSuccess) {
+    cudaFree(d);
+    return mlp_fail(PRRTC_ERR_OOM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(dv, &ev, sizeof(EnvView), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(d, 0, kVox);
+  if (e == cudaSuccess) {
+    occupancy_scatter_kernel<<<dim3(4, 1), 256>>>(dv, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d, kVox, cudaMemcpyDeviceToHost);
   cudaFree(d);
+  cudaFree(dv);
   if (e != cudaSuccess) return mlp_fail(PRRTC_ERR_CUDA, cudaGetErrorString(e));
   return PRRTC_OK;
 }
