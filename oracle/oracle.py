@@ -6,8 +6,9 @@ own shared library with gcc and never touches the CUDA path.
 
 Functions follow pRRTC (Huang et al. 2025): Alg. 1 (top-level loop), Alg. 2
 (pEXTEND), Sec. III-A (sphere-model collision checking), Sec. III-C (nearest
-neighbour); sampling uses Philox4x32-10 (Salmon et al., SC'11) in place of the
-paper's Halton sequences.
+neighbour); sampling uses Philox4x32-10 (Salmon et al., SC'11) or the paper's Halton
+sequence (Sec. IV-A); dynamic-domain sampling (Yershova et al. 2005, adaptive
+radius of Jaillet et al. 2005) is the heuristic the paper adds to Alg. 1.
 """
 from __future__ import annotations
 
@@ -48,6 +49,8 @@ class OrcParams(C.Structure):
         ("amb_band", C.c_double), ("amb_rel", C.c_double), ("seed", C.c_uint64),
         ("problem", C.c_uint32), ("max_iters", C.c_int32), ("tree_capacity", C.c_int32),
         ("path_capacity", C.c_int32), ("gmm", _PD), ("learned_ratio", C.c_double),
+        ("sampler", C.c_int32), ("halton_offset", C.c_uint32), ("dd_radius", C.c_double),
+        ("dd_alpha", C.c_double), ("dd_min_radius", C.c_double),
     ]
 
 
@@ -57,8 +60,8 @@ class OrcResult(C.Structure):
         ("join_a", C.c_int32), ("join_b", C.c_int32), ("path_n", C.c_int32),
         ("first_amb_iter", C.c_int32), ("first_amb_kind", C.c_int32), ("pad_", C.c_int32),
         ("cost", C.c_double), ("edges_checked", C.c_int64), ("states_checked", C.c_int64),
-        ("edge_states", C.c_int64), ("nodes_a", _PD), ("parent_a", _PI), ("nodes_b", _PD),
-        ("parent_b", _PI), ("path", _PD),
+        ("edge_states", C.c_int64), ("dd_rejected", C.c_int64), ("nodes_a", _PD), ("parent_a", _PI),
+        ("nodes_b", _PD), ("parent_b", _PI), ("path", _PD), ("radius_a", _PD), ("radius_b", _PD),
     ]
 
 
@@ -191,6 +194,12 @@ def sample_learned(robot, seed, problem, it, goal_bias, gmm, learned_ratio, amb_
     return int(kind), q, bool(amb.value)
 
 
+def halton(index, dim):
+    u = np.zeros(dim)
+    lib().orc_halton(C.c_uint32(index), C.c_int32(dim), u.ctypes.data_as(_PD))
+    return u
+
+
 def occupancy(scene, origin=(-0.8, -0.8, 0.0), cell=0.1, n=16, radius=0.05):
     e = make_env(scene)
     o = np.ascontiguousarray(origin, dtype=np.float64)
@@ -261,7 +270,9 @@ def accept(robot, scene, Q):
 
 DEFAULT_PARAMS = dict(range=1.0, resolution=1.0 / 32.0, goal_bias=0.05, amb_band=1e-5, amb_rel=1e-5,
                       seed=1, problem=0, max_iters=50000, tree_capacity=1 << 16, path_capacity=1 << 14,
-                      gmm=None, learned_ratio=0.5)
+                      gmm=None, learned_ratio=0.5, sampler=0, halton_offset=0, dd_radius=0.0,
+                      dd_alpha=0.0, dd_min_radius=0.0)
+SAMPLER_PHILOX, SAMPLER_HALTON = 0, 1
 
 
 def _params(keep=None, **kw):
@@ -270,7 +281,10 @@ def _params(keep=None, **kw):
     prm = OrcParams(range=p["range"], resolution=p["resolution"], goal_bias=p["goal_bias"],
                     amb_band=p["amb_band"], amb_rel=p["amb_rel"], seed=int(p["seed"]),
                     problem=int(p["problem"]), max_iters=int(p["max_iters"]),
-                    tree_capacity=int(p["tree_capacity"]), path_capacity=int(p["path_capacity"]))
+                    tree_capacity=int(p["tree_capacity"]), path_capacity=int(p["path_capacity"]),
+                    sampler=int(p["sampler"]), halton_offset=int(p["halton_offset"]),
+                    dd_radius=float(p["dd_radius"]), dd_alpha=float(p["dd_alpha"]),
+                    dd_min_radius=float(p["dd_min_radius"]))
     g = p.get("gmm")
     if g is not None:
         g = np.ascontiguousarray(g, dtype=np.float64)
@@ -287,15 +301,18 @@ def _result_dict(res, d, trees=None, path=None):
                join_a=int(res.join_a), join_b=int(res.join_b), cost=float(res.cost),
                path_n=int(res.path_n), first_amb_iter=int(res.first_amb_iter),
                first_amb_kind=int(res.first_amb_kind), edges_checked=int(res.edges_checked),
-               states_checked=int(res.states_checked), edge_states=int(res.edge_states))
+               states_checked=int(res.states_checked), edge_states=int(res.edge_states),
+               dd_rejected=int(res.dd_rejected))
     if path is not None:
         out["path"] = path[: min(out["path_n"], path.shape[0])].copy()
     if trees is not None:
-        na, pa, nb, pb = trees
+        na, pa, nb, pb, ra, rb = trees
         out["nodes_a"] = na[: out["n_a"]].copy()
         out["parent_a"] = pa[: out["n_a"]].copy()
         out["nodes_b"] = nb[: out["n_b"]].copy()
         out["parent_b"] = pb[: out["n_b"]].copy()
+        out["radius_a"] = ra[: out["n_a"]].copy()
+        out["radius_b"] = rb[: out["n_b"]].copy()
     return out
 
 
@@ -310,9 +327,11 @@ def plan(robot, scene, q_start, q_goal, want_trees=False, **kw):
     trees = None
     if want_trees:
         cap = prm.tree_capacity
-        trees = (np.zeros((cap, d)), np.zeros(cap, np.int32), np.zeros((cap, d)), np.zeros(cap, np.int32))
+        trees = (np.zeros((cap, d)), np.zeros(cap, np.int32), np.zeros((cap, d)), np.zeros(cap, np.int32),
+                 np.zeros(cap), np.zeros(cap))
         res.nodes_a, res.parent_a = trees[0].ctypes.data_as(_PD), trees[1].ctypes.data_as(_PI)
         res.nodes_b, res.parent_b = trees[2].ctypes.data_as(_PD), trees[3].ctypes.data_as(_PI)
+        res.radius_a, res.radius_b = trees[4].ctypes.data_as(_PD), trees[5].ctypes.data_as(_PD)
     s, sp = _d(q_start)
     g, gp = _d(q_goal)
     lib().orc_plan(C.byref(r), C.byref(e), sp, gp, C.byref(prm), C.byref(res))

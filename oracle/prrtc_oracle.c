@@ -134,6 +134,23 @@ int orc_sample_learned(const orc_robot* r, uint64_t seed, uint32_t problem, uint
   return 0;
 }
 
+/* Halton (1960): coordinate j of point `index` is the radical inverse of index
+ * in the j-th prime base.  Written as the mirrored digit string: with index =
+ * sum_k d_k b^k (m digits), the value is (sum_k d_k b^(m-1-k)) / b^m, formed
+ * exactly in integers and divided once. */
+void orc_halton(uint32_t index, int32_t dim, double* u) {
+  static const uint32_t primes[16] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53};
+  for (int32_t j = 0; j < dim && j < 16; ++j) {
+    const uint64_t b = primes[j];
+    uint64_t num = 0, den = 1;
+    for (uint64_t i = index; i > 0; i /= b) {
+      num = num * b + i % b;
+      den *= b;
+    }
+    u[j] = (double)num / (double)den;
+  }
+}
+
 void orc_occupancy(const orc_env* e, const double origin[3], double cell, int32_t n, double radius,
                    uint8_t* out) {
   for (int32_t k = 0; k < n; ++k)
@@ -296,6 +313,7 @@ void orc_check_states(const orc_robot* r, const orc_env* e, const double* Q, int
 typedef struct tree {
   double* q;      /* [cap*d] */
   int32_t* parent;
+  double* radius; /* [cap] dynamic-domain radius, INFINITY = unbounded */
   int32_t n, cap, d;
 } tree;
 
@@ -303,6 +321,7 @@ static int tree_add(tree* t, const double* q, int32_t parent) {
   if (t->n >= t->cap) return -1;
   memcpy(t->q + (size_t)t->n * t->d, q, (size_t)t->d * sizeof(double));
   t->parent[t->n] = parent;
+  t->radius[t->n] = INFINITY;
   return t->n++;
 }
 
@@ -437,6 +456,7 @@ int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
   res->first_amb_kind = ORC_AMB_NONE;
   res->cost = 0.0;
   res->edges_checked = res->states_checked = res->edge_states = 0;
+  res->dd_rejected = 0;
   if (d <= 0 || p->tree_capacity < 1 || p->range <= 0.0 || p->resolution <= 0.0) {
     res->status = ORC_BAD_INPUT;
     return res->status;
@@ -458,11 +478,14 @@ int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
   }
 
   size_t cap = (size_t)p->tree_capacity;
-  tree A = {res->nodes_a, res->parent_a, 0, p->tree_capacity, d};
-  tree B = {res->nodes_b, res->parent_b, 0, p->tree_capacity, d};
-  int own_a = 0, own_b = 0;
+  tree A = {res->nodes_a, res->parent_a, res->radius_a, 0, p->tree_capacity, d};
+  tree B = {res->nodes_b, res->parent_b, res->radius_b, 0, p->tree_capacity, d};
+  int own_a = 0, own_b = 0, own_ra = 0, own_rb = 0;
   if (!A.q) { A.q = (double*)malloc(cap * d * sizeof(double)); A.parent = (int32_t*)malloc(cap * sizeof(int32_t)); own_a = 1; }
   if (!B.q) { B.q = (double*)malloc(cap * d * sizeof(double)); B.parent = (int32_t*)malloc(cap * sizeof(int32_t)); own_b = 1; }
+  if (!A.radius) { A.radius = (double*)malloc(cap * sizeof(double)); own_ra = 1; }
+  if (!B.radius) { B.radius = (double*)malloc(cap * sizeof(double)); own_rb = 1; }
+  const int dd = p->dd_radius > 0.0;
 
   double* c_rand = (double*)malloc((size_t)d * sizeof(double));
   double* c_new = (double*)malloc((size_t)d * sizeof(double));
@@ -490,12 +513,26 @@ int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
                                   p->gmm ? p->learned_ratio : 0.0, p->amb_rel, c_rand, &amb_k);
     if (amb_k) note_amb(&ctx, ORC_AMB_COMPONENT);
     if (kind == 1) memcpy(c_rand, To->q, (size_t)d * sizeof(double));
+    if (kind == 0 && p->sampler == ORC_SAMPLER_HALTON) {
+      /* the paper's sampler: Halton point it + 1 + offset (index 0 is the origin) */
+      orc_halton((uint32_t)it + 1u + p->halton_offset, d, c_rand);
+      for (int j = 0; j < d; ++j) c_rand[j] = r->lower[j] + c_rand[j] * (r->upper[j] - r->lower[j]);
+    }
     /* line 5: NEAREST_NEIGHBOR in T_s. */
     int32_t nn = nearest(&ctx, Ts, c_rand);
     const double* c_nn = Ts->q + (size_t)nn * d;
     /* Alg. 2 line 2: INTERPOLATE -- step from c_nn toward c_rand by at most delta. */
     double dist = sqrt(dist2(c_rand, c_nn, d));
     if (dist <= 0.0) continue; /* no motion: nothing to add */
+    /* dynamic domain: a random sample outside the nearest node's radius is rejected */
+    if (dd && kind != 1) {
+      double rad = Ts->radius[nn];
+      if (isfinite(rad) && fabs(dist - rad) <= p->amb_rel * rad) note_amb(&ctx, ORC_AMB_DOMAIN);
+      if (dist > rad) {
+        res->dd_rejected++;
+        continue;
+      }
+    }
     if (fabs(dist - delta) <= p->amb_rel * delta) note_amb(&ctx, ORC_AMB_STEER);
     double len;
     int clamped = (dist > delta);
@@ -508,7 +545,19 @@ int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
     }
     /* Alg. 2 lines 3-5: N_cc = ceil(len / resolution) states, all must be free. */
     int32_t n_states = ceil_checked(&ctx, len / resol, clamped);
-    if (!check_edge(&ctx, c_nn, c_new, n_states)) continue;
+    int edge_ok = check_edge(&ctx, c_nn, c_new, n_states);
+    if (dd) {
+      /* radius of the nearest node after its extension (adaptive dynamic domain) */
+      double* rad = &Ts->radius[nn];
+      if (edge_ok) {
+        if (isfinite(*rad)) *rad *= 1.0 + p->dd_alpha;
+      } else if (isinf(*rad)) {
+        *rad = p->dd_radius;
+      } else {
+        *rad = fmax(*rad * (1.0 - p->dd_alpha), p->dd_min_radius);
+      }
+    }
+    if (!edge_ok) continue;
     /* line 7: add c_new to T_s. */
     int32_t idx_new = tree_add(Ts, c_new, nn);
     if (idx_new < 0) continue;
@@ -568,6 +617,8 @@ done:
   free(scratch);
   if (own_a) { free(A.q); free(A.parent); }
   if (own_b) { free(B.q); free(B.parent); }
+  if (own_ra) free(A.radius);
+  if (own_rb) free(B.radius);
   return res->status;
 }
 

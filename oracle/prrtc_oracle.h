@@ -13,8 +13,10 @@
  *     states of the edge at the fixed collision-checking resolution.
  *   - Sec. III-A: collision checking of a sphere model against cuboids,
  *     capped cylinders and spheres, plus self-collision between sphere pairs.
- *   - Philox4x32-10 (Salmon et al., SC'11) for the sampler (the paper samples
- *     with Halton sequences; the counter-based generator replaces them).
+ *   - Philox4x32-10 (Salmon et al., SC'11) for the sampler, or the
+ *     multi-dimensional Halton sequence the paper samples with (Sec. IV-A).
+ *   - Dynamic-domain sampling (Yershova et al. 2005, with the adaptive
+ *     radius of Jaillet et al. 2005), which the paper adds to Alg. 1 (Sec. III).
  * Every floating-point step is in IEEE binary64.
  *
  * Parity-pinned functions (see tests/test_oracle_pins.py):
@@ -26,6 +28,12 @@
  *   orc_occupancy      - closed-form voxel sets of a sphere and a box.
  *   orc_sample_learned - the mixture statistics of its draws (component
  *                        frequencies, per-component mean and spread).
+ *   orc_halton         - the printed van der Corput fractions of bases 2 and 3,
+ *                        exact stratification of the first b^m points.
+ *   dynamic domain     - an unbounded radius and an obstacle-free scene both
+ *                        reduce to the plain planner; a 1-DoF slider against a
+ *                        wall advances by at most the radius after its first
+ *                        failed extension.
  */
 #ifndef PRRTC_ORACLE_H
 #define PRRTC_ORACLE_H
@@ -54,8 +62,11 @@ enum {
   ORC_AMB_NN_TIE = 2,    /* best and second-best squared distances close  */
   ORC_AMB_CEIL = 3,      /* a ceil() argument lay next to an integer      */
   ORC_AMB_STEER = 4,     /* sample distance next to the range delta        */
-  ORC_AMB_COMPONENT = 5  /* mixture component draw next to a boundary      */
+  ORC_AMB_COMPONENT = 5, /* mixture component draw next to a boundary      */
+  ORC_AMB_DOMAIN = 6     /* sample distance next to a dynamic-domain radius */
 };
+
+enum { ORC_SAMPLER_PHILOX = 0, ORC_SAMPLER_HALTON = 1 };
 
 typedef struct orc_robot {
   int32_t dof;
@@ -98,6 +109,21 @@ typedef struct orc_params {
    * log_sigma[8*dof] (clamped to [-5, 2] when used) */
   const double* gmm;
   double learned_ratio;  /* probability of drawing from the mixture (after goal bias) */
+  /* uniform branch of RANDOM_CONFIG: ORC_SAMPLER_PHILOX (words 1..dof of the
+   * iteration's Philox stream) or ORC_SAMPLER_HALTON (point it + 1 +
+   * halton_offset of the Halton sequence in the first dof prime bases) */
+  int32_t sampler;
+  uint32_t halton_offset;
+  /* dynamic-domain sampling: every node carries a radius, unbounded when the
+   * node is added.  A random (not goal-bias) sample farther than the radius
+   * from its nearest node is rejected: the iteration ends there.  After the
+   * check of the edge from nearest node n: on success a bounded radius grows,
+   * r <- r (1 + alpha); on a collision an unbounded radius becomes dd_radius,
+   * a bounded one shrinks to max(r (1 - alpha), dd_min_radius).  Greedy
+   * connect steps leave radii alone.  dd_radius <= 0 turns it off. */
+  double dd_radius;
+  double dd_alpha;
+  double dd_min_radius;
 } orc_params;
 
 typedef struct orc_result {
@@ -113,12 +139,15 @@ typedef struct orc_result {
   int64_t edges_checked;       /* edges whose states were examined            */
   int64_t states_checked;      /* states examined (stop at the first collision) */
   int64_t edge_states;         /* sum over checked edges of their state count   */
+  int64_t dd_rejected;         /* iterations ended by the dynamic-domain test    */
   /* caller-owned buffers (nullable): trees and path */
   double* nodes_a;             /* [tree_capacity*dof] */
   int32_t* parent_a;           /* [tree_capacity]     */
   double* nodes_b;
   int32_t* parent_b;
   double* path;                /* [path_capacity*dof] */
+  double* radius_a;            /* [tree_capacity] dynamic-domain radii (INFINITY = unbounded) */
+  double* radius_b;
 } orc_result;
 
 /* Philox4x32-10 block: out = Philox(ctr, key).  Salmon et al. SC'11. */
@@ -136,6 +165,11 @@ int orc_sample(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it,
  * to a cumulative-probability boundary. */
 int orc_sample_learned(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it, double goal_bias,
                        const double* gmm, double learned_ratio, double amb_rel, double* q, int* amb);
+
+/* Point `index` of the Halton sequence in `dim` dimensions: coordinate j is
+ * the radical inverse of index in the j-th prime base (2, 3, 5, ...), i.e.
+ * its base-p digits mirrored about the radix point.  dim <= 16. */
+void orc_halton(uint32_t index, int32_t dim, double* u);
 
 /* Occupancy grid of an environment: voxel (i, j, k), index i + n*j + n*n*k,
  * centre origin + (index + 0.5) * cell per axis, is occupied iff its centre
