@@ -192,10 +192,17 @@ def c1_problem(accept):
     return W.problem_set("c1", 1, 1, accept)[0]
 
 
+PRIM_KINDS = ("aabb", "obb", "cyl", "sph")
+
+
 def op_count(path, env_counts, dof, dpad):
+    """Counted arithmetic of one problem: sphere passes over the whole obstacle set
+    (fine spheres of one-stage frames and bounding spheres of two-stage frames),
+    second-stage sphere-primitive tests, self pairs, FK joints, NN row distances."""
     a, o, c, s = env_counts
     per_sphere = OPS["centre"] + OPS["aabb"] * a + OPS["obb"] * o + OPS["cyl"] * c + OPS["sph"] * s
-    return (path["sphere_tests"] * per_sphere + path["pair_tests"] * OPS["pair"] +
+    prim = sum(n * OPS[k] for n, k in zip(path["prim_tests"], PRIM_KINDS))
+    return (path["sphere_tests"] * per_sphere + prim + path["pair_tests"] * OPS["pair"] +
             path["fk_states"] * OPS["joint"] * dof + path["nn_nodes"] * (2 * dpad + 1))
 
 
@@ -267,6 +274,58 @@ def serving_section(args, P, proposals):
         out["obstacle_updates"] = mover.ticks
         out["slices"] = server.stats()["slices"]
         server.close()
+    return out
+
+
+# ------------------------------------------------------------------ sampler / check variants
+
+DD_PARAMS = dict(dd_radius=5.0, dd_alpha=0.02, dd_min_radius=4.0)
+
+
+def variants_section(args, P, items, prm, counts, flush, torch, steps=5):
+    """The hot-path table's next rows on the benchmark batch, same keys and launch
+    shape: one-stage vs two-stage check, Philox vs Halton sampling, dynamic-domain
+    sampling on/off."""
+    import copy
+    robots = {id(it[0]): it[0] for it in items}
+    variants = [("baseline", {}, True), ("one_stage", {}, False),
+                ("halton", dict(sampler=P.SAMPLER_HALTON), True),
+                ("dynamic_domain", dict(DD_PARAMS), True),
+                ("halton_dynamic_domain", dict(DD_PARAMS, sampler=P.SAMPLER_HALTON), True)]
+    out = dict(workload=WORKLOAD, steps=steps, dynamic_domain_params=DD_PARAMS,
+               note="baseline = two-stage check, Philox sampling, no dynamic domain (the main line's step)")
+    for name, kw, two in variants:
+        for rb in robots.values():
+            rb.set_two_stage(two)
+        p = copy.copy(prm)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        for _ in range(2):
+            P.prrtc_plan_batch(items, p)
+        dev_ms, kms, states, ops, ttfs, iters, costs, solved, rej = 0.0, 0.0, 0, 0, [], [], [], 0, 0
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            res = P.prrtc_plan_batch(items, p)
+            st = P.prrtc_last_launch_stats()
+            dev_ms += st["kernel_ms"] + st["setup_ms"]
+            kms += st["kernel_ms"]
+            for r, (ec, dof, dpad) in zip(res, counts):
+                states += r["edge_states"]
+                ops += op_count(r, ec, dof, dpad)
+                iters.append(r["iterations"])
+                rej += r["dd_rejected"]
+                if r["status"] == P.SOLVED:
+                    solved += 1
+                    ttfs.append(r["solve_time_us"])
+                    costs.append(r["cost"])
+        n = len(items) * steps
+        out[name] = dict(ms_per_step=dev_ms / steps, edge_states_per_s=states / (dev_ms * 1e-3),
+                         ttfs_us=percentiles(ttfs), success_rate=solved / n,
+                         iterations_mean=float(np.mean(iters)), cost_mean=float(np.mean(costs)) if costs else None,
+                         dd_rejected_per_problem=rej / n, planner_gops=ops / (kms * 1e-3) * 1e-9)
+    for rb in robots.values():
+        rb.set_two_stage(True)
     return out
 
 
@@ -419,23 +478,33 @@ def run_ours(args):
         from paper_2503_06757_gb300 import workload as W
         Q = W.candidates(pb.robot, 7, 3, 1 << 21).astype(np.float32)
         F = Q[P.prrtc_check_states(rb, ev, Q)][: 1 << 20]
-        for _ in range(3):
-            P.prrtc_check_states(rb, ev, F)
-        ms = []
-        for _ in range(5):
-            flush.zero_()
-            torch.cuda.synchronize()
-            P.prrtc_check_states(rb, ev, F)
-            ms.append(P.prrtc_last_launch_stats()["kernel_ms"])
-        st = P.prrtc_last_launch_stats()
         ec = ev.info()
         per_sphere = OPS["centre"] + OPS["aabb"] * ec[0] + OPS["obb"] * ec[1] + OPS["cyl"] * ec[2] + OPS["sph"] * ec[3]
-        cc_ops = st["sphere_tests"] * per_sphere + st["pair_tests"] * OPS["pair"] + st["fk_states"] * OPS["joint"] * 7
-        kms = float(np.median(ms))
-        extra["roofline_cc_microbench"] = dict(
-            bound="alu", achieved=cc_ops / (kms * 1e-3) * 1e-9, peak=peak_gops, unit="Gop/s",
-            frac=cc_ops / (kms * 1e-3) * 1e-9 / peak_gops, states=int(len(F)), kernel_ms=kms,
-            states_per_s=len(F) / (kms * 1e-3), ops_per_state=cc_ops / len(F))
+        micro = {}
+        for name, two in (("two_stage", True), ("one_stage", False)):
+            rb.set_two_stage(two)
+            for _ in range(3):
+                P.prrtc_check_states(rb, ev, F)
+            ms = []
+            for _ in range(5):
+                flush.zero_()
+                torch.cuda.synchronize()
+                P.prrtc_check_states(rb, ev, F)
+                ms.append(P.prrtc_last_launch_stats()["kernel_ms"])
+            st = P.prrtc_last_launch_stats()
+            cc_ops = (st["sphere_tests"] * per_sphere + st["pair_tests"] * OPS["pair"] +
+                      st["fk_states"] * OPS["joint"] * 7 +
+                      sum(n * OPS[k] for n, k in zip(st["prim_tests"], PRIM_KINDS)))
+            kms = float(np.median(ms))
+            micro[name] = dict(
+                bound="alu", achieved=cc_ops / (kms * 1e-3) * 1e-9, peak=peak_gops, unit="Gop/s",
+                frac=cc_ops / (kms * 1e-3) * 1e-9 / peak_gops, states=int(len(F)), kernel_ms=kms,
+                states_per_s=len(F) / (kms * 1e-3), ops_per_state=cc_ops / len(F))
+        rb.set_two_stage(True)
+        extra["roofline_cc_microbench"] = dict(micro["two_stage"], one_stage=micro["one_stage"],
+                                               workload="1M collision-free 7-DoF states vs one shelf scene "
+                                                        "(every test runs)")
+        extra["variants"] = variants_section(args, P, items, prm, counts, flush, torch)
         extra["cpu_baseline"] = oracle_sample(probs, budget_s=args.cpu_budget)
         prop = None
         if not args.no_learned:

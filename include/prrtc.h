@@ -136,8 +136,25 @@ typedef struct prrtc_params {
                              (after the goal bias); 0 = uniform sampling only         */
   uint64_t seed;          /* Philox key used by prrtc_plan                             */
   double time_limit_s;    /* device-side wall-clock budget per launch; 0 = none        */
-  int32_t reserved[8];
+  int32_t sampler;        /* uniform branch of RANDOM_CONFIG (Alg. 1): PRRTC_SAMPLER_PHILOX
+                             (words of the iteration's Philox stream) or
+                             PRRTC_SAMPLER_HALTON (the paper's Halton sequence, Sec. IV-A:
+                             iteration `it` takes point it + 1 + halton_offset)          */
+  uint32_t halton_offset;
+  float dd_radius;        /* dynamic-domain sampling (Sec. III; Yershova et al. 2005): a
+                             random sample farther than its nearest node's radius is
+                             rejected and the iteration ends.  Radii start unbounded; the
+                             first collision of an extension from a node bounds its radius
+                             to dd_radius.  0 = off                                    */
+  float dd_alpha;         /* adaptive radius (Jaillet et al. 2005): a bounded radius grows
+                             by (1 + dd_alpha) after a free extension and shrinks by
+                             (1 - dd_alpha), not below dd_min_radius, after a collision */
+  float dd_min_radius;
+  int32_t reserved[3];
 } prrtc_params;
+
+#define PRRTC_SAMPLER_PHILOX 0
+#define PRRTC_SAMPLER_HALTON 1
 
 /* Fills the defaults: range 1.0, resolution 1/32, goal bias 0.05, 50000
  * iterations, 65536 nodes per tree, 16384 waypoints, async mode, seed 1. */
@@ -160,6 +177,10 @@ typedef struct prrtc_path {
   int64_t pair_tests;      /* lane-level self-collision pair tests                        */
   int64_t fk_states;       /* lane-level forward-kinematics evaluations                   */
   int64_t nn_nodes;        /* tree rows scanned by nearest-neighbour queries              */
+  int64_t dd_rejected;     /* iterations ended by the dynamic-domain test                 */
+  int64_t prim_tests[4];   /* lane-level tests of one fine sphere against one primitive in
+                              the second stage of the two-stage check, per primitive type
+                              (AABB, oriented box, capped cylinder, sphere)               */
 } prrtc_path;
 
 void prrtc_path_free(prrtc_path* path);
@@ -171,8 +192,11 @@ typedef struct prrtc_launch_stats {
   double setup_ms;           /* arena reset + root insertion kernel                   */
   int64_t edges_checked;
   int64_t edge_states;       /* states of all tested edges                            */
-  int64_t sphere_tests;      /* lane-level sphere passes over the environment         */
-  int64_t env_tests;         /* lane-level sphere-primitive tests                     */
+  int64_t sphere_tests;      /* lane-level sphere passes over the whole environment
+                                (fine spheres of one-stage frames, bounding spheres of
+                                two-stage frames)                                       */
+  int64_t env_tests;         /* lane-level second-stage sphere-primitive tests (sum of
+                                prim_tests)                                              */
   int64_t pair_tests;        /* lane-level self-collision pair tests                  */
   int64_t fk_states;         /* lane-level forward-kinematics evaluations              */
   int64_t nn_nodes;          /* tree nodes scanned by nearest-neighbour queries        */
@@ -187,6 +211,9 @@ typedef struct prrtc_launch_stats {
   int32_t reserved_;
   double prep_ms;            /* from the call's first device work to the setup kernel:
                                 learned-mixture inference and descriptor upload         */
+  int64_t prim_tests[4];     /* second-stage tests per primitive type (AABB, oriented
+                                box, capped cylinder, sphere)                            */
+  int64_t dd_rejected;       /* iterations ended by the dynamic-domain test            */
 } prrtc_launch_stats;
 
 int prrtc_last_launch_stats(prrtc_launch_stats* out);
@@ -225,6 +252,22 @@ void prrtc_robot_destroy(prrtc_robot* robot);
 /* Sizes after merging: DoF, distinct spheres, distinct self pairs and the
  * tree row stride in floats (any pointer may be null). */
 int prrtc_robot_info(const prrtc_robot* robot, int32_t* dof, int32_t* n_spheres, int32_t* n_pairs, int32_t* dpad);
+
+/* Two-stage collision checking (Sec. III-A: a low-resolution pass flags the
+ * links that may collide, only those are re-checked with the fine spheres).
+ * Every frame with two or more distinct spheres gets one bounding sphere that
+ * contains all of them with a 1e-5 m margin; the first stage tests it against
+ * every primitive, the second tests the frame's fine spheres only against the
+ * primitives that some state of the warp's edge flagged.  The verdicts equal
+ * those of the one-stage check.  On by default; `enabled` = 0 switches to the
+ * one-stage check.  Applies to calls issued after it returns (it writes the
+ * device copy of the robot synchronously). */
+int prrtc_robot_set_two_stage(prrtc_robot* robot, int32_t enabled);
+
+/* Bounding spheres of the first stage: out4[4*f .. 4*f+3] = centre (frame f
+ * coordinates) and radius, radius 0 where frame f has fewer than two distinct
+ * spheres (checked in one stage).  out4: host [dof*4]. */
+int prrtc_robot_bounds(const prrtc_robot* robot, float* out4);
 
 /* counts4 = {axis-aligned boxes, oriented boxes, cylinders, spheres}. */
 int prrtc_env_info(const prrtc_env* env, int32_t* counts4);

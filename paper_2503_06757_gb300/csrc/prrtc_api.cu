@@ -180,7 +180,8 @@ void free_arenas(DeviceCtx* c) {
 }
 
 // Tree arenas: slot p, tree t occupies cap rows of kMaxDof floats (the row
-// stride used is the problem's dpad, so any DoF fits).
+// stride used is the problem's dpad, so any DoF fits), cap parent indices and
+// cap dynamic-domain radii (the radii follow all parent arrays).
 int ensure_arenas(DeviceCtx* c, int slots, int cap, int path_cap) {
   if (c->slots >= slots && c->cap >= cap && c->path_cap >= path_cap) return PRRTC_OK;
   CK(cudaStreamSynchronize(c->stream));
@@ -190,7 +191,7 @@ int ensure_arenas(DeviceCtx* c, int slots, int cap, int path_cap) {
   free_arenas(c);
   const size_t rows = (size_t)slots * 2 * cap;
   bool ok = cudaMalloc(&c->nodes, rows * kMaxDof * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&c->parents, rows * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->parents, 2 * rows * sizeof(int)) == cudaSuccess &&   // parents, then radii
             cudaMalloc(&c->paths, (size_t)slots * path_cap * kMaxDof * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&c->path_idx, (size_t)slots * path_cap * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&c->d_desc, (size_t)slots * sizeof(ProblemDesc)) == cudaSuccess &&
@@ -205,7 +206,7 @@ int ensure_arenas(DeviceCtx* c, int slots, int cap, int path_cap) {
     return fail(PRRTC_ERR_OOM, "planner arena allocation failed");
   }
   CK(cudaMemsetAsync(c->nodes, 0xFF, rows * kMaxDof * sizeof(float), c->stream));   // NaN rows
-  CK(cudaMemsetAsync(c->parents, 0xFF, rows * sizeof(int), c->stream));             // unset parents
+  CK(cudaMemsetAsync(c->parents, 0xFF, 2 * rows * sizeof(int), c->stream));         // unset parents, NaN radii
   CK(cudaMemsetAsync(c->d_state, 0, (size_t)slots * sizeof(ProblemState), c->stream));
   c->slots = slots;
   c->cap = cap;
@@ -244,6 +245,7 @@ int validate_params(const prrtc_params* p) {
     return fail(PRRTC_ERR_INVALID_ARG, "learned_ratio must be in [0,1]");
   const double ratio = (double)p->range / (double)p->resolution;
   if (ratio > 4096.0) return fail(PRRTC_ERR_INVALID_ARG, "range / resolution too large");
+  if (const char* why = sampling_params_problem(*p)) return fail(PRRTC_ERR_INVALID_ARG, why);
   return PRRTC_OK;
 }
 
@@ -455,6 +457,42 @@ void prrtc_env_destroy(prrtc_env* env) {
 }
 
 // -------------------------------------------------------------- robot
+}  // extern "C"
+
+namespace {
+
+// First-stage spheres of the two-stage check: for each frame with two or more
+// distinct spheres, the sphere around the centre of their offsets' bounding
+// box that contains every one of them, enlarged by 1e-5 m (plus one part in
+// 10^6) so that FP32 rounding of the FK cannot make a fine sphere poke out.
+void set_bounding_spheres(RobotHeader& H) {
+  for (int f = 0; f < kMaxDof; ++f) H.coarse[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int f = 0; f < H.dof; ++f) {
+    const int s0 = H.sph_begin[f], s1 = H.sph_begin[f + 1];
+    if (s1 - s0 < 2) continue;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int s = s0; s < s1; ++s) {
+      const double o[3] = {H.sph[s].x, H.sph[s].y, H.sph[s].z};
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], o[a]);
+        hi[a] = std::max(hi[a], o[a]);
+      }
+    }
+    const float cx = (float)(0.5 * (lo[0] + hi[0])), cy = (float)(0.5 * (lo[1] + hi[1])),
+                cz = (float)(0.5 * (lo[2] + hi[2]));
+    double rad = 0.0;
+    for (int s = s0; s < s1; ++s) {
+      const double dx = (double)H.sph[s].x - cx, dy = (double)H.sph[s].y - cy, dz = (double)H.sph[s].z - cz;
+      rad = std::max(rad, std::sqrt(dx * dx + dy * dy + dz * dz) + (double)H.sph[s].w);
+    }
+    H.coarse[f] = make_float4(cx, cy, cz, (float)(rad * (1.0 + 1e-6) + 1e-5));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
 int prrtc_robot_create(const prrtc_robot_desc* d, prrtc_robot** out) {
   if (!out) return fail(PRRTC_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
@@ -541,6 +579,8 @@ int prrtc_robot_create(const prrtc_robot_desc* d, prrtc_robot** out) {
   for (size_t k = 0; k < distinct.size(); ++k)
     H.sph[k] = make_float4(std::get<1>(distinct[k]), std::get<2>(distinct[k]), std::get<3>(distinct[k]),
                            std::get<4>(distinct[k]));
+  set_bounding_spheres(H);
+  H.two_stage = 1;
   for (size_t k = 0; k < pairs.size(); ++k) {
     h->pair[k] = (uint32_t)pairs[k].first | ((uint32_t)pairs[k].second << 16);
     const float rr = H.sph[pairs[k].first].w + H.sph[pairs[k].second].w;
@@ -573,6 +613,30 @@ void prrtc_robot_destroy(prrtc_robot* robot) {
   cudaFree(robot->d);
   std::free(robot->h);
   delete robot;
+}
+
+int prrtc_robot_set_two_stage(prrtc_robot* robot, int32_t enabled) {
+  if (!robot || !robot->h) return fail(PRRTC_ERR_INVALID_ARG, "robot is null");
+  robot->h->h.two_stage = enabled ? 1 : 0;
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != robot->device) return fail(PRRTC_ERR_INVALID_ARG, "robot belongs to another device");
+  // everything queued on the device may still read the old header: wait for it
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&robot->d->h.two_stage, &robot->h->h.two_stage, sizeof(int), cudaMemcpyHostToDevice));
+  return PRRTC_OK;
+}
+
+int prrtc_robot_bounds(const prrtc_robot* robot, float* out4) {
+  if (!robot || !robot->h || !out4) return fail(PRRTC_ERR_INVALID_ARG, "null argument");
+  const RobotHeader& H = robot->h->h;
+  for (int f = 0; f < H.dof; ++f) {
+    out4[4 * f + 0] = H.coarse[f].x;
+    out4[4 * f + 1] = H.coarse[f].y;
+    out4[4 * f + 2] = H.coarse[f].z;
+    out4[4 * f + 3] = H.coarse[f].w;
+  }
+  return PRRTC_OK;
 }
 
 // Extra introspection used by tests and the benchmark.
@@ -668,7 +732,7 @@ int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const flo
   if (out_spheres)
     CK(cudaMemcpyAsync(out_spheres, c->d_spheres, (size_t)n * n_raw * 4 * sizeof(float), cudaMemcpyDeviceToHost,
                        c->stream));
-  unsigned long long cnt[3] = {0, 0, 0};
+  unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
   int err = 0;
   CK(cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&err, c->d_error, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -681,6 +745,10 @@ int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const flo
   c->last.sphere_tests = (int64_t)cnt[0];
   c->last.pair_tests = (int64_t)cnt[1];
   c->last.fk_states = (int64_t)cnt[2];
+  for (int k = 0; k < 4; ++k) {
+    c->last.prim_tests[k] = (int64_t)cnt[3 + k];
+    c->last.env_tests += (int64_t)cnt[3 + k];
+  }
   c->last.problems = 0;
   c->last.kernels = 1;
   c->last.h2d_bytes = (int64_t)n * dof * (int64_t)sizeof(float);
@@ -795,6 +863,9 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     D.nodes[1] = c->nodes + ((size_t)p * 2 + 1) * tree_stride;
     D.parent[0] = c->parents + ((size_t)p * 2 + 0) * c->cap;
     D.parent[1] = c->parents + ((size_t)p * 2 + 1) * c->cap;
+    float* radii = reinterpret_cast<float*>(c->parents + (size_t)c->slots * 2 * c->cap);
+    D.radius[0] = radii + ((size_t)p * 2 + 0) * c->cap;
+    D.radius[1] = radii + ((size_t)p * 2 + 1) * c->cap;
     D.path = c->paths + (size_t)p * c->path_cap * kMaxDof;
     D.path_idx = c->path_idx + (size_t)p * c->path_cap;
     D.cap = params->tree_capacity;
@@ -817,15 +888,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   PlanGlobals& G = *c->h_glob;
   std::memset(&G, 0, sizeof(G));
   G.n_problems = n;
-  G.mode = params->mode;
-  G.max_iters = params->max_iters;
-  G.n_full = (int)std::ceil((double)params->range / (double)params->resolution);
-  if (G.n_full < 1) G.n_full = 1;
-  G.range = params->range;
-  G.resolution = params->resolution;
-  G.bias_thr = (uint32_t)std::ceil((double)params->goal_bias * 16777216.0);
-  G.learned_thr = (uint32_t)std::ceil((double)params->learned_ratio * 16777216.0);
-  G.path_cap = params->path_capacity;
+  globals_from_params(G, *params);
   G.t0 = ULLONG_MAX;
   G.time_limit_ns = (unsigned long long)(params->time_limit_s * 1e9);
   G.cursor = 0;
@@ -979,6 +1042,11 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     L.fk_states += (int64_t)S.fk_states;
     L.nn_nodes += (int64_t)S.nn_nodes;
     L.iterations += (int64_t)S.iterations;
+    L.dd_rejected += (int64_t)S.dd_rejected;
+    for (int k = 0; k < 4; ++k) {
+      L.prim_tests[k] += (int64_t)S.prim_tests[k];
+      L.env_tests += (int64_t)S.prim_tests[k];
+    }
     if (out_status) out_status[p] = status[p];
     if (out_paths) {
       prrtc_path& P = out_paths[p];
@@ -996,6 +1064,8 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       P.pair_tests = (int64_t)S.pair_tests;
       P.fk_states = (int64_t)S.fk_states;
       P.nn_nodes = (int64_t)S.nn_nodes;
+      P.dd_rejected = (int64_t)S.dd_rejected;
+      for (int k = 0; k < 4; ++k) P.prim_tests[k] = (int64_t)S.prim_tests[k];
       if (status[p] == PRRTC_SOLVED) {
         P.n = S.path_n;
         P.cost = S.cost;

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_ok;
+  __shared__ WarpCount s_count[kCheckWarps];
   const int robot_bytes = robot_smem_bytes(np_pad);
   RobotHeader* R = reinterpret_cast<RobotHeader*>(smem);
   uint32_t* pair = reinterpret_cast<uint32_t*>(smem + sizeof(RobotHeader));
@@ -55,7 +56,8 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
   float* stage = qst + kQStageFloats;
   const int gw = blockIdx.x * kCheckWarps + warp;
   const int nw = gridDim.x * kCheckWarps;
-  WorkCount wc;
+  WarpCount* wc = &s_count[warp];
+  warp_count_clear(wc, lane);
   const LaneQ qs{qst, lane};
   for (int base = gw * 32; base < n; base += nw * 32) {
     const int idx = base + lane;
@@ -76,19 +78,9 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
       }
     }
   }
-  // warp-reduce the work counters
-  unsigned long long a = wc.sphere_tests, b = wc.pair_tests, c = wc.fk_states;
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    a += __shfl_xor_sync(kFull, a, off);
-    b += __shfl_xor_sync(kFull, b, off);
-    c += __shfl_xor_sync(kFull, c, off);
-  }
-  if (lane == 0 && counters) {
-    atomicAdd(counters + 0, a);
-    atomicAdd(counters + 1, b);
-    atomicAdd(counters + 2, c);
-  }
+  // the warp's work counters: sphere passes, pairs, FK states, second-stage tests
+  __syncwarp();
+  if (lane < 7 && counters) atomicAdd(counters + lane, reinterpret_cast<const unsigned long long*>(wc)[lane]);
 }
 
 }  // namespace

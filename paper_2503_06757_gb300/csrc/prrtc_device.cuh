@@ -10,6 +10,12 @@
 // after every sphere so that the whole edge stops at the first collision
 // (Sec. III-A, early exit).  Self-collision pairs are tested afterwards from
 // the sphere centres the lane staged in shared memory.
+//
+// Two-stage check (Sec. III-A, hierarchical): a frame with several spheres is
+// first tested through one bounding sphere against every primitive; its fine
+// spheres then meet only the primitives that the bounding sphere of some lane
+// touched.  Each bounding sphere contains its fine spheres with a margin far
+// above FP32 rounding, so the verdicts equal those of the one-stage check.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -32,7 +38,8 @@ struct RobotHeader {
   int n_spheres;       // distinct spheres
   int n_pairs;         // distinct self-collision pairs
   int n_raw;           // spheres as given
-  int pad_[3];
+  int two_stage;       // 1: frames with a bounding sphere are checked in two stages
+  int pad_[2];
   int jtype[kMaxDof];
   int jparent[kMaxDof];
   float jlen[kMaxDof];
@@ -42,6 +49,7 @@ struct RobotHeader {
   int sph_begin[kMaxDof + 1];
   int pad2_[3];
   float4 sph[kMaxDistinctSpheres];   // offset xyz in the frame, radius
+  float4 coarse[kMaxDof];            // bounding sphere of frame i's spheres (radius 0: none)
 };
 
 // Pair table follows the header in device memory: pair[k] = i | (j << 16),
@@ -80,63 +88,171 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // ------------------------------------------------------------------ counters
-struct WorkCount {
-  unsigned long long sphere_tests = 0;  // lane-level sphere passes over the environment
-  unsigned long long pair_tests = 0;    // lane-level self pair tests
-  unsigned long long fk_states = 0;     // lane-level FK evaluations
+// Work counters of one warp, kept in shared memory and updated by lane 0 with
+// warp-uniform increments (uniform work x active lanes), so that they hold no
+// registers in the checking loops.  The planner's per-iteration counters
+// follow the collision-checking ones.
+struct WarpCount {
+  unsigned long long sphere_tests;  // lane-level sphere passes over the environment
+  unsigned long long pair_tests;    // lane-level self pair tests
+  unsigned long long fk_states;     // lane-level FK evaluations
+  unsigned long long prim[4];       // second-stage sphere-primitive tests per type
+  unsigned long long edges, edge_states, nn_nodes, iterations, insert_fail, dd_rejected;
+  unsigned long long pad_[3];
 };
+static_assert(sizeof(WarpCount) == 128, "per-warp counter block is 128 bytes");
+
+__device__ __forceinline__ void warp_count_clear(WarpCount* wc, int lane) {
+  if (lane < 16) reinterpret_cast<unsigned long long*>(wc)[lane] = 0ull;
+  __syncwarp();
+}
 
 // ------------------------------------------------------------------ env tests
-// Does a sphere (centre c, radius r) touch any primitive?  Strict test on the
-// squared distance to each primitive (touching counts as free).
+// Squared distance from a point to one primitive (0 inside).  AABB: centre |
+// half extents; OBB: centre | half extents | rows of R^T; capped cylinder:
+// centre | radius, unit axis | half length.
+__device__ __forceinline__ float d2_aabb(const float4* __restrict__ e, float px, float py, float pz) {
+  const float4 c = e[0], h = e[1];
+  const float dx = fmaxf(fabsf(px - c.x) - h.x, 0.f);
+  const float dy = fmaxf(fabsf(py - c.y) - h.y, 0.f);
+  const float dz = fmaxf(fabsf(pz - c.z) - h.z, 0.f);
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+__device__ __forceinline__ float d2_obb(const float4* __restrict__ e, float px, float py, float pz) {
+  const float4 c = e[0], h = e[1], a = e[2], b = e[3], d = e[4];
+  const float vx = px - c.x, vy = py - c.y, vz = pz - c.z;
+  const float lx = fmaf(a.x, vx, fmaf(a.y, vy, a.z * vz));
+  const float ly = fmaf(b.x, vx, fmaf(b.y, vy, b.z * vz));
+  const float lz = fmaf(d.x, vx, fmaf(d.y, vy, d.z * vz));
+  const float dx = fmaxf(fabsf(lx) - h.x, 0.f);
+  const float dy = fmaxf(fabsf(ly) - h.y, 0.f);
+  const float dz = fmaxf(fabsf(lz) - h.z, 0.f);
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+__device__ __forceinline__ float d2_cyl(const float4* __restrict__ e, float px, float py, float pz) {
+  const float4 c = e[0], a = e[1];
+  const float vx = px - c.x, vy = py - c.y, vz = pz - c.z;
+  const float z = fmaf(a.x, vx, fmaf(a.y, vy, a.z * vz));
+  const float wx = fmaf(-z, a.x, vx), wy = fmaf(-z, a.y, vy), wz = fmaf(-z, a.z, vz);
+  const float rho2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+  const float rho = rho2 > 0.f ? rho2 * rsqrtf(rho2) : 0.f;
+  const float er = fmaxf(rho - c.w, 0.f);
+  const float ez = fmaxf(fabsf(z) - a.w, 0.f);
+  return fmaf(er, er, ez * ez);
+}
+
+// Strict sphere tests (touching counts as free), one primitive type each; a
+// sphere obstacle compares against the sum of the radii.
+enum PrimKind : int { kAabb = 0, kObb = 1, kCyl = 2, kSph = 3 };
+template <int K> struct Prim;
+template <> struct Prim<kAabb> {
+  static constexpr int kUnroll = 4;
+  static constexpr int kStride = 2;
+  __device__ static __forceinline__ bool hit(const float4* e, float x, float y, float z, float r) {
+    return d2_aabb(e, x, y, z) < r * r;
+  }
+};
+template <> struct Prim<kObb> {
+  static constexpr int kUnroll = 2;
+  static constexpr int kStride = 5;
+  __device__ static __forceinline__ bool hit(const float4* e, float x, float y, float z, float r) {
+    return d2_obb(e, x, y, z) < r * r;
+  }
+};
+template <> struct Prim<kCyl> {
+  static constexpr int kUnroll = 2;
+  static constexpr int kStride = 2;
+  __device__ static __forceinline__ bool hit(const float4* e, float x, float y, float z, float r) {
+    return d2_cyl(e, x, y, z) < r * r;
+  }
+};
+template <> struct Prim<kSph> {
+  static constexpr int kUnroll = 4;
+  static constexpr int kStride = 1;
+  __device__ static __forceinline__ bool hit(const float4* e, float x, float y, float z, float r) {
+    const float4 s = e[0];
+    const float dx = x - s.x, dy = y - s.y, dz = z - s.z;
+    const float rr = r + s.w;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
+  }
+};
+
+// Does a sphere (centre c, radius r) touch any primitive?
 __device__ __forceinline__ bool sphere_hits_env(float cx, float cy, float cz, float r, const float4* __restrict__ env,
                                                 int n_aabb, int n_obb, int n_cyl, int n_sph) {
-  const float r2 = r * r;
   bool hit = false;
   const float4* e = env;
 #pragma unroll 4
-  for (int o = 0; o < n_aabb; ++o) {
-    const float4 c = e[2 * o], h = e[2 * o + 1];
-    const float dx = fmaxf(fabsf(cx - c.x) - h.x, 0.f);
-    const float dy = fmaxf(fabsf(cy - c.y) - h.y, 0.f);
-    const float dz = fmaxf(fabsf(cz - c.z) - h.z, 0.f);
-    hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < r2;
-  }
+  for (int o = 0; o < n_aabb; ++o) hit |= Prim<kAabb>::hit(e + 2 * o, cx, cy, cz, r);
   e += 2 * n_aabb;
 #pragma unroll 2
-  for (int o = 0; o < n_obb; ++o) {
-    const float4 c = e[5 * o], h = e[5 * o + 1], a = e[5 * o + 2], b = e[5 * o + 3], d = e[5 * o + 4];
-    const float vx = cx - c.x, vy = cy - c.y, vz = cz - c.z;
-    const float lx = fmaf(a.x, vx, fmaf(a.y, vy, a.z * vz));
-    const float ly = fmaf(b.x, vx, fmaf(b.y, vy, b.z * vz));
-    const float lz = fmaf(d.x, vx, fmaf(d.y, vy, d.z * vz));
-    const float dx = fmaxf(fabsf(lx) - h.x, 0.f);
-    const float dy = fmaxf(fabsf(ly) - h.y, 0.f);
-    const float dz = fmaxf(fabsf(lz) - h.z, 0.f);
-    hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < r2;
-  }
+  for (int o = 0; o < n_obb; ++o) hit |= Prim<kObb>::hit(e + 5 * o, cx, cy, cz, r);
   e += 5 * n_obb;
 #pragma unroll 2
-  for (int o = 0; o < n_cyl; ++o) {
-    const float4 c = e[2 * o], a = e[2 * o + 1];
-    const float vx = cx - c.x, vy = cy - c.y, vz = cz - c.z;
-    const float z = fmaf(a.x, vx, fmaf(a.y, vy, a.z * vz));
-    const float wx = fmaf(-z, a.x, vx), wy = fmaf(-z, a.y, vy), wz = fmaf(-z, a.z, vz);
-    const float rho2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-    const float rho = rho2 > 0.f ? rho2 * rsqrtf(rho2) : 0.f;
-    const float er = fmaxf(rho - c.w, 0.f);
-    const float ez = fmaxf(fabsf(z) - a.w, 0.f);
-    hit |= fmaf(er, er, ez * ez) < r2;
-  }
+  for (int o = 0; o < n_cyl; ++o) hit |= Prim<kCyl>::hit(e + 2 * o, cx, cy, cz, r);
   e += 2 * n_cyl;
 #pragma unroll 4
-  for (int o = 0; o < n_sph; ++o) {
-    const float4 s = e[o];
-    const float dx = cx - s.x, dy = cy - s.y, dz = cz - s.z;
-    const float rr = r + s.w;
-    hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
+  for (int o = 0; o < n_sph; ++o) hit |= Prim<kSph>::hit(e + o, cx, cy, cz, r);
+  return hit;
+}
+
+// Two-stage test of one frame against the primitives of one type (Sec. III-A,
+// hierarchical check): the frame's bounding sphere (bx, by, bz, br) against
+// every primitive, 32 at a time; the flags of all active lanes are OR-ed, and
+// the frame's fine spheres s0..s1-1 (centres staged in `stage`) are tested
+// against the flagged primitives only.  The flag set is warp-uniform, so the
+// second stage runs without divergence.  Returns this lane's fine verdict and
+// adds the number of flagged primitives to *flagged.
+template <int K>
+__device__ __forceinline__ bool frame_two_stage(const float4* __restrict__ prims, int n, float bx, float by, float bz,
+                                                float br, const float* __restrict__ stage,
+                                                const float4* __restrict__ sph, int s0, int s1, bool active, int lane,
+                                                uint32_t& flagged) {
+  bool hit = false;
+  for (int base = 0; base < n; base += 32) {
+    const int m = min(32, n - base);
+    uint32_t flags = 0;
+#pragma unroll Prim<K>::kUnroll
+    for (int k = 0; k < m; ++k)
+      flags |= (uint32_t)Prim<K>::hit(prims + Prim<K>::kStride * (base + k), bx, by, bz, br) << k;
+    flags = __reduce_or_sync(kFull, active ? flags : 0u);
+    flagged += (uint32_t)__popc(flags);
+    while (flags) {
+      const int k = __ffs(flags) - 1;
+      flags &= flags - 1;
+      const float4* pk = prims + Prim<K>::kStride * (base + k);
+      for (int s = s0; s < s1; ++s) {
+        const float* st = stage + s * 96 + lane;
+        hit |= Prim<K>::hit(pk, st[0], st[32], st[64], sph[s].w);
+      }
+    }
   }
   return hit;
+}
+
+// Both stages of one frame against the whole environment, kept out of line so
+// that the register budget of the caller is not set by it.  Returns the
+// lane's verdict in bit 63 and the flagged primitives of each type in four
+// 15-bit fields (AABB lowest).
+static __device__ __noinline__ unsigned long long env_two_stage(const float4* __restrict__ env, int n_aabb, int n_obb,
+                                                         int n_cyl, int n_sph, float bx, float by, float bz, float br,
+                                                         const float* __restrict__ stage,
+                                                         const float4* __restrict__ sph, int s0, int s1, bool active,
+                                                         int lane) {
+  uint32_t f[4] = {0, 0, 0, 0};
+  bool hit = false;
+  const float4* e = env;
+  hit |= frame_two_stage<kAabb>(e, n_aabb, bx, by, bz, br, stage, sph, s0, s1, active, lane, f[kAabb]);
+  e += 2 * n_aabb;
+  hit |= frame_two_stage<kObb>(e, n_obb, bx, by, bz, br, stage, sph, s0, s1, active, lane, f[kObb]);
+  e += 5 * n_obb;
+  hit |= frame_two_stage<kCyl>(e, n_cyl, bx, by, bz, br, stage, sph, s0, s1, active, lane, f[kCyl]);
+  e += 2 * n_cyl;
+  hit |= frame_two_stage<kSph>(e, n_sph, bx, by, bz, br, stage, sph, s0, s1, active, lane, f[kSph]);
+  return ((unsigned long long)hit << 63) | (unsigned long long)f[0] | ((unsigned long long)f[1] << 15) |
+         ((unsigned long long)f[2] << 30) | ((unsigned long long)f[3] << 45);
 }
 
 // ------------------------------------------------------------------ FK + CC
@@ -167,14 +283,26 @@ template <bool kWarpVote, class QS>
 __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R, const uint32_t* __restrict__ pair,
                                                const float* __restrict__ thr, const float4* __restrict__ env,
                                                int n_aabb, int n_obb, int n_cyl, int n_sph, float* __restrict__ stage,
-                                               const QS& qs, bool active, int lane, WorkCount& wc) {
+                                               const QS& qs, bool active, int lane, WarpCount* wc) {
   const int dof = R->dof;
+  // uniform work of this call, multiplied by the active lanes on the way out
+  const unsigned long long na = (unsigned long long)__popc(__ballot_sync(kFull, active));
+  uint32_t passes = 0, pairs = 0;
+  uint32_t fine[4] = {0, 0, 0, 0};
+  auto flush = [&]() {
+    if (wc && lane == 0) {
+      wc->fk_states += na;
+      wc->sphere_tests += na * passes;
+      wc->pair_tests += na * pairs;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) wc->prim[k] += na * fine[k];
+    }
+  };
   float ax = 1.f, ay = 0.f, az = 0.f;  // rotation column 0 (local x in world)
   float bx = 0.f, by = 1.f, bz = 0.f;  // column 1
   float cx = 0.f, cy = 0.f, cz = 1.f;  // column 2
   float px = 0.f, py = 0.f, pz = 0.f;
   bool hit = false;
-  wc.fk_states += active;
 #pragma unroll 1
   for (int i = 0; i < dof; ++i) {
     if (R->jparent[i] < 0) {
@@ -212,8 +340,10 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
     const float L = R->jlen[i];
     px = fmaf(L, cx, px); py = fmaf(L, cy, py); pz = fmaf(L, cz, pz);
 
-    const int s1 = R->sph_begin[i + 1];
-    for (int s = R->sph_begin[i]; s < s1; ++s) {
+    const int s0 = R->sph_begin[i], s1 = R->sph_begin[i + 1];
+    const float4 cb = R->coarse[i];
+    const bool two = R->two_stage && cb.w > 0.f;  // robot-uniform
+    for (int s = s0; s < s1; ++s) {
       const float4 o = R->sph[s];
       const float sx = fmaf(ax, o.x, fmaf(bx, o.y, fmaf(cx, o.z, px)));
       const float sy = fmaf(ay, o.x, fmaf(by, o.y, fmaf(cy, o.z, py)));
@@ -222,10 +352,32 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       st[0] = sx;
       st[32] = sy;
       st[64] = sz;
-      hit |= sphere_hits_env(sx, sy, sz, o.w, env, n_aabb, n_obb, n_cyl, n_sph);
-      wc.sphere_tests += active;
+      if (!two) {
+        hit |= sphere_hits_env(sx, sy, sz, o.w, env, n_aabb, n_obb, n_cyl, n_sph);
+        passes++;
+        if (kWarpVote) {
+          if (__any_sync(kFull, hit && active)) {
+            flush();
+            return true;
+          }
+        }
+      }
+    }
+    if (two) {
+      const float gx = fmaf(ax, cb.x, fmaf(bx, cb.y, fmaf(cx, cb.z, px)));
+      const float gy = fmaf(ay, cb.x, fmaf(by, cb.y, fmaf(cy, cb.z, py)));
+      const float gz = fmaf(az, cb.x, fmaf(bz, cb.y, fmaf(cz, cb.z, pz)));
+      passes++;
+      const unsigned long long r =
+          env_two_stage(env, n_aabb, n_obb, n_cyl, n_sph, gx, gy, gz, cb.w, stage, R->sph, s0, s1, active, lane);
+      hit |= (r >> 63) != 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)(s1 - s0) * (uint32_t)((r >> (15 * k)) & 0x7fffu);
       if (kWarpVote) {
-        if (__any_sync(kFull, hit && active)) return true;
+        if (__any_sync(kFull, hit && active)) {
+          flush();
+          return true;
+        }
       }
     }
   }
@@ -245,12 +397,14 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
     hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr[k];
     if (kWarpVote && (k & 15) == 15) {
       if (__any_sync(kFull, hit && active)) {
-        wc.pair_tests += (unsigned long long)(k + 1) * active;
+        pairs = (uint32_t)(k + 1);
+        flush();
         return true;
       }
     }
   }
-  wc.pair_tests += (unsigned long long)np * active;
+  pairs = (uint32_t)np;
+  flush();
   if (kWarpVote) return __any_sync(kFull, hit && active);
   return hit;
 }

@@ -4,6 +4,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <cmath>
+
+#include "prrtc.h"
 #include "prrtc_device.cuh"
 
 namespace prrtc {
@@ -32,7 +35,42 @@ struct PlanGlobals {
   const int* active;     // problems of this launch as indices into the descriptors (null: 0..n-1)
   unsigned long long slice_ns;  // 0 = run problems to completion; else stop starting iterations
                                 // this long after the launch start (problems resume next launch)
+  int sampler;           // PRRTC_SAMPLER_*
+  uint32_t halton_offset;
+  float dd_radius;       // dynamic domain: 0 = off
+  float dd_alpha;
+  float dd_min_radius;
 };
+
+// Check of the sampler and dynamic-domain fields of a parameter block; null
+// when they are usable, else the reason.
+inline const char* sampling_params_problem(const prrtc_params& p) {
+  if (p.sampler != PRRTC_SAMPLER_PHILOX && p.sampler != PRRTC_SAMPLER_HALTON) return "unknown sampler";
+  if (!(p.dd_radius >= 0.f)) return "dd_radius must be >= 0";
+  if (p.dd_radius > 0.f) {
+    if (!(p.dd_alpha >= 0.f && p.dd_alpha < 1.f)) return "dd_alpha must be in [0, 1)";
+    if (!(p.dd_min_radius >= 0.f) || !std::isfinite(p.dd_min_radius)) return "dd_min_radius must be >= 0";
+  }
+  return nullptr;
+}
+
+// The launch-wide fields that follow from a parameter block alone.
+inline void globals_from_params(PlanGlobals& G, const prrtc_params& p) {
+  G.mode = p.mode;
+  G.max_iters = p.max_iters;
+  G.n_full = (int)std::ceil((double)p.range / (double)p.resolution);
+  if (G.n_full < 1) G.n_full = 1;
+  G.range = p.range;
+  G.resolution = p.resolution;
+  G.bias_thr = (uint32_t)std::ceil((double)p.goal_bias * 16777216.0);
+  G.learned_thr = (uint32_t)std::ceil((double)p.learned_ratio * 16777216.0);
+  G.path_cap = p.path_capacity;
+  G.sampler = p.sampler;
+  G.halton_offset = p.halton_offset;
+  G.dd_radius = p.dd_radius;
+  G.dd_alpha = p.dd_alpha;
+  G.dd_min_radius = p.dd_min_radius;
+}
 
 // Per-problem inputs (uploaded every call).
 struct ProblemDesc {
@@ -40,6 +78,7 @@ struct ProblemDesc {
   EnvView env;
   float* nodes[2];       // [cap * dpad] per tree, rows NaN until written
   int* parent[2];        // [cap] per tree
+  float* radius[2];      // [cap] per tree: dynamic-domain radius, NaN = unbounded
   float* path;           // [path_cap * dof]
   int* path_idx;         // [path_cap] scratch of (tree << 30 | node)
   int cap;
@@ -70,6 +109,8 @@ struct ProblemState {
   double cost;
   unsigned long long t_solve;
   unsigned long long edges, edge_states, sphere_tests, pair_tests, fk_states, nn_nodes, iterations, insert_fail;
+  unsigned long long dd_rejected;
+  unsigned long long prim_tests[4];
   // arena bookkeeping, preserved across launches
   int used_rows[2];
   int used_dpad;

@@ -37,6 +37,7 @@ struct alignas(256) NoAllocScratch {
   ProblemState state;
   alignas(16) int path_idx[kNoAllocRows];
   alignas(16) int parents[2][kNoAllocRows];
+  alignas(16) float radius[2][kNoAllocRows];
   alignas(16) float path[kNoAllocRows * kMaxDof];
   alignas(16) float nodes[2][kNoAllocRows * kMaxDof];
 };
@@ -65,6 +66,7 @@ int noalloc_setup(int dev, cudaStream_t stream, NoAllocScratch** out) {
     NoAllocScratch* s = static_cast<NoAllocScratch*>(p);
     e = cudaMemsetAsync(s->nodes, 0xFF, sizeof(s->nodes), stream);                       // NaN rows
     if (e == cudaSuccess) e = cudaMemsetAsync(s->parents, 0xFF, sizeof(s->parents), stream);  // unset parents
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->radius, 0xFF, sizeof(s->radius), stream);    // NaN radii
     if (e == cudaSuccess) e = cudaMemsetAsync(&s->state, 0, sizeof(s->state), stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return PRRTC_ERR_CUDA;
@@ -95,7 +97,7 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
       !(params->resolution > 0.f) || !(params->goal_bias >= 0.f && params->goal_bias <= 1.f) ||
       (params->mode != PRRTC_MODE_ASYNC && params->mode != PRRTC_MODE_SERIAL) || params->blocks < 0 ||
       params->warps_per_block < 0 || params->warps_per_block > 16 || params->time_limit_s < 0.0 ||
-      (double)params->range / (double)params->resolution > 4096.0)
+      (double)params->range / (double)params->resolution > 4096.0 || sampling_params_problem(*params))
     return PRRTC_ERR_INVALID_ARG;
   const void* robot_dev = nullptr;
   const void* header = nullptr;
@@ -125,6 +127,8 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
   D.nodes[1] = S->nodes[1];
   D.parent[0] = S->parents[0];
   D.parent[1] = S->parents[1];
+  D.radius[0] = S->radius[0];
+  D.radius[1] = S->radius[1];
   D.path = S->path;
   D.path_idx = S->path_idx;
   D.cap = params->tree_capacity;
@@ -142,13 +146,8 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
   PlanGlobals G;
   std::memset(&G, 0, sizeof(G));
   G.n_problems = 1;
-  G.mode = params->mode;
-  G.max_iters = params->max_iters;
-  G.n_full = std::max(1, (int)std::ceil((double)params->range / (double)params->resolution));
-  G.range = params->range;
-  G.resolution = params->resolution;
-  G.bias_thr = (uint32_t)std::ceil((double)params->goal_bias * 16777216.0);
-  G.path_cap = params->path_capacity;
+  globals_from_params(G, *params);
+  G.learned_thr = 0;  // no mixtures on this path
   G.t0 = ULLONG_MAX;
   G.time_limit_ns = (unsigned long long)(params->time_limit_s * 1e9);
 
@@ -198,6 +197,8 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
   info_out->pair_tests = (int64_t)st.pair_tests;
   info_out->fk_states = (int64_t)st.fk_states;
   info_out->nn_nodes = (int64_t)st.nn_nodes;
+  info_out->dd_rejected = (int64_t)st.dd_rejected;
+  for (int k = 0; k < 4; ++k) info_out->prim_tests[k] = (int64_t)st.prim_tests[k];
   if (gout.error) return gout.error;
   return PRRTC_OK;
 }

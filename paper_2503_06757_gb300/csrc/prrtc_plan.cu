@@ -45,10 +45,22 @@ __device__ __forceinline__ bool slice_over(const PlanGlobals* g) {
   return g->slice_ns && globaltimer_ns() - g->t0 > g->slice_ns;
 }
 
-struct Local {
-  unsigned long long edges = 0, edge_states = 0, nn_nodes = 0, iterations = 0, insert_fail = 0;
-  WorkCount wc;
-};
+
+// Halton point `index`, coordinate j (the paper's sampler, Sec. IV-A): the
+// radical inverse of index in the j-th prime base -- its base-p digits
+// mirrored about the radix point -- formed as an exact integer fraction and
+// divided once in FP64.  The primes 2..53 are packed six bits each.
+__device__ __forceinline__ float halton_coord(uint32_t index, int j) {
+  constexpr uint64_t kPrimesLo = 0x7574d134b1c50c2ull;  // 2, 3, 5, ..., 29
+  constexpr uint64_t kPrimesHi = 0xd6fae995full;        // 31, 37, 41, 43, 47, 53
+  const uint32_t b = (uint32_t)((j < 10 ? (kPrimesLo >> (6 * j)) : (kPrimesHi >> (6 * (j - 10)))) & 63u);
+  uint64_t num = 0, den = 1;
+  for (uint32_t i = index; i; i /= b) {
+    num = num * b + i % b;
+    den *= b;
+  }
+  return (float)((double)num / (double)den);
+}
 
 // Warp-uniform vectors of one worker, in shared memory; lane j owns element j.
 struct WarpVecs {
@@ -57,6 +69,7 @@ struct WarpVecs {
   float* b;     // edge end
 };
 constexpr int kWarpVecFloats = 3 * kMaxDof;
+constexpr int kCountFloats = (int)(sizeof(WarpCount) / sizeof(float));
 
 struct Ctx {
   const PlanGlobals* g;
@@ -68,6 +81,7 @@ struct Ctx {
   const float4* env;
   float* stage;
   WarpVecs v;
+  WarpCount* cnt;  // this warp's counters (shared memory, lane 0 writes)
   int lane;
 };
 
@@ -148,9 +162,11 @@ __device__ __noinline__ int nearest(const float* __restrict__ nodes, int n, int 
 // Alg. 2 lines 3-5: the N states a + (k/N)(b - a), k = 1..N, of the edge held
 // in c.v.a / c.v.b, one per lane (several passes if N > 32); false at the
 // first colliding state.
-__device__ __forceinline__ bool edge_free(const Ctx& c, int N, Local& lc) {
-  lc.edges++;
-  lc.edge_states += (unsigned long long)N;
+__device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
+  if (c.lane == 0) {
+    c.cnt->edges++;
+    c.cnt->edge_states += (unsigned long long)N;
+  }
   const float fN = (float)N;
   for (int base = 0; base < N; base += 32) {
     const int k = base + c.lane + 1;
@@ -158,7 +174,7 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N, Local& lc) {
     const int kk = active ? k : N;
     const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N};
     if (state_collides<true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
-                             c.D->env.n_sph, c.stage, qs, active, c.lane, lc.wc))
+                             c.D->env.n_sph, c.stage, qs, active, c.lane, c.cnt))
       return false;
   }
   return true;
@@ -166,12 +182,12 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N, Local& lc) {
 
 // Append the row held by lane j's `val` (element j) to tree t; returns its
 // index or -1 when the tree is full.
-__device__ __forceinline__ int insert(const Ctx& c, int t, float val, int parent, Local& lc) {
+__device__ __forceinline__ int insert(const Ctx& c, int t, float val, int parent) {
   int idx = 0;
   if (c.lane == 0) idx = atomicAdd(&c.S->count[t], 1);
   idx = __shfl_sync(kFull, idx, 0);
   if (idx >= c.D->cap) {
-    if (c.lane == 0) lc.insert_fail++;
+    if (c.lane == 0) c.cnt->insert_fail++;
     return -1;
   }
   if (c.lane == 0) {
@@ -301,7 +317,7 @@ __device__ __forceinline__ float mixture_draw(const float* __restrict__ gmm, con
 
 // Alg. 1 iterations of one worker warp on one problem until it is solved,
 // out of budget or out of time.  Lane j holds element j of every vector.
-__device__ void worker(const Ctx& c, Local& lc) {
+__device__ void worker(const Ctx& c) {
   const PlanGlobals* g = c.g;
   const ProblemDesc* D = c.D;
   ProblemState* S = c.S;
@@ -336,7 +352,7 @@ __device__ void worker(const Ctx& c, Local& lc) {
       }
       break;
     }
-    lc.iterations++;
+    if (lane == 0) c.cnt->iterations++;
 
     // Alg. 1 line 3: extend the smaller tree (ties: T_a).
     const int na = min(ld_relaxed(&S->count[0]), cap);
@@ -355,10 +371,16 @@ __device__ void worker(const Ctx& c, Local& lc) {
     const uint32_t wj = __shfl_sync(kFull, w, (lane + 1) & 31);
     const uint32_t wl = __shfl_sync(kFull, w, 20);
     float crand;
-    if ((w0 >> 8) < g->bias_thr) {
+    const bool goal_sample = (w0 >> 8) < g->bias_thr;
+    if (goal_sample) {
       crand = row_elem(D->nodes[o], 0, dpad, lane);  // goal bias: root of T_o
     } else if (D->gmm && (wl >> 8) < g->learned_thr) {
       crand = mixture_draw(D->gmm, R, D->pid, (uint32_t)it, key, w, lane, dof);
+    } else if (g->sampler == PRRTC_SAMPLER_HALTON) {
+      // Halton point it + 1 + offset (point 0 is the origin of the unit cube)
+      crand = (lane < dof)
+                  ? fmaf(halton_coord((uint32_t)it + 1u + g->halton_offset, lane), R->span[lane], R->lo[lane])
+                  : 0.f;
     } else {
       crand = (lane < dof) ? fmaf(u24(wj), R->span[lane], R->lo[lane]) : 0.f;
     }
@@ -366,7 +388,7 @@ __device__ void worker(const Ctx& c, Local& lc) {
     __syncwarp();
 
     // line 5: nearest node of T_s.
-    const int nn = nearest(D->nodes[s], n_s, dpad, c.v.rnd, lane, &lc.nn_nodes);
+    const int nn = nearest(D->nodes[s], n_s, dpad, c.v.rnd, lane, &c.cnt->nn_nodes);
     const float cnn = row_elem(D->nodes[s], nn, dpad, lane);
 
     // Alg. 2: steer from c_nn toward c_rand by at most delta.
@@ -374,6 +396,16 @@ __device__ void worker(const Ctx& c, Local& lc) {
     const float d2 = warp_sum(diff * diff);
     if (!(d2 > 0.f)) continue;
     const float dist = __fsqrt_rn(d2);
+    // Dynamic-domain sampling (Yershova et al. 2005): a random sample farther
+    // than the nearest node's radius ends the iteration.  NaN = unbounded
+    // (every comparison with NaN is false).
+    const bool dd = g->dd_radius > 0.f;
+    if (dd && !goal_sample) {
+      if (dist > __ldcg(D->radius[s] + nn)) {
+        if (lane == 0) c.cnt->dd_rejected++;
+        continue;
+      }
+    }
     float cnew;
     int N;
     if (dist > range) {
@@ -404,14 +436,27 @@ __device__ void worker(const Ctx& c, Local& lc) {
         if (lane == 0) solved = ld_volatile(&S->solved);
         if (__shfl_sync(kFull, solved, 0)) break;
       }
-      if (!edge_free(c, N, lc)) break;
-      const int added = insert(c, s, bval, prev, lc);
+      const bool free_edge = edge_free(c, N);
+      if (phase == 0 && dd && lane == 0) {
+        // adaptive radius of the nearest node (Jaillet et al. 2005): a bounded
+        // radius grows after a free extension; a collision bounds an unbounded
+        // radius to dd_radius and shrinks a bounded one, not below the floor
+        float* rp = D->radius[s] + nn;
+        const float r = __ldcg(rp);
+        if (free_edge) {
+          if (!isnan(r)) __stcg(rp, r * (1.f + g->dd_alpha));
+        } else {
+          __stcg(rp, isnan(r) ? g->dd_radius : fmaxf(r * (1.f - g->dd_alpha), g->dd_min_radius));
+        }
+      }
+      if (!free_edge) break;
+      const int added = insert(c, s, bval, prev);
       if (added < 0) break;
       prev = added;
       if (phase == 0) {
         // line 8: nearest node of T_o to c_new, and the connect length.
         const int n_o = min(ld_relaxed(&S->count[o]), cap);
-        nno = nearest(D->nodes[o], n_o, dpad, c.v.b, lane, &lc.nn_nodes);
+        nno = nearest(D->nodes[o], n_o, dpad, c.v.b, lane, &c.cnt->nn_nodes);
         ct = row_elem(D->nodes[o], nno, dpad, lane);
         const float dd = ct - cnew;
         Dd = __fsqrt_rn(warp_sum(dd * dd));
@@ -472,7 +517,7 @@ __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
   return -1;
 }
 
-__global__ void plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
+__global__ void __maxnreg__(96) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                             ProblemState* __restrict__ states, int robot_bytes, int env_bytes, int warp_floats) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
@@ -490,7 +535,6 @@ __global__ void plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __re
   }
   __syncthreads();
   uint32_t phase = 0;
-  Local lc;
   for (;;) {
     if (threadIdx.x == 0) s_prob = pick_problem(g, states);
     __syncthreads();
@@ -536,32 +580,30 @@ __global__ void plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __re
     c.pair = pair;
     c.thr = thr;
     c.env = senv;
+    // per-warp area: counters (128 B), the three vectors, sphere-centre staging
     float* warp_area = reinterpret_cast<float*>(smem + robot_bytes + env_bytes) + warp * (warp_floats);
-    c.v.rnd = warp_area;
-    c.v.a = warp_area + kMaxDof;
-    c.v.b = warp_area + 2 * kMaxDof;
-    c.stage = warp_area + kWarpVecFloats;
+    c.cnt = reinterpret_cast<WarpCount*>(warp_area);
+    warp_count_clear(c.cnt, lane);
+    float* vecs = warp_area + kCountFloats;
+    c.v.rnd = vecs;
+    c.v.a = vecs + kMaxDof;
+    c.v.b = vecs + 2 * kMaxDof;
+    c.stage = vecs + kWarpVecFloats;
     c.lane = lane;
-    worker(c, lc);
+    worker(c);
     // flush this warp's counters into the problem
-    unsigned long long v[8] = {lc.edges, lc.edge_states, lc.wc.sphere_tests, lc.wc.pair_tests,
-                               lc.wc.fk_states, lc.nn_nodes, lc.iterations, lc.insert_fail};
-#pragma unroll
-    for (int k = 2; k < 5; ++k)
-#pragma unroll
-      for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], off);
-    if (lane == 0) {
+    // flush this warp's counters into the problem
+    __syncwarp();
+    if (lane < 13) {
       ProblemState* S = states + p;
-      atomicAdd(&S->edges, v[0]);
-      atomicAdd(&S->edge_states, v[1]);
-      atomicAdd(&S->sphere_tests, v[2]);
-      atomicAdd(&S->pair_tests, v[3]);
-      atomicAdd(&S->fk_states, v[4]);
-      atomicAdd(&S->nn_nodes, v[5]);
-      atomicAdd(&S->iterations, v[6]);
-      atomicAdd(&S->insert_fail, v[7]);
+      const WarpCount& w = *c.cnt;
+      unsigned long long* dst[13] = {&S->sphere_tests, &S->pair_tests,  &S->fk_states,     &S->prim_tests[0],
+                                     &S->prim_tests[1], &S->prim_tests[2], &S->prim_tests[3], &S->edges,
+                                     &S->edge_states,  &S->nn_nodes,    &S->iterations,    &S->insert_fail,
+                                     &S->dd_rejected};
+      const unsigned long long val = reinterpret_cast<const unsigned long long*>(&w)[lane];
+      if (val) atomicAdd(dst[lane], val);
     }
-    lc = Local();
     __syncthreads();
   }
 }
@@ -579,10 +621,9 @@ struct EndpointQ {
 __device__ void check_endpoints(const ProblemDesc* D, ProblemState* S, float* stage) {
   const int lane = threadIdx.x & 31;
   const RobotHeader* R = &D->robot->h;
-  WorkCount wc;
   const EndpointQ qs{D->q_start, D->q_goal, lane};
   const bool hit = state_collides<false>(R, D->robot->pair, D->robot->thr, D->env.data, D->env.n_aabb, D->env.n_obb,
-                                         D->env.n_cyl, D->env.n_sph, stage, qs, lane < 2, lane, wc);
+                                         D->env.n_cyl, D->env.n_sph, stage, qs, lane < 2, lane, nullptr);
   const unsigned m = __ballot_sync(kFull, hit);
   if (lane == 0) {
     if (m & 1u) S->pre_status = PRRTC_START_IN_COLLISION;
@@ -604,7 +645,11 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
     const uint32_t nan_bits = 0xffffffffu;
     uint32_t* nodes = reinterpret_cast<uint32_t*>(D->nodes[t]);
     for (size_t k = threadIdx.x; k < nf; k += blockDim.x) nodes[k] = nan_bits;
-    for (int k = threadIdx.x; k < rows; k += blockDim.x) D->parent[t][k] = kUnsetParent;
+    uint32_t* radius = reinterpret_cast<uint32_t*>(D->radius[t]);
+    for (int k = threadIdx.x; k < rows; k += blockDim.x) {
+      D->parent[t][k] = kUnsetParent;
+      radius[k] = nan_bits;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -631,6 +676,8 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
       S->t_solve = 0;
       S->edges = S->edge_states = S->sphere_tests = S->pair_tests = 0;
       S->fk_states = S->nn_nodes = S->iterations = S->insert_fail = 0;
+      S->dd_rejected = 0;
+      S->prim_tests[0] = S->prim_tests[1] = S->prim_tests[2] = S->prim_tests[3] = 0;
     }
     __syncwarp();
     float* stage = reinterpret_cast<float*>(smem);
@@ -681,7 +728,7 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
   if (c.warps > 16) c.warps = 16;
   c.robot_bytes = robot_smem_bytes((max_pairs + 3) & ~3);
   c.env_bytes = max_env_f4 * 16;
-  c.stage_bytes = stage_bytes(max_spheres) + kWarpVecFloats * (int)sizeof(float);  // per warp
+  c.stage_bytes = (int)sizeof(WarpCount) + kWarpVecFloats * (int)sizeof(float) + stage_bytes(max_spheres);  // per warp
   c.smem = c.robot_bytes + c.env_bytes + c.warps * c.stage_bytes;
   int per_sm = 0;
   cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);

@@ -123,7 +123,7 @@ void free_server(prrtc_server* s) {
 }
 
 size_t slot_bytes(const prrtc_params& p) {
-  return (size_t)2 * p.tree_capacity * (kMaxDof * 4 + 4) + (size_t)p.path_capacity * (kMaxDof * 4 + 4) +
+  return (size_t)2 * p.tree_capacity * (kMaxDof * 4 + 8) + (size_t)p.path_capacity * (kMaxDof * 4 + 4) +
          (size_t)kEnvSnapF4 * 16 + kGmmStride * 4 + sizeof(ProblemDesc) + sizeof(ProblemState);
 }
 
@@ -183,6 +183,9 @@ bool server_round(prrtc_server* s) {
     D.nodes[1] = s->nodes + ((size_t)p * 2 + 1) * tree_stride;
     D.parent[0] = s->parents + ((size_t)p * 2 + 0) * prm.tree_capacity;
     D.parent[1] = s->parents + ((size_t)p * 2 + 1) * prm.tree_capacity;
+    float* radii = reinterpret_cast<float*>(s->parents + (size_t)s->slots * 2 * prm.tree_capacity);
+    D.radius[0] = radii + ((size_t)p * 2 + 0) * prm.tree_capacity;
+    D.radius[1] = radii + ((size_t)p * 2 + 1) * prm.tree_capacity;
     D.path = s->paths + (size_t)p * prm.path_capacity * kMaxDof;
     D.path_idx = s->path_idx + (size_t)p * prm.path_capacity;
     D.cap = prm.tree_capacity;
@@ -252,14 +255,7 @@ bool server_round(prrtc_server* s) {
   PlanGlobals& G = *s->h_glob;
   std::memset(&G, 0, sizeof(G));
   G.n_problems = n_active;
-  G.mode = prm.mode;
-  G.max_iters = prm.max_iters;
-  G.n_full = std::max(1, (int)std::ceil((double)prm.range / (double)prm.resolution));
-  G.range = prm.range;
-  G.resolution = prm.resolution;
-  G.bias_thr = (uint32_t)std::ceil((double)prm.goal_bias * 16777216.0);
-  G.learned_thr = (uint32_t)std::ceil((double)prm.learned_ratio * 16777216.0);
-  G.path_cap = prm.path_capacity;
+  globals_from_params(G, prm);
   G.t0 = ULLONG_MAX;
   G.active = s->d_active;
   G.slice_ns = (unsigned long long)s->slice_us * 1000ull;
@@ -309,6 +305,8 @@ bool server_round(prrtc_server* s) {
     P.pair_tests = (int64_t)S.pair_tests;
     P.fk_states = (int64_t)S.fk_states;
     P.nn_nodes = (int64_t)S.nn_nodes;
+    P.dd_rejected = (int64_t)S.dd_rejected;
+    for (int k = 0; k < 4; ++k) P.prim_tests[k] = (int64_t)S.prim_tests[k];
     P.cost = S.cost;
     P.solve_time_us = -1.0;
     if (P.status == PRRTC_SOLVED || P.status == PRRTC_PATH_OVERFLOW) P.n = S.path_n;
@@ -373,7 +371,8 @@ int prrtc_server_create(const prrtc_server_config* cfg, prrtc_server** out) {
   if (!(p.range > 0.f) || !(p.resolution > 0.f) || p.max_iters < 1 || p.tree_capacity < 2 || p.path_capacity < 2 ||
       cfg->slice_us < 10 || cfg->memory_budget_bytes <= 0 || cfg->max_slots < 0 ||
       !(p.learned_ratio >= 0.f && p.learned_ratio <= 1.f) || !(p.goal_bias >= 0.f && p.goal_bias <= 1.f) ||
-      (p.mode != PRRTC_MODE_ASYNC && p.mode != PRRTC_MODE_SERIAL) || (double)p.range / p.resolution > 4096.0) {
+      (p.mode != PRRTC_MODE_ASYNC && p.mode != PRRTC_MODE_SERIAL) || (double)p.range / p.resolution > 4096.0 ||
+      sampling_params_problem(p)) {
     prrtc_internal_set_error("invalid server configuration");
     return PRRTC_ERR_INVALID_ARG;
   }
@@ -396,7 +395,7 @@ int prrtc_server_create(const prrtc_server_config* cfg, prrtc_server** out) {
   const size_t rows = (size_t)slots * 2 * p.tree_capacity;
   cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
   bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaMalloc(&s->nodes, rows * kMaxDof * 4) == cudaSuccess && cudaMalloc(&s->parents, rows * 4) == cudaSuccess &&
+            cudaMalloc(&s->nodes, rows * kMaxDof * 4) == cudaSuccess && cudaMalloc(&s->parents, 2 * rows * 4) == cudaSuccess &&
             cudaMalloc(&s->paths, (size_t)slots * p.path_capacity * kMaxDof * 4) == cudaSuccess &&
             cudaMalloc(&s->path_idx, (size_t)slots * p.path_capacity * 4) == cudaSuccess &&
             cudaMalloc(&s->env_snap, (size_t)slots * kEnvSnapF4 * 16) == cudaSuccess &&
@@ -414,7 +413,7 @@ int prrtc_server_create(const prrtc_server_config* cfg, prrtc_server** out) {
             cudaMallocHost(&s->h_gmm, (size_t)slots * kGmmStride * 4) == cudaSuccess;
   if (ok)
     ok = cudaMemsetAsync(s->nodes, 0xFF, rows * kMaxDof * 4, s->stream) == cudaSuccess &&
-         cudaMemsetAsync(s->parents, 0xFF, rows * 4, s->stream) == cudaSuccess &&
+         cudaMemsetAsync(s->parents, 0xFF, 2 * rows * 4, s->stream) == cudaSuccess &&  // parents, NaN radii
          cudaMemsetAsync(s->d_state, 0, (size_t)slots * sizeof(ProblemState), s->stream) == cudaSuccess &&
          cudaStreamSynchronize(s->stream) == cudaSuccess;
   if (!ok) {

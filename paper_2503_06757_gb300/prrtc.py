@@ -44,7 +44,11 @@ class prrtc_params(C.Structure):
                 ("max_iters", C.c_int32), ("tree_capacity", C.c_int32), ("path_capacity", C.c_int32),
                 ("mode", C.c_int32), ("blocks", C.c_int32), ("warps_per_block", C.c_int32),
                 ("learned_ratio", C.c_float), ("seed", C.c_uint64), ("time_limit_s", C.c_double),
-                ("reserved", C.c_int32 * 8)]
+                ("sampler", C.c_int32), ("halton_offset", C.c_uint32), ("dd_radius", C.c_float),
+                ("dd_alpha", C.c_float), ("dd_min_radius", C.c_float), ("reserved", C.c_int32 * 3)]
+
+
+SAMPLER_PHILOX, SAMPLER_HALTON = 0, 1
 
 
 class prrtc_path(C.Structure):
@@ -52,7 +56,7 @@ class prrtc_path(C.Structure):
                 ("q", _f), ("cost", C.c_double), ("nodes_a", C.c_int32), ("nodes_b", C.c_int32),
                 ("edges_checked", C.c_int64), ("edge_states", C.c_int64), ("solve_time_us", C.c_double),
                 ("sphere_tests", C.c_int64), ("pair_tests", C.c_int64), ("fk_states", C.c_int64),
-                ("nn_nodes", C.c_int64)]
+                ("nn_nodes", C.c_int64), ("dd_rejected", C.c_int64), ("prim_tests", C.c_int64 * 4)]
 
 
 class prrtc_launch_stats(C.Structure):
@@ -62,7 +66,7 @@ class prrtc_launch_stats(C.Structure):
                 ("iterations", C.c_int64), ("grid", C.c_int32), ("block_threads", C.c_int32),
                 ("smem_bytes", C.c_int32), ("problems", C.c_int32), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("reserved_", C.c_int32),
-                ("prep_ms", C.c_double)]
+                ("prep_ms", C.c_double), ("prim_tests", C.c_int64 * 4), ("dd_rejected", C.c_int64)]
 
 
 class prrtc_server_config(C.Structure):
@@ -85,6 +89,7 @@ EXPORTS = [
     "prrtc_params_default", "prrtc_path_free", "prrtc_last_launch_stats", "prrtc_status_string",
     "prrtc_version", "prrtc_last_error", "prrtc_env_create", "prrtc_env_update", "prrtc_env_destroy",
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
+    "prrtc_robot_set_two_stage", "prrtc_robot_bounds",
     "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
     "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_error",
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
@@ -121,6 +126,8 @@ def lib():
     L.prrtc_robot_destroy.argtypes = [C.c_void_p]
     L.prrtc_robot_info.argtypes = [C.c_void_p, _i, _i, _i, _i]
     L.prrtc_env_info.argtypes = [C.c_void_p, _i]
+    L.prrtc_robot_set_two_stage.argtypes = [C.c_void_p, C.c_int32]
+    L.prrtc_robot_bounds.argtypes = [C.c_void_p, _f]
     L.prrtc_check_states.argtypes = [C.c_void_p, C.c_void_p, _f, C.c_int32, C.POINTER(C.c_uint8), _f]
     L.prrtc_check_states_device.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                                             C.c_void_p, C.c_void_p]
@@ -261,6 +268,14 @@ class Robot:
         _check(self._lib.prrtc_robot_info(self.handle, *[C.byref(x) for x in v]), "prrtc_robot_info")
         return dict(dof=v[0].value, n_spheres=v[1].value, n_pairs=v[2].value, dpad=v[3].value)
 
+    def set_two_stage(self, enabled: bool):
+        _check(self._lib.prrtc_robot_set_two_stage(self.handle, int(bool(enabled))), "prrtc_robot_set_two_stage")
+
+    def bounds(self) -> np.ndarray:
+        out = np.zeros((self.dof, 4), np.float32)
+        _check(self._lib.prrtc_robot_bounds(self.handle, out.ctypes.data_as(_f)), "prrtc_robot_bounds")
+        return out
+
     def close(self):
         if getattr(self, "handle", None):
             self._lib.prrtc_robot_destroy(self.handle)
@@ -344,7 +359,7 @@ def _path_dict(p: prrtc_path):
              nodes_a=int(p.nodes_a), nodes_b=int(p.nodes_b), edges_checked=int(p.edges_checked),
              edge_states=int(p.edge_states), solve_time_us=float(p.solve_time_us),
              sphere_tests=int(p.sphere_tests), pair_tests=int(p.pair_tests), fk_states=int(p.fk_states),
-             nn_nodes=int(p.nn_nodes))
+             nn_nodes=int(p.nn_nodes), dd_rejected=int(p.dd_rejected), prim_tests=[int(x) for x in p.prim_tests])
     if p.q and p.n > 0:
         d["path"] = np.ctypeslib.as_array(p.q, shape=(p.n * p.dof,)).reshape(p.n, p.dof).copy()
     else:
@@ -517,7 +532,7 @@ def prrtc_occupancy(env: Env):
 def prrtc_last_launch_stats():
     s = prrtc_launch_stats()
     _check(lib().prrtc_last_launch_stats(C.byref(s)), "prrtc_last_launch_stats")
-    return {k: getattr(s, k) for k, _ in s._fields_}
+    return {k: (list(getattr(s, k)) if isinstance(getattr(s, k), C.Array) else getattr(s, k)) for k, _ in s._fields_}
 
 
 def prrtc_debug_tree(problem: int, tree: int, dof: int):
