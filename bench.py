@@ -277,6 +277,72 @@ def serving_section(args, P, proposals):
     return out
 
 
+# ------------------------------------------------------------------ tensor-core GEMM
+
+GEMM_SHAPES = [
+    ("proposal layer 1 forward, training batch 512", 512, 1024, 4160),
+    ("proposal layer 1 weight gradient, training batch 512", 1024, 4160, 512),
+    ("proposal layer 1 inference, 200 problems", 200, 1024, 4160),
+    ("proposal layer 2 forward, training batch 512", 512, 512, 1024),
+    ("square 8192", 8192, 8192, 8192),
+]
+
+
+def gemm_section(P, torch, peak_tflops, reps=20):
+    """The tcgen05 GEMM (BF16 in, FP32 accumulate, BF16 out) at the learned
+    proposal's shapes and one large square; CUDA events on the launching stream
+    around a CUDA-graph replay of `reps` calls (device time), and around the
+    same calls issued one by one (device time plus host call cost); inputs
+    resident, split-K reduction included where the library splits."""
+    out = dict(peak_tflops=peak_tflops, peak="bf16_tflops (burst) of MEASURED_PEAKS.json", shapes=[])
+    stream = torch.cuda.current_stream()
+    for name, M, N, K in GEMM_SHAPES:
+        g = torch.Generator(device="cuda").manual_seed(M + N + K)
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C16 = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+        call_on = lambda st: P.prrtc_gemm_bf16(A.data_ptr(), B.data_ptr(), M, N, K, 0, False, 0, C16.data_ptr(),
+                                               st.cuda_stream)
+        call = lambda: call_on(stream)
+        n = reps if M * N * K < 1 << 36 else 5
+        # launches replayed from a CUDA graph, so host-side call cost does not
+        # hide the device time of these short kernels
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                call_on(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            for _ in range(n):
+                call_on(side)
+        graph.replay()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        graph.replay()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / n
+        # and through the C ABI call by call (host cost included)
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(n):
+            call()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_calls = ev0.elapsed_time(ev1) / n
+        tf = 2.0 * M * N * K / (ms * 1e-3) * 1e-12
+        err = P.prrtc_gemm_error()
+        out["shapes"].append(dict(name=name, M=M, N=N, K=K, us=ms * 1e3, tflops=tf, frac=tf / peak_tflops,
+                                  us_per_call_unbatched=ms_calls * 1e3, error=err))
+        del A, B, C16, graph
+    return out
+
+
 # ------------------------------------------------------------------ sampler / check variants
 
 DD_PARAMS = dict(dd_radius=5.0, dd_alpha=0.02, dd_min_radius=4.0)
@@ -505,6 +571,7 @@ def run_ours(args):
                                                workload="1M collision-free 7-DoF states vs one shelf scene "
                                                         "(every test runs)")
         extra["variants"] = variants_section(args, P, items, prm, counts, flush, torch)
+        extra["roofline_gemm"] = gemm_section(P, torch, float(peaks.get("bf16_tflops", 1900.0)))
         extra["cpu_baseline"] = oracle_sample(probs, budget_s=args.cpu_budget)
         prop = None
         if not args.no_learned:
@@ -554,11 +621,21 @@ def main():
     ap.add_argument("--learned-steps", type=int, default=4000)
     ap.add_argument("--learned-eval-scenes", type=int, default=500)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--gemm-only", action="store_true",
+                    help="only the tensor-core GEMM microbenchmark (one JSON line; for profiling the GEMM)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.gemm_only:
+        import torch
+        from paper_2503_06757_gb300 import build as B
+        B.build()
+        from paper_2503_06757_gb300 import prrtc as P
+        torch.cuda.init()
+        print(json.dumps(gemm_section(P, torch, float(measured_peaks().get("bf16_tflops", 1900.0)))))
+        return 0
     return run_ours(args)
 
 

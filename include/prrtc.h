@@ -334,6 +334,14 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
  * the kernels (a bounded device wait that gave up: PRRTC_ERR_TIMEOUT). */
 int prrtc_gemm_bf16(const void* a, const void* b, int32_t M, int32_t N, int32_t K, const float* bias,
                     int32_t relu, float* c32, void* c16, void* stream);
+/* As prrtc_gemm_bf16 with the K dimension split into `splits` ranges (0 = the
+ * library's choice, which splits while the 128 x 256 output tiles fill less
+ * than one wave of SMs).  Each range writes an FP32 partial tile to a
+ * library-owned workspace (per device and stream, grown on demand); a second
+ * kernel sums the partials in range order, so results do not depend on
+ * timing, then applies bias, ReLU and the output conversions. */
+int prrtc_gemm_bf16_splitk(const void* a, const void* b, int32_t M, int32_t N, int32_t K, const float* bias,
+                           int32_t relu, float* c32, void* c16, int32_t splits, void* stream);
 int prrtc_gemm_error(void);
 
 /* ------------------------------------------------------------ learned proposal */

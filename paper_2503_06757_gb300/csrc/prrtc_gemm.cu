@@ -3,21 +3,31 @@
 // FP32 accumulation in tensor memory, optional bias + ReLU and FP32 / BF16
 // outputs.
 //
-// One CTA computes a 128 x 128 tile:
-//   warp 0  -- one lane issues TMA loads of 128 x 64 BF16 tiles of A and B
-//              (128-byte swizzle) into a 4-stage shared-memory ring;
-//   warp 1  -- allocates 128 TMEM columns; one lane issues tcgen05.mma
-//              (M=128, N=128, K=16, kind::f16) four times per stage and
-//              commits each stage back to the producer;
-//   warps 2-5 -- wait for the final commit, read the accumulator with
-//              tcgen05.ld (each warp owns one 32-lane quarter of TMEM) and
-//              run the epilogue.
-// Every mbarrier wait is bounded; a wait that gives up records an error and
-// the CTA still frees its tensor memory.
+// Persistent kernel, one CTA per SM.  A work unit is one 128 x 256 output tile
+// over a range of K (split-K when the tiles alone cannot fill the GPU):
+//   warp 0    -- one lane issues TMA loads of the 128 x 64 A and 256 x 64 B
+//                tiles (128-byte swizzle) into a 4-stage shared-memory ring;
+//   warp 1    -- allocates all 512 TMEM columns (two 256-column
+//                accumulators); one lane issues tcgen05.mma (M=128, N=256,
+//                K=16, kind::f16) four times per stage, commits each stage
+//                back to the producer and each finished unit to the epilogue;
+//   warps 2-5 -- read an accumulator with tcgen05.ld (each warp owns one
+//                32-lane quarter of TMEM), run the epilogue, and hand the
+//                accumulator back, so the epilogue of one unit overlaps the
+//                main loop of the next.
+// The epilogue stages each 32 x 32 chunk in a swizzled shared-memory tile and
+// writes it with a TMA bulk tensor store (the TMA engine clips the matrix
+// edges).  With split-K each unit writes its FP32 partial tile to a workspace
+// and a second kernel sums the partials in split order (deterministic) and
+// applies bias, ReLU and the output conversions.
+// Every mbarrier wait is bounded; a wait that gives up records an error, the
+// roles stop, and the CTA still frees its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstring>
+#include <map>
 #include <mutex>
 
 #include "prrtc.h"
@@ -26,14 +36,20 @@
 namespace prrtc {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int EPI_TILE_BYTES = 32 * 128;   // one 32 x 32 FP32 chunk (or 32 x 32 BF16 in its first half)
+constexpr int EPI_BUFS = 2;                 // staging tiles per epilogue warp (double buffered)
+// ring | barriers (1 KB) | staging tiles, plus 1 KB for aligning the base
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 1024 + 4 * EPI_BUFS * EPI_TILE_BYTES;
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = BN;
+constexpr int EPI_WARPS = 4;
+constexpr uint32_t TMEM_COLS = 2 * BN;  // two accumulators
 constexpr uint32_t kPolls = 1u << 26;
+constexpr int kMinKTilesPerSplit = 4;
+constexpr int kMaxSplits = 16;
 
 __device__ int g_gemm_error;
 
@@ -41,10 +57,18 @@ struct Epilogue {
   int M, N, K;
   const float* bias;
   int relu;
-  float* c32;
-  int ldc32;
-  __nv_bfloat16* c16;
-  int ldc16;
+  int has_c32, has_c16;  // outputs written through the c32 / c16 tensor maps
+  int splits;            // > 1: raw partials through the workspace map, rows split * m_pad + row
+  int m_tiles, n_tiles, k_tiles;
+  int m_pad;             // rows of one split's partial (M rounded up to the tile), so that the
+                         // clipped-off rows of an edge tile never reach the next split's rows
+};
+
+// Output tensor maps of one launch: workspace (FP32, rows = splits * m_pad),
+// FP32 output and BF16 output; boxes of 32 x 32 elements, 128- / 64-byte
+// swizzle matching the staging layout below.
+struct OutMaps {
+  CUtensorMap ws, c32, c16;
 };
 
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
@@ -70,6 +94,10 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
   if (mbar_wait(bar, parity, kPolls)) return true;
   atomicExch(&g_gemm_error, PRRTC_ERR_TIMEOUT);
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y) {
@@ -108,68 +136,129 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Epilogue of one 32-column chunk of one output row: bias, ReLU, stores.
-__device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col0, const uint32_t (&v)[32]) {
+// Work unit -> tile (m fastest) and K range.
+struct Unit {
+  int m0, n0, split, kt0, kt1;
+};
+
+__device__ __forceinline__ Unit unit_of(const Epilogue& ep, int u) {
+  Unit w;
+  const int tile = u / ep.splits;
+  w.split = u - tile * ep.splits;
+  w.m0 = (tile % ep.m_tiles) * BM;
+  w.n0 = (tile / ep.m_tiles) * BN;
+  const int base = ep.k_tiles / ep.splits, rem = ep.k_tiles % ep.splits;
+  w.kt0 = w.split * base + min(w.split, rem);
+  w.kt1 = w.kt0 + base + (w.split < rem ? 1 : 0);
+  return w;
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until at most one committed bulk store still reads shared memory.
+__device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Stage one 32 x 32 chunk held one row per lane (lane = row, values v[0..31]
+// = columns) into a shared-memory tile laid out as the TMA engine expects
+// with the store map's swizzle, then let lane 0 store it with one bulk
+// tensor copy.  FP32 rows are 128 bytes (128-byte swizzle: 16-byte unit u of
+// row r sits at unit u ^ (r % 8)); BF16 rows are 64 bytes (64-byte swizzle:
+// unit u ^ ((r / 2) % 4)).  Each store instruction of the warp touches every
+// bank group once, and the TMA engine clips rows and columns outside the
+// matrix.  `buf` alternates between the warp's two staging tiles.
+__device__ __forceinline__ void stage_and_store(const CUtensorMap* map, unsigned char* tiles, int& buf, bool bf16,
+                                                int x, int y, int lane, const float (&f)[32]) {
+  unsigned char* tile = tiles + buf * EPI_TILE_BYTES;
+  if (lane == 0) bulk_wait_read_le1();  // the store issued from this tile two rounds ago has read it
+  __syncwarp();
+  if (!bf16) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float4* dst = reinterpret_cast<float4*>(tile + lane * 128 + ((u ^ (lane & 7)) << 4));
+      *dst = make_float4(f[4 * u], f[4 * u + 1], f[4 * u + 2], f[4 * u + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      uint4 pk;
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(f[8 * u], f[8 * u + 1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(f[8 * u + 2], f[8 * u + 3]);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(f[8 * u + 4], f[8 * u + 5]);
+      __nv_bfloat162 h3 = __floats2bfloat162_rn(f[8 * u + 6], f[8 * u + 7]);
+      pk.x = *reinterpret_cast<uint32_t*>(&h0);
+      pk.y = *reinterpret_cast<uint32_t*>(&h1);
+      pk.z = *reinterpret_cast<uint32_t*>(&h2);
+      pk.w = *reinterpret_cast<uint32_t*>(&h3);
+      *reinterpret_cast<uint4*>(tile + lane * 64 + ((u ^ ((lane >> 1) & 3)) << 4)) = pk;
+    }
+  }
+  fence_proxy_async_smem();  // make the generic-proxy writes visible to the TMA engine
+  __syncwarp();
+  if (lane == 0) {
+    tma_store_2d(map, tile, x, y);
+    bulk_commit();
+  }
+  buf ^= 1;
+}
+
+// Epilogue of one 32 x 32 chunk (rows row0.., columns col0..; lane = row).
+__device__ __forceinline__ void store_chunk(const Epilogue& ep, const OutMaps& om, unsigned char* tiles, int& buf,
+                                            int split, int row0, int col0, int lane, const uint32_t (&v)[32]) {
   float f[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    float x = __uint_as_float(v[j]);
-    if (ep.bias && col0 + j < ep.N) x += ep.bias[col0 + j];
-    if (ep.relu) x = fmaxf(x, 0.f);
-    f[j] = x;
+  for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+  if (ep.splits > 1) {  // raw partial; the reduction kernel finishes it
+    stage_and_store(&om.ws, tiles, buf, false, col0, split * ep.m_pad + row0, lane, f);
+    return;
   }
-  const bool full_chunk = col0 + 32 <= ep.N;
-  if (ep.c32) {
-    float* dst = ep.c32 + (size_t)row * ep.ldc32 + col0;
-    if (full_chunk) {
+  if (ep.bias) {
 #pragma unroll
-      for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
-    } else {
-      for (int j = 0; j < 32 && col0 + j < ep.N; ++j) dst[j] = f[j];
-    }
+    for (int j = 0; j < 32; ++j)
+      if (col0 + j < ep.N) f[j] += ep.bias[col0 + j];
   }
-  if (ep.c16) {
-    __nv_bfloat16* dst = ep.c16 + (size_t)row * ep.ldc16 + col0;
-    if (full_chunk) {
+  if (ep.relu) {
 #pragma unroll
-      for (int j = 0; j < 32; j += 8) {
-        uint4 pk;
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(f[j], f[j + 1]);
-        __nv_bfloat162 h1 = __floats2bfloat162_rn(f[j + 2], f[j + 3]);
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(f[j + 4], f[j + 5]);
-        __nv_bfloat162 h3 = __floats2bfloat162_rn(f[j + 6], f[j + 7]);
-        pk.x = *reinterpret_cast<uint32_t*>(&h0);
-        pk.y = *reinterpret_cast<uint32_t*>(&h1);
-        pk.z = *reinterpret_cast<uint32_t*>(&h2);
-        pk.w = *reinterpret_cast<uint32_t*>(&h3);
-        *reinterpret_cast<uint4*>(dst + j) = pk;
-      }
-    } else {
-      for (int j = 0; j < 32 && col0 + j < ep.N; ++j) dst[j] = __float2bfloat16_rn(f[j]);
-    }
+    for (int j = 0; j < 32; ++j) f[j] = fmaxf(f[j], 0.f);
   }
+  if (ep.has_c32) stage_and_store(&om.c32, tiles, buf, false, col0, row0, lane, f);
+  if (ep.has_c16) stage_and_store(&om.c16, tiles, buf, true, col0, row0, lane, f);
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Epilogue ep) {
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ OutMaps om, Epilogue ep) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* acc_full = empty + STAGES;   // [2] MMA -> epilogue
+  uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
+  uint64_t* roles_done = acc_empty + 2;  // every warp of the CTA -> TMEM release
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(roles_done + 1);
+  unsigned char* epi_tiles = smem + STAGES * STAGE_BYTES + 256 + 768;  // 1024-aligned staging tiles
+  __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int k_tiles = (ep.K + BK - 1) / BK;
+  const int n_units = ep.m_tiles * ep.n_tiles * ep.splits;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], EPI_WARPS);
+    }
+    mbar_init(roles_done, THREADS / 32);
+    s_abort = 0;
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
   }
@@ -183,62 +272,164 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
 
+  // Role loops run on all 32 lanes of a warp (lane 0 waits and issues, the
+  // warp reconverges every step), so every warp reaches the final CTA barrier
+  // converged.
   if (warp == 0) {
-    if (lane == 0) {
-      for (int kt = 0; kt < k_tiles; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-        if (!wait_bar(&empty[s], ph ^ 1u)) break;
-        unsigned char* a = smem + s * STAGE_BYTES;
-        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_2d(a, &tmA, &full[s], kt * BK, m0);
-        tma_load_2d(a + A_BYTES, &tmB, &full[s], kt * BK, n0);
+    int it = 0;  // stage counter across units
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const Unit w = unit_of(ep, u);
+      for (int kt = w.kt0; kt < w.kt1; ++kt, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        int got = 0;
+        if (lane == 0) got = (!*abort_flag && wait_bar(&empty[s], ph ^ 1u)) ? 1 : 0;
+        got = __shfl_sync(kFull, got, 0);
+        if (!got) {
+          if (lane == 0) *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          unsigned char* a = smem + s * STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(a, &tmA, &full[s], kt * BK, w.m0);
+          tma_load_2d(a + A_BYTES, &tmB, &full[s], kt * BK, w.n0);
+        }
+        __syncwarp();
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(BM, BN);
-      bool ok = true;
-      for (int kt = 0; kt < k_tiles; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-        if (!wait_bar(&full[s], ph)) {
+    const uint32_t idesc = idesc_bf16(BM, BN);
+    int it = 0, i = 0;  // stage counter, local unit counter
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++i) {
+      const Unit w = unit_of(ep, u);
+      const int acc = i & 1;
+      // wait until the epilogue has drained this accumulator (first use passes)
+      int got = 0;
+      if (lane == 0) got = (!*abort_flag && wait_bar(&acc_empty[acc], ((uint32_t)(i >> 1) & 1u) ^ 1u)) ? 1 : 0;
+      got = __shfl_sync(kFull, got, 0);
+      if (!got) {
+        if (lane == 0) *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t d = tmem + (uint32_t)(acc * BN);
+      for (int kt = w.kt0; kt < w.kt1; ++kt, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        got = 0;
+        if (lane == 0) got = wait_bar(&full[s], ph) ? 1 : 0;
+        got = __shfl_sync(kFull, got, 0);
+        if (!got) {
+          if (lane == 0) *abort_flag = 1;
           ok = false;
           break;
         }
         fence_after();
-        const uint32_t a = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b = a + A_BYTES;
+        if (lane == 0) {
+          const uint32_t a = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t b = a + A_BYTES;
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)
-          mma_bf16(tmem, smem_desc(a + 32u * k), smem_desc(b + 32u * k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
-        mma_commit(&empty[s]);
+          for (int k = 0; k < BK / 16; ++k)
+            mma_bf16(d, smem_desc(a + 32u * k), smem_desc(b + 32u * k), idesc, (kt > w.kt0 || k > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        __syncwarp();
       }
-      if (ok) mma_commit(done);
+      if (!ok) break;
+      if (lane == 0) mma_commit(&acc_full[acc]);
+      __syncwarp();
     }
   } else {
-    int ok = 0;
-    if (lane == 0) ok = wait_bar(done, 0) ? 1 : 0;
-    ok = __shfl_sync(kFull, ok, 0);
-    if (ok) {
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    unsigned char* tiles = epi_tiles + (warp - 2) * EPI_BUFS * EPI_TILE_BYTES;
+    int buf = 0;
+    int i = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++i) {
+      const Unit w = unit_of(ep, u);
+      const int acc = i & 1;
+      int ok = 0;
+      if (lane == 0) ok = wait_bar(&acc_full[acc], (uint32_t)(i >> 1) & 1u) ? 1 : 0;
+      ok = __shfl_sync(kFull, ok, 0);
+      if (!ok) {
+        if (lane == 0) *abort_flag = 1;
+        break;
+      }
       fence_after();
-      const int q = warp & 3;  // TMEM lane quarter this warp may access
-      const int row = m0 + 32 * q + lane;
+      const int row0 = w.m0 + 32 * q;
       for (int c = 0; c < BN; c += 32) {
         uint32_t v[32];
         __syncwarp();
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-        const int col0 = n0 + c;
-        if (row < ep.M && col0 < ep.N) store_chunk(ep, row, col0, v);
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + c), v);
+        const int col0 = w.n0 + c;
+        if (row0 < ep.M && col0 < ep.N) store_chunk(ep, om, tiles, buf, w.split, row0, col0, lane, v);
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
     }
+    if (lane == 0) bulk_wait_all();  // every bulk store of this warp has landed
+    __syncwarp();
   }
+  // Join: each warp signals that its role is over (its tensor-memory reads
+  // have completed); the allocating warp frees tensor memory only after all
+  // of them.  If the join times out the memory is still freed: the kernel is
+  // ending and the error word is set.
+  __syncwarp();
   fence_before();
-  __syncthreads();
+  if (lane == 0) mbar_arrive(roles_done);
   if (warp == 1) {
+    int joined = 0;
+    if (lane == 0) joined = wait_bar(roles_done, 0) ? 1 : 0;
+    joined = __shfl_sync(kFull, joined, 0);
+    (void)joined;
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Sum of the split-K partials (split s at rows s * m_pad ..) in split order,
+// then bias, ReLU and outputs; four columns per thread (N is a multiple of 8).
+__global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, int M, int m_pad, int N,
+                                     const float* __restrict__ bias, int relu, float* __restrict__ c32, int ldc32,
+                                     __nv_bfloat16* __restrict__ c16, int ldc16) {
+  const int n4 = N >> 2;
+  const size_t total = (size_t)M * n4;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(t / n4), col = (int)(t % n4) * 4;
+    float4 acc = *reinterpret_cast<const float4*>(ws + (size_t)row * N + col);
+    for (int s = 1; s < splits; ++s) {
+      const float4 p = *reinterpret_cast<const float4*>(ws + ((size_t)s * m_pad + row) * N + col);
+      acc.x += p.x;
+      acc.y += p.y;
+      acc.z += p.z;
+      acc.w += p.w;
+    }
+    if (bias) {
+      acc.x += bias[col];
+      acc.y += bias[col + 1];
+      acc.z += bias[col + 2];
+      acc.w += bias[col + 3];
+    }
+    if (relu) {
+      acc.x = fmaxf(acc.x, 0.f);
+      acc.y = fmaxf(acc.y, 0.f);
+      acc.z = fmaxf(acc.z, 0.f);
+      acc.w = fmaxf(acc.w, 0.f);
+    }
+    if (c32) *reinterpret_cast<float4*>(c32 + (size_t)row * ldc32 + col) = acc;
+    if (c16) {
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(acc.x, acc.y), h1 = __floats2bfloat162_rn(acc.z, acc.w);
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t*>(&h0);
+      pk.y = *reinterpret_cast<uint32_t*>(&h1);
+      *reinterpret_cast<uint2*>(c16 + (size_t)row * ldc16 + col) = pk;
+    }
   }
 }
 
@@ -258,41 +449,169 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return g_encode;
 }
 
-// Row-major [rows x K] BF16 matrix, K contiguous; boxes of 64 x 128.
-bool make_tmap(CUtensorMap* tm, const void* ptr, int rows, int K) {
+// Row-major [rows x K] BF16 matrix, K contiguous; boxes of 64 x box_rows.
+bool make_tmap(CUtensorMap* tm, const void* ptr, int rows, int K, int box_rows) {
   auto enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, 128};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Output matrix [rows x cols] with row stride ld elements (FP32 or BF16),
+// boxes of 32 x 32 with the swizzle of the epilogue's staging tiles.
+bool make_out_tmap(CUtensorMap* tm, const void* ptr, int rows, int cols, int ld, bool bf16) {
+  auto enc = encoder();
+  if (!enc) return false;
+  const int es_bytes = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * es_bytes};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  return enc(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr),
+             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Encoded tensor maps by (device, address, rows, inner extent, row stride,
+// kind): the MLP calls the same few layouts every step, and encoding costs
+// host time.  kind 0: BF16 operand with 128-row boxes, 1: with 256-row boxes,
+// 2: FP32 output, 3: BF16 output.
+struct MapKey {
+  int dev;
+  const void* ptr;
+  int rows, cols, ld, kind;
+  bool operator<(const MapKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (ptr != o.ptr) return ptr < o.ptr;
+    if (rows != o.rows) return rows < o.rows;
+    if (cols != o.cols) return cols < o.cols;
+    if (ld != o.ld) return ld < o.ld;
+    return kind < o.kind;
+  }
+};
+std::mutex g_map_mu;
+std::map<MapKey, CUtensorMap> g_maps;
+constexpr size_t kMaxCachedMaps = 256;
+
+bool cached_map(CUtensorMap* tm, const void* ptr, int rows, int cols, int ld, int kind) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  const MapKey key{dev, ptr, rows, cols, ld, kind};
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  auto it = g_maps.find(key);
+  if (it != g_maps.end()) {
+    *tm = it->second;
+    return true;
+  }
+  const bool ok = kind <= 1 ? make_tmap(tm, ptr, rows, cols, kind == 0 ? BM : BN)
+                            : make_out_tmap(tm, ptr, rows, cols, ld, kind == 3);
+  if (!ok) return false;
+  if (g_maps.size() >= kMaxCachedMaps) g_maps.clear();
+  g_maps.emplace(key, *tm);
+  return true;
+}
+
+// Split-K workspace per (device, stream), grown on demand.
+struct Workspace {
+  float* ptr = nullptr;
+  size_t floats = 0;
+};
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+float* workspace(size_t floats, cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace& w = g_ws[{dev, stream}];
+  if (w.floats >= floats && w.ptr) return w.ptr;
+  if (w.ptr) {
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return nullptr;  // earlier launches may still read it
+    cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.floats = 0;
+  }
+  if (cudaMalloc(&w.ptr, floats * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    w.ptr = nullptr;
+    return nullptr;
+  }
+  w.floats = floats;
+  return w.ptr;
+}
+
+int g_sms = 0;
+
 }  // namespace
 
-// Host launcher used by the MLP code and the C ABI entry point.
-int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32, int ldc32,
-              void* c16, int ldc16, cudaStream_t stream) {
+// Host launcher used by the MLP code and the C ABI entry point.  splits_hint:
+// 0 = choose (split K while the tiles fill less than one wave), else forced.
+int gemm_bf16_split(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32,
+                    int ldc32, void* c16, int ldc16, cudaStream_t stream, int splits_hint) {
   if (M <= 0 || N <= 0 || K <= 0 || !a || !b || (!c32 && !c16)) return PRRTC_ERR_INVALID_ARG;
   if (K % 8 || N % 8 || (c32 && ldc32 % 4) || (c16 && ldc16 % 8)) return PRRTC_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) return PRRTC_ERR_INVALID_ARG;
   if ((c32 && (reinterpret_cast<uintptr_t>(c32) & 15)) || (c16 && (reinterpret_cast<uintptr_t>(c16) & 15)))
     return PRRTC_ERR_INVALID_ARG;
   CUtensorMap ta, tb;
-  if (!make_tmap(&ta, a, M, K) || !make_tmap(&tb, b, N, K)) return PRRTC_ERR_CUDA;
+  if (!cached_map(&ta, a, M, K, K, 0) || !cached_map(&tb, b, N, K, K, 1)) return PRRTC_ERR_CUDA;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
       return PRRTC_ERR_CUDA;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     attr = true;
   }
-  Epilogue ep{M, N, K, bias, relu, c32, ldc32, static_cast<__nv_bfloat16*>(c16), ldc16};
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  gemm_bf16_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(ta, tb, ep);
-  return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
+  Epilogue ep{M, N, K, bias, relu, c32 ? 1 : 0, c16 ? 1 : 0, 1, 0, 0, 0, 0};
+  OutMaps om;
+  std::memset(&om, 0, sizeof(om));
+  if (c32 && !cached_map(&om.c32, c32, M, N, ldc32, 2)) return PRRTC_ERR_CUDA;
+  if (c16 && !cached_map(&om.c16, c16, M, N, ldc16, 3)) return PRRTC_ERR_CUDA;
+  ep.m_tiles = (M + BM - 1) / BM;
+  ep.n_tiles = (N + BN - 1) / BN;
+  ep.k_tiles = (K + BK - 1) / BK;
+  ep.m_pad = ep.m_tiles * BM;
+  const int tiles = ep.m_tiles * ep.n_tiles;
+  const int sms = g_sms > 0 ? g_sms : 1;
+  int splits = splits_hint;
+  if (splits <= 0) {
+    splits = 1;
+    while (splits < kMaxSplits && tiles * (splits * 2) <= sms && ep.k_tiles / (splits * 2) >= kMinKTilesPerSplit)
+      splits *= 2;
+  }
+  splits = std::max(1, std::min(splits, std::min(kMaxSplits, ep.k_tiles)));
+  ep.splits = splits;
+  float* ws = nullptr;
+  if (splits > 1) {
+    ws = workspace((size_t)splits * ep.m_pad * N, stream);
+    if (!ws) return PRRTC_ERR_OOM;
+    if (!cached_map(&om.ws, ws, splits * ep.m_pad, N, N, 2)) return PRRTC_ERR_CUDA;
+  }
+  const int units = tiles * splits;
+  const int grid = std::min(units, sms);
+  gemm_bf16_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(ta, tb, om, ep);
+  if (cudaGetLastError() != cudaSuccess) return PRRTC_ERR_CUDA;
+  if (splits > 1) {
+    const size_t work = (size_t)M * (N / 4);
+    const int blocks = (int)std::min<size_t>((work + 255) / 256, (size_t)sms * 8);
+    splitk_reduce_kernel<<<blocks, 256, 0, stream>>>(ws, splits, M, ep.m_pad, N, bias, relu, c32, ldc32,
+                                                     static_cast<__nv_bfloat16*>(c16), ldc16);
+    if (cudaGetLastError() != cudaSuccess) return PRRTC_ERR_CUDA;
+  }
+  return PRRTC_OK;
+}
+
+int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32, int ldc32,
+              void* c16, int ldc16, cudaStream_t stream) {
+  return gemm_bf16_split(a, b, M, N, K, bias, relu, c32, ldc32, c16, ldc16, stream, 0);
 }
 
 // Reads and clears the kernel's error word (synchronous).
@@ -308,6 +627,13 @@ int gemm_take_error() {
 extern "C" int prrtc_gemm_bf16(const void* a, const void* b, int32_t M, int32_t N, int32_t K, const float* bias,
                                int32_t relu, float* c32, void* c16, void* stream) {
   return prrtc::gemm_bf16(a, b, M, N, K, bias, relu, c32, N, c16, N, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int prrtc_gemm_bf16_splitk(const void* a, const void* b, int32_t M, int32_t N, int32_t K,
+                                      const float* bias, int32_t relu, float* c32, void* c16, int32_t splits,
+                                      void* stream) {
+  if (splits < 0) return PRRTC_ERR_INVALID_ARG;
+  return prrtc::gemm_bf16_split(a, b, M, N, K, bias, relu, c32, N, c16, N, static_cast<cudaStream_t>(stream), splits);
 }
 
 extern "C" int prrtc_gemm_error(void) { return prrtc::gemm_take_error(); }

@@ -91,7 +91,7 @@ EXPORTS = [
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
     "prrtc_robot_set_two_stage", "prrtc_robot_bounds",
     "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
-    "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_error",
+    "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_bf16_splitk", "prrtc_gemm_error",
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
     "prrtc_proposal_forward", "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
     "prrtc_proposal_load", "prrtc_occupancy", "prrtc_plan_batch_learned",
@@ -140,6 +140,8 @@ def lib():
     L.prrtc_debug_tree.argtypes = [C.c_int32, C.c_int32, _f, _i, C.c_int32, _i]
     L.prrtc_gemm_bf16.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
                                   C.c_void_p, C.c_void_p, C.c_void_p]
+    L.prrtc_gemm_bf16_splitk.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                         C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
     _u8 = C.POINTER(C.c_uint8)
     L.prrtc_proposal_create.argtypes = [C.c_int32, _f, _f, _f, C.POINTER(C.c_void_p)]
     L.prrtc_proposal_destroy.argtypes = [C.c_void_p]
@@ -572,6 +574,14 @@ def prrtc_gemm_bf16(a_ptr: int, b_ptr: int, M: int, N: int, K: int, bias_ptr: in
     _check(lib().prrtc_gemm_bf16(C.c_void_p(a_ptr), C.c_void_p(b_ptr), M, N, K, C.c_void_p(bias_ptr or None),
                                  int(bool(relu)), C.c_void_p(c32_ptr or None), C.c_void_p(c16_ptr or None),
                                  C.c_void_p(stream or None)), "prrtc_gemm_bf16")
+
+
+def prrtc_gemm_bf16_splitk(a_ptr: int, b_ptr: int, M: int, N: int, K: int, bias_ptr: int = 0, relu: bool = False,
+                           c32_ptr: int = 0, c16_ptr: int = 0, splits: int = 0, stream: int = 0):
+    """prrtc_gemm_bf16 with an explicit split of K (0 = the library's choice)."""
+    _check(lib().prrtc_gemm_bf16_splitk(C.c_void_p(a_ptr), C.c_void_p(b_ptr), M, N, K, C.c_void_p(bias_ptr or None),
+                                        int(bool(relu)), C.c_void_p(c32_ptr or None), C.c_void_p(c16_ptr or None),
+                                        int(splits), C.c_void_p(stream or None)), "prrtc_gemm_bf16_splitk")
 
 
 def prrtc_gemm_error() -> int:
