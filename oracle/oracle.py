@@ -39,7 +39,8 @@ class OrcRobot(C.Structure):
 class OrcEnv(C.Structure):
     _fields_ = [
         ("n_box", C.c_int32), ("box", _PD), ("n_cyl", C.c_int32), ("cyl", _PD),
-        ("n_sph", C.c_int32), ("sph", _PD),
+        ("n_sph", C.c_int32), ("sph", _PD), ("esdf", _PD), ("esdf_origin", C.c_double * 3),
+        ("esdf_voxel", C.c_double), ("esdf_dims", C.c_int32 * 3),
     ]
 
 
@@ -110,6 +111,7 @@ def lib():
         _lib.orc_revalidate.restype = C.c_int32
         _lib.orc_sample.restype = C.c_int
         _lib.orc_sample_learned.restype = C.c_int
+        _lib.orc_esdf_query.restype = C.c_double
     return _lib
 
 
@@ -154,15 +156,51 @@ def make_robot(robot):
     return s
 
 
-def make_env(scene):
+def make_env(scene, esdf=None):
+    """esdf (optional): (values [nz, ny, nx] or flat, origin xyz, voxel size)."""
     h = _Holder()
     b = scene.boxes.reshape(-1) if scene.boxes.size else np.zeros(15)
     c = scene.cylinders.reshape(-1) if scene.cylinders.size else np.zeros(8)
     p = scene.spheres.reshape(-1) if scene.spheres.size else np.zeros(4)
     s = OrcEnv(n_box=int(scene.boxes.shape[0]), box=h.d(b), n_cyl=int(scene.cylinders.shape[0]),
                cyl=h.d(c), n_sph=int(scene.spheres.shape[0]), sph=h.d(p))
+    if esdf is not None:
+        vals, origin, voxel, dims = esdf
+        s.esdf = h.d(np.asarray(vals, np.float64).reshape(-1))
+        s.esdf_origin[:] = [float(x) for x in origin]
+        s.esdf_voxel = float(voxel)
+        s.esdf_dims[:] = [int(x) for x in dims]
     s._holder = h
     return s
+
+
+def voxelize(scene, origin, voxel, dims):
+    """Occupancy [nz, ny, nx] (uint8): voxel centre strictly inside some primitive."""
+    e = make_env(scene)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    out = np.zeros(int(np.prod(dims)), dtype=np.uint8)
+    lib().orc_voxelize(C.byref(e), o.ctypes.data_as(_PD), C.c_double(voxel), d,
+                       out.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return out.reshape(dims[2], dims[1], dims[0])
+
+
+def esdf(occ, dims, voxel):
+    """Signed Euclidean distance field [nz, ny, nx] of an occupancy grid (brute force)."""
+    o = np.ascontiguousarray(np.asarray(occ, np.uint8).reshape(-1))
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    out = np.zeros(o.size)
+    lib().orc_esdf(o.ctypes.data_as(C.POINTER(C.c_uint8)), d, C.c_double(voxel), out.ctypes.data_as(_PD))
+    return out.reshape(dims[2], dims[1], dims[0])
+
+
+def esdf_query(values, origin, voxel, dims, p):
+    v = np.ascontiguousarray(np.asarray(values, np.float64).reshape(-1))
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    return float(lib().orc_esdf_query(v.ctypes.data_as(_PD), o.ctypes.data_as(_PD), C.c_double(voxel), d,
+                                      pp.ctypes.data_as(_PD)))
 
 
 # ------------------------------------------------------------------ primitives
@@ -236,16 +274,16 @@ def sd_sph(sph4, p):
     return float(lib().orc_sd_sph(bp, pp))
 
 
-def clearance(robot, scene, q):
-    r, e = make_robot(robot), make_env(scene)
+def clearance(robot, scene, q, esdf=None):
+    r, e = make_robot(robot), make_env(scene, esdf)
     q, qp = _d(q)
     ce, cs = C.c_double(), C.c_double()
     t = lib().orc_clearance(C.byref(r), C.byref(e), qp, C.byref(ce), C.byref(cs))
     return float(t), float(ce.value), float(cs.value)
 
 
-def check_states(robot, scene, Q):
-    r, e = make_robot(robot), make_env(scene)
+def check_states(robot, scene, Q, esdf=None):
+    r, e = make_robot(robot), make_env(scene, esdf)
     Q, qp = _d(np.asarray(Q).reshape(-1, robot.dof))
     n = Q.shape[0]
     free = np.zeros(n, dtype=np.uint8)
@@ -316,8 +354,8 @@ def _result_dict(res, d, trees=None, path=None):
     return out
 
 
-def plan(robot, scene, q_start, q_goal, want_trees=False, **kw):
-    r, e = make_robot(robot), make_env(scene)
+def plan(robot, scene, q_start, q_goal, want_trees=False, esdf=None, **kw):
+    r, e = make_robot(robot), make_env(scene, esdf)
     keep = []
     prm = _params(keep, **kw)
     d = robot.dof
@@ -338,8 +376,8 @@ def plan(robot, scene, q_start, q_goal, want_trees=False, **kw):
     return _result_dict(res, d, trees, path)
 
 
-def revalidate(robot, scene, path, res):
-    r, e = make_robot(robot), make_env(scene)
+def revalidate(robot, scene, path, res, esdf=None):
+    r, e = make_robot(robot), make_env(scene, esdf)
     p, pp = _d(np.asarray(path).reshape(-1, robot.dof))
     mc = C.c_double()
     bad = lib().orc_revalidate(C.byref(r), C.byref(e), pp, C.c_int32(p.shape[0]), C.c_double(res), C.byref(mc))

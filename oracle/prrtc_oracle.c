@@ -165,6 +165,70 @@ void orc_occupancy(const orc_env* e, const double origin[3], double cell, int32_
       }
 }
 
+/* ------------------------------------------------------- ESDF */
+static double min_signed_distance(const orc_env* e, const double p[3]) {
+  double best = DBL_MAX;
+  for (int o = 0; o < e->n_box; ++o) best = fmin(best, orc_sd_box(e->box + 15 * o, p));
+  for (int o = 0; o < e->n_cyl; ++o) best = fmin(best, orc_sd_cyl(e->cyl + 8 * o, p));
+  for (int o = 0; o < e->n_sph; ++o) best = fmin(best, orc_sd_sph(e->sph + 4 * o, p));
+  return best;
+}
+
+void orc_voxelize(const orc_env* e, const double origin[3], double voxel, const int32_t dims[3], uint8_t* occ) {
+  for (int32_t k = 0; k < dims[2]; ++k)
+    for (int32_t j = 0; j < dims[1]; ++j)
+      for (int32_t i = 0; i < dims[0]; ++i) {
+        double p[3] = {origin[0] + (i + 0.5) * voxel, origin[1] + (j + 0.5) * voxel, origin[2] + (k + 0.5) * voxel};
+        occ[i + (size_t)dims[0] * (j + (size_t)dims[1] * k)] = (uint8_t)(min_signed_distance(e, p) < 0.0);
+      }
+}
+
+void orc_esdf(const uint8_t* occ, const int32_t dims[3], double voxel, double* out) {
+  const int32_t nx = dims[0], ny = dims[1], nz = dims[2];
+  const size_t n = (size_t)nx * ny * nz;
+  const double diag = voxel * sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+  for (size_t v = 0; v < n; ++v) {
+    const int32_t vi = (int32_t)(v % nx), vj = (int32_t)((v / nx) % ny), vk = (int32_t)(v / ((size_t)nx * ny));
+    const uint8_t mine = occ[v];
+    double best2 = -1.0; /* squared distance in voxel units to the nearest voxel of the other kind */
+    for (size_t u = 0; u < n; ++u) {
+      if (occ[u] == mine) continue;
+      const double di = (double)((int32_t)(u % nx) - vi);
+      const double dj = (double)((int32_t)((u / nx) % ny) - vj);
+      const double dk = (double)((int32_t)(u / ((size_t)nx * ny)) - vk);
+      const double d2 = di * di + dj * dj + dk * dk;
+      if (best2 < 0.0 || d2 < best2) best2 = d2;
+    }
+    const double mag = best2 < 0.0 ? diag : voxel * sqrt(best2);
+    out[v] = mine ? -mag : mag;
+  }
+}
+
+double orc_esdf_query(const double* esdf, const double origin[3], double voxel, const int32_t dims[3],
+                      const double p[3]) {
+  int32_t base[3];
+  double t[3];
+  for (int a = 0; a < 3; ++a) {
+    double u = (p[a] - origin[a]) / voxel - 0.5;
+    u = fmin(fmax(u, 0.0), (double)(dims[a] - 1));
+    int32_t i0 = (int32_t)floor(u);
+    if (i0 > dims[a] - 2) i0 = dims[a] - 2;
+    base[a] = i0;
+    t[a] = u - (double)i0;
+  }
+  const int32_t nx = dims[0], ny = dims[1];
+  double c[2][2];
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj) {
+      const size_t row = (size_t)nx * ((size_t)(base[1] + dj) + (size_t)ny * (size_t)(base[2] + dk));
+      const double a = esdf[row + base[0]], b = esdf[row + base[0] + 1];
+      c[dk][dj] = a + t[0] * (b - a); /* along x */
+    }
+  const double y0 = c[0][0] + t[1] * (c[0][1] - c[0][0]); /* along y, k = base */
+  const double y1 = c[1][0] + t[1] * (c[1][1] - c[1][0]); /* along y, k = base + 1 */
+  return y0 + t[2] * (y1 - y0);                          /* along z */
+}
+
 /* ------------------------------------------------------- forward kinematics */
 static void mat4_identity(double M[16]) {
   memset(M, 0, 16 * sizeof(double));
@@ -288,6 +352,7 @@ double orc_clearance(const orc_robot* r, const orc_env* e, const double* q,
     for (int o = 0; o < e->n_box; ++o) ce = fmin(ce, orc_sd_box(e->box + 15 * o, p) - rs);
     for (int o = 0; o < e->n_cyl; ++o) ce = fmin(ce, orc_sd_cyl(e->cyl + 8 * o, p) - rs);
     for (int o = 0; o < e->n_sph; ++o) ce = fmin(ce, orc_sd_sph(e->sph + 4 * o, p) - rs);
+    if (e->esdf) ce = fmin(ce, orc_esdf_query(e->esdf, e->esdf_origin, e->esdf_voxel, e->esdf_dims, p) - rs);
   }
   for (int k = 0; k < r->n_pairs; ++k) {
     int i = r->pairs[2 * k], j = r->pairs[2 * k + 1];

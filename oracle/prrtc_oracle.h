@@ -26,6 +26,11 @@
  *   orc_plan           - tree invariants, obstacle-free and walled-off special
  *                        cases, grid-BFS reachability of a point robot.
  *   orc_occupancy      - closed-form voxel sets of a sphere and a box.
+ *   orc_voxelize / orc_esdf / orc_esdf_query - closed-form fields of one
+ *                        occupied voxel, of a half-space and of empty / full
+ *                        grids; exact reproduction of linear fields; the true
+ *                        signed distance of a sphere obstacle within the
+ *                        discretisation bound.
  *   orc_sample_learned - the mixture statistics of its draws (component
  *                        frequencies, per-component mean and spread).
  *   orc_halton         - the printed van der Corput fractions of bases 2 and 3,
@@ -91,6 +96,13 @@ typedef struct orc_env {
   const double* cyl;   /* [n_cyl*8]: centre(3) unit axis(3) radius half_length */
   int32_t n_sph;
   const double* sph;   /* [n_sph*4]: centre(3) radius */
+  /* optional Euclidean signed distance field (nullable): values at voxel
+   * centres origin + (index + 0.5) * voxel, index i + nx*(j + ny*k); spheres
+   * are tested against it (trilinear read) in addition to the primitives */
+  const double* esdf;
+  double esdf_origin[3];
+  double esdf_voxel;
+  int32_t esdf_dims[3];
 } orc_env;
 
 typedef struct orc_params {
@@ -176,6 +188,24 @@ void orc_halton(uint32_t index, int32_t dim, double* u);
  * lies closer than `radius` to some obstacle (signed distance < radius). */
 void orc_occupancy(const orc_env* e, const double origin[3], double cell, int32_t n, double radius,
                    uint8_t* out);
+
+/* ESDF collision checking (Sec. III-A, ESDF maps of the real-world setup):
+ * occupancy of a voxel grid (voxel centre strictly inside some primitive),
+ * the signed Euclidean distance transform of an occupancy grid, and its
+ * trilinear read.  dims = {nx, ny, nz}, index i + nx*(j + ny*k).
+ *   orc_voxelize:   occ = 1 iff the centre's signed distance to some primitive is < 0.
+ *   orc_esdf:       free voxel: +voxel * (distance in voxel units to the nearest
+ *                   occupied voxel centre); occupied voxel: -voxel * (distance to
+ *                   the nearest free voxel centre); written by brute force over all
+ *                   voxel pairs.  A grid without occupied (free) voxels gives every
+ *                   voxel +(-) the grid diagonal voxel * sqrt(nx^2 + ny^2 + nz^2).
+ *   orc_esdf_query: continuous index u = (p - origin) / voxel - 1/2 per axis,
+ *                   clamped to [0, n - 1]; base i0 = min(floor(u), n - 2),
+ *                   t = u - i0; linear blends along x, then y, then z.  n >= 2. */
+void orc_voxelize(const orc_env* e, const double origin[3], double voxel, const int32_t dims[3], uint8_t* occ);
+void orc_esdf(const uint8_t* occ, const int32_t dims[3], double voxel, double* out);
+double orc_esdf_query(const double* esdf, const double origin[3], double voxel, const int32_t dims[3],
+                      const double p[3]);
 
 /* Forward kinematics by 4x4 homogeneous products.  centres: [S*3];
  * frames (nullable): [dof*16] row-major world transforms. */
