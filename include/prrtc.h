@@ -60,6 +60,7 @@ extern "C" {
 #define PRRTC_MAX_SPHERES 128        /* spheres per robot as given (before merging)    */
 #define PRRTC_MAX_PAIRS 4096         /* self-collision sphere pairs as given           */
 #define PRRTC_MAX_OBSTACLES 1024
+#define PRRTC_ESDF_MAX_DIM 1024   /* voxels per axis of a distance field */
 
 /* ------------------------------------------------------------ geometry */
 #define PRRTC_OBS_BOX 0       /* cuboid: centre, half extents, rotation                 */
@@ -243,6 +244,37 @@ int prrtc_env_create(const prrtc_obstacle* obstacles, int32_t n, prrtc_env** out
 int prrtc_env_update(prrtc_env* env, const int32_t* ids, const prrtc_obstacle* obstacles, int32_t n);
 
 void prrtc_env_destroy(prrtc_env* env);
+
+/* ------------------------------------------------------------ distance-field environments */
+/* The paper's real-world setting checks spheres against a Euclidean signed
+ * distance field (ESDF) built from sensor data instead of primitives
+ * (Sec. III-A, Sec. IV).  Grids: dims = {nx, ny, nz} (each 2..PRRTC_ESDF_MAX_DIM,
+ * at most 2^28 voxels), voxel (i, j, k) has index i + nx*(j + ny*k) and centre
+ * origin + (i + 1/2, j + 1/2, k + 1/2) * voxel.
+ *
+ * prrtc_env_create_esdf: an environment holding the signed distance field of
+ * `occupancy` (host [nx*ny*nz], nonzero = occupied): free voxels get +voxel x
+ * the Euclidean distance (in voxels) to the nearest occupied voxel centre,
+ * occupied voxels -voxel x the distance to the nearest free one (exact,
+ * computed on the device); +/- the grid diagonal when the grid has no voxel
+ * of the other kind.  A sphere (c, r) of the robot collides with it iff the
+ * field's trilinear read at c is < r; the read clamps c into the grid of voxel
+ * centres (the field continues flat beyond it).  Such an environment has no
+ * primitives; planning and checking calls take it like any other.
+ * prrtc_env_update_esdf: replace the occupancy (same grid) and recompute;
+ * ordered with planning calls on the library's stream.
+ * prrtc_env_esdf_values: host [nx*ny*nz] copy of the field.
+ * prrtc_voxelize: occupancy of a grid from an environment's primitives
+ * (voxel centre strictly inside some primitive), host [nx*ny*nz] output --
+ * synthetic occupancy for distance-field environments.
+ * Errors: PRRTC_ERR_INVALID_ARG (bad grid, null pointers, env without field),
+ * PRRTC_ERR_OOM. */
+int prrtc_env_create_esdf(const float origin[3], float voxel, const int32_t dims[3], const uint8_t* occupancy,
+                          prrtc_env** out);
+int prrtc_env_update_esdf(prrtc_env* env, const uint8_t* occupancy);
+int prrtc_env_esdf_values(const prrtc_env* env, float* out);
+int prrtc_voxelize(const prrtc_env* env, const float origin[3], float voxel, const int32_t dims[3],
+                   uint8_t* occupancy);
 
 /* Upload a robot sphere model.  Coincident spheres of equal radius on the same
  * frame are merged (the verdicts do not change); self pairs are re-indexed. */

@@ -112,6 +112,7 @@ def lib():
         _lib.orc_sample.restype = C.c_int
         _lib.orc_sample_learned.restype = C.c_int
         _lib.orc_esdf_query.restype = C.c_double
+        _lib.orc_esdf_at.restype = C.c_double
     return _lib
 
 
@@ -192,6 +193,13 @@ def esdf(occ, dims, voxel):
     out = np.zeros(o.size)
     lib().orc_esdf(o.ctypes.data_as(C.POINTER(C.c_uint8)), d, C.c_double(voxel), out.ctypes.data_as(_PD))
     return out.reshape(dims[2], dims[1], dims[0])
+
+
+def esdf_at(occ, dims, voxel, i, j, k):
+    o = np.ascontiguousarray(np.asarray(occ, np.uint8).reshape(-1))
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    return float(lib().orc_esdf_at(o.ctypes.data_as(C.POINTER(C.c_uint8)), d, C.c_double(voxel), C.c_int32(i),
+                                   C.c_int32(j), C.c_int32(k)))
 
 
 def esdf_query(values, origin, voxel, dims, p):

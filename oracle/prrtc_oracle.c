@@ -183,25 +183,30 @@ void orc_voxelize(const orc_env* e, const double origin[3], double voxel, const 
       }
 }
 
-void orc_esdf(const uint8_t* occ, const int32_t dims[3], double voxel, double* out) {
+double orc_esdf_at(const uint8_t* occ, const int32_t dims[3], double voxel, int32_t vi, int32_t vj, int32_t vk) {
   const int32_t nx = dims[0], ny = dims[1], nz = dims[2];
   const size_t n = (size_t)nx * ny * nz;
   const double diag = voxel * sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
-  for (size_t v = 0; v < n; ++v) {
-    const int32_t vi = (int32_t)(v % nx), vj = (int32_t)((v / nx) % ny), vk = (int32_t)(v / ((size_t)nx * ny));
-    const uint8_t mine = occ[v];
-    double best2 = -1.0; /* squared distance in voxel units to the nearest voxel of the other kind */
-    for (size_t u = 0; u < n; ++u) {
-      if (occ[u] == mine) continue;
-      const double di = (double)((int32_t)(u % nx) - vi);
-      const double dj = (double)((int32_t)((u / nx) % ny) - vj);
-      const double dk = (double)((int32_t)(u / ((size_t)nx * ny)) - vk);
-      const double d2 = di * di + dj * dj + dk * dk;
-      if (best2 < 0.0 || d2 < best2) best2 = d2;
-    }
-    const double mag = best2 < 0.0 ? diag : voxel * sqrt(best2);
-    out[v] = mine ? -mag : mag;
+  const uint8_t mine = occ[vi + (size_t)nx * (vj + (size_t)ny * vk)] != 0;
+  double best2 = -1.0; /* squared distance in voxel units to the nearest voxel of the other kind */
+  for (size_t u = 0; u < n; ++u) {
+    if ((occ[u] != 0) == mine) continue;
+    const double di = (double)((int32_t)(u % nx) - vi);
+    const double dj = (double)((int32_t)((u / nx) % ny) - vj);
+    const double dk = (double)((int32_t)(u / ((size_t)nx * ny)) - vk);
+    const double d2 = di * di + dj * dj + dk * dk;
+    if (best2 < 0.0 || d2 < best2) best2 = d2;
   }
+  const double mag = best2 < 0.0 ? diag : voxel * sqrt(best2);
+  return mine ? -mag : mag;
+}
+
+void orc_esdf(const uint8_t* occ, const int32_t dims[3], double voxel, double* out) {
+  const int32_t nx = dims[0], ny = dims[1], nz = dims[2];
+  for (int32_t k = 0; k < nz; ++k)
+    for (int32_t j = 0; j < ny; ++j)
+      for (int32_t i = 0; i < nx; ++i)
+        out[i + (size_t)nx * (j + (size_t)ny * k)] = orc_esdf_at(occ, dims, voxel, i, j, k);
 }
 
 double orc_esdf_query(const double* esdf, const double origin[3], double voxel, const int32_t dims[3],

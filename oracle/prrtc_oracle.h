@@ -204,6 +204,8 @@ void orc_occupancy(const orc_env* e, const double origin[3], double cell, int32_
  *                   t = u - i0; linear blends along x, then y, then z.  n >= 2. */
 void orc_voxelize(const orc_env* e, const double origin[3], double voxel, const int32_t dims[3], uint8_t* occ);
 void orc_esdf(const uint8_t* occ, const int32_t dims[3], double voxel, double* out);
+/* The same field at one voxel (i, j, k), for spot checks of large grids. */
+double orc_esdf_at(const uint8_t* occ, const int32_t dims[3], double voxel, int32_t i, int32_t j, int32_t k);
 double orc_esdf_query(const double* esdf, const double origin[3], double voxel, const int32_t dims[3],
                       const double p[3]);
 

@@ -18,7 +18,8 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libprrtc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["prrtc_api.cu", "prrtc_check.cu", "prrtc_plan.cu", "prrtc_noalloc.cu", "prrtc_gemm.cu", "prrtc_mlp.cu", "prrtc_server.cu"]
+SOURCES = ["prrtc_api.cu", "prrtc_check.cu", "prrtc_plan.cu", "prrtc_noalloc.cu", "prrtc_gemm.cu", "prrtc_mlp.cu",
+           "prrtc_server.cu", "prrtc_esdf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -45,6 +45,14 @@ struct prrtc_env {
   int n_aabb = 0, n_obb = 0, n_cyl = 0, n_sph = 0;
   std::vector<int> kind;    // per obstacle id: 0 aabb, 1 obb, 2 cylinder, 3 sphere
   std::vector<int> offset;  // per obstacle id: first float4 in the blob
+  // optional distance field
+  float* d_esdf = nullptr;
+  uint8_t* d_occ = nullptr;
+  int2* d_tmp = nullptr;    // 2 x voxels, scratch of the transform
+  int dims[3] = {0, 0, 0};
+  float origin[3] = {0.f, 0.f, 0.f};
+  float voxel = 0.f;
+  size_t voxels() const { return (size_t)dims[0] * dims[1] * dims[2]; }
   EnvView view() const {
     EnvView v;
     v.data = d_data;
@@ -52,6 +60,8 @@ struct prrtc_env {
     v.n_obb = n_obb;
     v.n_cyl = n_cyl;
     v.n_sph = n_sph;
+    v.esdf = EsdfGrid{d_esdf, origin[0], origin[1], origin[2], d_esdf ? 1.f / voxel : 0.f, dims[0], dims[1], dims[2],
+                      0};
     return v;
   }
 };
@@ -453,7 +463,100 @@ int prrtc_internal_env_snapshot(prrtc_env* env, float4* dst, int max_f4, EnvView
 void prrtc_env_destroy(prrtc_env* env) {
   if (!env) return;
   cudaFree(env->d_data);
+  cudaFree(env->d_esdf);
+  cudaFree(env->d_occ);
+  cudaFree(env->d_tmp);
   delete env;
+}
+
+// -------------------------------------------------------------- distance fields
+static int check_grid(const float origin[3], float voxel, const int32_t dims[3]) {
+  if (!origin || !dims) return fail(PRRTC_ERR_INVALID_ARG, "null grid argument");
+  if (!(voxel > 0.f) || !std::isfinite(voxel) || !finite_all(origin, 3))
+    return fail(PRRTC_ERR_INVALID_ARG, "voxel must be > 0 and the origin finite");
+  size_t V = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 2 || dims[a] > PRRTC_ESDF_MAX_DIM) return fail(PRRTC_ERR_INVALID_ARG, "grid dimension out of range");
+    V *= (size_t)dims[a];
+  }
+  if (V > ((size_t)1 << 28)) return fail(PRRTC_ERR_INVALID_ARG, "grid has too many voxels");
+  return PRRTC_OK;
+}
+
+int prrtc_env_create_esdf(const float origin[3], float voxel, const int32_t dims[3], const uint8_t* occupancy,
+                          prrtc_env** out) {
+  if (!out) return fail(PRRTC_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  int rc = check_grid(origin, voxel, dims);
+  if (rc) return rc;
+  if (!occupancy) return fail(PRRTC_ERR_INVALID_ARG, "occupancy is null");
+  prrtc_env* e = nullptr;
+  if ((rc = prrtc_env_create(nullptr, 0, &e))) return rc;
+  for (int a = 0; a < 3; ++a) {
+    e->dims[a] = dims[a];
+    e->origin[a] = origin[a];
+  }
+  e->voxel = voxel;
+  const size_t V = e->voxels();
+  if (cudaMalloc(&e->d_esdf, V * sizeof(float)) != cudaSuccess || cudaMalloc(&e->d_occ, V) != cudaSuccess ||
+      cudaMalloc(&e->d_tmp, 2 * V * sizeof(int2)) != cudaSuccess) {
+    cudaGetLastError();
+    prrtc_env_destroy(e);
+    return fail(PRRTC_ERR_OOM, "distance field allocation failed");
+  }
+  if ((rc = prrtc_env_update_esdf(e, occupancy))) {
+    prrtc_env_destroy(e);
+    return rc;
+  }
+  *out = e;
+  return PRRTC_OK;
+}
+
+int prrtc_env_update_esdf(prrtc_env* env, const uint8_t* occupancy) {
+  if (!env || !occupancy || !env->d_esdf) return fail(PRRTC_ERR_INVALID_ARG, "env has no distance field");
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  if (c->device != env->device) return fail(PRRTC_ERR_INVALID_ARG, "env belongs to another device");
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::lock_guard<std::mutex> lk_env(env->mu);
+  const size_t V = env->voxels();
+  // stream-ordered: planning calls issued before see the old field, later ones the new
+  CK(cudaMemcpyAsync(env->d_occ, occupancy, V, cudaMemcpyHostToDevice, c->stream));
+  cudaError_t e = launch_esdf(env->d_occ, env->dims, env->voxel, env->d_tmp, env->d_tmp + V, env->d_esdf, c->stream);
+  if (e != cudaSuccess) return cuda_fail("distance transform launch", e);
+  CK(cudaStreamSynchronize(c->stream));
+  return PRRTC_OK;
+}
+
+int prrtc_env_esdf_values(const prrtc_env* env, float* out) {
+  if (!env || !out || !env->d_esdf) return fail(PRRTC_ERR_INVALID_ARG, "env has no distance field");
+  CK(cudaMemcpy(out, env->d_esdf, env->voxels() * sizeof(float), cudaMemcpyDeviceToHost));
+  return PRRTC_OK;
+}
+
+int prrtc_voxelize(const prrtc_env* env, const float origin[3], float voxel, const int32_t dims[3],
+                   uint8_t* occupancy) {
+  if (!env || !occupancy) return fail(PRRTC_ERR_INVALID_ARG, "null argument");
+  int rc = check_grid(origin, voxel, dims);
+  if (rc) return rc;
+  DeviceCtx* c = nullptr;
+  if ((rc = current_ctx(&c))) return rc;
+  if (c->device != env->device) return fail(PRRTC_ERR_INVALID_ARG, "env belongs to another device");
+  const size_t V = (size_t)dims[0] * dims[1] * dims[2];
+  uint8_t* d = nullptr;
+  if (cudaMalloc(&d, V) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PRRTC_ERR_OOM, "voxel buffer allocation failed");
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  const int dd[3] = {dims[0], dims[1], dims[2]};
+  cudaError_t e = launch_voxelize(env->view(), origin, voxel, dd, d, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(occupancy, d, V, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail("voxelize", e);
+  return PRRTC_OK;
 }
 
 // -------------------------------------------------------------- robot

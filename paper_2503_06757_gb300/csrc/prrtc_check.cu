@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
     const bool active = idx < n;
     const size_t src = (size_t)(active ? idx : n - 1) * dof;
     for (int j = 0; j < dof; ++j) qst[j * 32 + lane] = q[src + j];
-    const bool hit = state_collides<false>(R, pair, thr, senv, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph, stage,
-                                           qs, active, lane, wc);
+    const bool hit = state_collides<false>(R, pair, thr, senv, env.n_aabb, env.n_obb, env.n_cyl, env.n_sph, env.esdf,
+                                           stage, qs, active, lane, wc);
     if (active) {
       valid[idx] = hit ? 0 : 1;
       if (spheres) {

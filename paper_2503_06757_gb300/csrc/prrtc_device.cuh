@@ -61,14 +61,46 @@ struct RobotDev {
   int16_t raw_to_distinct[128];
 };
 
+// Euclidean signed distance field on a voxel grid (the paper's ESDF maps):
+// values at voxel centres (ox, oy, oz) + (index + 1/2) * voxel, index
+// i + nx*(j + ny*k); v == null when the environment has none.
+struct EsdfGrid {
+  const float* v;
+  float ox, oy, oz, inv_voxel;
+  int nx, ny, nz, pad_;
+};
+
 // Environment: one float4 array laid out as
 //   [AABB x2: centre|0, half|0][OBB x5: centre, half, R^T rows][CYL x2:
-//   centre|radius, axis|half_len][SPH x1: centre|radius].
+//   centre|radius, axis|half_len][SPH x1: centre|radius],
+// plus an optional distance field (read from global memory / L2).
 struct EnvView {
   const float4* data;
   int n_aabb, n_obb, n_cyl, n_sph;
+  EsdfGrid esdf;
   __host__ __device__ int n_float4() const { return 2 * n_aabb + 5 * n_obb + 2 * n_cyl + n_sph; }
 };
+
+// Trilinear read of the distance field at p: continuous index
+// u = (p - origin) / voxel - 1/2 per axis, clamped to [0, n - 1], base
+// min(floor(u), n - 2); blends along x, then y, then z.  Out of line, so that
+// environments without a field pay no registers for it.
+static __device__ __noinline__ float esdf_read(const EsdfGrid& g, float px, float py, float pz) {
+  float u = fminf(fmaxf(fmaf(px - g.ox, g.inv_voxel, -0.5f), 0.f), (float)(g.nx - 1));
+  float w = fminf(fmaxf(fmaf(py - g.oy, g.inv_voxel, -0.5f), 0.f), (float)(g.ny - 1));
+  float z = fminf(fmaxf(fmaf(pz - g.oz, g.inv_voxel, -0.5f), 0.f), (float)(g.nz - 1));
+  const int i0 = min((int)u, g.nx - 2), j0 = min((int)w, g.ny - 2), k0 = min((int)z, g.nz - 2);
+  const float tx = u - (float)i0, ty = w - (float)j0, tz = z - (float)k0;
+  const float* b = g.v + (size_t)i0 + (size_t)g.nx * ((size_t)j0 + (size_t)g.ny * (size_t)k0);
+  const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+  float c00 = __ldg(b), c01 = __ldg(b + sy), c10 = __ldg(b + sz), c11 = __ldg(b + sz + sy);
+  c00 = fmaf(tx, __ldg(b + 1) - c00, c00);
+  c01 = fmaf(tx, __ldg(b + sy + 1) - c01, c01);
+  c10 = fmaf(tx, __ldg(b + sz + 1) - c10, c10);
+  c11 = fmaf(tx, __ldg(b + sz + sy + 1) - c11, c11);
+  const float y0 = fmaf(ty, c01 - c00, c00), y1 = fmaf(ty, c11 - c10, c10);
+  return fmaf(tz, y1 - y0, y0);
+}
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products,
@@ -282,8 +314,11 @@ struct EdgeQ {
 template <bool kWarpVote, class QS>
 __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R, const uint32_t* __restrict__ pair,
                                                const float* __restrict__ thr, const float4* __restrict__ env,
-                                               int n_aabb, int n_obb, int n_cyl, int n_sph, float* __restrict__ stage,
-                                               const QS& qs, bool active, int lane, WarpCount* wc) {
+                                               int n_aabb, int n_obb, int n_cyl, int n_sph, const EsdfGrid& grid,
+                                               float* __restrict__ stage, const QS& qs, bool active, int lane,
+                                               WarpCount* wc) {
+  const bool has_grid = grid.v != nullptr;
+  const bool has_prims = (n_aabb | n_obb | n_cyl | n_sph) != 0;
   const int dof = R->dof;
   // uniform work of this call, multiplied by the active lanes on the way out
   const unsigned long long na = (unsigned long long)__popc(__ballot_sync(kFull, active));
@@ -342,7 +377,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
 
     const int s0 = R->sph_begin[i], s1 = R->sph_begin[i + 1];
     const float4 cb = R->coarse[i];
-    const bool two = R->two_stage && cb.w > 0.f;  // robot-uniform
+    const bool two = R->two_stage && cb.w > 0.f && has_prims;  // uniform
     for (int s = s0; s < s1; ++s) {
       const float4 o = R->sph[s];
       const float sx = fmaf(ax, o.x, fmaf(bx, o.y, fmaf(cx, o.z, px)));
@@ -352,6 +387,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       st[0] = sx;
       st[32] = sy;
       st[64] = sz;
+      if (has_grid) hit |= esdf_read(grid, sx, sy, sz) < o.w;  // the distance field, sphere by sphere
       if (!two) {
         hit |= sphere_hits_env(sx, sy, sz, o.w, env, n_aabb, n_obb, n_cyl, n_sph);
         passes++;

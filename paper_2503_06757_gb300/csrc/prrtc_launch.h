@@ -149,6 +149,14 @@ cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, in
 // is problem p's float range (n + 1 entries, device memory).
 cudaError_t launch_gather_paths(const ProblemDesc* desc, const int* offsets, int n, float* out, cudaStream_t stream);
 
+// Distance fields (prrtc_esdf.cu): occupancy of voxel centres inside the
+// environment's primitives, and the signed distance transform of an
+// occupancy grid (tmp_a, tmp_b: V int2 each).
+cudaError_t launch_voxelize(const EnvView& env, const float origin[3], float voxel, const int dims[3], uint8_t* occ,
+                            cudaStream_t stream);
+cudaError_t launch_esdf(const uint8_t* occ, const int dims[3], float voxel, int2* tmp_a, int2* tmp_b, float* out,
+                        cudaStream_t stream);
+
 // Tensor-core GEMM (prrtc_gemm.cu): C[M,N] = A[M,K] B[N,K]^T (+bias, ReLU).
 int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32, int ldc32,
               void* c16, int ldc16, cudaStream_t stream);

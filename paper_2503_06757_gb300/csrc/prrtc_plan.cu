@@ -174,7 +174,7 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
     const int kk = active ? k : N;
     const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N};
     if (state_collides<true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
-                             c.D->env.n_sph, c.stage, qs, active, c.lane, c.cnt))
+                             c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt))
       return false;
   }
   return true;
@@ -623,7 +623,8 @@ __device__ void check_endpoints(const ProblemDesc* D, ProblemState* S, float* st
   const RobotHeader* R = &D->robot->h;
   const EndpointQ qs{D->q_start, D->q_goal, lane};
   const bool hit = state_collides<false>(R, D->robot->pair, D->robot->thr, D->env.data, D->env.n_aabb, D->env.n_obb,
-                                         D->env.n_cyl, D->env.n_sph, stage, qs, lane < 2, lane, nullptr);
+                                         D->env.n_cyl, D->env.n_sph, D->env.esdf, stage, qs, lane < 2, lane,
+                                         nullptr);
   const unsigned m = __ballot_sync(kFull, hit);
   if (lane == 0) {
     if (m & 1u) S->pre_status = PRRTC_START_IN_COLLISION;

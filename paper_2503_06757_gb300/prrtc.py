@@ -89,7 +89,8 @@ EXPORTS = [
     "prrtc_params_default", "prrtc_path_free", "prrtc_last_launch_stats", "prrtc_status_string",
     "prrtc_version", "prrtc_last_error", "prrtc_env_create", "prrtc_env_update", "prrtc_env_destroy",
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
-    "prrtc_robot_set_two_stage", "prrtc_robot_bounds",
+    "prrtc_robot_set_two_stage", "prrtc_robot_bounds", "prrtc_env_create_esdf", "prrtc_env_update_esdf",
+    "prrtc_env_esdf_values", "prrtc_voxelize",
     "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
     "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_bf16_splitk", "prrtc_gemm_error",
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
@@ -127,6 +128,12 @@ def lib():
     L.prrtc_robot_info.argtypes = [C.c_void_p, _i, _i, _i, _i]
     L.prrtc_env_info.argtypes = [C.c_void_p, _i]
     L.prrtc_robot_set_two_stage.argtypes = [C.c_void_p, C.c_int32]
+    L.prrtc_env_create_esdf.argtypes = [C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
+                                        C.POINTER(C.c_void_p)]
+    L.prrtc_env_update_esdf.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
+    L.prrtc_env_esdf_values.argtypes = [C.c_void_p, _f]
+    L.prrtc_voxelize.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_uint8)]
     L.prrtc_robot_bounds.argtypes = [C.c_void_p, _f]
     L.prrtc_check_states.argtypes = [C.c_void_p, C.c_void_p, _f, C.c_int32, C.POINTER(C.c_uint8), _f]
     L.prrtc_check_states_device.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
@@ -221,6 +228,44 @@ class Env:
         out = (C.c_int32 * 4)()
         _check(self._lib.prrtc_env_info(self.handle, out), "prrtc_env_info")
         return tuple(out)
+
+    @classmethod
+    def from_occupancy(cls, occupancy, origin, voxel: float):
+        """Distance-field environment (prrtc_env_create_esdf); occupancy [nz, ny, nx]."""
+        occ = np.ascontiguousarray(np.asarray(occupancy) != 0, dtype=np.uint8)
+        nz, ny, nx = occ.shape
+        self = cls.__new__(cls)
+        self._lib = lib()
+        o = (C.c_float * 3)(*[float(x) for x in origin])
+        d = (C.c_int32 * 3)(nx, ny, nz)
+        h = C.c_void_p()
+        _check(self._lib.prrtc_env_create_esdf(o, C.c_float(voxel), d, occ.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                               C.byref(h)), "prrtc_env_create_esdf")
+        self.handle = h
+        self.n = 0
+        self.grid = ((nx, ny, nz), tuple(float(x) for x in origin), float(voxel))
+        return self
+
+    def update_occupancy(self, occupancy):
+        occ = np.ascontiguousarray(np.asarray(occupancy) != 0, dtype=np.uint8)
+        _check(self._lib.prrtc_env_update_esdf(self.handle, occ.ctypes.data_as(C.POINTER(C.c_uint8))),
+               "prrtc_env_update_esdf")
+
+    def esdf(self) -> np.ndarray:
+        (nx, ny, nz), _, _ = self.grid
+        out = np.zeros((nz, ny, nx), np.float32)
+        _check(self._lib.prrtc_env_esdf_values(self.handle, out.ctypes.data_as(_f)), "prrtc_env_esdf_values")
+        return out
+
+    def voxelize(self, origin, voxel: float, dims) -> np.ndarray:
+        """Occupancy [nz, ny, nx] of this environment's primitives (prrtc_voxelize)."""
+        nx, ny, nz = (int(x) for x in dims)
+        out = np.zeros((nz, ny, nx), np.uint8)
+        o = (C.c_float * 3)(*[float(x) for x in origin])
+        d = (C.c_int32 * 3)(nx, ny, nz)
+        _check(self._lib.prrtc_voxelize(self.handle, o, C.c_float(voxel), d, out.ctypes.data_as(C.POINTER(C.c_uint8))),
+               "prrtc_voxelize")
+        return out
 
     def close(self):
         if getattr(self, "handle", None):
