@@ -136,7 +136,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Work unit -> tile (m fastest) and K range.
+// Work unit -> tile and K range.  Tiles go in groups of kGroupM row tiles:
+// m fastest inside a group, then n, then the next group, so that the tiles in
+// flight at once (one per SM) share a slab of A rows and a few B columns that
+// stay in L2 instead of sweeping all of A for every column of B.
+constexpr int kGroupM = 16;
 struct Unit {
   int m0, n0, split, kt0, kt1;
 };
@@ -145,8 +149,12 @@ __device__ __forceinline__ Unit unit_of(const Epilogue& ep, int u) {
   Unit w;
   const int tile = u / ep.splits;
   w.split = u - tile * ep.splits;
-  w.m0 = (tile % ep.m_tiles) * BM;
-  w.n0 = (tile / ep.m_tiles) * BN;
+  const int span = kGroupM * ep.n_tiles;
+  const int first_m = (tile / span) * kGroupM;
+  const int gm = min(ep.m_tiles - first_m, kGroupM);
+  const int in = tile - (tile / span) * span;
+  w.m0 = (first_m + in % gm) * BM;
+  w.n0 = (in / gm) * BN;
   const int base = ep.k_tiles / ep.splits, rem = ep.k_tiles % ep.splits;
   w.kt0 = w.split * base + min(w.split, rem);
   w.kt1 = w.kt0 + base + (w.split < rem ? 1 : 0);
