@@ -621,13 +621,33 @@ int prrtc_robot_create(const prrtc_robot_desc* d, prrtc_robot** out) {
   }
   if (!finite_all(d->joint_base, 3 * dof) || !finite_all(d->link_length, dof))
     return fail(PRRTC_ERR_INVALID_ARG, "non-finite joint table");
+  // Home frame of every sphere: a sphere on the rotation axis of a revolute
+  // joint whose link has zero length does not move with that joint, so it is
+  // carried by the parent frame with the same offset (T_f o = T_{f-1} J_f o
+  // = T_{f-1} o).  This puts the joint-housing spheres into the group of the
+  // link that ends at the joint, where the two-stage check bounds them; FK
+  // places them at bit-identical centres (the offset is on the axis).
+  std::vector<int> home(d->n_spheres, 0);
+  for (int s = 0; s < d->n_spheres; ++s) {
+    int f = d->sphere_frame[s];
+    if (f < 0 || f >= dof) return fail(PRRTC_ERR_INVALID_ARG, "sphere frame out of range");
+    const float* o = d->sphere_offset + 3 * s;
+    while (f > 0 && d->joint_parent[f] == f - 1 && d->link_length[f] == 0.f) {
+      const int ty = d->joint_type[f];
+      const bool on_axis = (ty == PRRTC_JOINT_REV_Z && o[0] == 0.f && o[1] == 0.f) ||
+                           (ty == PRRTC_JOINT_REV_Y && o[0] == 0.f && o[2] == 0.f) ||
+                           (ty == PRRTC_JOINT_REV_X && o[1] == 0.f && o[2] == 0.f);
+      if (!on_axis) break;
+      --f;
+    }
+    home[s] = f;
+  }
   // merge coincident equal-radius spheres of one frame; keep them grouped by frame
   std::vector<int> raw_to(d->n_spheres, -1);
   std::vector<std::tuple<int, float, float, float, float>> distinct;
   for (int f = 0; f < dof; ++f) {
     for (int s = 0; s < d->n_spheres; ++s) {
-      const int fr = d->sphere_frame[s];
-      if (fr < 0 || fr >= dof) return fail(PRRTC_ERR_INVALID_ARG, "sphere frame out of range");
+      const int fr = home[s];
       if (fr != f) continue;
       const float* o = d->sphere_offset + 3 * s;
       const float r = d->sphere_radius[s];
@@ -889,10 +909,12 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   std::lock_guard<std::mutex> lk(c->mu);
   if ((rc = ensure_arenas(c, n, params->tree_capacity, params->path_capacity))) return rc;
 
-  CK(cudaEventRecord(c->ev[3], c->stream));
   // learned mixtures: given by the caller (host) or inferred on the device
   bool any_gmm = false;
   for (int p = 0; p < n; ++p) any_gmm |= (problems[p].gmm != nullptr) || (proposals && proposals[p]);
+  // prep time runs from the call's first device work: the mixture upload or
+  // inference when there is one, else the descriptor upload of the launch
+  if (any_gmm) CK(cudaEventRecord(c->ev[3], c->stream));
   if (any_gmm && c->gmm_cap < (size_t)n) {
     cudaFree(c->d_gmm);
     cudaFreeHost(c->h_gmm);
@@ -1034,7 +1056,8 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     return PRRTC_OK;
   };
   static const bool no_graph = std::getenv("PRRTC_NO_GRAPH") != nullptr;
-  if (no_graph || (proposals && any_gmm)) {
+  if (!any_gmm) CK(cudaEventRecord(c->ev[3], c->stream));
+  if (no_graph) {
     if ((rc = enqueue(false))) return rc;
   } else {
     const DeviceCtx::GraphKey key{n, cfg.grid, cfg.warps, cfg.smem, cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes,

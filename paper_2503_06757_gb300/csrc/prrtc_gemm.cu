@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -532,6 +533,7 @@ struct Workspace {
 };
 std::mutex g_ws_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+std::atomic<uint64_t> g_ws_epoch{0};  // bumped whenever a workspace is (re)allocated
 
 float* workspace(size_t floats, cudaStream_t stream) {
   int dev = 0;
@@ -545,6 +547,7 @@ float* workspace(size_t floats, cudaStream_t stream) {
     w.ptr = nullptr;
     w.floats = 0;
   }
+  g_ws_epoch.fetch_add(1);
   if (cudaMalloc(&w.ptr, floats * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     w.ptr = nullptr;
@@ -621,6 +624,10 @@ int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bi
               void* c16, int ldc16, cudaStream_t stream) {
   return gemm_bf16_split(a, b, M, N, K, bias, relu, c32, ldc32, c16, ldc16, stream, 0);
 }
+
+// Changes whenever a split-K workspace is allocated or moved: work captured
+// into a CUDA graph before the change may point at a freed workspace.
+uint64_t gemm_workspace_epoch() { return g_ws_epoch.load(); }
 
 // Reads and clears the kernel's error word (synchronous).
 int gemm_take_error() {

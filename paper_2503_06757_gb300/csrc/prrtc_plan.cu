@@ -19,6 +19,8 @@
 //     iterations of the serial Alg. 1 in order.
 #include <cfloat>
 #include <climits>
+#include <map>
+#include <mutex>
 
 #include "prrtc.h"
 #include "prrtc_launch.h"
@@ -722,6 +724,29 @@ cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, in
   return cudaGetLastError();
 }
 
+// Resident planner blocks per SM for a block shape, cached: the occupancy
+// query and the shared-memory attribute cost host time on every call.
+int resident_blocks_per_sm(int warps, int smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  static std::map<int, int> attr_smem;  // per device: the attribute value set so far
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::pair<int, int> key{warps + 64 * dev, smem};
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  if (smem > attr_smem[dev]) {
+    cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr_smem[dev] = smem;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel, warps * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  cache.emplace(key, per_sm);
+  return per_sm;
+}
+
 PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, int max_spheres, int max_pairs,
                               int max_env_f4, int sm_count) {
   PlanLaunch c{};
@@ -731,10 +756,7 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
   c.env_bytes = max_env_f4 * 16;
   c.stage_bytes = (int)sizeof(WarpCount) + kWarpVecFloats * (int)sizeof(float) + stage_bytes(max_spheres);  // per warp
   c.smem = c.robot_bytes + c.env_bytes + c.warps * c.stage_bytes;
-  int per_sm = 0;
-  cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel, c.warps * 32, c.smem);
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = resident_blocks_per_sm(c.warps, c.smem);
   int resident = per_sm * sm_count;
   if (blocks > 0) {
     c.grid = blocks;
@@ -753,8 +775,8 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
 
 cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
                         cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg.smem);
-  if (e != cudaSuccess) return e;
+  resident_blocks_per_sm(cfg.warps, cfg.smem);  // sets the shared-memory attribute once per size
+  cudaError_t e;
   plan_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
                                                               cfg.robot_bytes, cfg.env_bytes,
                                                               cfg.stage_bytes / (int)sizeof(float));

@@ -154,6 +154,14 @@ def evaluate(robot: W.Robot, n_scenes: int, pairs_per_scene: int, seed0: int, pr
     rb, scenes, envs, probs = shelf_problem_batch(robot, n_scenes, pairs_per_scene, seed0)
     items = [(rb, envs[k], s, g, 0, i) for i, (k, s, g) in enumerate(probs)]
     out = {}
+    # one untimed call per mode first: both launch sequences are then replayed
+    # from CUDA graphs, as in steady use
+    warm = P.params() if params is None else params
+    P.prrtc_plan_batch([it[:4] + (97, it[5]) for it in items], warm)
+    warm_l = P.params() if params is None else params
+    warm_l.learned_ratio = ratio
+    for _ in range(2):
+        P.prrtc_plan_batch_learned([it[:4] + (97, it[5]) for it in items], [prop] * len(items), warm_l)
     for name in ("plain", "learned"):
         ttfs, ok, iters, cost, dev_ms, prep_ms = [], 0, [], [], 0.0, 0.0
         for key in keys:

@@ -197,3 +197,21 @@ def test_learned_batch_plans_with_device_inference(c1_problems):
         assert r["status"] == P.SOLVED
         bad, mc = O.revalidate(pb.robot, pb.scene, r["path"].astype(np.float64), F32(1 / 32) / 4)
         assert bad == 0 or mc > -1e-3
+
+
+def test_learned_inference_replay_is_exact(c1_problems):
+    """The inference chain runs eagerly, is captured on its second call with the same
+    buffers and replayed afterwards: serial plans of all three calls are identical, and
+    a different batch size in between does not disturb the replay."""
+    rb7 = W.arm7()
+    prop = P.Proposal(7, rb7.lower, rb7.upper, flat(init(7, 17)))
+    items = [(P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 5, k)
+             for k, pb in enumerate(c1_problems)]
+    prm = P.params(learned_ratio=0.5, mode=P.MODE_SERIAL, tree_capacity=1 << 14)
+    runs = [P.prrtc_plan_batch_learned(items, [prop] * len(items), prm) for _ in range(3)]
+    P.prrtc_plan_batch_learned(items[:2], [prop] * 2, prm)
+    runs.append(P.prrtc_plan_batch_learned(items, [prop] * len(items), prm))
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            assert a["status"] == b["status"] and a["iterations"] == b["iterations"]
+            np.testing.assert_array_equal(a["path"], b["path"])
