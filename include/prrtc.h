@@ -182,6 +182,10 @@ typedef struct prrtc_path {
   int64_t prim_tests[4];   /* lane-level tests of one fine sphere against one primitive in
                               the second stage of the two-stage check, per primitive type
                               (AABB, oriented box, capped cylinder, sphere)               */
+  int64_t verdict_states;  /* states whose collision verdict was established: every state
+                              of a free edge, and for an edge found in collision the states
+                              of its earlier passes plus the colliding one (states stopped by
+                              the early exit are not counted)                              */
 } prrtc_path;
 
 void prrtc_path_free(prrtc_path* path);
@@ -215,6 +219,7 @@ typedef struct prrtc_launch_stats {
   int64_t prim_tests[4];     /* second-stage tests per primitive type (AABB, oriented
                                 box, capped cylinder, sphere)                            */
   int64_t dd_rejected;       /* iterations ended by the dynamic-domain test            */
+  int64_t verdict_states;    /* see prrtc_path.verdict_states                          */
 } prrtc_launch_stats;
 
 int prrtc_last_launch_stats(prrtc_launch_stats* out);

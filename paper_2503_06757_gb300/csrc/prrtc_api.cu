@@ -1169,6 +1169,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     L.nn_nodes += (int64_t)S.nn_nodes;
     L.iterations += (int64_t)S.iterations;
     L.dd_rejected += (int64_t)S.dd_rejected;
+    L.verdict_states += (int64_t)S.verdict_states;
     for (int k = 0; k < 4; ++k) {
       L.prim_tests[k] += (int64_t)S.prim_tests[k];
       L.env_tests += (int64_t)S.prim_tests[k];
@@ -1191,6 +1192,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       P.fk_states = (int64_t)S.fk_states;
       P.nn_nodes = (int64_t)S.nn_nodes;
       P.dd_rejected = (int64_t)S.dd_rejected;
+      P.verdict_states = (int64_t)S.verdict_states;
       for (int k = 0; k < 4; ++k) P.prim_tests[k] = (int64_t)S.prim_tests[k];
       if (status[p] == PRRTC_SOLVED) {
         P.n = S.path_n;

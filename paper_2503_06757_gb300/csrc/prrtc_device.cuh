@@ -130,7 +130,8 @@ struct WarpCount {
   unsigned long long fk_states;     // lane-level FK evaluations
   unsigned long long prim[4];       // second-stage sphere-primitive tests per type
   unsigned long long edges, edge_states, nn_nodes, iterations, insert_fail, dd_rejected;
-  unsigned long long pad_[3];
+  unsigned long long verdict_states;  // states whose verdict was established (early-exit states excluded)
+  unsigned long long pad_[2];
 };
 static_assert(sizeof(WarpCount) == 128, "per-warp counter block is 128 bytes");
 
@@ -264,10 +265,58 @@ __device__ __forceinline__ bool frame_two_stage(const float4* __restrict__ prims
   return hit;
 }
 
+// Three-stage test of one frame for a warp whose lanes hold the states of
+// one edge (the planner): first one sphere (ux, uy, uz, ur) around every
+// active lane's bounding sphere against the primitives, one primitive per
+// lane; then each lane's bounding sphere (bx, by, bz, br) against the
+// primitives the enclosing sphere touched; then the fine spheres against
+// the primitives some lane's bounding sphere touched.  Each sphere contains
+// the next with a margin, so the verdict equals the one-stage test.  Adds the
+// lane-level tests of the three stages to *tests.
+template <int K>
+__device__ __forceinline__ bool frame_three_stage(const float4* __restrict__ prims, int n, float ux, float uy,
+                                                  float uz, float ur, float bx, float by, float bz, float br,
+                                                  const float* __restrict__ stage, const float4* __restrict__ sph,
+                                                  int s0, int s1, bool active, int lane, uint32_t& tests) {
+  bool hit = false;
+  for (int base = 0; base < n; base += 32) {
+    const int k = base + lane;
+    const bool near = k < n && Prim<K>::hit(prims + Prim<K>::kStride * k, ux, uy, uz, ur);
+    uint32_t cand = __ballot_sync(kFull, near);
+    tests += 1u + (uint32_t)__popc(cand);
+    uint32_t flags = 0;
+    while (cand) {
+      const int b = __ffs(cand) - 1;
+      cand &= cand - 1;
+      flags |= (uint32_t)Prim<K>::hit(prims + Prim<K>::kStride * (base + b), bx, by, bz, br) << b;
+    }
+    flags = __reduce_or_sync(kFull, active ? flags : 0u);
+    tests += (uint32_t)(s1 - s0) * (uint32_t)__popc(flags);
+    while (flags) {
+      const int b = __ffs(flags) - 1;
+      flags &= flags - 1;
+      const float4* pk = prims + Prim<K>::kStride * (base + b);
+      for (int s = s0; s < s1; ++s) {
+        const float* st = stage + s * 96 + lane;
+        hit |= Prim<K>::hit(pk, st[0], st[32], st[64], sph[s].w);
+      }
+    }
+  }
+  return hit;
+}
+
+// Packs a verdict (bit 63) and four per-type test counts (15 bits each,
+// saturated; AABB lowest).
+__device__ __forceinline__ unsigned long long pack_tests(bool hit, const uint32_t (&t)[4]) {
+  unsigned long long r = (unsigned long long)hit << 63;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r |= (unsigned long long)min(t[k], 0x7fffu) << (15 * k);
+  return r;
+}
+
 // Both stages of one frame against the whole environment, kept out of line so
 // that the register budget of the caller is not set by it.  Returns the
-// lane's verdict in bit 63 and the flagged primitives of each type in four
-// 15-bit fields (AABB lowest).
+// lane's verdict and its second-stage tests per primitive type (pack_tests).
 static __device__ __noinline__ unsigned long long env_two_stage(const float4* __restrict__ env, int n_aabb, int n_obb,
                                                          int n_cyl, int n_sph, float bx, float by, float bz, float br,
                                                          const float* __restrict__ stage,
@@ -283,8 +332,53 @@ static __device__ __noinline__ unsigned long long env_two_stage(const float4* __
   hit |= frame_two_stage<kCyl>(e, n_cyl, bx, by, bz, br, stage, sph, s0, s1, active, lane, f[kCyl]);
   e += 2 * n_cyl;
   hit |= frame_two_stage<kSph>(e, n_sph, bx, by, bz, br, stage, sph, s0, s1, active, lane, f[kSph]);
-  return ((unsigned long long)hit << 63) | (unsigned long long)f[0] | ((unsigned long long)f[1] << 15) |
-         ((unsigned long long)f[2] << 30) | ((unsigned long long)f[3] << 45);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) f[k] *= (uint32_t)(s1 - s0);
+  return pack_tests(hit, f);
+}
+
+// The three stages of one frame (warp = one edge), out of line; same return.
+static __device__ __noinline__ unsigned long long env_three_stage(const float4* __restrict__ env, int n_aabb,
+                                                           int n_obb, int n_cyl, int n_sph, float ux, float uy,
+                                                           float uz, float ur, float bx, float by, float bz, float br,
+                                                           const float* __restrict__ stage,
+                                                           const float4* __restrict__ sph, int s0, int s1,
+                                                           bool active, int lane) {
+  uint32_t t[4] = {0, 0, 0, 0};
+  bool hit = false;
+  const float4* e = env;
+  hit |= frame_three_stage<kAabb>(e, n_aabb, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
+                                  t[kAabb]);
+  e += 2 * n_aabb;
+  hit |= frame_three_stage<kObb>(e, n_obb, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
+                                 t[kObb]);
+  e += 5 * n_obb;
+  hit |= frame_three_stage<kCyl>(e, n_cyl, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
+                                 t[kCyl]);
+  e += 2 * n_cyl;
+  hit |= frame_three_stage<kSph>(e, n_sph, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
+                                 t[kSph]);
+  return pack_tests(hit, t);
+}
+
+// Sphere around the active lanes' spheres (centre (x, y, z), common radius r):
+// centre of the lanes' bounding box, radius half its diagonal + r, enlarged by
+// 1e-5 m and one part in 10^6 so that FP32 rounding keeps every lane inside.
+__device__ __forceinline__ float4 warp_enclosing_sphere(float x, float y, float z, float r, bool active) {
+  float lx = active ? x : INFINITY, ly = active ? y : INFINITY, lz = active ? z : INFINITY;
+  float hx = active ? x : -INFINITY, hy = active ? y : -INFINITY, hz = active ? z : -INFINITY;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(kFull, lx, off));
+    ly = fminf(ly, __shfl_xor_sync(kFull, ly, off));
+    lz = fminf(lz, __shfl_xor_sync(kFull, lz, off));
+    hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, off));
+    hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, off));
+    hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, off));
+  }
+  const float dx = hx - lx, dy = hy - ly, dz = hz - lz;
+  const float half = 0.5f * sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  return make_float4(0.5f * (lx + hx), 0.5f * (ly + hy), 0.5f * (lz + hz), (half + r) * 1.000001f + 1e-5f);
 }
 
 // ------------------------------------------------------------------ FK + CC
@@ -403,12 +497,18 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       const float gx = fmaf(ax, cb.x, fmaf(bx, cb.y, fmaf(cx, cb.z, px)));
       const float gy = fmaf(ay, cb.x, fmaf(by, cb.y, fmaf(cy, cb.z, py)));
       const float gz = fmaf(az, cb.x, fmaf(bz, cb.y, fmaf(cz, cb.z, pz)));
-      passes++;
-      const unsigned long long r =
-          env_two_stage(env, n_aabb, n_obb, n_cyl, n_sph, gx, gy, gz, cb.w, stage, R->sph, s0, s1, active, lane);
+      unsigned long long r;
+      if (kWarpVote) {  // the lanes are the states of one edge: bound them all first
+        const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
+        r = env_three_stage(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz, cb.w, stage, R->sph, s0,
+                            s1, active, lane);
+      } else {
+        passes++;
+        r = env_two_stage(env, n_aabb, n_obb, n_cyl, n_sph, gx, gy, gz, cb.w, stage, R->sph, s0, s1, active, lane);
+      }
       hit |= (r >> 63) != 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)(s1 - s0) * (uint32_t)((r >> (15 * k)) & 0x7fffu);
+      for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)((r >> (15 * k)) & 0x7fffu);
       if (kWarpVote) {
         if (__any_sync(kFull, hit && active)) {
           flush();

@@ -111,6 +111,7 @@ struct ProblemState {
   unsigned long long edges, edge_states, sphere_tests, pair_tests, fk_states, nn_nodes, iterations, insert_fail;
   unsigned long long dd_rejected;
   unsigned long long prim_tests[4];
+  unsigned long long verdict_states;
   // arena bookkeeping, preserved across launches
   int used_rows[2];
   int used_dpad;

@@ -198,6 +198,7 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
   info_out->fk_states = (int64_t)st.fk_states;
   info_out->nn_nodes = (int64_t)st.nn_nodes;
   info_out->dd_rejected = (int64_t)st.dd_rejected;
+  info_out->verdict_states = (int64_t)st.verdict_states;
   for (int k = 0; k < 4; ++k) info_out->prim_tests[k] = (int64_t)st.prim_tests[k];
   if (gout.error) return gout.error;
   return PRRTC_OK;

@@ -176,9 +176,14 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
     const int kk = active ? k : N;
     const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N};
     if (state_collides<true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
-                             c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt))
+                             c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt)) {
+      // the states of earlier passes were all shown free, and one state of this
+      // pass collides; the other states of the pass stopped early
+      if (c.lane == 0) c.cnt->verdict_states += (unsigned long long)base + 1ull;
       return false;
+    }
   }
+  if (c.lane == 0) c.cnt->verdict_states += (unsigned long long)N;
   return true;
 }
 
@@ -596,13 +601,13 @@ __global__ void __maxnreg__(96) plan_kernel(PlanGlobals* __restrict__ g, const P
     // flush this warp's counters into the problem
     // flush this warp's counters into the problem
     __syncwarp();
-    if (lane < 13) {
+    if (lane < 14) {
       ProblemState* S = states + p;
       const WarpCount& w = *c.cnt;
-      unsigned long long* dst[13] = {&S->sphere_tests, &S->pair_tests,  &S->fk_states,     &S->prim_tests[0],
+      unsigned long long* dst[14] = {&S->sphere_tests, &S->pair_tests,  &S->fk_states,     &S->prim_tests[0],
                                      &S->prim_tests[1], &S->prim_tests[2], &S->prim_tests[3], &S->edges,
                                      &S->edge_states,  &S->nn_nodes,    &S->iterations,    &S->insert_fail,
-                                     &S->dd_rejected};
+                                     &S->dd_rejected,  &S->verdict_states};
       const unsigned long long val = reinterpret_cast<const unsigned long long*>(&w)[lane];
       if (val) atomicAdd(dst[lane], val);
     }
@@ -680,6 +685,7 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
       S->edges = S->edge_states = S->sphere_tests = S->pair_tests = 0;
       S->fk_states = S->nn_nodes = S->iterations = S->insert_fail = 0;
       S->dd_rejected = 0;
+      S->verdict_states = 0;
       S->prim_tests[0] = S->prim_tests[1] = S->prim_tests[2] = S->prim_tests[3] = 0;
     }
     __syncwarp();

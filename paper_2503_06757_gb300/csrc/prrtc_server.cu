@@ -306,6 +306,7 @@ bool server_round(prrtc_server* s) {
     P.fk_states = (int64_t)S.fk_states;
     P.nn_nodes = (int64_t)S.nn_nodes;
     P.dd_rejected = (int64_t)S.dd_rejected;
+    P.verdict_states = (int64_t)S.verdict_states;
     for (int k = 0; k < 4; ++k) P.prim_tests[k] = (int64_t)S.prim_tests[k];
     P.cost = S.cost;
     P.solve_time_us = -1.0;

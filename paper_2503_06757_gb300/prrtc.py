@@ -56,7 +56,8 @@ class prrtc_path(C.Structure):
                 ("q", _f), ("cost", C.c_double), ("nodes_a", C.c_int32), ("nodes_b", C.c_int32),
                 ("edges_checked", C.c_int64), ("edge_states", C.c_int64), ("solve_time_us", C.c_double),
                 ("sphere_tests", C.c_int64), ("pair_tests", C.c_int64), ("fk_states", C.c_int64),
-                ("nn_nodes", C.c_int64), ("dd_rejected", C.c_int64), ("prim_tests", C.c_int64 * 4)]
+                ("nn_nodes", C.c_int64), ("dd_rejected", C.c_int64), ("prim_tests", C.c_int64 * 4),
+                ("verdict_states", C.c_int64)]
 
 
 class prrtc_launch_stats(C.Structure):
@@ -66,7 +67,8 @@ class prrtc_launch_stats(C.Structure):
                 ("iterations", C.c_int64), ("grid", C.c_int32), ("block_threads", C.c_int32),
                 ("smem_bytes", C.c_int32), ("problems", C.c_int32), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("reserved_", C.c_int32),
-                ("prep_ms", C.c_double), ("prim_tests", C.c_int64 * 4), ("dd_rejected", C.c_int64)]
+                ("prep_ms", C.c_double), ("prim_tests", C.c_int64 * 4), ("dd_rejected", C.c_int64),
+                ("verdict_states", C.c_int64)]
 
 
 class prrtc_server_config(C.Structure):
@@ -406,7 +408,8 @@ def _path_dict(p: prrtc_path):
              nodes_a=int(p.nodes_a), nodes_b=int(p.nodes_b), edges_checked=int(p.edges_checked),
              edge_states=int(p.edge_states), solve_time_us=float(p.solve_time_us),
              sphere_tests=int(p.sphere_tests), pair_tests=int(p.pair_tests), fk_states=int(p.fk_states),
-             nn_nodes=int(p.nn_nodes), dd_rejected=int(p.dd_rejected), prim_tests=[int(x) for x in p.prim_tests])
+             nn_nodes=int(p.nn_nodes), dd_rejected=int(p.dd_rejected), prim_tests=[int(x) for x in p.prim_tests],
+             verdict_states=int(p.verdict_states))
     if p.q and p.n > 0:
         d["path"] = np.ctypeslib.as_array(p.q, shape=(p.n * p.dof,)).reshape(p.n, p.dof).copy()
     else:
