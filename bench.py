@@ -222,6 +222,26 @@ def algorithmic_ops(path, env_counts, dof, dpad, n_spheres, n_pairs):
             path["nn_nodes"] * (2 * dpad + 1))
 
 
+# ------------------------------------------------------------------ multi-GPU (weak scaling)
+
+def rank_problem_seed(rank: int) -> int:
+    """First scene seed of a rank's problem set: every rank plans its own problems
+    (independent units, no data-path collective)."""
+    return 1000 + 10000 * rank
+
+
+def reduce_over_ranks(dist, torch, device_s, wall_s, units, device):
+    """Whole-job timing and work: the slowest rank's device and wall time, the sum
+    of the units all ranks processed.  Without a process group: the inputs."""
+    if dist is None:
+        return device_s, wall_s, units
+    t = torch.tensor([device_s, wall_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(n)
+    return float(t[0]), float(t[1]), float(n[0])
+
+
 # ------------------------------------------------------------------ CPU baseline
 
 def oracle_sample(problems, budget_s=12.0, threads=None):
@@ -519,7 +539,7 @@ def run_ours(args):
     sms = dev_props.multi_processor_count
 
     accept = gpu_accept_factory(P)
-    probs = shelf_problems(accept, count=args.problems, seed0=1000 + 10000 * rank)
+    probs = shelf_problems(accept, count=args.problems, seed0=rank_problem_seed(rank))
     robots, envs, items, counts = {}, [], [], []
     for k, pb in enumerate(probs):
         if pb.robot.name not in robots:
@@ -578,15 +598,8 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
 
-    total_states = edge_states
-    device_s = dev_ms * 1e-3
-    if dist:
-        t = torch.tensor([device_s, wall_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        device_s, wall_s = float(t[0]), float(t[1])
-        n = torch.tensor([total_states], dtype=torch.float64, device="cuda")
-        dist.all_reduce(n)
-        total_states = float(n[0])
+    device_s, wall_s, total_states = reduce_over_ranks(dist, torch, dev_ms * 1e-3, wall_s, edge_states,
+                                                       "cuda" if torch.cuda.is_available() else "cpu")
     value = total_states / device_s
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
