@@ -704,6 +704,40 @@ int prrtc_robot_create(const prrtc_robot_desc* d, prrtc_robot** out) {
                            std::get<4>(distinct[k]));
   set_bounding_spheres(H);
   H.two_stage = 1;
+  // group sphere per link for the self-collision first stage: its bounding
+  // sphere when it has several spheres, else its only sphere
+  for (int f = 0; f < kMaxDof; ++f) H.grp[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int f = 0; f < dof; ++f) {
+    const int n_f = H.sph_begin[f + 1] - H.sph_begin[f];
+    if (n_f >= 2) H.grp[f] = H.coarse[f];
+    else if (n_f == 1) H.grp[f] = H.sph[H.sph_begin[f]];
+  }
+  // pairs in blocks of one link pair each, sorted by first sphere inside a block
+  auto frame_of = [&](int k) { return std::get<0>(distinct[k]); };
+  std::sort(pairs.begin(), pairs.end(), [&](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+    const int fa = frame_of(a.first), fb = frame_of(b.first), ga = frame_of(a.second), gb = frame_of(b.second);
+    if (fa != fb) return fa < fb;
+    if (ga != gb) return ga < gb;
+    return a < b;
+  });
+  int nb = 0;
+  for (size_t k = 0; k < pairs.size();) {
+    const int fa = frame_of(pairs[k].first), fb = frame_of(pairs[k].second);
+    size_t e = k;
+    while (e < pairs.size() && frame_of(pairs[e].first) == fa && frame_of(pairs[e].second) == fb) ++e;
+    if (nb >= kMaxPairBlocks) {
+      std::free(h);
+      return fail(PRRTC_ERR_UNSUPPORTED, "too many self-collision link pairs");
+    }
+    H.blk_frames[nb] = (uint32_t)fa | ((uint32_t)fb << 16);
+    H.blk_range[nb] = (uint32_t)k | ((uint32_t)e << 16);
+    const float rr = H.grp[fa].w + H.grp[fb].w;
+    // one pair, or pairs within one link: no first stage
+    H.blk_thr[nb] = (e - k > 1 && fa != fb) ? rr * rr : INFINITY;
+    ++nb;
+    k = e;
+  }
+  H.n_blocks = nb;
   for (size_t k = 0; k < pairs.size(); ++k) {
     h->pair[k] = (uint32_t)pairs[k].first | ((uint32_t)pairs[k].second << 16);
     const float rr = H.sph[pairs[k].first].w + H.sph[pairs[k].second].w;
@@ -1006,7 +1040,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       D.q_start[j] = pb.q_start[j];
       D.q_goal[j] = pb.q_goal[j];
     }
-    max_spheres = std::max(max_spheres, H.n_spheres);
+    max_spheres = std::max(max_spheres, H.n_spheres + H.dof);  // staging slots: spheres + group centres
     max_pairs = std::max(max_pairs, H.n_pairs);
     max_env = std::max(max_env, D.env.n_float4());
   }
@@ -1236,7 +1270,7 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
     const RobotHeader& H = problems[0].robot->h->h;
     int max_env = 0;
     for (int p = 0; p < n; ++p) max_env = std::max(max_env, problems[p].env->view().n_float4());
-    resident = plan_launch_config(n, params->mode, 0, 4, H.n_spheres, H.n_pairs, max_env, c->sms).grid;
+    resident = plan_launch_config(n, params->mode, 0, 4, H.n_spheres + H.dof, H.n_pairs, max_env, c->sms).grid;
     if (n == 1) resident = c->sms * 4;
   }
   std::vector<std::pair<int, int>> cands;

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int dof = R->dof;
   const int n_raw = R->n_raw;
-  float* qst = warp_all + warp * (kQStageFloats + R->n_spheres * 96);
+  float* qst = warp_all + warp * (kQStageFloats + (R->n_spheres + R->dof) * 96);
   float* stage = qst + kQStageFloats;
   const int gw = blockIdx.x * kCheckWarps + warp;
   const int nw = gridDim.x * kCheckWarps;
@@ -91,7 +91,7 @@ cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& h, Env
   if (n <= 0) return cudaSuccess;
   const int np_pad = (h.n_pairs + 3) & ~3;
   const int smem = robot_smem_bytes(np_pad) + env.n_float4() * 16 +
-                   kCheckWarps * (kQStageFloats * (int)sizeof(float) + stage_bytes(h.n_spheres));
+                   kCheckWarps * (kQStageFloats * (int)sizeof(float) + stage_bytes(h.n_spheres + h.dof));
   cudaError_t e = cudaFuncSetAttribute(check_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;

@@ -25,6 +25,7 @@ namespace prrtc {
 constexpr int kMaxDof = 16;
 constexpr int kMaxDistinctSpheres = 64;
 constexpr int kMaxDistinctPairs = 3072;
+constexpr int kMaxPairBlocks = 144;  // link pairs with self-collision pairs: <= 16 * 17 / 2
 constexpr unsigned kFull = 0xffffffffu;
 
 enum JointType : int { kRevZ = 0, kRevY = 1, kPrismZ = 2, kPrismX = 3, kPrismY = 4, kRevX = 5 };
@@ -39,7 +40,8 @@ struct RobotHeader {
   int n_pairs;         // distinct self-collision pairs
   int n_raw;           // spheres as given
   int two_stage;       // 1: frames with a bounding sphere are checked in two stages
-  int pad_[2];
+  int n_blocks;        // self-collision pair blocks (one per pair of links)
+  int pad_;
   int jtype[kMaxDof];
   int jparent[kMaxDof];
   float jlen[kMaxDof];
@@ -50,6 +52,16 @@ struct RobotHeader {
   int pad2_[3];
   float4 sph[kMaxDistinctSpheres];   // offset xyz in the frame, radius
   float4 coarse[kMaxDof];            // bounding sphere of frame i's spheres (radius 0: none)
+  // Group sphere of frame i for the self-collision first stage: its bounding
+  // sphere, or its only sphere, or radius 0 (no spheres).  Centres are staged
+  // after the fine spheres (stage slot n_spheres + i).
+  float4 grp[kMaxDof];
+  // Self-collision pair blocks: the pairs between the spheres of links fa and
+  // fb are pair[begin .. end); thr = (R_fa + R_fb)^2 of the group spheres, or
+  // +inf when the block is tested without a first stage.
+  uint32_t blk_frames[kMaxPairBlocks];  // fa | fb << 16
+  uint32_t blk_range[kMaxPairBlocks];   // begin | end << 16
+  float blk_thr[kMaxPairBlocks];
 };
 
 // Pair table follows the header in device memory: pair[k] = i | (j << 16),
@@ -472,6 +484,19 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
     const int s0 = R->sph_begin[i], s1 = R->sph_begin[i + 1];
     const float4 cb = R->coarse[i];
     const bool two = R->two_stage && cb.w > 0.f && has_prims;  // uniform
+    const float4 gs = R->grp[i];
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (gs.w > 0.f) {  // group sphere of this link (equals cb when the link has a bounding sphere)
+      gx = fmaf(ax, gs.x, fmaf(bx, gs.y, fmaf(cx, gs.z, px)));
+      gy = fmaf(ay, gs.x, fmaf(by, gs.y, fmaf(cy, gs.z, py)));
+      gz = fmaf(az, gs.x, fmaf(bz, gs.y, fmaf(cz, gs.z, pz)));
+      if (kWarpVote) {  // staged for the self-collision first stage (edge warps only)
+        float* gst = stage + (R->n_spheres + i) * 96 + lane;
+        gst[0] = gx;
+        gst[32] = gy;
+        gst[64] = gz;
+      }
+    }
     for (int s = s0; s < s1; ++s) {
       const float4 o = R->sph[s];
       const float sx = fmaf(ax, o.x, fmaf(bx, o.y, fmaf(cx, o.z, px)));
@@ -494,9 +519,6 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       }
     }
     if (two) {
-      const float gx = fmaf(ax, cb.x, fmaf(bx, cb.y, fmaf(cx, cb.z, px)));
-      const float gy = fmaf(ay, cb.x, fmaf(by, cb.y, fmaf(cy, cb.z, py)));
-      const float gz = fmaf(az, cb.x, fmaf(bz, cb.y, fmaf(cz, cb.z, pz)));
       unsigned long long r;
       if (kWarpVote) {  // the lanes are the states of one edge: bound them all first
         const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
@@ -517,36 +539,56 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       }
     }
   }
-  const int np = R->n_pairs;
-  int last_i = -1;
-  float ix = 0.f, iy = 0.f, iz = 0.f;
-  for (int k = 0; k < np; ++k) {
-    const uint32_t pr = pair[k];
-    const int i = (int)(pr & 0xffffu), j = (int)(pr >> 16);
-    if (i != last_i) {
-      const float* si = stage + i * 96 + lane;
-      ix = si[0]; iy = si[32]; iz = si[64];
-      last_i = i;
+  // Self-collision by link-pair blocks: when the lanes are the states of one
+  // edge, a block's fine sphere pairs run only if the group spheres of its two
+  // links overlap for some active lane (the group spheres contain the fine
+  // ones, so the verdict is that of testing every pair).  Lanes holding
+  // unrelated states would nearly always find one overlap, so they test every
+  // pair.  Pairs within a block are sorted by their first sphere.
+  const int nb = R->n_blocks;
+  const int grp_base = R->n_spheres;  // stage slot of frame 0's group centre
+  for (int b = 0; b < nb; ++b) {
+    const uint32_t fr = R->blk_frames[b], rg = R->blk_range[b];
+    const float bt = R->blk_thr[b];
+    if (kWarpVote && bt < INFINITY) {
+      const float* ga = stage + (grp_base + (int)(fr & 0xffffu)) * 96 + lane;
+      const float* gb = stage + (grp_base + (int)(fr >> 16)) * 96 + lane;
+      const float dx = ga[0] - gb[0], dy = ga[32] - gb[32], dz = ga[64] - gb[64];
+      const bool near = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < bt;
+      pairs++;
+      if (!__any_sync(kFull, near && active)) continue;
     }
-    const float* sj = stage + j * 96 + lane;
-    const float dx = ix - sj[0], dy = iy - sj[32], dz = iz - sj[64];
-    hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr[k];
-    if (kWarpVote && (k & 15) == 15) {
+    const int k0 = (int)(rg & 0xffffu), k1 = (int)(rg >> 16);
+    pairs += (uint32_t)(k1 - k0);
+    int last_i = -1;
+    float ix = 0.f, iy = 0.f, iz = 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const uint32_t pr = pair[k];
+      const int i = (int)(pr & 0xffffu), j = (int)(pr >> 16);
+      if (i != last_i) {
+        const float* si = stage + i * 96 + lane;
+        ix = si[0]; iy = si[32]; iz = si[64];
+        last_i = i;
+      }
+      const float* sj = stage + j * 96 + lane;
+      const float dx = ix - sj[0], dy = iy - sj[32], dz = iz - sj[64];
+      hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr[k];
+    }
+    if (kWarpVote) {
       if (__any_sync(kFull, hit && active)) {
-        pairs = (uint32_t)(k + 1);
         flush();
         return true;
       }
     }
   }
-  pairs = (uint32_t)np;
   flush();
   if (kWarpVote) return __any_sync(kFull, hit && active);
   return hit;
 }
 
-// Byte size of a warp's sphere-centre staging buffer.
-__host__ __device__ inline int stage_bytes(int n_spheres) { return n_spheres * 96 * (int)sizeof(float); }
+// Byte size of a warp's staging buffer of sphere centres: the robot's
+// distinct spheres, then one group centre per frame (`slots` = spheres + dof).
+__host__ __device__ inline int stage_bytes(int slots) { return slots * 96 * (int)sizeof(float); }
 
 // Shared-memory image of a robot: header, then pairs, then thresholds.
 __host__ __device__ inline int robot_smem_bytes(int n_pairs) {

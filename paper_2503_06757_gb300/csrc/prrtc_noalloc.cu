@@ -155,12 +155,12 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PRRTC_ERR_CUDA;
   const PlanLaunch cfg = plan_launch_config(1, params->mode, params->blocks, params->warps_per_block,
-                                            std::max(1, H.n_spheres), H.n_pairs, ev.n_float4(), sms);
+                                            H.n_spheres + H.dof, H.n_pairs, ev.n_float4(), sms);
   if (cfg.smem > 227 * 1024) return PRRTC_ERR_UNSUPPORTED;
 
   cudaError_t e = cudaMemcpyAsync(&S->desc, &D, sizeof(D), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&S->glob, &G, sizeof(G), cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = launch_setup(&S->desc, &S->state, 1, std::max(1, H.n_spheres), H.n_pairs, ev.n_float4(), stream);
+  if (e == cudaSuccess) e = launch_setup(&S->desc, &S->state, 1, H.n_spheres + H.dof, H.n_pairs, ev.n_float4(), stream);
   if (e == cudaSuccess) e = launch_plan(&S->glob, &S->desc, &S->state, cfg, stream);
   if (e == cudaSuccess) e = launch_record_usage(&S->desc, &S->state, 1, stream);
   ProblemState st;

@@ -243,7 +243,7 @@ bool server_round(prrtc_server* s) {
     if (!s->slot_query[p]) continue;
     s->h_active[n_active++] = p;
     const ProblemDesc& D = s->h_desc[p];
-    max_spheres = std::max(max_spheres, D.n_spheres);
+    max_spheres = std::max(max_spheres, D.n_spheres + D.dof);  // staging slots: spheres + group centres
     max_pairs = std::max(max_pairs, D.n_pairs);
     max_env = std::max(max_env, D.env.n_float4());
   }
