@@ -268,6 +268,20 @@ def oracle_sample(problems, budget_s=12.0, threads=None):
                 mean_cost=float(np.mean(costs)) if costs else None)
 
 
+def oracle_agreement(P, items, cpu):
+    """Success rate and mean cost of the device planner on the problems the oracle
+    sample solved (same Philox key 1 and problem ids): serial mode (Alg. 1 in order,
+    the oracle's algorithm) and async mode (the parallel workers of the timed step)."""
+    n = cpu["problems"]
+    sub = [it[:4] + (1, k) for k, it in enumerate(items[:n])]
+    out = dict(problems=n, oracle=dict(success_rate=cpu["success_rate"], mean_cost=cpu["mean_cost"]))
+    for name, mode in (("serial", P.MODE_SERIAL), ("async", P.MODE_ASYNC)):
+        res = P.prrtc_plan_batch(sub, P.params(mode=mode))
+        ok = [r for r in res if r["status"] == P.SOLVED]
+        out[name] = dict(success_rate=len(ok) / n, mean_cost=float(np.mean([r["cost"] for r in ok])) if ok else None)
+    return out
+
+
 # ------------------------------------------------------------------ learned proposal and serving
 
 def learned_section(args, P):
@@ -668,6 +682,7 @@ def run_ours(args):
         extra["esdf"] = esdf_section(P, torch, items, prm, flush, F, rb)
         extra["roofline_gemm"] = gemm_section(P, torch, float(peaks.get("bf16_tflops", 1900.0)))
         extra["cpu_baseline"] = oracle_sample(probs, budget_s=args.cpu_budget)
+        extra["oracle_agreement"] = oracle_agreement(P, items, extra["cpu_baseline"])
         prop = None
         if not args.no_learned:
             extra["learned"], prop = learned_section(args, P)

@@ -267,3 +267,29 @@ def test_autotune_picks_a_candidate_and_later_calls_use_it(c1_problems):
     st = P.prrtc_last_launch_stats()
     assert st["grid"] == best.blocks and st["block_threads"] == 32 * best.warps_per_block
     assert all(r["status"] == P.SOLVED for r in res)
+
+
+def test_serial_batch_success_and_mean_cost_match_oracle():
+    """Over 64 cubby-shelf problems (one launch, one worker per problem), success rate
+    within 1 percentage point and mean path cost within 2% of the serial oracle's.
+    Problems whose runs part at an ambiguous decision still count: the bound is on
+    the set, not on each problem."""
+    probs = W.problem_set("shelf", 64, 1000, O.accept)
+    robots = {}
+    items = []
+    for k, pb in enumerate(probs):
+        rb = robots.setdefault(pb.robot.name, P.make_robot(pb.robot))
+        items.append((rb, P.make_env(pb.scene), pb.q_start, pb.q_goal, 1, k))
+    g = P.prrtc_plan_batch(items, P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 15, max_iters=20000))
+    o = O.plan_batch(probs, seeds=[1] * len(probs), problem_ids=list(range(len(probs))), range=1.0,
+                     resolution=RES, goal_bias=BIAS, tree_capacity=1 << 15, max_iters=20000)
+    g_ok = np.array([r["status"] == P.SOLVED for r in g])
+    o_ok = np.array([r["status"] == 0 for r in o])
+    assert abs(g_ok.mean() - o_ok.mean()) <= 0.01 + 1e-9
+    both = g_ok & o_ok
+    g_cost = np.mean([r["cost"] for r, b in zip(g, both) if b])
+    o_cost = np.mean([r["cost"] for r, b in zip(o, both) if b])
+    assert abs(g_cost - o_cost) <= 0.02 * o_cost, (g_cost, o_cost)
+    # and most problems are decided identically end to end
+    same = sum(abs(a["cost"] - b["cost"]) <= 1e-4 * b["cost"] for a, b, ok in zip(g, o, both) if ok)
+    assert same >= 0.5 * both.sum()
