@@ -299,10 +299,68 @@ def learned_section(args, P):
                  loss_first=float(np.mean(losses[:10])), loss_last=float(np.mean(losses[-10:])),
                  heldout_nll=L.held_out_nll(prop, held), heldout_nll_untrained=L.held_out_nll(untrained, held))
     ev = L.evaluate(rb, args.learned_eval_scenes, 1, 9000, prop, ratio=0.5)
+    ev_25 = L.evaluate(rb, args.learned_eval_scenes, 1, 9000, prop, ratio=0.25)["learned"]
     return dict(workload="cubby shelf, 7-DoF arm; held-out scenes 9000.. (one problem each), Philox keys 1..3",
-                ratio=0.5, train=train, eval=ev,
+                ratio=0.5, train=train, eval=ev, learned_ratio_0_25=ev_25,
                 note="TTFS includes the on-device inference (occupancy, features, 4 tensor-core GEMMs) "
                      "that precedes planning"), prop
+
+
+def door_section(P, door, keys=(1, 2, 3)):
+    """The learned proposal where its gain is structural: a point robot in two rooms
+    joined by a door in a wall (opening `door` in y).  Train on 256 plain-planner
+    solutions, then plan 200 held-out pairs in one batched launch, plain vs 50%
+    learned, same keys; TTFS includes the call's device prep (for the learned form
+    the on-device inference) and setup."""
+    from paper_2503_06757_gb300 import learned as L
+    from paper_2503_06757_gb300 import workload as W
+    rb, sc = W.point2(), W.scene_two_rooms(door=door)
+    h, ev = P.make_robot(rb), P.make_env(sc)
+    base = dict(range=0.2, resolution=0.01, max_iters=20000, tree_capacity=1 << 14, path_capacity=1 << 12)
+    s, g = W.two_rooms_pairs(256, 11)
+    res = P.prrtc_plan_batch([(h, ev, s[k], g[k], 3, k) for k in range(len(s))],
+                             P.params(mode=P.MODE_SERIAL, **base))
+    qs, qg, tg = [], [], []
+    for k, r in enumerate(res):
+        if r["status"] == P.SOLVED:
+            wp = L.waypoints(r["path"].astype(np.float64), spacing=0.05)
+            qs += [s[k]] * len(wp)
+            qg += [g[k]] * len(wp)
+            tg += list(wp)
+    init = W.proposal_init(2, 7)
+    prop = P.Proposal(2, rb.lower, rb.upper,
+                      np.concatenate([np.concatenate([Wm.ravel(), b]) for Wm, b in init]).astype(np.float32))
+    losses = prop.train(P.prrtc_occupancy(ev)[None, :], np.zeros(len(tg), np.int32), np.array(qs, np.float32),
+                        np.array(qg, np.float32), np.array(tg, np.float32), batch=256, steps=1500, lr=1e-3, seed=1)
+    s2, g2 = W.two_rooms_pairs(200, 12)
+    width = door[1] - door[0]
+    out = dict(workload=f"point robot (2 cm sphere), two rooms joined by a {100 * width:.0f} cm door "
+                        f"({100 * (width - 0.04):.0f} cm free for the centre); 256 training, 200 held-out pairs, "
+                        f"keys {keys[0]}..{keys[-1]}",
+               train=dict(samples=len(tg), loss_first=float(losses[:10].mean()), loss_last=float(losses[-10:].mean())))
+    for name in ("plain", "learned"):
+        for mode_name, mode in (("async", P.MODE_ASYNC), ("serial", P.MODE_SERIAL)):
+            prm = P.params(mode=mode, learned_ratio=0.5 if name == "learned" else 0.0, **base)
+            call = (lambda its: P.prrtc_plan_batch_learned(its, [prop] * len(its), prm)) if name == "learned" \
+                else (lambda its: P.prrtc_plan_batch(its, prm))
+            for _ in range(2):  # warm-up: graphs captured
+                call([(h, ev, s2[k], g2[k], 97, k) for k in range(len(s2))])
+            ttfs, iters, ok, prep, infer = [], [], 0, [], []
+            for key in keys:
+                rs = call([(h, ev, s2[k], g2[k], key, k) for k in range(len(s2))])
+                st = P.prrtc_last_launch_stats()
+                prep.append(st["prep_ms"] * 1e3)
+                infer.append(st["infer_ms"] * 1e3)
+                for r in rs:
+                    iters.append(r["iterations"])
+                    if r["status"] == P.SOLVED:
+                        ok += 1
+                        ttfs.append(r["solve_time_us"] + 1e3 * (st["prep_ms"] + st["setup_ms"]))
+            out[f"{name}_{mode_name}"] = dict(success_rate=ok / (len(s2) * len(keys)),
+                                              iterations_mean=float(np.mean(iters)),
+                                              ttfs_us=percentiles(ttfs, (50, 95)) if mode == P.MODE_ASYNC else None,
+                                              prep_us_mean=float(np.mean(prep)), infer_us_mean=float(np.mean(infer)))
+    return out
 
 
 def serving_section(args, P, proposals):
@@ -686,6 +744,8 @@ def run_ours(args):
         prop = None
         if not args.no_learned:
             extra["learned"], prop = learned_section(args, P)
+            extra["learned"]["door_8cm"] = door_section(P, (0.85, 0.93))
+            extra["learned"]["door_5cm"] = door_section(P, (0.865, 0.915))
         if not args.no_serving:
             extra["serving"] = serving_section(args, P, {"arm7": prop} if prop is not None else None)
 
@@ -731,7 +791,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--learned-scenes", type=int, default=300)
     ap.add_argument("--learned-pairs", type=int, default=40)
-    ap.add_argument("--learned-steps", type=int, default=4000)
+    ap.add_argument("--learned-steps", type=int, default=1000)
     ap.add_argument("--learned-eval-scenes", type=int, default=500)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--gemm-only", action="store_true",

@@ -220,6 +220,8 @@ typedef struct prrtc_launch_stats {
                                 box, capped cylinder, sphere)                            */
   int64_t dd_rejected;       /* iterations ended by the dynamic-domain test            */
   int64_t verdict_states;    /* see prrtc_path.verdict_states                          */
+  double infer_ms;           /* device time of the learned-mixture inference (staging
+                                copy and kernel chain; part of prep_ms), 0 without     */
 } prrtc_launch_stats;
 
 int prrtc_last_launch_stats(prrtc_launch_stats* out);
@@ -425,6 +427,17 @@ int prrtc_proposal_save(const prrtc_proposal* proposal, const char* path);
 int prrtc_proposal_load(const char* path, prrtc_proposal** out);
 /* Occupancy grid of an environment (host [4096]), computed on the device. */
 int prrtc_occupancy(const prrtc_env* env, uint8_t* out);
+/* The mixtures prrtc_plan_batch_learned would sample from for B problems
+ * (envs[b], q_start / q_goal host [B * dof]), inferred on the device by the
+ * same code: out host [B * (8 + 16 dof)] in the layout of prrtc_problem.gmm,
+ * log-sigmas clamped to [-5, 2].  The occupancy part of the first layer is
+ * computed once per distinct environment of the batch (environments are
+ * told apart by their device data); the first layer then differs from
+ * prrtc_proposal_forward's single contraction by FP32 summation order only.
+ * Errors: PRRTC_ERR_INVALID_ARG (null or non-finite input), PRRTC_ERR_OOM,
+ * PRRTC_ERR_CUDA. */
+int prrtc_proposal_mixtures(prrtc_proposal* proposal, const prrtc_env* const* envs, const float* q_start,
+                            const float* q_goal, int32_t B, float* out);
 
 /* prrtc_plan_batch with the learned proposal: for every problem whose
  * proposals[p] is non-null (its DoF must match the robot's), the mixture is

@@ -918,8 +918,10 @@ int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const flo
 }  // extern "C"
 
 // Implemented in prrtc_mlp.cu.
-int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, const float* qs_host,
-                                     const float* qg_host, int B, float* const* gmm_rows, cudaStream_t stream);
+int prrtc_internal_proposal_stage(prrtc_proposal* p, const EnvView* envs, const float* qs_host, const float* qg_host,
+                                  int B, float* const* gmm_rows);
+int prrtc_internal_proposal_submit(prrtc_proposal* p, cudaStream_t stream);
+float prrtc_internal_proposal_infer_ms(prrtc_proposal* p);
 extern "C" int prrtc_proposal_info(const prrtc_proposal*, int32_t*, int32_t*, int64_t*, int32_t*);
 
 static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc_params* params,
@@ -946,9 +948,6 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   // learned mixtures: given by the caller (host) or inferred on the device
   bool any_gmm = false;
   for (int p = 0; p < n; ++p) any_gmm |= (problems[p].gmm != nullptr) || (proposals && proposals[p]);
-  // prep time runs from the call's first device work: the mixture upload or
-  // inference when there is one, else the descriptor upload of the launch
-  if (any_gmm) CK(cudaEventRecord(c->ev[3], c->stream));
   if (any_gmm && c->gmm_cap < (size_t)n) {
     cudaFree(c->d_gmm);
     cudaFreeHost(c->h_gmm);
@@ -962,53 +961,6 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     }
     c->gmm_cap = (size_t)n;
   }
-  bool host_gmm = false;
-  for (int p = 0; p < n; ++p) {
-    const prrtc_problem& pb = problems[p];
-    if (!pb.gmm || (proposals && proposals[p])) continue;
-    const int dof = pb.robot->h->h.dof;
-    float* g = c->h_gmm + (size_t)p * kGmmStride;
-    std::memset(g, 0, kGmmStride * sizeof(float));
-    for (int k = 0; k < kMixK; ++k) {
-      g[k] = pb.gmm[k];
-      for (int j = 0; j < dof; ++j) {
-        g[kMixK + k * kMaxDof + j] = pb.gmm[kMixK + k * dof + j];
-        g[kMixK + kMixK * kMaxDof + k * kMaxDof + j] =
-            std::min(std::max(pb.gmm[kMixK + kMixK * dof + k * dof + j], -5.f), 2.f);
-      }
-    }
-    if (!finite_all(g, kGmmStride)) return fail(PRRTC_ERR_INVALID_ARG, "non-finite mixture");
-    host_gmm = true;
-  }
-  if (host_gmm)
-    CK(cudaMemcpyAsync(c->d_gmm, c->h_gmm, (size_t)n * kGmmStride * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  if (proposals) {
-    // group problems by proposal; each group is one batched inference
-    std::vector<int> done(n, 0);
-    for (int p = 0; p < n; ++p) {
-      if (!proposals[p] || done[p]) continue;
-      prrtc_proposal* prop = proposals[p];
-      int pdof = 0;
-      prrtc_proposal_info(prop, &pdof, nullptr, nullptr, nullptr);
-      std::vector<EnvView> envs;
-      std::vector<float> qs, qg;
-      std::vector<float*> rows;
-      for (int r = p; r < n; ++r) {
-        if (proposals[r] != prop) continue;
-        const prrtc_problem& pb = problems[r];
-        if (pb.robot->h->h.dof != pdof) return fail(PRRTC_ERR_INVALID_ARG, "proposal DoF does not match the robot");
-        envs.push_back(pb.env->view());
-        qs.insert(qs.end(), pb.q_start, pb.q_start + pdof);
-        qg.insert(qg.end(), pb.q_goal, pb.q_goal + pdof);
-        rows.push_back(c->d_gmm + (size_t)r * kGmmStride);
-        done[r] = 1;
-      }
-      int rc2 = prrtc_internal_proposal_mixtures(prop, envs.data(), qs.data(), qg.data(), (int)envs.size(),
-                                                 rows.data(), c->stream);
-      if (rc2) return rc2;
-    }
-  }
-
   int max_spheres = 1, max_pairs = 0, max_env = 0;
   for (int p = 0; p < n; ++p) {
     const prrtc_problem& pb = problems[p];
@@ -1065,6 +1017,66 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   if (cfg.smem > 227 * 1024) return fail(PRRTC_ERR_UNSUPPORTED, "robot + environment exceed shared memory");
   const int head_rows = (n == 1) ? std::min(kHeadRows, params->path_capacity) : 0;
 
+  // Host half of the learned inference (grouping, staging), before the timed
+  // device work like the descriptors: one batch per distinct proposal.
+  std::vector<prrtc_proposal*> staged;
+  if (proposals) {
+    std::vector<int> done(n, 0);
+    for (int p = 0; p < n; ++p) {
+      if (!proposals[p] || done[p]) continue;
+      prrtc_proposal* prop = proposals[p];
+      int pdof = 0;
+      prrtc_proposal_info(prop, &pdof, nullptr, nullptr, nullptr);
+      std::vector<EnvView> envs;
+      std::vector<float> qs, qg;
+      std::vector<float*> rows;
+      for (int r = p; r < n; ++r) {
+        if (proposals[r] != prop) continue;
+        const prrtc_problem& pb = problems[r];
+        if (pb.robot->h->h.dof != pdof) return fail(PRRTC_ERR_INVALID_ARG, "proposal DoF does not match the robot");
+        envs.push_back(pb.env->view());
+        qs.insert(qs.end(), pb.q_start, pb.q_start + pdof);
+        qg.insert(qg.end(), pb.q_goal, pb.q_goal + pdof);
+        rows.push_back(c->d_gmm + (size_t)r * kGmmStride);
+        done[r] = 1;
+      }
+      const int rc2 = prrtc_internal_proposal_stage(prop, envs.data(), qs.data(), qg.data(), (int)envs.size(),
+                                                    rows.data());
+      if (rc2) return rc2;
+      staged.push_back(prop);
+    }
+  }
+
+  // Prep time runs from the call's first device work -- the mixture upload or
+  // inference, else the descriptor upload -- to the setup kernel.  The host
+  // work above (descriptors, launch shape, inference staging) comes before it
+  // in both cases.
+  CK(cudaEventRecord(c->ev[3], c->stream));
+  bool host_gmm = false;
+  for (int p = 0; p < n; ++p) {
+    const prrtc_problem& pb = problems[p];
+    if (!pb.gmm || (proposals && proposals[p])) continue;
+    const int dof = pb.robot->h->h.dof;
+    float* g = c->h_gmm + (size_t)p * kGmmStride;
+    std::memset(g, 0, kGmmStride * sizeof(float));
+    for (int k = 0; k < kMixK; ++k) {
+      g[k] = pb.gmm[k];
+      for (int j = 0; j < dof; ++j) {
+        g[kMixK + k * kMaxDof + j] = pb.gmm[kMixK + k * dof + j];
+        g[kMixK + kMixK * kMaxDof + k * kMaxDof + j] =
+            std::min(std::max(pb.gmm[kMixK + kMixK * dof + k * dof + j], -5.f), 2.f);
+      }
+    }
+    if (!finite_all(g, kGmmStride)) return fail(PRRTC_ERR_INVALID_ARG, "non-finite mixture");
+    host_gmm = true;
+  }
+  if (host_gmm)
+    CK(cudaMemcpyAsync(c->d_gmm, c->h_gmm, (size_t)n * kGmmStride * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  for (prrtc_proposal* prop : staged) {
+    const int rc2 = prrtc_internal_proposal_submit(prop, c->stream);
+    if (rc2) return rc2;
+  }
+
   // The launch sequence: descriptors in, setup, planner, bookkeeping, results
   // out (and, for one problem, the head of its path).  Replayed as a CUDA graph
   // while its shape stays the same.
@@ -1090,7 +1102,6 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     return PRRTC_OK;
   };
   static const bool no_graph = std::getenv("PRRTC_NO_GRAPH") != nullptr;
-  if (!any_gmm) CK(cudaEventRecord(c->ev[3], c->stream));
   if (no_graph) {
     if ((rc = enqueue(false))) return rc;
   } else {
@@ -1181,6 +1192,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   cudaGetLastError();  // timing is best effort: leave no error behind for later calls
   prrtc_launch_stats L{};
   L.prep_ms = prep_ms;
+  for (prrtc_proposal* prop : staged) L.infer_ms += prrtc_internal_proposal_infer_ms(prop);
   L.kernel_ms = plan_ms;
   L.setup_ms = setup_ms;
   L.grid = cfg.grid;

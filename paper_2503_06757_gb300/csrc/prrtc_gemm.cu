@@ -22,17 +22,21 @@
 // applies bias, ReLU and the output conversions.
 // Every mbarrier wait is bounded; a wait that gives up records an error, the
 // roles stop, and the CTA still frees its tensor memory.
+//
+// The same file holds the fused inference kernel of the proposal (one launch
+// for layers 1 (second half), 2, 3 and the head; see mlp_infer_kernel).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
 
 #include "prrtc.h"
-#include "prrtc_device.cuh"
+#include "prrtc_launch.h"
 
 namespace prrtc {
 namespace {
@@ -442,6 +446,339 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, i
   }
 }
 
+// ------------------------------------------------------------ fused inference
+// The learned proposal's forward pass for planning, after the occupancy part
+// of the first layer, in one launch.  A cluster of kIC CTAs owns 128 problem
+// rows; CTA r of the cluster owns 1/kIC of every layer's output columns:
+//   layer 1 (CUDA cores): h1[:, r-th eighth] = ReLU(b1 + occupancy part of
+//            the row's environment + start / goal columns);
+//   layers 2, 3, head (tensor cores): the row tile of the previous
+//            activations times this CTA's slice of the weights, FP32
+//            accumulator in TMEM, bias (+ ReLU) -- or, for the head, the
+//            mixture parameters written into the planner's rows.
+// Operands live in global memory pre-tiled: one 64-column k-block of 128
+// activation rows, or of this CTA's weight rows, is one contiguous block in
+// the 128-byte-swizzled layout the MMA reads, so each pipeline stage is two
+// plain bulk copies.  Each layer's writer produces exactly the k-blocks of
+// the next layer's input that its columns cover.  Between layers every thread
+// of the cluster makes its global writes visible to the async proxy (the next
+// layer's bulk copies) and meets the cluster barrier; the barriers sit
+// outside the role branches, so every thread meets each one even after a
+// bounded mbarrier wait has given up.
+constexpr int kIC = 8;
+constexpr int kIThreads = 192;
+constexpr int kIStages = 6;
+constexpr int kIBRows = 64;  // most weight rows one CTA takes per layer
+constexpr int kIStageBytes = A_BYTES + kIBRows * BK * 2;
+constexpr int kIQMax = 32;   // start + goal inputs
+constexpr int kIL0Cols = 128;
+constexpr int kIBiasMax = kIL0Cols + 3 * kIBRows;  // this CTA's bias slices of all four layers
+// ring | barriers | layer-1 scratch (inputs, weights, bias, env rows), plus alignment
+constexpr int kISmemBytes =
+    kIStages * kIStageBytes + 1024 + (BM * kIQMax + kIQMax * kIL0Cols + kIBiasMax) * 4 + BM * 4 + 1024;
+constexpr uint32_t kITmemCols = 256;
+
+// Byte offset of element (i, c) inside one k-block tile (rows of 64 BF16 =
+// 128 bytes; 16-byte unit u of row i stored at unit u ^ (i % 8)), the layout
+// a TMA load with 128-byte swizzle would produce and the MMA descriptors read.
+__host__ __device__ __forceinline__ uint32_t tile_off(int i, int c) {
+  return (uint32_t)i * 128u + ((((uint32_t)c >> 3) ^ ((uint32_t)i & 7u)) << 4) + (((uint32_t)c & 7u) << 1);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Global writes of this thread -> visible to the cluster's async-proxy reads
+// after the barrier; every thread of the cluster calls it.
+__device__ __forceinline__ void cluster_publish() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Weight matrix [N x K] (BF16, row-major) -> tiles [kIC slices][K/64 k-blocks]
+// of N/kIC rows each, in the tile layout above.
+__global__ void tile_weights_kernel(const __nv_bfloat16* __restrict__ w, int N, int K, __nv_bfloat16* __restrict__ out) {
+  const int nc = N / kIC, kts = K / BK;
+  const size_t total = (size_t)N * K;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(t / K), k = (int)(t % K);
+    const int r = n / nc, i = n % nc, kt = k / BK, c = k % BK;
+    unsigned char* tile = reinterpret_cast<unsigned char*>(out) + ((size_t)r * kts + kt) * (size_t)nc * 128;
+    *reinterpret_cast<__nv_bfloat16*>(tile + tile_off(i, c)) = w[t];
+  }
+}
+
+__global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
+    mlp_infer_kernel(const MlpInferArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kIStages * kIStageBytes);
+  uint64_t* empty = full + kIStages;
+  uint64_t* acc_full = empty + kIStages;  // [3] MMA -> epilogue, once per layer
+  uint64_t* roles_done = acc_full + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(roles_done + 1);
+  float* s_x = reinterpret_cast<float*>(smem + kIStages * kIStageBytes + 1024);  // [BM][kIQMax]
+  float* s_w = s_x + BM * kIQMax;                                               // [kIQMax][kIL0Cols]
+  float* s_b = s_w + kIQMax * kIL0Cols;                                         // [kIBiasMax] bias slices
+  int* s_e = reinterpret_cast<int*>(s_b + kIBiasMax);                           // [BM]
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int r = (int)rank;
+  const int mt = (int)(blockIdx.x / kIC), m0 = mt * BM;
+  const int dof = args.dof, nq = 2 * dof;
+  const int n_out[3] = {args.h1, args.h2, args.head};
+  const int k_in[3] = {args.h0, args.h1, args.h2};
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kIStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int l = 0; l < 3; ++l) mbar_init(&acc_full[l], 1);
+    mbar_init(roles_done, kIThreads / 32);
+    s_abort = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kITmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+
+  // ---- layer 1 on the CUDA cores: columns c0 .. c0 + 127 of this row tile
+  const int c0 = r * kIL0Cols;
+  for (int i = threadIdx.x; i < BM; i += kIThreads) {
+    const int row = m0 + i;
+    s_e[i] = row < args.B ? args.row_env[row] : -1;
+    s_b[i] = args.bias[0][c0 + i];
+  }
+  // bias slices of layers 2, 3 and the head at s_b + kIL0Cols + l * kIBRows
+  for (int i = threadIdx.x; i < 3 * kIBRows; i += kIThreads) {
+    const int l = i / kIBRows, j = i % kIBRows, nc = n_out[l] / kIC;
+    if (j < nc) s_b[kIL0Cols + i] = args.bias[l + 1][r * nc + j];
+  }
+  for (int i = threadIdx.x; i < BM * nq; i += kIThreads) {
+    const int rr = i / nq, c = i % nq, row = m0 + rr;
+    float v = 0.f;
+    if (row < args.B) {
+      const int j = c < dof ? c : c - dof;
+      const float* q = c < dof ? args.qs : args.qg;
+      v = __bfloat162float(__float2bfloat16_rn(2.f * (q[(size_t)row * dof + j] - args.lo[j]) / args.span[j] - 1.f));
+    }
+    s_x[rr * kIQMax + c] = v;
+  }
+  const __nv_bfloat16* wq = static_cast<const __nv_bfloat16*>(args.wq);
+  for (int i = threadIdx.x; i < nq * kIL0Cols; i += kIThreads) {
+    const int c = i / kIL0Cols, jj = i % kIL0Cols;
+    const int wrow = c < dof ? c : args.qpad + (c - dof);
+    s_w[c * kIL0Cols + jj] = __bfloat162float(wq[(size_t)wrow * args.h0 + c0 + jj]);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+  {
+    // item = (row, 8 columns): one 16-byte unit of the tiled output; all 128
+    // rows of the tile are written (rows past B as zeros).  Groups of items
+    // per thread put their loads in flight together.
+    unsigned char* h1 = static_cast<unsigned char*>(args.act[0]) + ((size_t)mt * (args.h0 / BK)) * (BM * 128);
+    constexpr int kUnits = kIL0Cols / 8, kItems = BM * kUnits, kGroup = 6;
+    for (int base = threadIdx.x; base < kItems; base += kIThreads * kGroup) {
+      float4 h[kGroup][2];
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int i = base + u * kIThreads, rr = i / kUnits, j8 = (i % kUnits) * 8;
+        h[u][0] = h[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < kItems && s_e[rr] >= 0) {
+          const float4* src = reinterpret_cast<const float4*>(args.h1o + (size_t)s_e[rr] * args.h0 + c0 + j8);
+          h[u][0] = __ldg(src);
+          h[u][1] = __ldg(src + 1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int i = base + u * kIThreads, rr = i / kUnits, j8 = (i % kUnits) * 8;
+        if (i >= kItems) continue;
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        if (s_e[rr] >= 0) {
+          float v[8] = {h[u][0].x, h[u][0].y, h[u][0].z, h[u][0].w, h[u][1].x, h[u][1].y, h[u][1].z, h[u][1].w};
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] += s_b[j8 + e];
+          for (int c = 0; c < nq; ++c) {
+            const float x = s_x[rr * kIQMax + c];
+            const float* w = s_w + c * kIL0Cols + j8;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = fmaf(w[e], x, v[e]);
+          }
+          pk = make_uint4(pack_bf16x2(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f)), pack_bf16x2(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f)),
+                          pack_bf16x2(fmaxf(v[4], 0.f), fmaxf(v[5], 0.f)), pack_bf16x2(fmaxf(v[6], 0.f), fmaxf(v[7], 0.f)));
+        }
+        const int col = c0 + j8;  // k-block col / 64 of the next layer, unit (col % 64) / 8
+        *reinterpret_cast<uint4*>(h1 + (size_t)(col / BK) * (BM * 128) + tile_off(rr, col % BK)) = pk;
+      }
+    }
+  }
+  __syncwarp();
+  cluster_publish();
+
+  // ---- layers 2, 3 and the head on the tensor cores
+  int it_p = 0, it_m = 0;  // stage counters of the producer and the MMA issuer
+  uint32_t tcol = 0;       // TMEM column of this layer's accumulator
+  for (int l = 0; l < 3; ++l) {
+    const int nc = n_out[l] / kIC, n0 = r * nc, kts = k_in[l] / BK;
+    if (warp == 0) {
+      const uint32_t b_bytes = (uint32_t)(nc * BK * 2);
+      const unsigned char* a_src = static_cast<const unsigned char*>(args.act[l]) + (size_t)mt * kts * (BM * 128);
+      const unsigned char* b_src = static_cast<const unsigned char*>(args.w[l]) + (size_t)r * kts * b_bytes;
+      for (int kt = 0; kt < kts; ++kt, ++it_p) {
+        const int st = it_p % kIStages;
+        const uint32_t ph = (uint32_t)(it_p / kIStages) & 1u;
+        int got = 0;
+        if (lane == 0) got = (!*abort_flag && wait_bar(&empty[st], ph ^ 1u)) ? 1 : 0;
+        got = __shfl_sync(kFull, got, 0);
+        if (!got) {
+          if (lane == 0) *abort_flag = 1;
+          break;
+        }
+        if (lane == 0) {
+          unsigned char* a = smem + st * kIStageBytes;
+          mbar_arrive_expect_tx(&full[st], (uint32_t)A_BYTES + b_bytes);
+          bulk_g2s(a, a_src + (size_t)kt * (BM * 128), (uint32_t)A_BYTES, &full[st]);
+          bulk_g2s(a + A_BYTES, b_src + (size_t)kt * b_bytes, b_bytes, &full[st]);
+        }
+        __syncwarp();
+      }
+    } else if (warp == 1) {
+      const uint32_t idesc = idesc_bf16(BM, nc);
+      bool ok = true;
+      for (int kt = 0; kt < kts; ++kt, ++it_m) {
+        const int st = it_m % kIStages;
+        const uint32_t ph = (uint32_t)(it_m / kIStages) & 1u;
+        int got = 0;
+        if (lane == 0) got = (!*abort_flag && wait_bar(&full[st], ph)) ? 1 : 0;
+        got = __shfl_sync(kFull, got, 0);
+        if (!got) {
+          if (lane == 0) *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        fence_after();
+        if (lane == 0) {
+          const uint32_t a = smem_u32(smem + st * kIStageBytes);
+          const uint32_t b = a + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            mma_bf16(tmem + tcol, smem_desc(a + 32u * k), smem_desc(b + 32u * k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&empty[st]);
+        }
+        __syncwarp();
+      }
+      if (ok && lane == 0) mma_commit(&acc_full[l]);
+      __syncwarp();
+    } else {
+      const int q = warp & 3;  // TMEM lane quarter this warp may access
+      const int i = 32 * q + lane, row = m0 + i;
+      int ok = 0;
+      if (lane == 0) ok = (!*abort_flag && wait_bar(&acc_full[l], 0u)) ? 1 : 0;
+      ok = __shfl_sync(kFull, ok, 0);
+      if (!ok) {
+        if (lane == 0) *abort_flag = 1;
+      } else {
+        fence_after();
+        const float* bias = s_b + kIL0Cols + l * kIBRows;  // this CTA's slice: column n0 + j at j
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + tcol;
+        if (l < 2) {
+          // columns n0 .. n0 + 63 = k-block r of the next layer's input: row i
+          // of that tile is this lane's 128 bytes
+          unsigned char* tile = static_cast<unsigned char*>(args.act[l + 1]) +
+                                ((size_t)mt * (n_out[l] / BK) + (size_t)(n0 / BK)) * (BM * 128);
+          for (int c = 0; c < nc; c += 32) {
+            uint32_t v[32];
+            __syncwarp();
+            tmem_ld32(taddr + (uint32_t)c, v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              uint4 pk;
+              const int j = c + 8 * u;
+              pk.x = pack_bf16x2(fmaxf(__uint_as_float(v[8 * u]) + bias[j], 0.f),
+                                 fmaxf(__uint_as_float(v[8 * u + 1]) + bias[j + 1], 0.f));
+              pk.y = pack_bf16x2(fmaxf(__uint_as_float(v[8 * u + 2]) + bias[j + 2], 0.f),
+                                 fmaxf(__uint_as_float(v[8 * u + 3]) + bias[j + 3], 0.f));
+              pk.z = pack_bf16x2(fmaxf(__uint_as_float(v[8 * u + 4]) + bias[j + 4], 0.f),
+                                 fmaxf(__uint_as_float(v[8 * u + 5]) + bias[j + 5], 0.f));
+              pk.w = pack_bf16x2(fmaxf(__uint_as_float(v[8 * u + 6]) + bias[j + 6], 0.f),
+                                 fmaxf(__uint_as_float(v[8 * u + 7]) + bias[j + 7], 0.f));
+              *reinterpret_cast<uint4*>(tile + tile_off(i, j)) = pk;
+            }
+          }
+        } else {
+          // head columns n0 .. n0 + nc - 1 -> the planner's mixture row
+          const int K = args.mix_k, G = args.gmm_dof;
+          const int head = K * (1 + 2 * dof);
+          float* g = row < args.B ? args.gmm_rows[row] : nullptr;
+          for (int c = 0; c < nc; c += 16) {
+            uint32_t v[16];
+            __syncwarp();
+            tmem_ld16(taddr + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int t = n0 + c + j;
+              if (!g || t >= head) continue;
+              const float val = __uint_as_float(v[j]) + bias[c + j];
+              if (t < K) {
+                g[t] = val;
+              } else if (t < K + K * dof) {
+                const int k = (t - K) / dof, jj = (t - K) % dof;
+                g[K + k * G + jj] = val;
+              } else {
+                const int k = (t - K - K * dof) / dof, jj = (t - K - K * dof) % dof;
+                g[K + K * G + k * G + jj] = fminf(fmaxf(val, args.logsig_lo), args.logsig_hi);
+              }
+            }
+          }
+        }
+      }
+    }
+    tcol += (uint32_t)nc;
+    if (l < 2) {
+      __syncwarp();
+      fence_before();
+      cluster_publish();
+      fence_after();
+    }
+  }
+  // join, then the allocating warp frees tensor memory (as in the GEMM)
+  __syncwarp();
+  fence_before();
+  if (lane == 0) mbar_arrive(roles_done);
+  if (warp == 1) {
+    int joined = 0;
+    if (lane == 0) joined = wait_bar(roles_done, 0) ? 1 : 0;
+    joined = __shfl_sync(kFull, joined, 0);
+    (void)joined;
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kITmemCols) : "memory");
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::mutex g_encode_mu;
 
@@ -458,12 +795,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return g_encode;
 }
 
-// Row-major [rows x K] BF16 matrix, K contiguous; boxes of 64 x box_rows.
-bool make_tmap(CUtensorMap* tm, const void* ptr, int rows, int K, int box_rows) {
+// Row-major [rows x K] BF16 matrix with row stride ld elements, K
+// contiguous; boxes of 64 x box_rows.
+bool make_tmap(CUtensorMap* tm, const void* ptr, int rows, int K, int ld, int box_rows) {
   auto enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
@@ -488,38 +826,38 @@ bool make_out_tmap(CUtensorMap* tm, const void* ptr, int rows, int cols, int ld,
 }
 
 // Encoded tensor maps by (device, address, rows, inner extent, row stride,
-// kind): the MLP calls the same few layouts every step, and encoding costs
-// host time.  kind 0: BF16 operand with 128-row boxes, 1: with 256-row boxes,
-// 2: FP32 output, 3: BF16 output.
+// kind, box rows): the MLP calls the same few layouts every step, and encoding
+// costs host time.  kind 0: BF16 operand (boxes of 64 x box rows), 2: FP32
+// output, 3: BF16 output.
 struct MapKey {
   int dev;
   const void* ptr;
-  int rows, cols, ld, kind;
+  int rows, cols, ld, kind, box;
   bool operator<(const MapKey& o) const {
     if (dev != o.dev) return dev < o.dev;
     if (ptr != o.ptr) return ptr < o.ptr;
     if (rows != o.rows) return rows < o.rows;
     if (cols != o.cols) return cols < o.cols;
     if (ld != o.ld) return ld < o.ld;
-    return kind < o.kind;
+    if (kind != o.kind) return kind < o.kind;
+    return box < o.box;
   }
 };
 std::mutex g_map_mu;
 std::map<MapKey, CUtensorMap> g_maps;
 constexpr size_t kMaxCachedMaps = 256;
 
-bool cached_map(CUtensorMap* tm, const void* ptr, int rows, int cols, int ld, int kind) {
+bool cached_map(CUtensorMap* tm, const void* ptr, int rows, int cols, int ld, int kind, int box = 0) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  const MapKey key{dev, ptr, rows, cols, ld, kind};
+  const MapKey key{dev, ptr, rows, cols, ld, kind, box};
   std::lock_guard<std::mutex> lk(g_map_mu);
   auto it = g_maps.find(key);
   if (it != g_maps.end()) {
     *tm = it->second;
     return true;
   }
-  const bool ok = kind <= 1 ? make_tmap(tm, ptr, rows, cols, kind == 0 ? BM : BN)
-                            : make_out_tmap(tm, ptr, rows, cols, ld, kind == 3);
+  const bool ok = kind == 0 ? make_tmap(tm, ptr, rows, cols, ld, box) : make_out_tmap(tm, ptr, rows, cols, ld, kind == 3);
   if (!ok) return false;
   if (g_maps.size() >= kMaxCachedMaps) g_maps.clear();
   g_maps.emplace(key, *tm);
@@ -563,15 +901,16 @@ int g_sms = 0;
 
 // Host launcher used by the MLP code and the C ABI entry point.  splits_hint:
 // 0 = choose (split K while the tiles fill less than one wave), else forced.
-int gemm_bf16_split(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32,
-                    int ldc32, void* c16, int ldc16, cudaStream_t stream, int splits_hint) {
+int gemm_bf16_ld(const void* a, int lda, const void* b, int ldb, int M, int N, int K, const float* bias, int relu,
+                 float* c32, int ldc32, void* c16, int ldc16, cudaStream_t stream, int splits_hint) {
   if (M <= 0 || N <= 0 || K <= 0 || !a || !b || (!c32 && !c16)) return PRRTC_ERR_INVALID_ARG;
   if (K % 8 || N % 8 || (c32 && ldc32 % 4) || (c16 && ldc16 % 8)) return PRRTC_ERR_UNSUPPORTED;
+  if (lda < K || ldb < K || lda % 8 || ldb % 8) return PRRTC_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) return PRRTC_ERR_INVALID_ARG;
   if ((c32 && (reinterpret_cast<uintptr_t>(c32) & 15)) || (c16 && (reinterpret_cast<uintptr_t>(c16) & 15)))
     return PRRTC_ERR_INVALID_ARG;
   CUtensorMap ta, tb;
-  if (!cached_map(&ta, a, M, K, K, 0) || !cached_map(&tb, b, N, K, K, 1)) return PRRTC_ERR_CUDA;
+  if (!cached_map(&ta, a, M, K, lda, 0, BM) || !cached_map(&tb, b, N, K, ldb, 0, BN)) return PRRTC_ERR_CUDA;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
@@ -620,9 +959,56 @@ int gemm_bf16_split(const void* a, const void* b, int M, int N, int K, const flo
   return PRRTC_OK;
 }
 
+int gemm_bf16_split(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32,
+                    int ldc32, void* c16, int ldc16, cudaStream_t stream, int splits_hint) {
+  return gemm_bf16_ld(a, K, b, K, M, N, K, bias, relu, c32, ldc32, c16, ldc16, stream, splits_hint);
+}
+
 int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32, int ldc32,
               void* c16, int ldc16, cudaStream_t stream) {
   return gemm_bf16_split(a, b, M, N, K, bias, relu, c32, ldc32, c16, ldc16, stream, 0);
+}
+
+int mlp_check_shapes(int h0, int h1, int h2, int head) {
+  if (h0 != kIC * kIL0Cols || h1 % BK || h2 % BK) return PRRTC_ERR_UNSUPPORTED;
+  const int n_out[3] = {h1, h2, head};
+  int cols = 0;
+  for (int l = 0; l < 3; ++l) {
+    if (n_out[l] % (kIC * 16) || n_out[l] / kIC > kIBRows) return PRRTC_ERR_UNSUPPORTED;
+    cols += n_out[l] / kIC;
+  }
+  return cols <= (int)kITmemCols ? PRRTC_OK : PRRTC_ERR_UNSUPPORTED;
+}
+
+int mlp_tile_weights(const void* w, int N, int K, void* out, cudaStream_t stream) {
+  if (N % (kIC * 16) || K % BK || (reinterpret_cast<uintptr_t>(out) & 15)) return PRRTC_ERR_UNSUPPORTED;
+  const size_t total = (size_t)N * K;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  tile_weights_kernel<<<blocks, 256, 0, stream>>>(static_cast<const __nv_bfloat16*>(w), N, K,
+                                                  static_cast<__nv_bfloat16*>(out));
+  return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
+}
+
+int mlp_infer(const MlpInferArgs& a, cudaStream_t stream) {
+  if (a.rows <= 0 || a.B <= 0 || a.B > a.rows || a.dof < 1 || 2 * a.dof > kIQMax || a.dof > a.gmm_dof)
+    return PRRTC_ERR_INVALID_ARG;
+  int rc = mlp_check_shapes(a.h0, a.h1, a.h2, a.head);
+  if (rc) return rc;
+  if (a.mix_k * (1 + 2 * a.dof) > a.head) return PRRTC_ERR_INVALID_ARG;
+  for (int l = 0; l < 3; ++l)
+    if (reinterpret_cast<uintptr_t>(a.act[l]) & 15 || reinterpret_cast<uintptr_t>(a.w[l]) & 15)
+      return PRRTC_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(a.h1o) & 15) return PRRTC_ERR_INVALID_ARG;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kISmemBytes) !=
+        cudaSuccess)
+      return PRRTC_ERR_CUDA;
+    attr = true;
+  }
+  const int m_tiles = (a.rows + BM - 1) / BM;
+  mlp_infer_kernel<<<m_tiles * kIC, kIThreads, kISmemBytes, stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
 }
 
 // Changes whenever a split-K workspace is allocated or moved: work captured

@@ -161,6 +161,43 @@ cudaError_t launch_esdf(const uint8_t* occ, const int dims[3], float voxel, int2
 // Tensor-core GEMM (prrtc_gemm.cu): C[M,N] = A[M,K] B[N,K]^T (+bias, ReLU).
 int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bias, int relu, float* c32, int ldc32,
               void* c16, int ldc16, cudaStream_t stream);
+// The same with row strides lda / ldb (elements, multiples of 8, >= K) of the
+// operands, e.g. a column range of a wider weight matrix; splits_hint 0 = auto.
+int gemm_bf16_ld(const void* a, int lda, const void* b, int ldb, int M, int N, int K, const float* bias, int relu,
+                 float* c32, int ldc32, void* c16, int ldc16, cudaStream_t stream, int splits_hint);
 int gemm_take_error();
+
+// Fused inference of the learned proposal after the occupancy part of its
+// first layer (prrtc_gemm.cu): first hidden layer from its per-environment
+// occupancy part plus the start / goal part, the three tensor-core layers,
+// and the mixture parameters written into the planner's rows -- one launch.
+// Weights and activations are pre-tiled: [slice or row tile][64-column
+// k-block] blocks in the 128-byte-swizzled layout of the MMA operands
+// (weights: kIC = 8 slices of out/8 rows, tiled by mlp_tile_weights;
+// activations: 128-row tiles, buffers of ceil(rows / 128) * 128 rows).
+struct MlpInferArgs {
+  int rows, B, dof;            // rows: activation rows (B rounded up to 8)
+  int h0, h1, h2, head;        // widths: hidden 1, 2, 3 and the padded head
+  int qpad;                    // start / goal input columns per side
+  const float* h1o;            // [U x h0] occupancy part of hidden 1, one row per environment
+  const int* row_env;          // [rows] environment row of each problem
+  const float* qs;             // [B x dof] starts
+  const float* qg;             // [B x dof] goals
+  const float* lo;             // [dof] joint lower limits
+  const float* span;           // [dof] upper - lower
+  const void* wq;              // BF16 [2 qpad x h0]: start / goal columns of layer 1, transposed
+  const void* w[3];            // tiled BF16 weights of layers 2, 3 and the head
+  const float* bias[4];        // biases of layers 1..4
+  void* act[3];                // tiled BF16 activations of hidden layers 1, 2, 3
+  float* const* gmm_rows;      // [B] planner mixture rows (device pointers)
+  int mix_k, gmm_dof;          // planner layout: logits[mix_k] | means[mix_k][gmm_dof] | log-sigmas
+                               // (entries of joints >= dof are not written; the planner skips them)
+  float logsig_lo, logsig_hi;  // log-sigma clamp
+};
+// PRRTC_OK when the fused kernel supports these layer widths.
+int mlp_check_shapes(int h0, int h1, int h2, int head);
+// Weight matrix [N x K] (BF16, row-major) -> the tiled layout above.
+int mlp_tile_weights(const void* w, int N, int K, void* out, cudaStream_t stream);
+int mlp_infer(const MlpInferArgs& a, cudaStream_t stream);
 
 }  // namespace prrtc

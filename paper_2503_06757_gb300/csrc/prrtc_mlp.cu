@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <map>
 #include <random>
 #include <string>
 #include <vector>
@@ -135,6 +136,65 @@ __global__ void features_kernel(const uint8_t* __restrict__ occ, const int* __re
   }
 }
 
+// Occupancy part of the first layer for a few environments, W[:, :4096] x_occ,
+// read straight from the 0/1 grids: one warp per output feature streams its
+// weight row once (16-byte loads) and sums the weights of occupied voxels for
+// every environment; fixed order, so the result is deterministic.
+constexpr int kGemvMaxEnvs = 32;
+
+__global__ void __launch_bounds__(256) l1_occ_gemv_kernel(const uint8_t* __restrict__ occ, int U,
+                                                           const bf16* __restrict__ w, float* __restrict__ out) {
+  __shared__ uint32_t bits[kGemvMaxEnvs][kVox / 32];
+  for (int t = threadIdx.x; t < U * (kVox / 32); t += blockDim.x) {
+    const int u = t / (kVox / 32), word = t % (kVox / 32);
+    const uint8_t* o = occ + (size_t)u * kVox + word * 32;
+    uint32_t b = 0;
+    for (int i = 0; i < 32; ++i) b |= (o[i] ? 1u : 0u) << i;
+    bits[u][word] = b;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= kHid0) return;
+  // the whole 8 KB weight row in flight at once: 16 loads of 16 bytes per lane
+  const uint4* row = reinterpret_cast<const uint4*>(w + (size_t)j * kIn);
+  uint4 raw[kVox / 256];
+#pragma unroll
+  for (int it = 0; it < kVox / 256; ++it) raw[it] = __ldg(row + it * 32 + lane);
+  for (int u0 = 0; u0 < U; u0 += 8) {
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int it = 0; it < kVox / 256; ++it) {
+      const int c0 = it * 256 + lane * 8;  // this lane's 8 consecutive voxels
+      const bf16* wv = reinterpret_cast<const bf16*>(&raw[it]);
+      float wf[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) wf[i] = __bfloat162float(wv[i]);
+#pragma unroll
+      for (int du = 0; du < 8; ++du) {
+        if (u0 + du < U) {
+          const uint32_t b8 = bits[u0 + du][c0 / 32] >> (c0 % 32);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[du] += ((b8 >> i) & 1u) ? wf[i] : 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int du = 0; du < 8; ++du) {
+      float v = acc[du];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && u0 + du < U) out[(size_t)(u0 + du) * kHid0 + j] = v;
+    }
+  }
+}
+
+// Occupancy rows (one per distinct environment) as BF16 inputs of the
+// occupancy part of the first layer, for batches with many environments.
+__global__ void occ_bf16_kernel(const uint8_t* __restrict__ occ, bf16* __restrict__ x) {
+  const size_t base = (size_t)blockIdx.x * kVox;
+  for (int c = threadIdx.x; c < kVox; c += blockDim.x) x[base + c] = __float2bfloat16_rn(occ[base + c] ? 1.f : 0.f);
+}
+
 // Mixture negative log-likelihood of each sample's target and its gradient
 // with respect to the head output (scaled by 1/B).  One warp per sample;
 // lane k < 8 owns component k.
@@ -248,29 +308,6 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   }
 }
 
-// Mixture parameters of each row's head output, in the planner's layout:
-// [logits(8) | mean (8 x 16) | log-sigma clamped (8 x 16)].
-__global__ void mixture_params_kernel(const float* __restrict__ out, int P, int B, int dof,
-                                      float* const* __restrict__ rows) {
-  const int b = blockIdx.x;
-  if (b >= B) return;
-  const float* o = out + (size_t)b * P;
-  float* g = rows[b];
-  for (int t = threadIdx.x; t < kK + 2 * kK * kMaxDof; t += blockDim.x) {
-    float v = 0.f;
-    if (t < kK) {
-      v = o[t];
-    } else if (t < kK + kK * kMaxDof) {
-      const int k = (t - kK) / kMaxDof, j = (t - kK) % kMaxDof;
-      v = (j < dof) ? o[kK + k * dof + j] : 0.f;
-    } else {
-      const int k = (t - kK - kK * kMaxDof) / kMaxDof, j = (t - kK - kK * kMaxDof) % kMaxDof;
-      v = (j < dof) ? fminf(fmaxf(o[kK + kK * dof + k * dof + j], kLogSigMin), kLogSigMax) : 0.f;
-    }
-    g[t] = v;
-  }
-}
-
 int blocks_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
 
 }  // namespace
@@ -279,6 +316,17 @@ int blocks_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); 
 using namespace prrtc;
 
 // ------------------------------------------------------------------ handle
+namespace prrtc {
+namespace {
+// One staged inference batch: offsets into the staging block and its shape.
+struct Pending {
+  size_t o_env = 0, o_map = 0, o_rows = 0, o_qs = 0, o_qg = 0, bytes = 0;
+  int B = 0, rows = 0, U = 0;
+  uint64_t sig = 0;
+};
+}  // namespace
+}  // namespace prrtc
+
 struct prrtc_proposal {
   int device = -1;
   int dof = 0, P = 0;
@@ -290,6 +338,7 @@ struct prrtc_proposal {
   float* v = nullptr;
   bf16* w16[4] = {};
   bf16* w16t[4] = {};
+  bf16* wtile[3] = {};  // layers 2, 3 and the head, tiled for the fused inference kernel
   int step = 0;
   float lo[kMaxDof], span[kMaxDof];
   float* d_lims = nullptr;  // lo[16] | span[16]
@@ -318,6 +367,17 @@ struct prrtc_proposal {
   size_t d_stage_cap = 0;
   uint8_t* inf_occ = nullptr;
   size_t inf_occ_cap = 0;
+  // first layer split by distinct environment (occupancy part once per environment)
+  bf16* xo16 = nullptr;    // [envs x kVox]
+  size_t xo16_cap = 0;
+  float* h1o32 = nullptr;  // [envs x kHid0]
+  size_t h1o32_cap = 0;
+  bf16* atile[3] = {};     // tiled hidden activations, 128-row tiles
+  size_t atile_cap[3] = {};
+  Pending pend;            // the staged, not yet submitted, inference batch
+  bool pend_ok = false;
+  cudaEvent_t inf_ev[2] = {};  // timing of the last submitted chain
+  bool inf_timed = false;
   cudaGraphExec_t infer_exec = nullptr;
   uint64_t infer_sig = 0;  // signature of the buffers baked into infer_exec
   uint64_t seen_sig = 0;   // signature of the last chain run eagerly
@@ -410,6 +470,8 @@ int refresh_weights(prrtc_proposal* p) {
     to_bf16_kernel<<<blocks_for(n), 256, 0, p->stream>>>(p->master + p->w_off[l], n, p->w16[l]);
     int rc = transpose(p->w16[l], p->out_dim[l], p->in_dim[l], p->w16t[l], p->stream);
     if (rc) return rc;
+    if (l > 0 && (rc = mlp_tile_weights(p->w16[l], p->out_dim[l], p->in_dim[l], p->wtile[l - 1], p->stream)))
+      return rc;
   }
   return cudaGetLastError() == cudaSuccess ? PRRTC_OK : PRRTC_ERR_CUDA;
 }
@@ -419,12 +481,13 @@ int gemm(const bf16* a, const bf16* b, int M, int N, int K, const float* bias, i
   return gemm_bf16(a, b, M, N, K, bias, relu, c32, N, c16, N, s);
 }
 
-// Forward of `rows` feature rows already in x16; out32 receives the head.
-int forward_rows(prrtc_proposal* p, int rows) {
+// Forward of `rows` feature rows already in x16 (or, from layer 1 on, first
+// activations already in h16[0]); out32 receives the head.
+int forward_rows(prrtc_proposal* p, int rows, int first_layer = 0) {
   const cudaStream_t s = p->stream;
   int rc;
-  const bf16* in = p->x16;
-  for (int l = 0; l < 3; ++l) {
+  const bf16* in = first_layer == 0 ? p->x16 : p->h16[first_layer - 1];
+  for (int l = first_layer; l < 3; ++l) {
     if ((rc = gemm(in, p->w16[l], rows, p->out_dim[l], p->in_dim[l], p->master + p->b_off[l], 1, nullptr, p->h16[l],
                    s)))
       return rc;
@@ -496,19 +559,52 @@ uint64_t chain_signature(std::initializer_list<uint64_t> vals) {
   return h;
 }
 
-// Kernel chain of one inference batch on p->stream: occupancy, features, the
-// four dense layers, mixture parameters into the planner's rows.
-int enqueue_inference(prrtc_proposal* p, const EnvView* d_envs, float* const* d_rows, const float* d_qs,
-                      const float* d_qg, int B, int rows) {
-  MCK(cudaMemsetAsync(p->inf_occ, 0, (size_t)B * kVox, p->stream));
-  occupancy_scatter_kernel<<<dim3(4, B), 256, 0, p->stream>>>(d_envs, p->inf_occ);
-  features_kernel<<<rows, 256, 0, p->stream>>>(p->inf_occ, nullptr, nullptr, d_qs, d_qg, p->d_lims,
-                                               p->d_lims + kMaxDof, B, p->dof, p->x16);
-  int rc = forward_rows(p, rows);
-  if (rc) return rc;
-  mixture_params_kernel<<<B, 128, 0, p->stream>>>(p->out32, p->P, B, p->dof, d_rows);
+// Kernel chain of one inference batch on p->stream: occupancy grids of the
+// U distinct environments, the occupancy part of the first layer once per
+// environment, then one fused launch for the rest of the network and the
+// mixture parameters in the planner's rows.
+int enqueue_inference(prrtc_proposal* p, const EnvView* d_envs, int U, const int* d_row_env, float* const* d_rows,
+                      const float* d_qs, const float* d_qg, int B, int rows) {
+  const cudaStream_t s = p->stream;
+  MCK(cudaMemsetAsync(p->inf_occ, 0, (size_t)U * kVox, s));
+  occupancy_scatter_kernel<<<dim3(4, U), 256, 0, s>>>(d_envs, p->inf_occ);
+  int rc;
+  if (U <= kGemvMaxEnvs) {
+    l1_occ_gemv_kernel<<<kHid0 / 8, 256, 0, s>>>(p->inf_occ, U, p->w16[0], p->h1o32);
+  } else {
+    occ_bf16_kernel<<<U, 256, 0, s>>>(p->inf_occ, p->xo16);
+    if ((rc = gemm_bf16_ld(p->xo16, kVox, p->w16[0], kIn, U, kHid0, kVox, nullptr, 0, p->h1o32, kHid0, nullptr, 0, s,
+                           0)))
+      return rc;
+  }
   MCK(cudaGetLastError());
-  return PRRTC_OK;
+  MlpInferArgs a{};
+  a.rows = rows;
+  a.B = B;
+  a.dof = p->dof;
+  a.h0 = kHid0;
+  a.h1 = kHid1;
+  a.h2 = kHid2;
+  a.head = p->P;
+  a.qpad = kQPad;
+  a.h1o = p->h1o32;
+  a.row_env = d_row_env;
+  a.qs = d_qs;
+  a.qg = d_qg;
+  a.lo = p->d_lims;
+  a.span = p->d_lims + kMaxDof;
+  a.wq = p->w16t[0] + (size_t)kVox * kHid0;
+  for (int l = 0; l < 3; ++l) {
+    a.w[l] = p->wtile[l];
+    a.act[l] = p->atile[l];
+  }
+  for (int l = 0; l < 4; ++l) a.bias[l] = p->master + p->b_off[l];
+  a.gmm_rows = d_rows;
+  a.mix_k = kK;
+  a.gmm_dof = kMaxDof;
+  a.logsig_lo = kLogSigMin;
+  a.logsig_hi = kLogSigMax;
+  return mlp_infer(a, s);
 }
 
 }  // namespace
@@ -535,46 +631,98 @@ int grow_pinned(unsigned char** p, size_t* cap, size_t need) {
 
 }  // namespace
 
-// Internal: the mixture parameters of `B` problems into device memory (the
-// planner's layout), one destination row pointer per problem; ordered before
-// later work on `stream`.  Used by prrtc_plan_batch_learned.
-int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, const float* qs_host,
-                                     const float* qg_host, int B, float* const* gmm_rows, cudaStream_t stream) {
+// Internal, two halves of one inference batch.  Stage: the host work -- group
+// the problems by environment, fill the pinned staging block -- for `B`
+// problems whose mixtures go to the device rows gmm_rows[b] (the planner's
+// layout).  Submit: the device work -- one staging copy, the kernel chain
+// (eager, captured on the second call with the same buffers, replayed after)
+// -- ordered before later work on `stream`.  Used by prrtc_plan_batch_learned
+// (which stages before its timed device work begins) and the serving loop.
+int prrtc_internal_proposal_stage(prrtc_proposal* p, const EnvView* envs, const float* qs_host, const float* qg_host,
+                                  int B, float* const* gmm_rows) {
   if (!p || B <= 0) return PRRTC_ERR_INVALID_ARG;
   cudaGetLastError();
+  p->pend_ok = false;
   const int rows = (B + 7) & ~7;
   int rc;
   if ((rc = ensure_scratch(p, rows))) return rc;
-  if ((rc = grow(&p->inf_occ, &p->inf_occ_cap, (size_t)B * kVox))) return rc;
-  // one staging block: env views | planner row pointers | starts | goals
+  // distinct environments of the batch (by their device data) and each
+  // problem's index among them
+  std::vector<EnvView> uniq;
+  std::vector<int> row_env(rows, 0);
+  {
+    std::map<std::pair<const void*, const void*>, int> seen;
+    for (int b = 0; b < B; ++b) {
+      const auto key = std::make_pair(static_cast<const void*>(envs[b].data),
+                                      static_cast<const void*>(envs[b].esdf.v));
+      auto it = seen.find(key);
+      if (it == seen.end()) {
+        it = seen.emplace(key, (int)uniq.size()).first;
+        uniq.push_back(envs[b]);
+      }
+      row_env[b] = it->second;
+    }
+  }
+  const int U = (int)uniq.size();
+  if ((rc = grow(&p->inf_occ, &p->inf_occ_cap, (size_t)U * kVox))) return rc;
+  if (U > kGemvMaxEnvs && (rc = grow(&p->xo16, &p->xo16_cap, (size_t)U * kVox))) return rc;
+  if ((rc = grow(&p->h1o32, &p->h1o32_cap, (size_t)U * kHid0))) return rc;
+  {
+    const size_t m_pad = (size_t)((rows + 127) / 128) * 128;
+    const int width[3] = {kHid0, kHid1, kHid2};
+    for (int l = 0; l < 3; ++l)
+      if ((rc = grow(&p->atile[l], &p->atile_cap[l], m_pad * width[l]))) return rc;
+  }
+  // one staging block: env views | row -> env | planner row pointers | starts | goals
   auto up16 = [](size_t x) { return (x + 15) & ~size_t(15); };
-  const size_t o_env = 0;
-  const size_t o_rows = up16(o_env + (size_t)B * sizeof(EnvView));
-  const size_t o_qs = up16(o_rows + (size_t)B * sizeof(float*));
-  const size_t o_qg = up16(o_qs + (size_t)B * p->dof * sizeof(float));
-  const size_t bytes = up16(o_qg + (size_t)B * p->dof * sizeof(float));
-  if ((rc = grow_pinned(&p->h_stage, &p->h_stage_cap, bytes))) return rc;
-  if ((rc = grow(&p->d_stage, &p->d_stage_cap, bytes))) return rc;
+  Pending& q = p->pend;
+  q.o_env = 0;
+  q.o_map = up16(q.o_env + (size_t)U * sizeof(EnvView));
+  q.o_rows = up16(q.o_map + (size_t)rows * sizeof(int));
+  q.o_qs = up16(q.o_rows + (size_t)B * sizeof(float*));
+  q.o_qg = up16(q.o_qs + (size_t)B * p->dof * sizeof(float));
+  q.bytes = up16(q.o_qg + (size_t)B * p->dof * sizeof(float));
+  if ((rc = grow_pinned(&p->h_stage, &p->h_stage_cap, q.bytes))) return rc;
+  if ((rc = grow(&p->d_stage, &p->d_stage_cap, q.bytes))) return rc;
   // the previous call's copy may still be reading the pinned block
   MCK(cudaStreamSynchronize(p->stream));
-  std::memcpy(p->h_stage + o_env, envs, (size_t)B * sizeof(EnvView));
-  std::memcpy(p->h_stage + o_rows, gmm_rows, (size_t)B * sizeof(float*));
-  std::memcpy(p->h_stage + o_qs, qs_host, (size_t)B * p->dof * sizeof(float));
-  std::memcpy(p->h_stage + o_qg, qg_host, (size_t)B * p->dof * sizeof(float));
-  MCK(cudaMemcpyAsync(p->d_stage, p->h_stage, bytes, cudaMemcpyHostToDevice, p->stream));
-  const EnvView* d_envs = reinterpret_cast<const EnvView*>(p->d_stage + o_env);
-  float* const* d_rows = reinterpret_cast<float* const*>(p->d_stage + o_rows);
-  const float* d_qs = reinterpret_cast<const float*>(p->d_stage + o_qs);
-  const float* d_qg = reinterpret_cast<const float*>(p->d_stage + o_qg);
-  const uint64_t sig = chain_signature(
-      {(uint64_t)B, (uint64_t)rows, (uint64_t)(uintptr_t)p->d_stage, (uint64_t)(uintptr_t)p->inf_occ,
+  std::memcpy(p->h_stage + q.o_env, uniq.data(), (size_t)U * sizeof(EnvView));
+  std::memcpy(p->h_stage + q.o_map, row_env.data(), (size_t)rows * sizeof(int));
+  std::memcpy(p->h_stage + q.o_rows, gmm_rows, (size_t)B * sizeof(float*));
+  std::memcpy(p->h_stage + q.o_qs, qs_host, (size_t)B * p->dof * sizeof(float));
+  std::memcpy(p->h_stage + q.o_qg, qg_host, (size_t)B * p->dof * sizeof(float));
+  q.B = B;
+  q.rows = rows;
+  q.U = U;
+  q.sig = chain_signature(
+      {(uint64_t)B, (uint64_t)rows, (uint64_t)U, (uint64_t)(uintptr_t)p->xo16,
+       (uint64_t)(uintptr_t)p->h1o32, (uint64_t)(uintptr_t)p->w16t[0], (uint64_t)(uintptr_t)p->atile[0],
+       (uint64_t)(uintptr_t)p->atile[1], (uint64_t)(uintptr_t)p->atile[2], (uint64_t)(uintptr_t)p->wtile[0],
+       (uint64_t)(uintptr_t)p->wtile[1], (uint64_t)(uintptr_t)p->wtile[2],
+       (uint64_t)(uintptr_t)p->d_stage, (uint64_t)(uintptr_t)p->inf_occ,
        (uint64_t)(uintptr_t)p->x16, (uint64_t)(uintptr_t)p->h16[0], (uint64_t)(uintptr_t)p->h16[1],
        (uint64_t)(uintptr_t)p->h16[2], (uint64_t)(uintptr_t)p->out32, (uint64_t)(uintptr_t)p->w16[0],
        (uint64_t)(uintptr_t)p->w16[1], (uint64_t)(uintptr_t)p->w16[2], (uint64_t)(uintptr_t)p->w16[3],
        (uint64_t)(uintptr_t)p->master, (uint64_t)(uintptr_t)p->d_lims, gemm_workspace_epoch()});
-  if (p->infer_exec && p->infer_sig == sig) {
+  p->pend_ok = true;
+  return PRRTC_OK;
+}
+
+int prrtc_internal_proposal_submit(prrtc_proposal* p, cudaStream_t stream) {
+  if (!p || !p->pend_ok) return PRRTC_ERR_INVALID_ARG;
+  p->pend_ok = false;
+  const Pending& q = p->pend;
+  int rc;
+  MCK(cudaEventRecord(p->inf_ev[0], p->stream));
+  MCK(cudaMemcpyAsync(p->d_stage, p->h_stage, q.bytes, cudaMemcpyHostToDevice, p->stream));
+  const EnvView* d_envs = reinterpret_cast<const EnvView*>(p->d_stage + q.o_env);
+  const int* d_row_env = reinterpret_cast<const int*>(p->d_stage + q.o_map);
+  float* const* d_rows = reinterpret_cast<float* const*>(p->d_stage + q.o_rows);
+  const float* d_qs = reinterpret_cast<const float*>(p->d_stage + q.o_qs);
+  const float* d_qg = reinterpret_cast<const float*>(p->d_stage + q.o_qg);
+  if (p->infer_exec && p->infer_sig == q.sig) {
     MCK(cudaGraphLaunch(p->infer_exec, p->stream));
-  } else if (p->seen_sig == sig) {
+  } else if (p->seen_sig == q.sig) {
     // second call with the same buffers: capture the chain (no allocation can
     // happen inside it now) and replay it from here on
     if (p->infer_exec) {
@@ -582,7 +730,7 @@ int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, con
       p->infer_exec = nullptr;
     }
     MCK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_inference(p, d_envs, d_rows, d_qs, d_qg, B, rows);
+    rc = enqueue_inference(p, d_envs, q.U, d_row_env, d_rows, d_qs, d_qg, q.B, q.rows);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
     if (rc || ce != cudaSuccess || !graph) {
@@ -596,16 +744,38 @@ int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, con
       p->infer_exec = nullptr;
       return mlp_fail(PRRTC_ERR_CUDA, "inference graph instantiation failed");
     }
-    p->infer_sig = sig;
+    p->infer_sig = q.sig;
     MCK(cudaGraphLaunch(p->infer_exec, p->stream));
   } else {
-    if ((rc = enqueue_inference(p, d_envs, d_rows, d_qs, d_qg, B, rows))) return rc;
-    p->seen_sig = sig;
+    if ((rc = enqueue_inference(p, d_envs, q.U, d_row_env, d_rows, d_qs, d_qg, q.B, q.rows))) return rc;
+    p->seen_sig = q.sig;
   }
+  MCK(cudaEventRecord(p->inf_ev[1], p->stream));
   // the planner runs on another stream: order it after this work
   MCK(cudaEventRecord(p->done, p->stream));
   MCK(cudaStreamWaitEvent(stream, p->done, 0));
+  p->inf_timed = true;
   return PRRTC_OK;
+}
+
+int prrtc_internal_proposal_mixtures(prrtc_proposal* p, const EnvView* envs, const float* qs_host,
+                                     const float* qg_host, int B, float* const* gmm_rows, cudaStream_t stream) {
+  const int rc = prrtc_internal_proposal_stage(p, envs, qs_host, qg_host, B, gmm_rows);
+  return rc ? rc : prrtc_internal_proposal_submit(p, stream);
+}
+
+// Device time of the last submitted inference (staging copy and chain), ms;
+// waits for it.  0 when none was submitted since the last query.
+float prrtc_internal_proposal_infer_ms(prrtc_proposal* p) {
+  if (!p || !p->inf_timed) return 0.f;
+  p->inf_timed = false;
+  float ms = 0.f;
+  if (cudaEventSynchronize(p->inf_ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, p->inf_ev[0], p->inf_ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
 }
 
 extern "C" {
@@ -620,6 +790,7 @@ int prrtc_proposal_create(int32_t dof, const float* lower, const float* upper, c
     return mlp_fail(PRRTC_ERR_NO_DEVICE, "no CUDA device");
   for (int j = 0; j < dof; ++j)
     if (!(upper[j] > lower[j])) return mlp_fail(PRRTC_ERR_INVALID_ARG, "joint limits must have upper > lower");
+  if (mlp_check_shapes(kHid0, kHid1, kHid2, head_pad(dof))) return mlp_fail(PRRTC_ERR_UNSUPPORTED, "layer widths");
   prrtc_proposal* p = new prrtc_proposal();
   p->device = dev;
   p->dof = dof;
@@ -641,12 +812,14 @@ int prrtc_proposal_create(int32_t dof, const float* lower, const float* upper, c
   }
   bool ok = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreate(&p->inf_ev[0]) == cudaSuccess && cudaEventCreate(&p->inf_ev[1]) == cudaSuccess &&
             cudaMalloc(&p->master, off * 4) == cudaSuccess && cudaMalloc(&p->grad, off * 4) == cudaSuccess &&
             cudaMalloc(&p->m, off * 4) == cudaSuccess && cudaMalloc(&p->v, off * 4) == cudaSuccess &&
             cudaMalloc(&p->d_lims, 2 * kMaxDof * 4) == cudaSuccess;
   for (int l = 0; l < 4 && ok; ++l)
     ok = cudaMalloc(&p->w16[l], (size_t)dims[l + 1] * dims[l] * 2) == cudaSuccess &&
-         cudaMalloc(&p->w16t[l], (size_t)dims[l + 1] * dims[l] * 2) == cudaSuccess;
+         cudaMalloc(&p->w16t[l], (size_t)dims[l + 1] * dims[l] * 2) == cudaSuccess &&
+         (l == 0 || cudaMalloc(&p->wtile[l - 1], (size_t)dims[l + 1] * dims[l] * 2) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
     prrtc_proposal_destroy(p);
@@ -675,13 +848,18 @@ void prrtc_proposal_destroy(prrtc_proposal* p) {
   for (int l = 0; l < 4; ++l) {
     cudaFree(p->w16[l]);
     cudaFree(p->w16t[l]);
+    if (l > 0) cudaFree(p->wtile[l - 1]);
   }
   cudaFree(p->occ); cudaFree(p->qs); cudaFree(p->qg); cudaFree(p->tgt); cudaFree(p->scene_of); cudaFree(p->rows);
   cudaFree(p->envs); cudaFree(p->gmm_rows);
   cudaFree(p->d_stage); cudaFree(p->inf_occ);
+  cudaFree(p->xo16); cudaFree(p->h1o32);
+  for (bf16* t : p->atile) cudaFree(t);
   if (p->h_stage) cudaFreeHost(p->h_stage);
   if (p->infer_exec) cudaGraphExecDestroy(p->infer_exec);
   if (p->done) cudaEventDestroy(p->done);
+  for (cudaEvent_t e : p->inf_ev)
+    if (e) cudaEventDestroy(e);
   if (p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -829,6 +1007,51 @@ int prrtc_occupancy(const prrtc_env* env, uint8_t* out) {
   cudaFree(d);
   cudaFree(dv);
   if (e != cudaSuccess) return mlp_fail(PRRTC_ERR_CUDA, cudaGetErrorString(e));
+  return PRRTC_OK;
+}
+
+int prrtc_proposal_mixtures(prrtc_proposal* p, const prrtc_env* const* envs, const float* q_start,
+                            const float* q_goal, int32_t B, float* out) {
+  cudaGetLastError();
+  if (!p || !envs || !q_start || !q_goal || !out || B < 1) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  const int dof = p->dof;
+  for (size_t i = 0; i < (size_t)B * dof; ++i)
+    if (!std::isfinite(q_start[i]) || !std::isfinite(q_goal[i]))
+      return mlp_fail(PRRTC_ERR_INVALID_ARG, "non-finite start or goal");
+  std::vector<EnvView> views(B);
+  for (int b = 0; b < B; ++b) {
+    if (!envs[b]) return mlp_fail(PRRTC_ERR_INVALID_ARG, "null environment");
+    int dev = -1;
+    int rc = prrtc_internal_env_view(envs[b], &views[b], &dev);
+    if (rc) return rc;
+    if (dev != p->device) return mlp_fail(PRRTC_ERR_INVALID_ARG, "environment on another device");
+  }
+  float* d = nullptr;
+  MCK(cudaMalloc(&d, (size_t)B * kGmmStride * sizeof(float)));
+  std::vector<float*> rows(B);
+  for (int b = 0; b < B; ++b) rows[b] = d + (size_t)b * kGmmStride;
+  int rc = prrtc_internal_proposal_mixtures(p, views.data(), q_start, q_goal, B, rows.data(), p->stream);
+  std::vector<float> padded((size_t)B * kGmmStride);
+  cudaError_t e = cudaSuccess;
+  if (!rc) e = cudaMemcpyAsync(padded.data(), d, padded.size() * sizeof(float), cudaMemcpyDeviceToHost, p->stream);
+  if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  cudaFree(d);
+  if (rc) return rc;
+  if (e != cudaSuccess) return mlp_fail(PRRTC_ERR_CUDA, cudaGetErrorString(e));
+  if ((rc = check_gemm_error())) return rc;
+  // the planner's padded rows -> [logits | means (8 x dof) | log-sigmas (8 x dof)]
+  const int stride = kK + 2 * kK * dof;
+  for (int b = 0; b < B; ++b) {
+    const float* g = padded.data() + (size_t)b * kGmmStride;
+    float* o = out + (size_t)b * stride;
+    for (int k = 0; k < kK; ++k) {
+      o[k] = g[k];
+      for (int j = 0; j < dof; ++j) {
+        o[kK + k * dof + j] = g[kK + k * kMaxDof + j];
+        o[kK + kK * dof + k * dof + j] = g[kK + kK * kMaxDof + k * kMaxDof + j];
+      }
+    }
+  }
   return PRRTC_OK;
 }
 

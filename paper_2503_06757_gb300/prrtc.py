@@ -68,7 +68,7 @@ class prrtc_launch_stats(C.Structure):
                 ("smem_bytes", C.c_int32), ("problems", C.c_int32), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("reserved_", C.c_int32),
                 ("prep_ms", C.c_double), ("prim_tests", C.c_int64 * 4), ("dd_rejected", C.c_int64),
-                ("verdict_states", C.c_int64)]
+                ("verdict_states", C.c_int64), ("infer_ms", C.c_double)]
 
 
 class prrtc_server_config(C.Structure):
@@ -97,7 +97,7 @@ EXPORTS = [
     "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_bf16_splitk", "prrtc_gemm_error",
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
     "prrtc_proposal_forward", "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
-    "prrtc_proposal_load", "prrtc_occupancy", "prrtc_plan_batch_learned",
+    "prrtc_proposal_load", "prrtc_occupancy", "prrtc_proposal_mixtures", "prrtc_plan_batch_learned",
     "prrtc_server_config_default", "prrtc_server_create", "prrtc_server_submit", "prrtc_server_poll",
     "prrtc_server_wait", "prrtc_server_get_stats", "prrtc_server_destroy", "prrtc_autotune",
 ]
@@ -163,6 +163,7 @@ def lib():
     L.prrtc_proposal_save.argtypes = [C.c_void_p, C.c_char_p]
     L.prrtc_proposal_load.argtypes = [C.c_char_p, C.POINTER(C.c_void_p)]
     L.prrtc_occupancy.argtypes = [C.c_void_p, _u8]
+    L.prrtc_proposal_mixtures.argtypes = [C.c_void_p, C.POINTER(C.c_void_p), _f, _f, C.c_int32, _f]
     L.prrtc_plan_batch_learned.argtypes = [C.POINTER(prrtc_problem), C.POINTER(C.c_void_p), C.c_int32,
                                            C.POINTER(prrtc_params), C.POINTER(prrtc_path), _i]
     L.prrtc_server_config_default.argtypes = [C.POINTER(prrtc_server_config)]
@@ -560,6 +561,18 @@ class Proposal:
                                               sp, gp, tp, N, int(batch), int(steps), float(lr), int(seed),
                                               losses.ctypes.data_as(_f)), "prrtc_proposal_train")
         return losses[:steps]
+
+    def mixtures(self, envs, q_start, q_goal):
+        """Mixtures the learned planner samples from, one row of 8 + 16 dof
+        floats per (env, start, goal) triple (prrtc_proposal_mixtures)."""
+        B = len(envs)
+        s, sp = _fa(np.asarray(q_start).reshape(B, self.dof))
+        g, gp = _fa(np.asarray(q_goal).reshape(B, self.dof))
+        eh = (C.c_void_p * B)(*[e.handle for e in envs])
+        out = np.zeros((B, 8 + 16 * self.dof), np.float32)
+        _check(self._lib.prrtc_proposal_mixtures(self.handle, eh, sp, gp, B, out.ctypes.data_as(_f)),
+               "prrtc_proposal_mixtures")
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

@@ -236,6 +236,36 @@ def dual14() -> Robot:
 ROBOTS = {"arm7": arm7, "arm8": arm8, "dual14": dual14}
 
 
+def point2(lo=0.0, hi=1.2, z0=0.5, radius=0.02) -> Robot:
+    """2-DoF point robot: prismatic x then prismatic y at height z0, one sphere."""
+    return Robot(name="point2", dof=2, joint_type=np.asarray([JOINT_PRISM_X, JOINT_PRISM_Y], np.int32),
+                 joint_parent=np.asarray([-1, 0], np.int32),
+                 joint_base=_f32(np.asarray([[0.0, 0.0, z0], [0.0, 0.0, 0.0]])), link_length=_f32([0.0, 0.0]),
+                 lower=_f32([lo, lo]), upper=_f32([hi, hi]), sphere_frame=np.asarray([1], np.int32),
+                 sphere_offset=_f32(np.zeros((1, 3))), sphere_radius=_f32([radius]),
+                 sphere_link=np.asarray([1], np.int32), self_pairs=np.zeros((0, 2), np.int32), ee_frames=[1])
+
+
+def scene_two_rooms(z0=0.5, door=(0.85, 0.93)) -> "Scene":
+    """Two rooms of the point robot's plane joined by a narrow door: a wall at
+    x in [0.58, 0.62] with an opening for y in door (8 cm by default; the
+    point robot's 2 cm sphere leaves its centre 4 cm)."""
+    eye = np.eye(3).reshape(9)
+    y0, y1 = door
+    below = np.concatenate([[0.60, y0 / 2, z0], [0.02, y0 / 2, 0.3], eye])
+    above = np.concatenate([[0.60, (y1 + 1.2) / 2, z0], [0.02, (1.2 - y1) / 2, 0.3], eye])
+    return Scene(boxes=_f32(np.stack([below, above])), cylinders=np.zeros((0, 8)), spheres=np.zeros((0, 4)))
+
+
+def two_rooms_pairs(n: int, seed: int):
+    """Start in the left room, goal in the right room."""
+    st = Stream(seed, 1)
+    u = st.uniform(4 * n).reshape(n, 4)
+    s = np.stack([0.05 + 0.45 * u[:, 0], 0.05 + 1.1 * u[:, 1]], 1)
+    g = np.stack([0.70 + 0.45 * u[:, 2], 0.05 + 1.1 * u[:, 3]], 1)
+    return _f32(s), _f32(g)
+
+
 def robot_bases(robot: Robot) -> np.ndarray:
     """World positions of the chain roots (used for the base keep-out rule)."""
     return robot.joint_base[robot.joint_parent < 0]

@@ -11,7 +11,6 @@ import pytest
 from paper_2503_06757_gb300 import learned as L
 from paper_2503_06757_gb300 import prrtc as P
 from paper_2503_06757_gb300 import workload as W
-from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -23,19 +22,11 @@ def _built():
 
 
 def two_rooms():
-    rb = H.point_robot(z0=0.5, radius=0.02, lo=0.0, hi=1.2)
-    # wall x in [0.58, 0.62] with a door y in [0.85, 0.93]
-    below = H.aabb([0.60, 0.425, 0.5], [0.02, 0.425, 0.3])
-    above = H.aabb([0.60, 1.065, 0.5], [0.02, 0.135, 0.3])
-    return rb, H.scene(boxes=[below, above])
+    return W.point2(), W.scene_two_rooms()
 
 
 def pairs(n, seed):
-    st = W.Stream(seed, 1)
-    u = st.uniform(4 * n).reshape(n, 4)
-    s = np.stack([0.05 + 0.45 * u[:, 0], 0.05 + 1.1 * u[:, 1]], 1)
-    g = np.stack([0.70 + 0.45 * u[:, 2], 0.05 + 1.1 * u[:, 3]], 1)
-    return s.astype(np.float32), g.astype(np.float32)
+    return W.two_rooms_pairs(n, seed)
 
 
 def test_trained_proposal_needs_fewer_iterations_through_a_door():

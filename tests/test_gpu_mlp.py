@@ -215,3 +215,34 @@ def test_learned_inference_replay_is_exact(c1_problems):
         for a, b in zip(runs[0], r):
             assert a["status"] == b["status"] and a["iterations"] == b["iterations"]
             np.testing.assert_array_equal(a["path"], b["path"])
+
+
+@pytest.mark.parametrize("distinct,B", [(False, 24), (True, 24), (True, 40), (False, 300)])
+def test_planner_mixtures_match_oracle(distinct, B):
+    """The mixtures the learned planner samples from, read back.  The occupancy part
+    of the first layer is computed once per distinct environment (a GEMV for up to 32
+    environments, the tensor-core GEMM beyond), the rest of the network in one fused
+    launch per 128-row tile (300 rows: three tiles, the last ragged)."""
+    rb = W.arm7()
+    params = init(rb.dof, 18)
+    prop = P.Proposal(rb.dof, rb.lower, rb.upper, flat(params))
+    n_sc = B if distinct else 3
+    scenes = [W.scene_shelf(1000 + k) for k in range(n_sc)]
+    made = [P.make_env(sc) for sc in scenes]
+    envs = [made[k % n_sc] for k in range(B)]
+    st = W.Stream(19, 3)
+    u = st.uniform(2 * B * rb.dof).reshape(2, B, rb.dof)
+    qs, qg = ((rb.lower + u[i] * (rb.upper - rb.lower)).astype(np.float32) for i in range(2))
+    got = prop.mixtures(envs, qs, qg)
+    occ = np.stack([O.occupancy(scenes[k % n_sc]) for k in range(B)])
+    out, _ = M.forward(params, oracle_x(rb, occ, qs, qg))
+    logits, mean, raw = M.split_head(out, rb.dof)
+    want = np.concatenate([logits, mean.reshape(B, -1), np.clip(raw, M.LOGSIG_MIN, M.LOGSIG_MAX).reshape(B, -1)],
+                          axis=1)
+    assert got.shape == want.shape
+    assert rel(got, want) <= FWD_TOL, rel(got, want)
+    worst = max(rel(got[b], want[b]) for b in range(B))
+    assert worst <= 2 * FWD_TOL, worst
+    # the second call is captured, the third replays the capture: identical output
+    np.testing.assert_array_equal(prop.mixtures(envs, qs, qg), got)
+    np.testing.assert_array_equal(prop.mixtures(envs, qs, qg), got)
