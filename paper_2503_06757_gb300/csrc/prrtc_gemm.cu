@@ -458,8 +458,13 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, i
 //            mixture parameters written into the planner's rows.
 // Operands live in global memory pre-tiled: one 64-column k-block of 128
 // activation rows, or of this CTA's weight rows, is one contiguous block in
-// the 128-byte-swizzled layout the MMA reads, so each pipeline stage is two
-// plain bulk copies.  Each layer's writer produces exactly the k-blocks of
+// the 128-byte-swizzled layout the MMA reads.  The activation tile is the
+// same for every CTA of the cluster (they all sit in one GPC, whose link to
+// L2 they share), so each CTA fetches one eighth of it with a multicast bulk
+// copy into all eight CTAs, and its own weight slice with a plain one.  A
+// stage is refilled only when the MMAs of all eight CTAs have released it
+// (their commits arrive on every CTA's `empty` barrier), and a CTA leaves
+// only after the last of those arrivals and a cluster barrier.  Each layer's writer produces exactly the k-blocks of
 // the next layer's input that its columns cover.  Between layers every thread
 // of the cluster makes its global writes visible to the async proxy (the next
 // layer's bulk copies) and meets the cluster barrier; the barriers sit
@@ -467,15 +472,17 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, i
 // bounded mbarrier wait has given up.
 constexpr int kIC = 8;
 constexpr int kIThreads = 192;
-constexpr int kIStages = 6;
+constexpr int kIStages = 4;
+constexpr int kIKB = 2;      // 64-column k-blocks per pipeline stage
 constexpr int kIBRows = 64;  // most weight rows one CTA takes per layer
-constexpr int kIStageBytes = A_BYTES + kIBRows * BK * 2;
+constexpr int kIStageBytes = kIKB * (A_BYTES + kIBRows * BK * 2);  // A tiles, then B tiles
 constexpr int kIQMax = 32;   // start + goal inputs
 constexpr int kIL0Cols = 128;
 constexpr int kIBiasMax = kIL0Cols + 3 * kIBRows;  // this CTA's bias slices of all four layers
-// ring | barriers | layer-1 scratch (inputs, weights, bias, env rows), plus alignment
-constexpr int kISmemBytes =
-    kIStages * kIStageBytes + 1024 + (BM * kIQMax + kIQMax * kIL0Cols + kIBiasMax) * 4 + BM * 4 + 1024;
+// ring (whose first bytes hold layer 1's inputs and weights until the ring's
+// first use) | barriers | bias slices and env rows, plus alignment
+constexpr int kISmemBytes = kIStages * kIStageBytes + 1024 + kIBiasMax * 4 + BM * 4 + 1024;
+static_assert((BM * kIQMax + kIQMax * kIL0Cols) * 4 <= kIStages * kIStageBytes, "layer-1 scratch fits the ring");
 constexpr uint32_t kITmemCols = 256;
 
 // Byte offset of element (i, c) inside one k-block tile (rows of 64 BF16 =
@@ -492,6 +499,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Bulk copy global -> shared memory of every CTA in `mask` (same offset in
+// each), completing on the barrier at the same offset in each.
+__device__ __forceinline__ void bulk_g2s_multicast(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                   uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+// Arrive on the barrier at this offset in every CTA of `mask` once the MMAs
+// issued so far have completed.
+__device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(smem_u32(bar)),
+               "h"(mask)
+               : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // Global writes of this thread -> visible to the cluster's async-proxy reads
@@ -531,9 +563,9 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
   uint64_t* acc_full = empty + kIStages;  // [3] MMA -> epilogue, once per layer
   uint64_t* roles_done = acc_full + 3;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(roles_done + 1);
-  float* s_x = reinterpret_cast<float*>(smem + kIStages * kIStageBytes + 1024);  // [BM][kIQMax]
-  float* s_w = s_x + BM * kIQMax;                                               // [kIQMax][kIL0Cols]
-  float* s_b = s_w + kIQMax * kIL0Cols;                                         // [kIBiasMax] bias slices
+  float* s_x = reinterpret_cast<float*>(smem);                                  // [BM][kIQMax], layer 1 only
+  float* s_w = s_x + BM * kIQMax;                                               // [kIQMax][kIL0Cols], layer 1 only
+  float* s_b = reinterpret_cast<float*>(smem + kIStages * kIStageBytes + 1024);  // [kIBiasMax] bias slices
   int* s_e = reinterpret_cast<int*>(s_b + kIBiasMax);                           // [BM]
   __shared__ int s_abort;
 
@@ -549,7 +581,7 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < kIStages; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], kIC);  // one MMA commit from every CTA of the cluster
     }
     for (int l = 0; l < 3; ++l) mbar_init(&acc_full[l], 1);
     mbar_init(roles_done, kIThreads / 32);
@@ -637,18 +669,21 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
     }
   }
   __syncwarp();
+  // the ring held layer 1's scratch: order these generic accesses before the
+  // bulk copies (ours and the peers') that will overwrite it
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   cluster_publish();
 
   // ---- layers 2, 3 and the head on the tensor cores
   int it_p = 0, it_m = 0;  // stage counters of the producer and the MMA issuer
   uint32_t tcol = 0;       // TMEM column of this layer's accumulator
   for (int l = 0; l < 3; ++l) {
-    const int nc = n_out[l] / kIC, n0 = r * nc, kts = k_in[l] / BK;
+    const int nc = n_out[l] / kIC, n0 = r * nc, kts = k_in[l] / BK, stages = kts / kIKB;
     if (warp == 0) {
       const uint32_t b_bytes = (uint32_t)(nc * BK * 2);
       const unsigned char* a_src = static_cast<const unsigned char*>(args.act[l]) + (size_t)mt * kts * (BM * 128);
       const unsigned char* b_src = static_cast<const unsigned char*>(args.w[l]) + (size_t)r * kts * b_bytes;
-      for (int kt = 0; kt < kts; ++kt, ++it_p) {
+      for (int ks = 0; ks < stages; ++ks, ++it_p) {
         const int st = it_p % kIStages;
         const uint32_t ph = (uint32_t)(it_p / kIStages) & 1u;
         int got = 0;
@@ -660,16 +695,23 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
         }
         if (lane == 0) {
           unsigned char* a = smem + st * kIStageBytes;
-          mbar_arrive_expect_tx(&full[st], (uint32_t)A_BYTES + b_bytes);
-          bulk_g2s(a, a_src + (size_t)kt * (BM * 128), (uint32_t)A_BYTES, &full[st]);
-          bulk_g2s(a + A_BYTES, b_src + (size_t)kt * b_bytes, b_bytes, &full[st]);
+          mbar_arrive_expect_tx(&full[st], (uint32_t)(kIKB * (A_BYTES + b_bytes)));
+          // rows 16 r .. 16 r + 15 of each activation tile to every CTA; the
+          // other seven eighths arrive from the peers
+          constexpr uint32_t kPiece = A_BYTES / kIC;
+          for (int j = 0; j < kIKB; ++j)
+            bulk_g2s_multicast(a + j * A_BYTES + r * kPiece,
+                               a_src + (size_t)(ks * kIKB + j) * (BM * 128) + r * kPiece, kPiece, &full[st],
+                               (uint16_t)((1u << kIC) - 1u));
+          bulk_g2s(a + kIKB * A_BYTES, b_src + (size_t)ks * kIKB * b_bytes, kIKB * b_bytes, &full[st]);
         }
         __syncwarp();
       }
     } else if (warp == 1) {
       const uint32_t idesc = idesc_bf16(BM, nc);
+      const uint32_t b_bytes = (uint32_t)(nc * BK * 2);
       bool ok = true;
-      for (int kt = 0; kt < kts; ++kt, ++it_m) {
+      for (int ks = 0; ks < stages; ++ks, ++it_m) {
         const int st = it_m % kIStages;
         const uint32_t ph = (uint32_t)(it_m / kIStages) & 1u;
         int got = 0;
@@ -683,11 +725,14 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
         fence_after();
         if (lane == 0) {
           const uint32_t a = smem_u32(smem + st * kIStageBytes);
-          const uint32_t b = a + A_BYTES;
+          const uint32_t b = a + kIKB * A_BYTES;
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            mma_bf16(tmem + tcol, smem_desc(a + 32u * k), smem_desc(b + 32u * k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
-          mma_commit(&empty[st]);
+          for (int j = 0; j < kIKB; ++j)
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+              mma_bf16(tmem + tcol, smem_desc(a + j * A_BYTES + 32u * k), smem_desc(b + j * b_bytes + 32u * k), idesc,
+                       (ks > 0 || j > 0 || k > 0) ? 1u : 0u);
+          mma_commit_multicast(&empty[st], (uint16_t)((1u << kIC) - 1u));
         }
         __syncwarp();
       }
@@ -765,6 +810,18 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
       fence_after();
     }
   }
+  // drain: the last release of every stage from all eight CTAs has arrived
+  // here, so no peer writes into this CTA's shared memory any more
+  if (warp == 0) {
+    if (lane == 0) {  // bounded waits, also after an abort
+      for (int st = 0; st < kIStages && st < it_p; ++st) {
+        const int uses = (it_p - 1 - st) / kIStages + 1;
+        if (!wait_bar(&empty[st], (uint32_t)(uses - 1) & 1u)) break;
+      }
+    }
+    __syncwarp();
+  }
+  cluster_sync_all();
   // join, then the allocating warp frees tensor memory (as in the GEMM)
   __syncwarp();
   fence_before();
@@ -970,7 +1027,7 @@ int gemm_bf16(const void* a, const void* b, int M, int N, int K, const float* bi
 }
 
 int mlp_check_shapes(int h0, int h1, int h2, int head) {
-  if (h0 != kIC * kIL0Cols || h1 % BK || h2 % BK) return PRRTC_ERR_UNSUPPORTED;
+  if (h0 != kIC * kIL0Cols || h1 % (BK * kIKB) || h2 % (BK * kIKB) || h0 % (BK * kIKB)) return PRRTC_ERR_UNSUPPORTED;
   const int n_out[3] = {h1, h2, head};
   int cols = 0;
   for (int l = 0; l < 3; ++l) {
