@@ -318,48 +318,22 @@ def door_section(P, door, keys=(1, 2, 3)):
     h, ev = P.make_robot(rb), P.make_env(sc)
     base = dict(range=0.2, resolution=0.01, max_iters=20000, tree_capacity=1 << 14, path_capacity=1 << 12)
     s, g = W.two_rooms_pairs(256, 11)
-    res = P.prrtc_plan_batch([(h, ev, s[k], g[k], 3, k) for k in range(len(s))],
-                             P.params(mode=P.MODE_SERIAL, **base))
-    qs, qg, tg = [], [], []
-    for k, r in enumerate(res):
-        if r["status"] == P.SOLVED:
-            wp = L.waypoints(r["path"].astype(np.float64), spacing=0.05)
-            qs += [s[k]] * len(wp)
-            qg += [g[k]] * len(wp)
-            tg += list(wp)
-    init = W.proposal_init(2, 7)
-    prop = P.Proposal(2, rb.lower, rb.upper,
-                      np.concatenate([np.concatenate([Wm.ravel(), b]) for Wm, b in init]).astype(np.float32))
-    losses = prop.train(P.prrtc_occupancy(ev)[None, :], np.zeros(len(tg), np.int32), np.array(qs, np.float32),
-                        np.array(qg, np.float32), np.array(tg, np.float32), batch=256, steps=1500, lr=1e-3, seed=1)
+    prop, samples, losses = L.train_on_plain_solutions(rb, h, ev, s, g, P.params(mode=P.MODE_SERIAL, **base),
+                                                        steps=1500)
     s2, g2 = W.two_rooms_pairs(200, 12)
     width = door[1] - door[0]
     out = dict(workload=f"point robot (2 cm sphere), two rooms joined by a {100 * width:.0f} cm door "
                         f"({100 * (width - 0.04):.0f} cm free for the centre); 256 training, 200 held-out pairs, "
                         f"keys {keys[0]}..{keys[-1]}",
-               train=dict(samples=len(tg), loss_first=float(losses[:10].mean()), loss_last=float(losses[-10:].mean())))
+               train=dict(samples=samples, loss_first=float(losses[:10].mean()), loss_last=float(losses[-10:].mean())))
     for name in ("plain", "learned"):
         for mode_name, mode in (("async", P.MODE_ASYNC), ("serial", P.MODE_SERIAL)):
             prm = P.params(mode=mode, learned_ratio=0.5 if name == "learned" else 0.0, **base)
-            call = (lambda its: P.prrtc_plan_batch_learned(its, [prop] * len(its), prm)) if name == "learned" \
-                else (lambda its: P.prrtc_plan_batch(its, prm))
-            for _ in range(2):  # warm-up: graphs captured
-                call([(h, ev, s2[k], g2[k], 97, k) for k in range(len(s2))])
-            ttfs, iters, ok, prep, infer = [], [], 0, [], []
-            for key in keys:
-                rs = call([(h, ev, s2[k], g2[k], key, k) for k in range(len(s2))])
-                st = P.prrtc_last_launch_stats()
-                prep.append(st["prep_ms"] * 1e3)
-                infer.append(st["infer_ms"] * 1e3)
-                for r in rs:
-                    iters.append(r["iterations"])
-                    if r["status"] == P.SOLVED:
-                        ok += 1
-                        ttfs.append(r["solve_time_us"] + 1e3 * (st["prep_ms"] + st["setup_ms"]))
-            out[f"{name}_{mode_name}"] = dict(success_rate=ok / (len(s2) * len(keys)),
-                                              iterations_mean=float(np.mean(iters)),
-                                              ttfs_us=percentiles(ttfs, (50, 95)) if mode == P.MODE_ASYNC else None,
-                                              prep_us_mean=float(np.mean(prep)), infer_us_mean=float(np.mean(infer)))
+            m = L.batched_ttfs(h, ev, s2, g2, prm, prop if name == "learned" else None, keys=keys)
+            out[f"{name}_{mode_name}"] = dict(success_rate=m["success_rate"], iterations_mean=m["iterations_mean"],
+                                              ttfs_us=percentiles(m["ttfs_us"], (50, 95)) if mode == P.MODE_ASYNC
+                                              else None,
+                                              prep_us_mean=m["prep_us_mean"], infer_us_mean=m["infer_us_mean"])
     return out
 
 

@@ -191,3 +191,58 @@ def evaluate(robot: W.Robot, n_scenes: int, pairs_per_scene: int, seed0: int, pr
                          prep_ms=prep_ms / len(keys),
                          problems=len(items), keys=len(keys))
     return out
+
+
+def train_on_plain_solutions(robot: W.Robot, rb: P.Robot, ev: P.Env, starts: np.ndarray, goals: np.ndarray,
+                             params: P.prrtc_params, steps: int, batch: int = 256, lr: float = 1e-3,
+                             init_seed: int = 7, seed: int = 1, key: int = 3):
+    """A proposal for one environment trained on the plain planner's solutions of
+    (starts[k], goals[k]) -- waypoints of each solution path as targets, the pair as
+    input.  Returns (proposal, training samples, losses)."""
+    res = P.prrtc_plan_batch([(rb, ev, starts[k], goals[k], key, k) for k in range(len(starts))], params)
+    qs, qg, tg = [], [], []
+    for k, r in enumerate(res):
+        if r["status"] != P.SOLVED:
+            continue
+        wp = waypoints(r["path"].astype(np.float64), spacing=0.05)
+        qs += [starts[k]] * len(wp)
+        qg += [goals[k]] * len(wp)
+        tg += list(wp)
+    init = W.proposal_init(robot.dof, init_seed)
+    prop = P.Proposal(robot.dof, robot.lower, robot.upper,
+                      np.concatenate([np.concatenate([Wm.ravel(), b]) for Wm, b in init]).astype(np.float32))
+    losses = prop.train(P.prrtc_occupancy(ev)[None, :], np.zeros(len(tg), np.int32), np.array(qs, np.float32),
+                        np.array(qg, np.float32), np.array(tg, np.float32), batch=batch, steps=steps, lr=lr,
+                        seed=seed)
+    return prop, len(tg), losses
+
+
+def batched_ttfs(rb: P.Robot, ev: P.Env, starts: np.ndarray, goals: np.ndarray, params: P.prrtc_params,
+                 proposal: P.Proposal | None, keys=(1, 2, 3), warmup: int = 2):
+    """Plan every pair in one batched call per key (plain when proposal is None,
+    else with the learned proposal) and return per-problem TTFS in microseconds
+    (device prep, which includes the inference, + setup + the problem's solve
+    time), success rate, mean iterations, and the mean prep and inference
+    times."""
+    def call(key):
+        items = [(rb, ev, starts[k], goals[k], key, k) for k in range(len(starts))]
+        if proposal is None:
+            return P.prrtc_plan_batch(items, params)
+        return P.prrtc_plan_batch_learned(items, [proposal] * len(items), params)
+
+    for _ in range(warmup):
+        call(97)
+    ttfs, iters, ok, prep, infer = [], [], 0, [], []
+    for key in keys:
+        rs = call(key)
+        st = P.prrtc_last_launch_stats()
+        prep.append(st["prep_ms"] * 1e3)
+        infer.append(st["infer_ms"] * 1e3)
+        for r in rs:
+            iters.append(r["iterations"])
+            if r["status"] == P.SOLVED:
+                ok += 1
+                ttfs.append(r["solve_time_us"] + 1e3 * (st["prep_ms"] + st["setup_ms"]))
+    return dict(ttfs_us=np.array(ttfs), success_rate=ok / (len(starts) * len(keys)),
+                iterations_mean=float(np.mean(iters)), prep_us_mean=float(np.mean(prep)),
+                infer_us_mean=float(np.mean(infer)))
