@@ -430,34 +430,132 @@ def prrtc_plan(robot: Robot, env: Env, q_start, q_goal, prm: prrtc_params | None
         lib().prrtc_path_free(C.byref(out))
 
 
+def _numpy_dtype(cls):
+    """numpy structured dtype with the layout of a ctypes Structure (pointers as
+    uint64), so that arrays of it can be filled and read column-wise."""
+    def np_type(t):
+        if issubclass(t, C.Array):
+            return (np_type(t._type_), (t._length_,))
+        if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+            return np.uint64
+        return np.dtype(t)
+    names = [n for n, _ in cls._fields_]
+    return np.dtype(dict(names=names, formats=[np_type(t) for _, t in cls._fields_],
+                         offsets=[getattr(cls, n).offset for n in names], itemsize=C.sizeof(cls)))
+
+
+_PROBLEM_DT = _numpy_dtype(prrtc_problem)
+_PATH_DT = _numpy_dtype(prrtc_path)
+_PATH_FIELDS = [n for n, _ in prrtc_path._fields_ if n != "q"]
+
+
+def _handle(x):
+    h = x.handle
+    return h.value if isinstance(h, C.c_void_p) else int(h)
+
+
 def _problem_array(problems, keep):
+    """The C problem array for a sequence of (Robot, Env, q_start, q_goal, seed,
+    problem_id[, gmm]), filled column-wise; `keep` holds what it points into."""
     n = len(problems)
-    arr = (prrtc_problem * n)()
-    for k, item in enumerate(problems):
-        rb, ev, qs, qg, seed, pid = item[:6]
-        gmm = item[6] if len(item) > 6 else None
-        s, sp = _fa(qs)
-        g, gp = _fa(qg)
-        keep += [s, g]
-        arr[k].robot = rb.handle
-        arr[k].env = ev.handle
-        arr[k].q_start = sp
-        arr[k].q_goal = gp
-        arr[k].seed = int(seed)
-        arr[k].problem_id = int(pid)
-        if gmm is not None:
-            m, mp = _fa(gmm)
+    v = np.zeros(n, _PROBLEM_DT)
+    qs = [np.ascontiguousarray(it[2], np.float32).ravel() for it in problems]
+    qg = [np.ascontiguousarray(it[3], np.float32).ravel() for it in problems]
+    lens = np.fromiter((len(q) for q in qs), np.int64, n)
+    flat = np.concatenate(qs + qg) if n else np.zeros(0, np.float32)
+    keep.append(flat)
+    base = flat.ctypes.data
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]]) if n else np.zeros(0, np.int64)
+    v["q_start"] = base + 4 * off
+    v["q_goal"] = base + 4 * (off + int(lens.sum()))
+    v["robot"] = np.fromiter((_handle(it[0]) for it in problems), np.uint64, n)
+    v["env"] = np.fromiter((_handle(it[1]) for it in problems), np.uint64, n)
+    v["seed"] = np.fromiter((int(it[4]) for it in problems), np.uint64, n)
+    v["problem_id"] = np.fromiter((int(it[5]) for it in problems), np.uint32, n)
+    for k, it in enumerate(problems):
+        if len(it) > 6 and it[6] is not None:
+            m = np.ascontiguousarray(it[6], np.float32)
             keep.append(m)
-            arr[k].gmm = mp
-    return arr
+            v["gmm"][k] = m.ctypes.data
+    keep.append(v)
+    return v.ctypes.data_as(C.POINTER(prrtc_problem))
 
 
 def _collect(paths, n):
+    """Per-problem result dicts (and path arrays); frees the C paths."""
+    v = np.frombuffer((C.c_char * (n * C.sizeof(prrtc_path))).from_address(C.addressof(paths)), _PATH_DT, n)
+    rows = v[_PATH_FIELDS].tolist()
     out = []
+    free = lib().prrtc_path_free
     for k in range(n):
-        out.append(_path_dict(paths[k]))
-        lib().prrtc_path_free(C.byref(paths[k]))
+        d = dict(zip(_PATH_FIELDS, rows[k]))
+        d["prim_tests"] = list(d["prim_tests"])
+        p = paths[k]
+        if p.q and p.n > 0:
+            d["path"] = np.ctypeslib.as_array(p.q, shape=(p.n * p.dof,)).reshape(p.n, p.dof).copy()
+        else:
+            d["path"] = np.zeros((0, p.dof), np.float32)
+        out.append(d)
+        free(C.byref(p))
     return out
+
+
+class PlanBatch:
+    """A batch of planning problems marshalled once and planned many times
+    (prrtc_plan_batch / prrtc_plan_batch_learned).  run() returns a BatchResult
+    whose per-problem scalars are numpy columns; paths are read from the C
+    buffers on first access."""
+
+    def __init__(self, problems, proposals=None):
+        self._keep = []
+        self.n = len(problems)
+        self._arr = _problem_array(problems, self._keep)
+        self._view = self._keep[-1]
+        self._props = None
+        if proposals is not None:
+            self._props = (C.c_void_p * self.n)(*[(pp.handle.value if pp is not None else None) for pp in proposals])
+
+    def set_seeds(self, seeds):
+        self._view["seed"] = np.asarray(seeds, np.uint64)
+
+    def run(self, prm: prrtc_params | None = None):
+        prm = prm or prrtc_params_default()
+        paths = (prrtc_path * self.n)()
+        status = (C.c_int32 * self.n)()
+        if self._props is None:
+            rc = lib().prrtc_plan_batch(self._arr, self.n, C.byref(prm), paths, status)
+        else:
+            rc = lib().prrtc_plan_batch_learned(self._arr, self._props, self.n, C.byref(prm), paths, status)
+        _check(rc, "prrtc_plan_batch")
+        return BatchResult(paths, self.n)
+
+
+class BatchResult:
+    """Results of one PlanBatch.run: numpy columns named as prrtc_path's fields
+    (result["status"], result["edge_states"], ...), paths(k) for problem k."""
+
+    def __init__(self, paths, n):
+        self._paths = paths
+        self.n = n
+        self._v = np.frombuffer((C.c_char * (n * C.sizeof(prrtc_path))).from_address(C.addressof(paths)), _PATH_DT,
+                                n).copy()
+
+    def __getitem__(self, name):
+        return self._v[name]
+
+    def path(self, k):
+        p = self._paths[k]
+        if not p.q or p.n <= 0:
+            return np.zeros((0, p.dof), np.float32)
+        return np.ctypeslib.as_array(p.q, shape=(p.n * p.dof,)).reshape(p.n, p.dof).copy()
+
+    def __del__(self):
+        try:
+            free = lib().prrtc_path_free
+            for k in range(self.n):
+                free(C.byref(self._paths[k]))
+        except Exception:
+            pass
 
 
 def prrtc_plan_batch(problems, prm: prrtc_params | None = None):
@@ -469,6 +567,7 @@ def prrtc_plan_batch(problems, prm: prrtc_params | None = None):
     paths = (prrtc_path * n)()
     status = (C.c_int32 * n)()
     _check(lib().prrtc_plan_batch(arr, n, C.byref(prm), paths, status), "prrtc_plan_batch")
+    del keep
     return _collect(paths, n)
 
 

@@ -96,3 +96,33 @@ def test_params_default(lib):
 def test_status_strings(lib):
     for code in (0, 1, 2, 3, 4, 5, -1, -2, -3, -4, -5, -6, -7):
         assert P.status_string(code) != "unknown status"
+
+
+def test_numpy_views_match_the_ctypes_structs():
+    """The column-wise views used to marshal batches have the C layout."""
+    for cls, dt in ((P.prrtc_problem, P._PROBLEM_DT), (P.prrtc_path, P._PATH_DT)):
+        assert dt.itemsize == C.sizeof(cls)
+        for name, _ in cls._fields_:
+            assert dt.fields[name][1] == getattr(cls, name).offset, (cls.__name__, name)
+
+
+def test_problem_array_points_at_each_problems_data():
+    import numpy as np
+
+    class Handle:
+        def __init__(self, v):
+            self.handle = C.c_void_p(v)
+
+    items = [(Handle(100 + k), Handle(200 + k), np.arange(d, dtype=np.float32) + k,
+              -np.arange(d, dtype=np.float32) - k, 7 * k, k) for k, d in enumerate((7, 8, 14, 7))]
+    items.append(items[0][:6] + (np.full(8 + 16 * 7, 0.5, np.float32),))
+    keep = []
+    arr = P._problem_array(items, keep)
+    for k, it in enumerate(items):
+        pb = arr[k]
+        d = len(it[2])
+        assert pb.robot == 100 + (k % 4) and pb.env == 200 + (k % 4)
+        assert pb.seed == it[4] and pb.problem_id == it[5]
+        np.testing.assert_array_equal(np.ctypeslib.as_array(pb.q_start, shape=(d,)), it[2])
+        np.testing.assert_array_equal(np.ctypeslib.as_array(pb.q_goal, shape=(d,)), it[3])
+        assert bool(pb.gmm) == (len(it) > 6)

@@ -108,6 +108,25 @@ def test_serial_batch_equals_serial_alone(c1_problems):
         assert alone["iterations"] == batch[k]["iterations"]
 
 
+def test_plan_batch_object_equals_list_call(c1_problems):
+    """PlanBatch (marshalled once, run many times, results as columns) returns what
+    prrtc_plan_batch returns, run after run (serial mode: bitwise)."""
+    probs = [(P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 5, k)
+             for k, pb in enumerate(c1_problems)]
+    prm = P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14)
+    ref = P.prrtc_plan_batch(probs, prm)
+    batch = P.PlanBatch(probs)
+    for _ in range(2):
+        out = batch.run(prm)
+        for k, r in enumerate(ref):
+            for name in ("status", "iterations", "cost", "nodes_a", "nodes_b", "edge_states", "verdict_states"):
+                assert out[name][k] == r[name], (k, name)
+            np.testing.assert_array_equal(out.path(k), r["path"])
+    batch.set_seeds([6] * len(probs))
+    other = batch.run(prm)
+    assert any(other["iterations"][k] != ref[k]["iterations"] for k in range(len(probs)))
+
+
 # ------------------------------------------------------------------ async mode
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
