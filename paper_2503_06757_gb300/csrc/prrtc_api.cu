@@ -1286,7 +1286,7 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
     if (n == 1) resident = c->sms * 4;
   }
   std::vector<std::pair<int, int>> cands;
-  const int warp_opts[3] = {2, 4, 8};
+  const int warp_opts[5] = {2, 3, 4, 6, 8};
   for (int w : warp_opts) {
     if (params->mode == PRRTC_MODE_SERIAL && w != 1) continue;
     if (n == 1) {
