@@ -752,9 +752,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--learned-scenes", type=int, default=300)
+    ap.add_argument("--learned-scenes", type=int, default=1250)
     ap.add_argument("--learned-pairs", type=int, default=40)
-    ap.add_argument("--learned-steps", type=int, default=1000)
+    ap.add_argument("--learned-steps", type=int, default=3000)
     ap.add_argument("--learned-eval-scenes", type=int, default=500)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--gemm-only", action="store_true",
