@@ -596,6 +596,86 @@ __host__ __device__ inline int robot_smem_bytes(int n_pairs) {
   return (b + 15) & ~15;
 }
 
+// One configuration q [dof] checked by a whole warp (start / goal checks):
+// every lane runs the same FK, lane l places spheres l, l + 32, ... , tests
+// them against every primitive (or the distance field) and stages their
+// centres (3 floats each at stage[3 s]); after a warp barrier lane l tests
+// self pairs l, l + 32, ....  Each test is the arithmetic of state_collides's
+// one-stage path, which the bounding-sphere stages reproduce exactly, so the
+// verdict is the same.  Returns the warp-wide verdict.
+static __device__ __noinline__ bool config_collides_warp(const RobotHeader* __restrict__ R, const uint32_t* __restrict__ pair,
+                                                  const float* __restrict__ thr, const float4* __restrict__ env,
+                                                  int n_aabb, int n_obb, int n_cyl, int n_sph, const EsdfGrid& grid,
+                                                  float* __restrict__ stage, const float* __restrict__ q, int lane) {
+  const bool has_grid = grid.v != nullptr;
+  const int dof = R->dof;
+  const float qv = lane < dof ? q[lane] : 0.f;  // one load per lane, broadcast per joint below
+  float ax = 1.f, ay = 0.f, az = 0.f;
+  float bx = 0.f, by = 1.f, bz = 0.f;
+  float cx = 0.f, cy = 0.f, cz = 1.f;
+  float px = 0.f, py = 0.f, pz = 0.f;
+  bool hit = false;
+  for (int i = 0; i < dof; ++i) {
+    if (R->jparent[i] < 0) {
+      ax = 1.f; ay = 0.f; az = 0.f;
+      bx = 0.f; by = 1.f; bz = 0.f;
+      cx = 0.f; cy = 0.f; cz = 1.f;
+      const float4 b = R->jbase[i];
+      px = b.x; py = b.y; pz = b.z;
+    }
+    const int ty = R->jtype[i];
+    const float qi = __shfl_sync(kFull, qv, i);
+    if (ty == kRevZ || ty == kRevY || ty == kRevX) {
+      float s, c;
+      sincosf(qi, &s, &c);
+      if (ty == kRevZ) {
+        const float nx = fmaf(c, ax, s * bx), ny = fmaf(c, ay, s * by), nz = fmaf(c, az, s * bz);
+        bx = fmaf(c, bx, -s * ax); by = fmaf(c, by, -s * ay); bz = fmaf(c, bz, -s * az);
+        ax = nx; ay = ny; az = nz;
+      } else if (ty == kRevY) {
+        const float nx = fmaf(c, ax, -s * cx), ny = fmaf(c, ay, -s * cy), nz = fmaf(c, az, -s * cz);
+        cx = fmaf(c, cx, s * ax); cy = fmaf(c, cy, s * ay); cz = fmaf(c, cz, s * az);
+        ax = nx; ay = ny; az = nz;
+      } else {
+        const float nx = fmaf(c, bx, s * cx), ny = fmaf(c, by, s * cy), nz = fmaf(c, bz, s * cz);
+        cx = fmaf(c, cx, -s * bx); cy = fmaf(c, cy, -s * by); cz = fmaf(c, cz, -s * bz);
+        bx = nx; by = ny; bz = nz;
+      }
+    } else if (ty == kPrismZ) {
+      px = fmaf(qi, cx, px); py = fmaf(qi, cy, py); pz = fmaf(qi, cz, pz);
+    } else if (ty == kPrismX) {
+      px = fmaf(qi, ax, px); py = fmaf(qi, ay, py); pz = fmaf(qi, az, pz);
+    } else {
+      px = fmaf(qi, bx, px); py = fmaf(qi, by, py); pz = fmaf(qi, bz, pz);
+    }
+    const float L = R->jlen[i];
+    px = fmaf(L, cx, px); py = fmaf(L, cy, py); pz = fmaf(L, cz, pz);
+    const int s0 = R->sph_begin[i], s1 = R->sph_begin[i + 1];
+    for (int s = s0 + lane; s < s1; s += 32) {
+      const float4 o = R->sph[s];
+      const float sx = fmaf(ax, o.x, fmaf(bx, o.y, fmaf(cx, o.z, px)));
+      const float sy = fmaf(ay, o.x, fmaf(by, o.y, fmaf(cy, o.z, py)));
+      const float sz = fmaf(az, o.x, fmaf(bz, o.y, fmaf(cz, o.z, pz)));
+      stage[3 * s] = sx;
+      stage[3 * s + 1] = sy;
+      stage[3 * s + 2] = sz;
+      if (has_grid) hit |= esdf_read(grid, sx, sy, sz) < o.w;
+      hit |= sphere_hits_env(sx, sy, sz, o.w, env, n_aabb, n_obb, n_cyl, n_sph);
+    }
+  }
+  __syncwarp();
+  const int np = R->n_pairs;
+  for (int k = lane; k < np; k += 32) {
+    const uint32_t pr = pair[k];
+    const int i = (int)(pr & 0xffffu), j = (int)(pr >> 16);
+    const float dx = stage[3 * i] - stage[3 * j], dy = stage[3 * i + 1] - stage[3 * j + 1],
+                dz = stage[3 * i + 2] - stage[3 * j + 2];
+    hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr[k];
+  }
+  __syncwarp();
+  return __any_sync(kFull, hit);
+}
+
 // ------------------------------------------------------------------ TMA staging
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -615,38 +615,47 @@ __global__ void __maxnreg__(96) plan_kernel(PlanGlobals* __restrict__ g, const P
   }
 }
 
-// One block per problem: clear the rows the previous launch wrote (back to
-// NaN / unset parent), insert the roots, reset the counters, and reject a
-// start or goal in collision (Alg. 1 lines 1-2).
-struct EndpointQ {
-  const float* start;
-  const float* goal;
-  int lane;
-  __device__ __forceinline__ float operator()(int i) const { return lane == 0 ? start[i] : goal[i]; }
-};
-
-__device__ void check_endpoints(const ProblemDesc* D, ProblemState* S, float* stage) {
-  const int lane = threadIdx.x & 31;
-  const RobotHeader* R = &D->robot->h;
-  const EndpointQ qs{D->q_start, D->q_goal, lane};
-  const bool hit = state_collides<false>(R, D->robot->pair, D->robot->thr, D->env.data, D->env.n_aabb, D->env.n_obb,
-                                         D->env.n_cyl, D->env.n_sph, D->env.esdf, stage, qs, lane < 2, lane,
-                                         nullptr);
-  const unsigned m = __ballot_sync(kFull, hit);
-  if (lane == 0) {
-    if (m & 1u) S->pre_status = PRRTC_START_IN_COLLISION;
-    else if (m & 2u) S->pre_status = PRRTC_GOAL_IN_COLLISION;
-    if (m & 3u) S->done = 1;
-  }
+// Reject a start or goal in collision (Alg. 1 lines 1-2): warp 0 checks the
+// start and warp 1 the goal, each with the whole warp; the verdicts meet in
+// shared memory.
+__device__ bool endpoint_collides(const ProblemDesc* D, int which, const RobotHeader* R, const uint32_t* pair,
+                                  const float* thr, const float4* env, float* stage) {
+  return config_collides_warp(R, pair, thr, env, D->env.n_aabb, D->env.n_obb, D->env.n_cyl, D->env.n_sph, D->env.esdf,
+                              stage, which == 0 ? D->q_start : D->q_goal, threadIdx.x & 31);
 }
 
+// One block per problem: clear the rows the previous launch wrote (back to
+// NaN / unset parent), insert the roots, reset the counters, check start and
+// goal.  Robot and environment are staged in shared
+// memory (bulk copies, overlapping the clearing) for the endpoint check;
+// should the copy not complete in time the check reads them from global.
 __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states,
-                             const int* __restrict__ idx) {
+                             const int* __restrict__ idx, int robot_bytes, int env_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_hit[2];
   const int p = idx ? idx[blockIdx.x] : blockIdx.x;
   const ProblemDesc* D = descs + p;
   ProblemState* S = states + p;
   const int dpad = D->dpad;
+  const int np_pad = (D->n_pairs + 3) & ~3;
+  const int env_f4 = D->env.n_float4();
+  RobotHeader* sR = reinterpret_cast<RobotHeader*>(smem);
+  uint32_t* spair = reinterpret_cast<uint32_t*>(smem + sizeof(RobotHeader));
+  float* sthr = reinterpret_cast<float*>(spair + np_pad);
+  float4* senv = reinterpret_cast<float4*>(smem + robot_bytes);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async_smem();
+    const uint32_t bytes = (uint32_t)sizeof(RobotHeader) + 8u * (uint32_t)np_pad + 16u * (uint32_t)env_f4;
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_g2s(sR, &D->robot->h, sizeof(RobotHeader), &bar);
+    if (np_pad) {
+      bulk_g2s(spair, D->robot->pair, 4u * np_pad, &bar);
+      bulk_g2s(sthr, D->robot->thr, 4u * np_pad, &bar);
+    }
+    if (env_f4) bulk_g2s(senv, D->env.data, 16u * env_f4, &bar);
+  }
   for (int t = 0; t < 2; ++t) {
     const int rows = S->used_rows[t];
     const size_t nf = (size_t)rows * S->used_dpad;
@@ -688,9 +697,23 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
       S->verdict_states = 0;
       S->prim_tests[0] = S->prim_tests[1] = S->prim_tests[2] = S->prim_tests[3] = 0;
     }
-    __syncwarp();
-    float* stage = reinterpret_cast<float*>(smem);
-    check_endpoints(D, S, stage);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 2) {
+    int ok = 0;
+    if (lane == 0) ok = mbar_wait(&bar, 0, 1u << 26) ? 1 : 0;
+    ok = __shfl_sync(kFull, ok, 0);
+    // each warp's sphere centres: 3 floats per sphere
+    float* stage = reinterpret_cast<float*>(smem + robot_bytes + env_bytes) + warp * 3 * D->n_spheres;
+    const bool hit = ok ? endpoint_collides(D, warp, sR, spair, sthr, senv, stage)
+                        : endpoint_collides(D, warp, &D->robot->h, D->robot->pair, D->robot->thr, D->env.data, stage);
+    if (lane == 0) s_hit[warp] = hit ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_hit[0]) S->pre_status = PRRTC_START_IN_COLLISION;
+    else if (s_hit[1]) S->pre_status = PRRTC_GOAL_IN_COLLISION;
+    if (s_hit[0] | s_hit[1]) S->done = 1;
   }
 }
 
@@ -720,13 +743,13 @@ __global__ void gather_paths_kernel(const ProblemDesc* __restrict__ descs, const
 
 cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
                          int max_env_f4, cudaStream_t stream, const int* idx) {
-  (void)max_pairs;
-  (void)max_env_f4;
   if (n <= 0) return cudaSuccess;
-  const int smem = stage_bytes(max_spheres);
+  const int robot_bytes = robot_smem_bytes((max_pairs + 3) & ~3);
+  const int env_bytes = max_env_f4 * 16;
+  const int smem = robot_bytes + env_bytes + stage_bytes(max_spheres);
   cudaError_t e = cudaFuncSetAttribute(setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  setup_kernel<<<n, 256, smem, stream>>>(desc, state, idx);
+  setup_kernel<<<n, 256, smem, stream>>>(desc, state, idx, robot_bytes, env_bytes);
   return cudaGetLastError();
 }
 

@@ -281,7 +281,7 @@ def test_graph_replay_is_exact_and_recaptures_on_shape_change(c1_problems):
 def test_autotune_picks_a_candidate_and_later_calls_use_it(c1_problems):
     items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, 1, k) for k, q in enumerate(c1_problems)]
     best, ms = P.prrtc_autotune(items, P.params(), trials=2)
-    assert best.warps_per_block in (2, 4, 8) and best.blocks >= 1 and ms > 0
+    assert best.warps_per_block in (2, 3, 4, 6, 8) and best.blocks >= 1 and ms > 0
     res = P.prrtc_plan_batch(items, P.params())
     st = P.prrtc_last_launch_stats()
     assert st["grid"] == best.blocks and st["block_threads"] == 32 * best.warps_per_block
