@@ -220,19 +220,29 @@ __device__ __forceinline__ int parent_of(const int* par, int node, int* err) {
 // was extended and vice versa, so the path lists each waypoint once.
 __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   const ProblemDesc* D = c.D;
-  const int o = 1 - s;
   int err = 0;
-  int ns = 0, no = 0;
-  if (c.lane == 0) {
-    for (int x = js; x >= 0 && ns <= D->cap; x = parent_of(D->parent[s], x, &err)) ns++;
-    for (int x = jo; x >= 0 && no <= D->cap; x = parent_of(D->parent[o], x, &err)) no++;
+  // the T_a-side chain (root first) then the T_b-side chain without its join row
+  const int a_join = (s == 0) ? js : jo;
+  const int b_join = (s == 0) ? jo : js;
+  // Lane 0 walks T_a from its join row to the root and lane 1 T_b, at the same
+  // time; each records the rows it visits in the warp's staging area (the
+  // sphere-centre scratch, free now) while they fit, so that the path can be
+  // laid out without a second walk.
+  const int rec_cap = (c.R->n_spheres + c.R->dof) * 48;  // ints per side: half the staging area
+  int* rec = reinterpret_cast<int*>(c.stage) + (c.lane & 1) * rec_cap;
+  int n = 0;
+  if (c.lane < 2) {
+    const int* par = D->parent[c.lane];
+    for (int x = c.lane == 0 ? a_join : b_join; x >= 0 && n <= D->cap; x = parent_of(par, x, &err)) {
+      if (n < rec_cap) rec[n] = x;
+      ++n;
+    }
   }
-  ns = __shfl_sync(kFull, ns, 0);
-  no = __shfl_sync(kFull, no, 0);
-  err = __shfl_sync(kFull, err, 0);
-  const int K = ns + no - 1;
+  const int na = __shfl_sync(kFull, n, 0), nb = __shfl_sync(kFull, n, 1);
+  err = __reduce_or_sync(kFull, err);
+  const int K = na + nb - 1;
   if (c.lane == 0) c.S->path_n = K;
-  if (err || ns > D->cap || no > D->cap) {
+  if (err || na > D->cap || nb > D->cap) {
     if (c.lane == 0) c.S->path_status = PRRTC_ERR_TIMEOUT;
     return;
   }
@@ -240,19 +250,23 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
     if (c.lane == 0) c.S->path_status = PRRTC_PATH_OVERFLOW;
     return;
   }
-  // the T_a-side chain (root first) then the T_b-side chain without its join row
-  const int a_join = (s == 0) ? js : jo;
-  const int b_join = (s == 0) ? jo : js;
-  const int na = (s == 0) ? ns : no;
-  if (c.lane == 0) {
-    // both walks are bounded by the chain lengths counted above
+  __syncwarp();
+  const int* rec_a = reinterpret_cast<const int*>(c.stage);
+  const int* rec_b = rec_a + rec_cap;
+  if (na <= rec_cap) {
+    for (int r = c.lane; r < na; r += 32) D->path_idx[r] = rec_a[na - 1 - r];
+  } else if (c.lane == 0) {  // a chain longer than the record: walk it again
     int pos = na - 1;
     for (int x = a_join; x >= 0 && pos >= 0; x = parent_of(D->parent[0], x, &err)) D->path_idx[pos--] = x;
-    pos = na;
+  }
+  if (nb <= rec_cap) {
+    for (int k = c.lane; k < nb - 1; k += 32) D->path_idx[na + k] = (1 << 30) | rec_b[k + 1];
+  } else if (c.lane == 1) {
+    int pos = na;
     for (int x = parent_of(D->parent[1], b_join, &err); x >= 0 && pos < K; x = parent_of(D->parent[1], x, &err))
       D->path_idx[pos++] = (1 << 30) | x;
-    __threadfence_block();
   }
+  __threadfence_block();
   __syncwarp();
   const int dof = D->dof, dpad = D->dpad;
   double seg = 0.0;
