@@ -506,36 +506,61 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       st[0] = sx;
       st[32] = sy;
       st[64] = sz;
+      if (kWarpVote) continue;  // edge warps test the environment in a second pass, distal links first
       if (has_grid) hit |= esdf_read(grid, sx, sy, sz) < o.w;  // the distance field, sphere by sphere
       if (!two) {
         hit |= sphere_hits_env(sx, sy, sz, o.w, env, n_aabb, n_obb, n_cyl, n_sph);
         passes++;
-        if (kWarpVote) {
-          if (__any_sync(kFull, hit && active)) {
-            flush();
-            return true;
-          }
-        }
       }
     }
-    if (two) {
-      unsigned long long r;
-      if (kWarpVote) {  // the lanes are the states of one edge: bound them all first
-        const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
-        r = env_three_stage(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz, cb.w, stage, R->sph, s0,
-                            s1, active, lane);
-      } else {
-        passes++;
-        r = env_two_stage(env, n_aabb, n_obb, n_cyl, n_sph, gx, gy, gz, cb.w, stage, R->sph, s0, s1, active, lane);
-      }
+    if (two && !kWarpVote) {
+      passes++;
+      const unsigned long long r =
+          env_two_stage(env, n_aabb, n_obb, n_cyl, n_sph, gx, gy, gz, cb.w, stage, R->sph, s0, s1, active, lane);
       hit |= (r >> 63) != 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)((r >> (15 * k)) & 0x7fffu);
-      if (kWarpVote) {
-        if (__any_sync(kFull, hit && active)) {
-          flush();
-          return true;
+    }
+  }
+  if (kWarpVote) {
+    // The lanes are the states of one edge, all placed and staged above.  Test
+    // the links against the environment from the last one back: collisions
+    // come mostly at the distal links, and the first hit ends the check.  The
+    // verdict is the OR of the same tests in any order.
+    for (int i = dof - 1; i >= 0; --i) {
+      const int s0 = R->sph_begin[i], s1 = R->sph_begin[i + 1];
+      if (s0 == s1) continue;
+      const float4 cb = R->coarse[i];
+      const bool two = R->two_stage && cb.w > 0.f && has_prims;  // uniform
+      if (two) {
+        if (has_grid) {
+          for (int s = s0; s < s1; ++s) {
+            const float* st = stage + s * 96 + lane;
+            hit |= esdf_read(grid, st[0], st[32], st[64]) < R->sph[s].w;
+          }
         }
+        // the link's bounding sphere, staged as its group centre
+        const float* gst = stage + (R->n_spheres + i) * 96 + lane;
+        const float gx = gst[0], gy = gst[32], gz = gst[64];
+        const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
+        const unsigned long long r = env_three_stage(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz,
+                                                     cb.w, stage, R->sph, s0, s1, active, lane);
+        hit |= (r >> 63) != 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)((r >> (15 * k)) & 0x7fffu);
+      } else {
+        for (int s = s0; s < s1; ++s) {
+          const float4 o = R->sph[s];
+          const float* st = stage + s * 96 + lane;
+          const float sx = st[0], sy = st[32], sz = st[64];
+          if (has_grid) hit |= esdf_read(grid, sx, sy, sz) < o.w;
+          hit |= sphere_hits_env(sx, sy, sz, o.w, env, n_aabb, n_obb, n_cyl, n_sph);
+          passes++;
+        }
+      }
+      if (__any_sync(kFull, hit && active)) {
+        flush();
+        return true;
       }
     }
   }
