@@ -48,12 +48,19 @@ OPS = dict(centre=9, aabb=13, obb=22, cyl=24, sph=9, pair=7, joint=17)
 
 
 def kernel_source_hash():
+    """Hash of the planner kernel's code (its sources with comments and blank lines
+    removed), to tell whether the committed ncu counters still describe it."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ["prrtc_device.cuh", "prrtc_launch.h", "prrtc_plan.cu"]:
         h.update(f.encode())
-        with open(os.path.join(ROOT, "paper_2503_06757_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2503_06757_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

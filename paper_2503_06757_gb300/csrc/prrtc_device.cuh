@@ -412,11 +412,14 @@ struct EdgeQ {
 };
 
 // Collision test of one configuration per lane.  `stage` is this warp's
-// [n_spheres][3][32] shared-memory buffer of sphere centres.  With kWarpVote
-// the whole warp returns true as soon as any active lane collides (the edge
-// verdict), otherwise each lane returns its own verdict and the warp runs to
-// completion.  The joint loop is a runtime loop so that the obstacle loops
-// exist once in the code.
+// [n_spheres + dof][3][32] shared-memory buffer of sphere centres (and, with
+// kWarpVote, link group centres).  Without kWarpVote each lane tests its own
+// state link by link, in chain order, and returns its own verdict.  With
+// kWarpVote the lanes are the states of one edge: the joint loop only places
+// and stages every sphere, then the links are tested against the environment
+// from the distal end back (three stages per link) and the whole warp returns
+// true as soon as any active lane collides (the edge verdict).  The joint loop
+// is a runtime loop so that the obstacle loops exist once in the code.
 template <bool kWarpVote, class QS>
 __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R, const uint32_t* __restrict__ pair,
                                                const float* __restrict__ thr, const float4* __restrict__ env,
