@@ -143,7 +143,8 @@ struct WarpCount {
   unsigned long long prim[4];       // second-stage sphere-primitive tests per type
   unsigned long long edges, edge_states, nn_nodes, iterations, insert_fail, dd_rejected;
   unsigned long long verdict_states;  // states whose verdict was established (early-exit states excluded)
-  unsigned long long pad_[2];
+  unsigned long long aborted;         // set when an edge check stopped because the problem was solved
+  unsigned long long pad_;
 };
 static_assert(sizeof(WarpCount) == 128, "per-warp counter block is 128 bytes");
 
@@ -401,6 +402,7 @@ struct LaneQ {
   const float* q;  // [kMaxDof][32]
   int lane;
   __device__ __forceinline__ float operator()(int i) const { return q[i * 32 + lane]; }
+  __device__ __forceinline__ int poll() const { return 0; }
 };
 
 struct EdgeQ {
@@ -408,7 +410,9 @@ struct EdgeQ {
   const float* b;
   float t;
   bool end;
+  const int* solved;  // the problem's solved flag: once set, the edge's verdict no longer matters
   __device__ __forceinline__ float operator()(int i) const { return end ? b[i] : fmaf(t, b[i] - a[i], a[i]); }
+  __device__ __forceinline__ int poll() const { return *reinterpret_cast<const volatile int*>(solved); }
 };
 
 // Collision test of one configuration per lane.  `stage` is this warp's
@@ -429,6 +433,9 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
   const bool has_grid = grid.v != nullptr;
   const bool has_prims = (n_aabb | n_obb | n_cyl | n_sph) != 0;
   const int dof = R->dof;
+  // edge warps read the problem's solved flag now and look at it after
+  // placing the spheres (the load's latency hides behind the FK)
+  const int solved_early = (kWarpVote && lane == 0) ? qs.poll() : 0;
   // uniform work of this call, multiplied by the active lanes on the way out
   const unsigned long long na = (unsigned long long)__popc(__ballot_sync(kFull, active));
   uint32_t passes = 0, pairs = 0;
@@ -526,6 +533,13 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
     }
   }
   if (kWarpVote) {
+    // Another warp has solved the problem: the verdict no longer matters, and
+    // the warp leaves with "collides" so that it stops at its next check.
+    if (__shfl_sync(kFull, solved_early, 0)) {
+      if (wc && lane == 0) wc->aborted = 1;
+      flush();
+      return true;
+    }
     // The lanes are the states of one edge, all placed and staged above.  Test
     // the links against the environment from the last one back: collisions
     // come mostly at the distal links, and the first hit ends the check.  The

@@ -174,9 +174,22 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
     const int k = base + c.lane + 1;
     const bool active = k <= N;
     const int kk = active ? k : N;
-    const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N};
+    const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N, &c.S->solved};
     if (state_collides<true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
                              c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt)) {
+      __syncwarp();  // lane 0 may have just set the flag
+      if (c.cnt->aborted) {
+        // the problem was solved meanwhile and the check stopped early: this
+        // edge is not counted as checked
+        __syncwarp();
+        if (c.lane == 0) {
+          c.cnt->aborted = 0;
+          c.cnt->edges--;
+          c.cnt->edge_states -= (unsigned long long)N;
+        }
+        __syncwarp();
+        return false;
+      }
       // the states of earlier passes were all shown free, and one state of this
       // pass collides; the other states of the pass stopped early
       if (c.lane == 0) c.cnt->verdict_states += (unsigned long long)base + 1ull;
