@@ -240,15 +240,36 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   // Lane 0 walks T_a from its join row to the root and lane 1 T_b, at the same
   // time; each records the rows it visits in the warp's staging area (the
   // sphere-centre scratch, free now) while they fit, so that the path can be
-  // laid out without a second walk.
-  const int rec_cap = (c.R->n_spheres + c.R->dof) * 48;  // ints per side: half the staging area
-  int* rec = reinterpret_cast<int*>(c.stage) + (c.lane & 1) * rec_cap;
+  // laid out without a second walk.  When both trees' parent arrays fit in
+  // half of the area, the warp first copies them there with coalesced loads
+  // and the walks run in shared memory (a walk in global memory pays one L2
+  // round trip per step).  Every row on a chain had its parent written before
+  // it was linked; an entry still unset in the copy falls back to the global
+  // read.
+  const int area = (c.R->n_spheres + c.R->dof) * 96;  // ints
+  const int n0 = min(ld_relaxed(&c.S->count[0]), D->cap), n1 = min(ld_relaxed(&c.S->count[1]), D->cap);
+  const bool in_smem = n0 + n1 <= area / 2;
+  int* sp = reinterpret_cast<int*>(c.stage);
+  if (in_smem) {
+    for (int k = c.lane; k < n0; k += 32) sp[k] = __ldcg(D->parent[0] + k);
+    for (int k = c.lane; k < n1; k += 32) sp[n0 + k] = __ldcg(D->parent[1] + k);
+    __syncwarp();
+  }
+  const int rec_cap = in_smem ? area / 4 : area / 2;  // ints per side
+  int* rec_base = reinterpret_cast<int*>(c.stage) + (in_smem ? area / 2 : 0);
+  int* rec = rec_base + (c.lane & 1) * rec_cap;
   int n = 0;
   if (c.lane < 2) {
-    const int* par = D->parent[c.lane];
-    for (int x = c.lane == 0 ? a_join : b_join; x >= 0 && n <= D->cap; x = parent_of(par, x, &err)) {
+    const int t = c.lane, nt = t == 0 ? n0 : n1;
+    const int* par = D->parent[t];
+    const int* spt = sp + (t == 0 ? 0 : n0);
+    int x = t == 0 ? a_join : b_join;
+    while (x >= 0 && n <= D->cap) {
       if (n < rec_cap) rec[n] = x;
       ++n;
+      int p = kUnsetParent;
+      if (in_smem && x < nt) p = spt[x];
+      x = (p != kUnsetParent) ? p : parent_of(par, x, &err);
     }
   }
   const int na = __shfl_sync(kFull, n, 0), nb = __shfl_sync(kFull, n, 1);
@@ -264,7 +285,7 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
     return;
   }
   __syncwarp();
-  const int* rec_a = reinterpret_cast<const int*>(c.stage);
+  const int* rec_a = rec_base;
   const int* rec_b = rec_a + rec_cap;
   if (na <= rec_cap) {
     for (int r = c.lane; r < na; r += 32) D->path_idx[r] = rec_a[na - 1 - r];
