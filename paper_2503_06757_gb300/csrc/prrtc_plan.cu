@@ -572,7 +572,7 @@ __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
   return -1;
 }
 
-__global__ void __maxnreg__(96) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
+__global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                             ProblemState* __restrict__ states, int robot_bytes, int env_bytes, int warp_floats) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
