@@ -647,7 +647,6 @@ __global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const 
     c.lane = lane;
     worker(c);
     // flush this warp's counters into the problem
-    // flush this warp's counters into the problem
     __syncwarp();
     if (lane < 14) {
       ProblemState* S = states + p;
