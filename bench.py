@@ -593,7 +593,7 @@ def run_ours(args):
     prm = P.params()
     tuned = None
     if not args.no_autotune:
-        prm, tuned_ms = P.prrtc_autotune(items, prm, trials=2)
+        prm, tuned_ms = P.prrtc_autotune(items, prm, trials=4)
         tuned = dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, mean_ms=tuned_ms)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
