@@ -296,8 +296,8 @@ def learned_section(args, P):
     ev_25 = L.evaluate(rb, args.learned_eval_scenes, 1, 9000, prop, ratio=0.25)["learned"]
     return dict(workload="cubby shelf, 7-DoF arm; held-out scenes 9000.. (one problem each), Philox keys 1..3",
                 ratio=0.5, train=train, eval=ev, learned_ratio_0_25=ev_25,
-                note="TTFS includes the on-device inference (occupancy, features, 4 tensor-core GEMMs) "
-                     "that precedes planning"), prop
+                note="TTFS includes the on-device inference (occupancy grids, layer 1 per distinct scene, one "
+                     "fused kernel for the rest) that precedes planning"), prop
 
 
 def door_section(P, door, keys=(1, 2, 3)):
@@ -490,7 +490,7 @@ def variants_section(args, P, items, prm, counts, flush, torch, steps=5):
                 ("dynamic_domain", dict(DD_PARAMS), True),
                 ("halton_dynamic_domain", dict(DD_PARAMS, sampler=P.SAMPLER_HALTON), True)]
     out = dict(workload=WORKLOAD, steps=steps, dynamic_domain_params=DD_PARAMS,
-               note="baseline = two-stage check, Philox sampling, no dynamic domain (the main line's step)")
+               note="baseline = multi-stage check, Philox sampling, no dynamic domain (the main line's step)")
     for name, kw, two in variants:
         for rb in robots.values():
             rb.set_two_stage(two)
