@@ -467,7 +467,12 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
     const float qi = qs(i);
     if (ty == kRevZ || ty == kRevY || ty == kRevX) {
       float s, c;
-      sincosf(qi, &s, &c);
+      // the hardware sine/cosine (absolute error about 2^-21 on [-pi, pi]: sphere
+      // centres within about 1e-6 m of exact FK); the library routine beyond
+      if (fabsf(qi) <= 3.2f)
+        __sincosf(qi, &s, &c);
+      else
+        sincosf(qi, &s, &c);
       if (ty == kRevZ) {  // R * Rz: col0' = c col0 + s col1, col1' = -s col0 + c col1
         const float nx = fmaf(c, ax, s * bx), ny = fmaf(c, ay, s * by), nz = fmaf(c, az, s * bz);
         bx = fmaf(c, bx, -s * ax); by = fmaf(c, by, -s * ay); bz = fmaf(c, bz, -s * az);
