@@ -201,9 +201,9 @@ def op_count(path, env_counts, dof, dpad):
 
 
 def one_stage_ops_per_state(env_counts, dof, n_spheres, n_pairs):
-    """Algorithmic work of one collision verdict (the hot-path table's per-state
-    figure): FK of every joint, every distinct sphere against every primitive,
-    every self pair -- the one-stage check, whatever the kernel skips."""
+    """Algorithmic work of one collision verdict, in counted lane-ops: FK of every
+    joint, every distinct sphere against every primitive, every self pair -- the
+    one-stage check, whatever the kernel skips."""
     a, o, c, s = env_counts
     per_sphere = OPS["centre"] + OPS["aabb"] * a + OPS["obb"] * o + OPS["cyl"] * c + OPS["sph"] * s
     return OPS["joint"] * dof + n_spheres * per_sphere + n_pairs * OPS["pair"]
