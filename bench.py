@@ -480,9 +480,9 @@ DD_PARAMS = dict(dd_radius=5.0, dd_alpha=0.02, dd_min_radius=4.0)
 
 
 def variants_section(args, P, items, prm, counts, flush, torch, steps=5):
-    """The hot-path table's next rows on the benchmark batch, same keys and launch
-    shape: one-stage vs two-stage check, Philox vs Halton sampling, dynamic-domain
-    sampling on/off."""
+    """The method's optional parts on the benchmark batch, same keys and launch
+    shape: one-stage vs multi-stage check, Philox vs Halton sampling,
+    dynamic-domain sampling on/off."""
     import copy
     robots = {id(it[0]): it[0] for it in items}
     variants = [("baseline", {}, True), ("one_stage", {}, False),
