@@ -181,9 +181,9 @@ def shelf_problems(accept, count=200, seed0=1000):
     return W.problem_set("shelf", count, seed0, accept)
 
 
-def c1_problem(accept):
+def boxes8_problem(accept):
     from paper_2503_06757_gb300 import workload as W
-    return W.problem_set("c1", 1, 1, accept)[0]
+    return W.problem_set("boxes8", 1, 1, accept)[0]
 
 
 PRIM_KINDS = ("aabb", "obb", "cyl", "sph")
@@ -652,24 +652,24 @@ def run_ours(args):
     extra = {}
     if rank == 0 and not args.quick:
         # single-problem TTFS through prrtc_plan (host wall clock, env resident)
-        c1 = c1_problem(accept)
-        rb1, ev1 = P.make_robot(c1.robot), P.make_env(c1.scene)
+        boxes8 = boxes8_problem(accept)
+        rb1, ev1 = P.make_robot(boxes8.robot), P.make_env(boxes8.scene)
         p1 = P.params()
         if not args.no_autotune:
-            p1, _ = P.prrtc_autotune([(rb1, ev1, c1.q_start, c1.q_goal, 101, 0)], p1, trials=8)
+            p1, _ = P.prrtc_autotune([(rb1, ev1, boxes8.q_start, boxes8.q_goal, 101, 0)], p1, trials=8)
         for key in range(1, 4):
             p1.seed = key
-            P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, p1)
+            P.prrtc_plan(rb1, ev1, boxes8.q_start, boxes8.q_goal, p1)
         tt, ok = [], 0
         for key in range(1, 101):
             p1.seed = key
             t = time.perf_counter()
-            r = P.prrtc_plan(rb1, ev1, c1.q_start, c1.q_goal, p1)
+            r = P.prrtc_plan(rb1, ev1, boxes8.q_start, boxes8.q_goal, p1)
             tt.append((time.perf_counter() - t) * 1e3)
             ok += r["status"] == P.SOLVED
-        extra["ttfs_single_c1_ms"] = dict(percentiles(tt), success_rate=ok / 100, keys=100,
+        extra["ttfs_single_boxes8_ms"] = dict(percentiles(tt), success_rate=ok / 100, keys=100,
                                           launch=dict(blocks=p1.blocks, warps_per_block=p1.warps_per_block),
-                                          workload="c1: 7-DoF arm, 8 random cuboids, one problem, keys 1..100")
+                                          workload="boxes8: 7-DoF arm, 8 random cuboids, one problem, keys 1..100")
         # collision-check microbenchmark: collision-free shelf states, every test runs
         pb = probs[0]
         rb, ev = robots[pb.robot.name], envs[0]

@@ -563,14 +563,14 @@ def choose_problem(robot: Robot, scene: Scene, seed: int, accept, goal_in_cells:
 def problem_set(kind: str, count: int, seed0: int, accept, n_obstacles=None):
     """Seeded problem sets shaped like the paper's workloads.
 
-    kind: "c1" random boxes + arm7; "shelf" cubby shelf + arm7 (goals in
+    kind: "boxes8" 8 random cuboids + arm7; "shelf" cubby shelf + arm7 (goals in
     cubbies); "mixed" 7/8/14-DoF in equal thirds with 10..120 mixed obstacles.
     Scenes for which no start/goal pair is found are replaced by the next seed.
     """
     out = []
     seed = seed0
     while len(out) < count:
-        if kind == "c1":
+        if kind == "boxes8":
             robot = arm7()
             scene = scene_random_boxes(seed)
             pair = choose_problem(robot, scene, seed, accept)

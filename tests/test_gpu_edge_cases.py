@@ -22,26 +22,26 @@ def _built():
 
 
 @pytest.fixture(scope="module")
-def c1():
-    return W.problem_set("c1", 1, 1, O.accept)[0]
+def boxes8():
+    return W.problem_set("boxes8", 1, 1, O.accept)[0]
 
 
 @pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
-def test_non_finite_endpoints_rejected(c1, bad):
-    rb, ev = P.make_robot(c1.robot), P.make_env(c1.scene)
-    q = c1.q_start.astype(np.float32).copy()
+def test_non_finite_endpoints_rejected(boxes8, bad):
+    rb, ev = P.make_robot(boxes8.robot), P.make_env(boxes8.scene)
+    q = boxes8.q_start.astype(np.float32).copy()
     q[3] = bad
-    for s, g in ((q, c1.q_goal), (c1.q_start, q)):
+    for s, g in ((q, boxes8.q_goal), (boxes8.q_start, q)):
         with pytest.raises(P.PrrtcError) as e:
             P.prrtc_plan(rb, ev, s, g, P.params())
         assert e.value.code == P.ERR_INVALID_ARG
 
 
-def test_start_equals_goal_matches_oracle(c1):
-    rb, ev = P.make_robot(c1.robot), P.make_env(c1.scene)
-    q = c1.q_start.astype(np.float32)
+def test_start_equals_goal_matches_oracle(boxes8):
+    rb, ev = P.make_robot(boxes8.robot), P.make_env(boxes8.scene)
+    q = boxes8.q_start.astype(np.float32)
     g = P.prrtc_plan(rb, ev, q, q, P.params(seed=1, mode=P.MODE_SERIAL, tree_capacity=1024))
-    o = O.plan(c1.robot, c1.scene, q.astype(np.float64), q.astype(np.float64), seed=1, tree_capacity=1024,
+    o = O.plan(boxes8.robot, boxes8.scene, q.astype(np.float64), q.astype(np.float64), seed=1, tree_capacity=1024,
                range=1.0, resolution=F32(1 / 32), goal_bias=F32(0.05))
     assert g["status"] == o["status"] == P.SOLVED
     assert g["iterations"] == o["iterations"]
@@ -106,8 +106,8 @@ def test_sixteen_dof_chain_checks_against_oracle():
     assert 0.02 < free.mean() < 0.98
 
 
-def test_empty_calls(c1):
-    rb, ev = P.make_robot(c1.robot), P.make_env(c1.scene)
+def test_empty_calls(boxes8):
+    rb, ev = P.make_robot(boxes8.robot), P.make_env(boxes8.scene)
     assert P.prrtc_check_states(rb, ev, np.zeros((0, 7), np.float32)).shape == (0,)
     with pytest.raises(P.PrrtcError) as e:
         P.prrtc_plan_batch([], P.params())

@@ -163,13 +163,13 @@ def test_occupancy_matches_oracle():
 
 
 @pytest.fixture(scope="module")
-def c1_problems():
-    return W.problem_set("c1", 4, 1, O.accept)
+def boxes8_problems():
+    return W.problem_set("boxes8", 4, 1, O.accept)
 
 
 @pytest.mark.parametrize("k", range(4))
-def test_serial_planner_with_mixture_matches_oracle(c1_problems, k):
-    pb = c1_problems[k]
+def test_serial_planner_with_mixture_matches_oracle(boxes8_problems, k):
+    pb = boxes8_problems[k]
     gmm = W.random_mixture(7, 100 + k)
     rb, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
     prm = P.params(seed=3, mode=P.MODE_SERIAL, tree_capacity=1 << 14, learned_ratio=0.5)
@@ -185,28 +185,28 @@ def test_serial_planner_with_mixture_matches_oracle(c1_problems, k):
     np.testing.assert_allclose(g["path"], o["path"], atol=1e-4)
 
 
-def test_learned_batch_plans_with_device_inference(c1_problems):
+def test_learned_batch_plans_with_device_inference(boxes8_problems):
     rb7 = W.arm7()
     prop = P.Proposal(7, rb7.lower, rb7.upper, flat(init(7, 16)))
     items, props = [], []
-    for k, pb in enumerate(c1_problems):
+    for k, pb in enumerate(boxes8_problems):
         items.append((P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 9, k))
         props.append(prop if k % 2 == 0 else None)
     res = P.prrtc_plan_batch_learned(items, props, P.params(learned_ratio=0.5))
-    for pb, r in zip(c1_problems, res):
+    for pb, r in zip(boxes8_problems, res):
         assert r["status"] == P.SOLVED
         bad, mc = O.revalidate(pb.robot, pb.scene, r["path"].astype(np.float64), F32(1 / 32) / 4)
         assert bad == 0 or mc > -1e-3
 
 
-def test_learned_inference_replay_is_exact(c1_problems):
+def test_learned_inference_replay_is_exact(boxes8_problems):
     """The inference chain runs eagerly, is captured on its second call with the same
     buffers and replayed afterwards: serial plans of all three calls are identical, and
     a different batch size in between does not disturb the replay."""
     rb7 = W.arm7()
     prop = P.Proposal(7, rb7.lower, rb7.upper, flat(init(7, 17)))
     items = [(P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 5, k)
-             for k, pb in enumerate(c1_problems)]
+             for k, pb in enumerate(boxes8_problems)]
     prm = P.params(learned_ratio=0.5, mode=P.MODE_SERIAL, tree_capacity=1 << 14)
     runs = [P.prrtc_plan_batch_learned(items, [prop] * len(items), prm) for _ in range(3)]
     P.prrtc_plan_batch_learned(items[:2], [prop] * 2, prm)

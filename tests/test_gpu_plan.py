@@ -31,8 +31,8 @@ def _built():
 
 
 @pytest.fixture(scope="module")
-def c1_problems():
-    return W.problem_set("c1", 6, 1, O.accept)
+def boxes8_problems():
+    return W.problem_set("boxes8", 6, 1, O.accept)
 
 
 def gpu_plan(pb, seed, **kw):
@@ -65,8 +65,8 @@ def assert_path_valid(pb, r, delta=RANGE, res=RES):
 
 @pytest.mark.parametrize("k", range(6))
 @pytest.mark.parametrize("seed", [1, 2])
-def test_serial_mode_matches_oracle(c1_problems, k, seed):
-    pb = c1_problems[k]
+def test_serial_mode_matches_oracle(boxes8_problems, k, seed):
+    pb = boxes8_problems[k]
     g = gpu_plan(pb, seed, mode=P.MODE_SERIAL, tree_capacity=1 << 14)
     o = oracle_plan(pb, seed, tree_capacity=1 << 14)
     amb = o["first_amb_iter"]
@@ -85,20 +85,20 @@ def test_serial_mode_matches_oracle(c1_problems, k, seed):
     assert g["edge_states"] == o["edge_states"]
 
 
-def test_serial_mode_unambiguous_cases_exist(c1_problems):
+def test_serial_mode_unambiguous_cases_exist(boxes8_problems):
     """The lockstep comparison above must not be vacuous."""
     clean = 0
-    for pb in c1_problems:
+    for pb in boxes8_problems:
         for seed in (1, 2):
             o = oracle_plan(pb, seed, tree_capacity=1 << 14)
             clean += o["first_amb_iter"] == -1 or o["first_amb_iter"] >= o["iterations"]
     assert clean >= 6
 
 
-def test_serial_batch_equals_serial_alone(c1_problems):
+def test_serial_batch_equals_serial_alone(boxes8_problems):
     """Each problem's result is the same alone and in a batch (serial mode: bitwise)."""
     probs = [(P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 3, k)
-             for k, pb in enumerate(c1_problems)]
+             for k, pb in enumerate(boxes8_problems)]
     prm = P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14)
     batch = P.prrtc_plan_batch(probs, prm)
     for k, pr in enumerate(probs):
@@ -108,11 +108,11 @@ def test_serial_batch_equals_serial_alone(c1_problems):
         assert alone["iterations"] == batch[k]["iterations"]
 
 
-def test_plan_batch_object_equals_list_call(c1_problems):
+def test_plan_batch_object_equals_list_call(boxes8_problems):
     """PlanBatch (marshalled once, run many times, results as columns) returns what
     prrtc_plan_batch returns, run after run (serial mode: bitwise)."""
     probs = [(P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, 5, k)
-             for k, pb in enumerate(c1_problems)]
+             for k, pb in enumerate(boxes8_problems)]
     prm = P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14)
     ref = P.prrtc_plan_batch(probs, prm)
     batch = P.PlanBatch(probs)
@@ -130,15 +130,15 @@ def test_plan_batch_object_equals_list_call(c1_problems):
 # ------------------------------------------------------------------ async mode
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_async_paths_revalidate(c1_problems, seed):
-    for pb in c1_problems:
+def test_async_paths_revalidate(boxes8_problems, seed):
+    for pb in boxes8_problems:
         r = gpu_plan(pb, seed)
         bad, mc = assert_path_valid(pb, r)
         assert bad == 0 or mc > -1e-3, (bad, mc)
 
 
-def test_async_tree_invariants(c1_problems):
-    pb = c1_problems[0]
+def test_async_tree_invariants(boxes8_problems):
+    pb = boxes8_problems[0]
     r = gpu_plan(pb, 7, goal_bias=0.0, max_iters=400)  # no goal bias: trees grow before they meet
     rng = np.random.default_rng(0)
     for t, root in ((0, pb.q_start), (1, pb.q_goal)):
@@ -158,8 +158,8 @@ def test_async_tree_invariants(c1_problems):
     assert r["status"] in (P.SOLVED, P.NO_SOLUTION)
 
 
-def test_async_success_matches_oracle_on_c1_keys(c1_problems):
-    pb = c1_problems[1]
+def test_async_success_matches_oracle_on_c1_keys(boxes8_problems):
+    pb = boxes8_problems[1]
     g_ok = o_ok = 0
     for seed in range(1, 21):
         g_ok += gpu_plan(pb, seed)["status"] == P.SOLVED
@@ -221,8 +221,8 @@ def test_walled_off_goal_no_solution():
     assert r["status"] == P.NO_SOLUTION and r["iterations"] == 1500
 
 
-def test_budget_and_capacity_edges(c1_problems):
-    pb = c1_problems[2]
+def test_budget_and_capacity_edges(boxes8_problems):
+    pb = boxes8_problems[2]
     r = gpu_plan(pb, 1, max_iters=1, goal_bias=0.0)
     assert r["iterations"] == 1 and r["status"] in (P.SOLVED, P.NO_SOLUTION)
     r = gpu_plan(pb, 1, tree_capacity=2)
@@ -233,8 +233,8 @@ def test_budget_and_capacity_edges(c1_problems):
         assert r["n"] > 2
 
 
-def test_invalid_params_rejected(c1_problems):
-    pb = c1_problems[0]
+def test_invalid_params_rejected(boxes8_problems):
+    pb = boxes8_problems[0]
     for bad in (dict(range=0.0), dict(resolution=-1.0), dict(goal_bias=2.0), dict(max_iters=0), dict(mode=7)):
         with pytest.raises(P.PrrtcError) as e:
             gpu_plan(pb, 1, **bad)
@@ -261,13 +261,13 @@ def test_mixed_dof_batch_one_launch():
 
 # ------------------------------------------------------------------ graph replay and autotuning
 
-def test_graph_replay_is_exact_and_recaptures_on_shape_change(c1_problems):
-    pb = c1_problems[3]
+def test_graph_replay_is_exact_and_recaptures_on_shape_change(boxes8_problems):
+    pb = boxes8_problems[3]
     rb, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
     prm = P.params(seed=4, mode=P.MODE_SERIAL, tree_capacity=1 << 14)
     first = P.prrtc_plan(rb, ev, pb.q_start, pb.q_goal, prm)          # captures
     again = P.prrtc_plan(rb, ev, pb.q_start, pb.q_goal, prm)          # replays
-    items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, 4, k) for k, q in enumerate(c1_problems)]
+    items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, 4, k) for k, q in enumerate(boxes8_problems)]
     P.prrtc_plan_batch(items, prm)                                     # another shape
     third = P.prrtc_plan(rb, ev, pb.q_start, pb.q_goal, prm)           # re-captures
     for r in (again, third):
@@ -278,8 +278,8 @@ def test_graph_replay_is_exact_and_recaptures_on_shape_change(c1_problems):
     assert P.prrtc_last_launch_stats()["kernels"] == 3
 
 
-def test_autotune_picks_a_candidate_and_later_calls_use_it(c1_problems):
-    items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, 1, k) for k, q in enumerate(c1_problems)]
+def test_autotune_picks_a_candidate_and_later_calls_use_it(boxes8_problems):
+    items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, 1, k) for k, q in enumerate(boxes8_problems)]
     best, ms = P.prrtc_autotune(items, P.params(), trials=2)
     assert best.warps_per_block in (2, 3, 4, 6, 8) and best.blocks >= 1 and ms > 0
     res = P.prrtc_plan_batch(items, P.params())

@@ -33,8 +33,8 @@ def _built():
 
 
 @pytest.fixture(scope="module")
-def c1_problems():
-    return W.problem_set("c1", 6, 1, O.accept)
+def boxes8_problems():
+    return W.problem_set("boxes8", 6, 1, O.accept)
 
 
 def oracle_plan(pb, seed, **kw):
@@ -113,10 +113,10 @@ def test_two_stage_verdicts_equal_one_stage_and_oracle(name, kind):
     np.testing.assert_array_equal(v2[clear], free[clear])
 
 
-def test_two_stage_on_off_serial_plans_identical(c1_problems):
+def test_two_stage_on_off_serial_plans_identical(boxes8_problems):
     shelf = W.problem_set("shelf", 2, 1, O.accept)
     second_stage = 0
-    for pb in list(c1_problems[:3]) + shelf:
+    for pb in list(boxes8_problems[:3]) + shelf:
         h, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
         prm = P.params(seed=5, mode=P.MODE_SERIAL, tree_capacity=1 << 14, max_iters=4000)
         a = P.prrtc_plan(h, ev, pb.q_start, pb.q_goal, prm)
@@ -151,8 +151,8 @@ def test_halton_first_step_free_space():
 
 
 @pytest.mark.parametrize("k", range(6))
-def test_serial_halton_matches_oracle(c1_problems, k):
-    pb = c1_problems[k]
+def test_serial_halton_matches_oracle(boxes8_problems, k):
+    pb = boxes8_problems[k]
     h, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
     prm = P.params(seed=2, mode=P.MODE_SERIAL, tree_capacity=1 << 14, sampler=P.SAMPLER_HALTON,
                    halton_offset=37 * k)
@@ -168,8 +168,8 @@ DD = dict(dd_radius=F32(0.6), dd_alpha=F32(0.05), dd_min_radius=F32(0.3))
 
 @pytest.mark.parametrize("k", range(6))
 @pytest.mark.parametrize("seed", [1, 2])
-def test_serial_dynamic_domain_matches_oracle(c1_problems, k, seed):
-    pb = c1_problems[k]
+def test_serial_dynamic_domain_matches_oracle(boxes8_problems, k, seed):
+    pb = boxes8_problems[k]
     h, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
     prm = P.params(seed=seed, mode=P.MODE_SERIAL, tree_capacity=1 << 14, **DD)
     g = P.prrtc_plan(h, ev, pb.q_start, pb.q_goal, prm)
@@ -177,9 +177,9 @@ def test_serial_dynamic_domain_matches_oracle(c1_problems, k, seed):
     compare_serial(pb, g, o)
 
 
-def test_serial_dynamic_domain_unambiguous_cases_exist(c1_problems):
+def test_serial_dynamic_domain_unambiguous_cases_exist(boxes8_problems):
     clean, rejected = 0, 0
-    for pb in c1_problems:
+    for pb in boxes8_problems:
         for seed in (1, 2):
             o = oracle_plan(pb, seed, tree_capacity=1 << 14, **DD)
             ok = o["first_amb_iter"] == -1 or o["first_amb_iter"] >= o["iterations"]
@@ -209,12 +209,12 @@ def test_serial_dynamic_domain_slider_matches_oracle(seed):
 
 
 @pytest.mark.parametrize("seed", [1, 2])
-def test_async_halton_dynamic_domain_paths_revalidate(c1_problems, seed):
+def test_async_halton_dynamic_domain_paths_revalidate(boxes8_problems, seed):
     items = [(P.make_robot(pb.robot), P.make_env(pb.scene), pb.q_start, pb.q_goal, seed, k)
-             for k, pb in enumerate(c1_problems)]
+             for k, pb in enumerate(boxes8_problems)]
     prm = P.params(sampler=P.SAMPLER_HALTON, **DD)
     res = P.prrtc_plan_batch(items, prm)
-    for pb, r in zip(c1_problems, res):
+    for pb, r in zip(boxes8_problems, res):
         assert r["status"] == P.SOLVED
         path = r["path"].astype(np.float64)
         np.testing.assert_array_equal(r["path"][0], pb.q_start.astype(np.float32))
@@ -225,8 +225,8 @@ def test_async_halton_dynamic_domain_paths_revalidate(c1_problems, seed):
         assert bad == 0 or mc > -1e-3, (bad, mc)
 
 
-def test_sampling_params_validated(c1_problems):
-    pb = c1_problems[0]
+def test_sampling_params_validated(boxes8_problems):
+    pb = boxes8_problems[0]
     h, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
     for bad in (dict(sampler=7), dict(dd_radius=-1.0), dict(dd_radius=0.5, dd_alpha=1.0),
                 dict(dd_radius=0.5, dd_min_radius=float("nan"))):

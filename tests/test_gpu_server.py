@@ -29,7 +29,7 @@ def _built():
 
 @pytest.fixture(scope="module")
 def problems():
-    return W.problem_set("c1", 3, 1, O.accept) + W.problem_set("mixed", 6, 2000, O.accept)
+    return W.problem_set("boxes8", 3, 1, O.accept) + W.problem_set("mixed", 6, 2000, O.accept)
 
 
 def handles(pb):

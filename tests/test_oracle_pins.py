@@ -396,12 +396,12 @@ def test_plan_walled_off_goal_fails():
     assert r["status"] == 3 and r["iterations"] == 1500
 
 
-def _c1_problems(k):
-    return W.problem_set("c1", k, 1, O.accept)
+def _boxes8_problems(k):
+    return W.problem_set("boxes8", k, 1, O.accept)
 
 
 def test_plan_tree_invariants_c1():
-    for pb in _c1_problems(3):
+    for pb in _boxes8_problems(3):
         for seed in (1, 2):
             r = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=seed, want_trees=True, tree_capacity=1 << 14)
             assert r["status"] == 0
@@ -429,7 +429,7 @@ def test_plan_tree_invariants_c1():
 
 
 def test_plan_deterministic_and_seed_dependent():
-    pb = _c1_problems(1)[0]
+    pb = _boxes8_problems(1)[0]
     r1 = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=4)
     r2 = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=4)
     r3 = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=5)
@@ -438,7 +438,7 @@ def test_plan_deterministic_and_seed_dependent():
 
 
 def test_plan_batch_matches_single():
-    pbs = _c1_problems(3)
+    pbs = _boxes8_problems(3)
     rs = O.plan_batch(pbs, threads=3, seed=2)
     for pb, r in zip(pbs, rs):
         one = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=2)

@@ -73,7 +73,7 @@ def test_plan_halton_first_sample_free_space():
 
 
 def test_plan_halton_does_not_depend_on_seed_without_goal_bias():
-    pb = W.problem_set("c1", 1, 1, O.accept)[0]
+    pb = W.problem_set("boxes8", 1, 1, O.accept)[0]
     kw = dict(goal_bias=0.0, sampler=O.SAMPLER_HALTON, max_iters=3000)
     r1 = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=1, **kw)
     r2 = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=99, **kw)
@@ -83,7 +83,7 @@ def test_plan_halton_does_not_depend_on_seed_without_goal_bias():
 # ----------------------------------------------------------------- dynamic domain
 
 def _c1(k):
-    return W.problem_set("c1", k, 1, O.accept)
+    return W.problem_set("boxes8", k, 1, O.accept)
 
 
 def _same_plan(a, b):

@@ -22,7 +22,7 @@ TOL = 1e-4
 def problems():
     from paper_2503_06757_gb300 import build
     build.build()
-    return W.problem_set("c1", 2, 1, O.accept)
+    return W.problem_set("boxes8", 2, 1, O.accept)
 
 
 def _same(a, b):
