@@ -51,7 +51,7 @@ def compare(robot, scene, Q, check_centres=True, max_centre_rows=3000):
 
 
 SCENES = {
-    "c1_boxes": lambda: (W.arm7(), W.scene_random_boxes(1)),
+    "boxes8": lambda: (W.arm7(), W.scene_random_boxes(1)),
     "shelf": lambda: (W.arm7(), W.scene_shelf(1000)),
     "mixed_arm8": lambda: (W.arm8(), W.scene_mixed(2001, 60)),
     "mixed_dual14": lambda: (W.dual14(), W.scene_mixed(2002, 120, bases=W.robot_bases(W.dual14()))),
@@ -101,7 +101,7 @@ def test_empty_scene_and_no_self_pairs():
 
 @pytest.mark.parametrize("n", [0, 1, 31, 32, 33])
 def test_small_and_ragged_sizes(n):
-    robot, scene = SCENES["c1_boxes"]()
+    robot, scene = SCENES["boxes8"]()
     Q = _states(robot, max(n, 1), 5)[:n]
     if n == 0:
         valid = P.prrtc_check_states(P.make_robot(robot), P.make_env(scene), np.zeros((0, 7), np.float32))

@@ -158,7 +158,7 @@ def test_async_tree_invariants(boxes8_problems):
     assert r["status"] in (P.SOLVED, P.NO_SOLUTION)
 
 
-def test_async_success_matches_oracle_on_c1_keys(boxes8_problems):
+def test_async_success_matches_oracle_on_boxes8_keys(boxes8_problems):
     pb = boxes8_problems[1]
     g_ok = o_ok = 0
     for seed in range(1, 21):

@@ -400,7 +400,7 @@ def _boxes8_problems(k):
     return W.problem_set("boxes8", k, 1, O.accept)
 
 
-def test_plan_tree_invariants_c1():
+def test_plan_tree_invariants_boxes8():
     for pb in _boxes8_problems(3):
         for seed in (1, 2):
             r = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=seed, want_trees=True, tree_capacity=1 << 14)

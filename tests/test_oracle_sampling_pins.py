@@ -82,7 +82,7 @@ def test_plan_halton_does_not_depend_on_seed_without_goal_bias():
 
 # ----------------------------------------------------------------- dynamic domain
 
-def _c1(k):
+def _boxes8(k):
     return W.problem_set("boxes8", k, 1, O.accept)
 
 
@@ -95,7 +95,7 @@ def _same_plan(a, b):
 
 
 def test_dynamic_domain_unbounded_radius_is_plain():
-    for pb in _c1(2):
+    for pb in _boxes8(2):
         plain = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=2, want_trees=True, tree_capacity=1 << 14)
         dd = O.plan(pb.robot, pb.scene, pb.q_start, pb.q_goal, seed=2, want_trees=True, tree_capacity=1 << 14,
                     dd_radius=np.inf, dd_alpha=0.1, dd_min_radius=0.5)
