@@ -458,14 +458,12 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, i
 //            mixture parameters written into the planner's rows.
 // Operands live in global memory pre-tiled: one 64-column k-block of 128
 // activation rows, or of this CTA's weight rows, is one contiguous block in
-// the 128-byte-swizzled layout the MMA reads.  The activation tile is the
-// same for every CTA of the cluster (they all sit in one GPC, whose link to
-// L2 they share), so each CTA fetches one eighth of it with a multicast bulk
-// copy into all eight CTAs, and its own weight slice with a plain one.  A
-// stage is refilled only when the MMAs of all eight CTAs have released it
-// (their commits arrive on every CTA's `empty` barrier), and a CTA leaves
-// only after the last of those arrivals and a cluster barrier.  Each layer's writer produces exactly the k-blocks of
-// the next layer's input that its columns cover.  Between layers every thread
+// the 128-byte-swizzled layout the MMA reads.  Every CTA of the cluster reads
+// the same activation tile and its own weight slice, each with a plain bulk
+// copy into its own shared memory (no copy writes into a peer's shared
+// memory).  A stage is refilled once this CTA's MMAs have released it.  Each
+// layer's writer produces exactly the k-blocks of the next layer's input that
+// its columns cover.  Between layers every thread
 // of the cluster makes its global writes visible to the async proxy (the next
 // layer's bulk copies) and meets the cluster barrier; the barriers sit
 // outside the role branches, so every thread meets each one even after a
@@ -499,26 +497,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Bulk copy global -> shared memory of every CTA in `mask` (same offset in
-// each), completing on the barrier at the same offset in each.
-__device__ __forceinline__ void bulk_g2s_multicast(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                                   uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-// Arrive on the barrier at this offset in every CTA of `mask` once the MMAs
-// issued so far have completed.
-__device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(smem_u32(bar)),
-               "h"(mask)
-               : "memory");
 }
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -581,7 +559,7 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < kIStages; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kIC);  // one MMA commit from every CTA of the cluster
+      mbar_init(&empty[i], 1);  // this CTA's MMA commit
     }
     for (int l = 0; l < 3; ++l) mbar_init(&acc_full[l], 1);
     mbar_init(roles_done, kIThreads / 32);
@@ -670,7 +648,7 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
   }
   __syncwarp();
   // the ring held layer 1's scratch: order these generic accesses before the
-  // bulk copies (ours and the peers') that will overwrite it
+  // bulk copies that will overwrite it
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   cluster_publish();
 
@@ -696,13 +674,9 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
         if (lane == 0) {
           unsigned char* a = smem + st * kIStageBytes;
           mbar_arrive_expect_tx(&full[st], (uint32_t)(kIKB * (A_BYTES + b_bytes)));
-          // rows 16 r .. 16 r + 15 of each activation tile to every CTA; the
-          // other seven eighths arrive from the peers
-          constexpr uint32_t kPiece = A_BYTES / kIC;
-          for (int j = 0; j < kIKB; ++j)
-            bulk_g2s_multicast(a + j * A_BYTES + r * kPiece,
-                               a_src + (size_t)(ks * kIKB + j) * (BM * 128) + r * kPiece, kPiece, &full[st],
-                               (uint16_t)((1u << kIC) - 1u));
+          // the stage's 128-row activation k-blocks (contiguous), then this
+          // CTA's weight k-blocks
+          bulk_g2s(a, a_src + (size_t)ks * kIKB * (BM * 128), (uint32_t)(kIKB * A_BYTES), &full[st]);
           bulk_g2s(a + kIKB * A_BYTES, b_src + (size_t)ks * kIKB * b_bytes, kIKB * b_bytes, &full[st]);
         }
         __syncwarp();
@@ -732,7 +706,7 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
             for (int k = 0; k < BK / 16; ++k)
               mma_bf16(tmem + tcol, smem_desc(a + j * A_BYTES + 32u * k), smem_desc(b + j * b_bytes + 32u * k), idesc,
                        (ks > 0 || j > 0 || k > 0) ? 1u : 0u);
-          mma_commit_multicast(&empty[st], (uint16_t)((1u << kIC) - 1u));
+          mma_commit(&empty[st]);
         }
         __syncwarp();
       }
@@ -810,8 +784,8 @@ __global__ void __cluster_dims__(kIC, 1, 1) __launch_bounds__(kIThreads, 1)
       fence_after();
     }
   }
-  // drain: the last release of every stage from all eight CTAs has arrived
-  // here, so no peer writes into this CTA's shared memory any more
+  // drain: the last release of every stage has arrived, so no MMA reads
+  // this CTA's shared memory any more
   if (warp == 0) {
     if (lane == 0) {  // bounded waits, also after an abort
       for (int st = 0; st < kIStages && st < it_p; ++st) {
