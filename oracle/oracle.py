@@ -51,7 +51,7 @@ class OrcParams(C.Structure):
         ("problem", C.c_uint32), ("max_iters", C.c_int32), ("tree_capacity", C.c_int32),
         ("path_capacity", C.c_int32), ("gmm", _PD), ("learned_ratio", C.c_double),
         ("sampler", C.c_int32), ("halton_offset", C.c_uint32), ("dd_radius", C.c_double),
-        ("dd_alpha", C.c_double), ("dd_min_radius", C.c_double),
+        ("dd_alpha", C.c_double), ("dd_min_radius", C.c_double), ("workers", C.c_int32),
     ]
 
 
@@ -317,7 +317,7 @@ def accept(robot, scene, Q):
 DEFAULT_PARAMS = dict(range=1.0, resolution=1.0 / 32.0, goal_bias=0.05, amb_band=1e-5, amb_rel=1e-5,
                       seed=1, problem=0, max_iters=50000, tree_capacity=1 << 16, path_capacity=1 << 14,
                       gmm=None, learned_ratio=0.5, sampler=0, halton_offset=0, dd_radius=0.0,
-                      dd_alpha=0.0, dd_min_radius=0.0)
+                      dd_alpha=0.0, dd_min_radius=0.0, workers=0)
 SAMPLER_PHILOX, SAMPLER_HALTON = 0, 1
 
 
@@ -330,7 +330,7 @@ def _params(keep=None, **kw):
                     tree_capacity=int(p["tree_capacity"]), path_capacity=int(p["path_capacity"]),
                     sampler=int(p["sampler"]), halton_offset=int(p["halton_offset"]),
                     dd_radius=float(p["dd_radius"]), dd_alpha=float(p["dd_alpha"]),
-                    dd_min_radius=float(p["dd_min_radius"]))
+                    dd_min_radius=float(p["dd_min_radius"]), workers=int(p["workers"]))
     g = p.get("gmm")
     if g is not None:
         g = np.ascontiguousarray(g, dtype=np.float64)

@@ -514,6 +514,198 @@ static void build_path(plan_ctx* c, const tree* A, const tree* B, int32_t ja, in
   free(cb);
 }
 
+/* ------------------------------------------------------- lockstep rounds */
+/* The concurrent iterations of Sec. III on a fixed schedule: B workers per
+ * round, worker b running iteration r B + b against the trees as they stood
+ * when round r began.  A worker's new rows are held back until the round
+ * ends: row 0 (c_new) hangs from snapshot row nn of T_s, row k from row k-1
+ * (the greedy connect's steps). */
+typedef struct held {
+  int32_t n, cap_rows;
+  double* q;      /* [cap_rows * dof] */
+  int32_t nn;     /* snapshot row of T_s that row 0 extends */
+  int32_t nno;    /* snapshot row of T_o the connect aims at */
+  int connected;  /* the connect reached c_nno */
+  int32_t dd_node; /* node whose dynamic-domain radius the extension updates, -1 none */
+  int dd_free;     /* that extension's edge was free */
+  int64_t edges;   /* edges this iteration checked (the extension and each connect step) */
+} held;
+
+static void held_push(held* h, const double* q, int d) {
+  if (h->n == h->cap_rows) {
+    h->cap_rows = h->cap_rows ? 2 * h->cap_rows : 8;
+    h->q = (double*)realloc(h->q, (size_t)h->cap_rows * d * sizeof(double));
+  }
+  memcpy(h->q + (size_t)h->n * d, q, (size_t)d * sizeof(double));
+  h->n++;
+}
+
+/* Alg. 1 lines 4-15 for iteration `it` against the views vs / vo (T_s and T_o
+ * with their sizes at the start of the round), the new rows held in h. */
+static void lockstep_iteration(plan_ctx* ctx, const tree* vs, const tree* vo, int32_t it, held* h,
+                               double* c_rand, double* c_new, double* c_ext, double* c_tgt) {
+  const orc_robot* r = ctx->r;
+  const orc_params* p = ctx->p;
+  const int d = r->dof;
+  const double delta = p->range, resol = p->resolution;
+  h->n = 0;
+  h->nn = h->nno = -1;
+  h->connected = 0;
+  h->dd_node = -1;
+  h->dd_free = 0;
+  const int64_t edges_before = ctx->res->edges_checked;
+  ctx->it = it;
+  /* line 4: RANDOM_CONFIG (goal bias toward the opposite root, learned or uniform) */
+  int amb_k = 0;
+  int kind = orc_sample_learned(r, p->seed, p->problem, (uint32_t)it, p->goal_bias, p->gmm,
+                                p->gmm ? p->learned_ratio : 0.0, p->amb_rel, c_rand, &amb_k);
+  if (amb_k) note_amb(ctx, ORC_AMB_COMPONENT);
+  if (kind == 1) memcpy(c_rand, vo->q, (size_t)d * sizeof(double));
+  if (kind == 0 && p->sampler == ORC_SAMPLER_HALTON) {
+    orc_halton((uint32_t)it + 1u + p->halton_offset, d, c_rand);
+    for (int j = 0; j < d; ++j) c_rand[j] = r->lower[j] + c_rand[j] * (r->upper[j] - r->lower[j]);
+  }
+  /* line 5: nearest node of T_s as the round found it */
+  int32_t nn = nearest(ctx, vs, c_rand);
+  const double* c_nn = vs->q + (size_t)nn * d;
+  double dist = sqrt(dist2(c_rand, c_nn, d));
+  if (dist <= 0.0) return;
+  const int dd = p->dd_radius > 0.0;
+  if (dd && kind != 1) {
+    double rad = vs->radius[nn];
+    if (isfinite(rad) && fabs(dist - rad) <= p->amb_rel * rad) note_amb(ctx, ORC_AMB_DOMAIN);
+    if (dist > rad) {
+      ctx->res->dd_rejected++;
+      return;
+    }
+  }
+  /* Alg. 2: steer by at most delta, check ceil(len / resolution) states */
+  if (fabs(dist - delta) <= p->amb_rel * delta) note_amb(ctx, ORC_AMB_STEER);
+  double len;
+  int clamped = (dist > delta);
+  if (clamped) {
+    for (int j = 0; j < d; ++j) c_new[j] = c_nn[j] + (c_rand[j] - c_nn[j]) * (delta / dist);
+    len = delta;
+  } else {
+    memcpy(c_new, c_rand, (size_t)d * sizeof(double));
+    len = dist;
+  }
+  int32_t n_states = ceil_checked(ctx, len / resol, clamped);
+  int edge_ok = check_edge(ctx, c_nn, c_new, n_states);
+  if (dd) {
+    h->dd_node = nn;
+    h->dd_free = edge_ok;
+  }
+  h->edges = ctx->res->edges_checked - edges_before;
+  if (!edge_ok) return;
+  /* line 7, held back; a tree that is full counting this worker's own rows
+   * takes nothing more */
+  if (vs->n + h->n >= vs->cap) return;
+  held_push(h, c_new, d);
+  h->nn = nn;
+  /* line 8: nearest node of T_o (as the round found it) to c_new */
+  int32_t nno = nearest(ctx, vo, c_new);
+  memcpy(c_tgt, vo->q + (size_t)nno * d, (size_t)d * sizeof(double));
+  h->nno = nno;
+  /* lines 9-15: greedy connect, the same steps as the serial form */
+  double D = sqrt(dist2(c_tgt, c_new, d));
+  int32_t n_ext = (D > 0.0) ? ceil_checked(ctx, D / delta, 0) : 0;
+  for (int32_t i = 1; i <= n_ext; ++i) {
+    double step_len;
+    if (i < n_ext) {
+      double f = (double)i * delta / D;
+      for (int j = 0; j < d; ++j) c_ext[j] = c_new[j] + f * (c_tgt[j] - c_new[j]);
+      step_len = delta;
+    } else {
+      memcpy(c_ext, c_tgt, (size_t)d * sizeof(double));
+      step_len = D - (double)(n_ext - 1) * delta;
+    }
+    int32_t ns = ceil_checked(ctx, step_len / resol, i < n_ext);
+    if (ns < 1) ns = 1;
+    int ok = check_edge(ctx, h->q + (size_t)(h->n - 1) * d, c_ext, ns);
+    h->edges = ctx->res->edges_checked - edges_before;
+    if (!ok) return;
+    if (vs->n + h->n >= vs->cap) return;
+    held_push(h, c_ext, d);
+  }
+  h->connected = 1;
+}
+
+/* End of a round: the dynamic-domain radius updates, then every worker's
+ * held rows, in worker order.  Among the workers whose connect reached its
+ * target with all their rows in the tree, the one a concurrent run would
+ * finish first wins: fewest edges checked in its iteration, ties to the
+ * lowest worker.  Returns the winner (-1: none); *join_s is its last row's
+ * index in T_s. */
+static int lockstep_commit(tree* Ts, held* hs, int nb, const orc_params* p, int32_t* join_s) {
+  for (int b = 0; b < nb; ++b) {
+    if (hs[b].dd_node < 0) continue;
+    double* rad = &Ts->radius[hs[b].dd_node];
+    if (hs[b].dd_free) {
+      if (isfinite(*rad)) *rad *= 1.0 + p->dd_alpha;
+    } else if (isinf(*rad)) {
+      *rad = p->dd_radius;
+    } else {
+      *rad = fmax(*rad * (1.0 - p->dd_alpha), p->dd_min_radius);
+    }
+  }
+  int winner = -1;
+  for (int b = 0; b < nb; ++b) {
+    int32_t prev = hs[b].nn;
+    int all_in = 1;
+    for (int32_t k = 0; k < hs[b].n; ++k) {
+      int32_t idx = tree_add(Ts, hs[b].q + (size_t)k * Ts->d, prev);
+      if (idx < 0) {
+        all_in = 0;
+        break;
+      }
+      prev = idx;
+    }
+    if (hs[b].connected && all_in && (winner < 0 || hs[b].edges < hs[winner].edges)) {
+      winner = b;
+      *join_s = prev;
+    }
+  }
+  return winner;
+}
+
+static void plan_lockstep(plan_ctx* ctx, tree* A, tree* B, double* c_rand, double* c_new, double* c_ext,
+                          double* c_tgt) {
+  const orc_params* p = ctx->p;
+  orc_result* res = ctx->res;
+  const int32_t nw = p->workers;
+  held* hs = (held*)calloc((size_t)nw, sizeof(held));
+  res->status = ORC_NO_SOLUTION;
+  for (int64_t it0 = 0; it0 < p->max_iters; it0 += nw) {
+    /* line 3 at the start of the round: every worker extends the smaller tree */
+    int s_is_a = (A->n <= B->n);
+    tree* Ts = s_is_a ? A : B;
+    tree* To = s_is_a ? B : A;
+    const tree vs = *Ts, vo = *To;  /* the trees as the round found them */
+    int nb = (int)((p->max_iters - it0) < nw ? (p->max_iters - it0) : nw);
+    for (int b = 0; b < nb; ++b)
+      lockstep_iteration(ctx, &vs, &vo, (int32_t)(it0 + b), &hs[b], c_rand, c_new, c_ext, c_tgt);
+    res->iterations = (int32_t)(it0 + nb);
+    int32_t js = -1;
+    int w = lockstep_commit(Ts, hs, nb, p, &js);
+    if (w >= 0) {
+      /* line 16: the winner's last row coincides with row nno of T_o */
+      res->join_a = s_is_a ? js : hs[w].nno;
+      res->join_b = s_is_a ? hs[w].nno : js;
+      res->n_a = A->n;
+      res->n_b = B->n;
+      build_path(ctx, A, B, res->join_a, res->join_b);
+      break;
+    }
+  }
+  if (res->status == ORC_NO_SOLUTION) {
+    res->n_a = A->n;
+    res->n_b = B->n;
+  }
+  for (int b = 0; b < nw; ++b) free(hs[b].q);
+  free(hs);
+}
+
 int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
                  const double* q_goal, const orc_params* p, orc_result* res) {
   int d = r->dof;
@@ -568,6 +760,10 @@ int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
   tree_add(&A, q_start, -1);
   tree_add(&B, q_goal, -1);
 
+  if (p->workers >= 1) {
+    plan_lockstep(&ctx, &A, &B, c_rand, c_new, c_ext, c_tgt);
+    goto done;
+  }
   const double delta = p->range, resol = p->resolution;
   for (int32_t it = 0; it < p->max_iters; ++it) {
     ctx.it = it;

@@ -8,7 +8,9 @@
  *
  * What it computes (pRRTC, Huang et al. 2025):
  *   - Alg. 1 (pRRTC top level) executed serially: balanced tree choice,
- *     sampling, nearest neighbour, pEXTEND, insertion, greedy connect, PATH.
+ *     sampling, nearest neighbour, pEXTEND, insertion, greedy connect, PATH;
+ *     or by B workers in lockstep rounds, a deterministic schedule of the
+ *     concurrent iterations of Sec. III.
  *   - Alg. 2 (pEXTEND): steer by at most delta, then check the interpolated
  *     states of the edge at the fixed collision-checking resolution.
  *   - Sec. III-A: collision checking of a sphere model against cuboids,
@@ -24,7 +26,10 @@
  *   orc_fk             - closed-form tip positions of 1-, 2- and 3-link chains.
  *   orc_sd_box/cyl/sph - brute-force surface/volume sampling on tiny inputs.
  *   orc_plan           - tree invariants, obstacle-free and walled-off special
- *                        cases, grid-BFS reachability of a point robot.
+ *                        cases, grid-BFS reachability of a point robot; the
+ *                        lockstep form: one worker reproduces the serial
+ *                        trees, the obstacle-free round in closed form, the
+ *                        round structure of every tree it builds.
  *   orc_occupancy      - closed-form voxel sets of a sphere and a box.
  *   orc_voxelize / orc_esdf / orc_esdf_query - closed-form fields of one
  *                        occupied voxel, of a half-space and of empty / full
@@ -136,6 +141,16 @@ typedef struct orc_params {
   double dd_radius;
   double dd_alpha;
   double dd_min_radius;
+  /* concurrent workers (Sec. III: iterations of Alg. 1 run in parallel
+   * against two shared trees).  0: serial Alg. 1.  B >= 1: lockstep
+   * rounds (B = 1 gives the serial trees by a separate route) -- in round r, worker b runs iteration r B + b (sampling, nearest
+   * neighbour, pEXTEND and the greedy connect) against the trees as they
+   * stood when the round began, holding its new rows back; at the end of the
+   * round the held rows are appended in worker order.  Of the workers whose
+   * connect reached its target (with every row they added in the tree), the
+   * one a concurrent run would finish first -- fewest edges checked in its
+   * iteration, ties to the lowest worker -- ends the search with PATH. */
+  int32_t workers;
 } orc_params;
 
 typedef struct orc_result {
@@ -228,7 +243,8 @@ double orc_clearance(const orc_robot* r, const orc_env* e, const double* q,
 void orc_check_states(const orc_robot* r, const orc_env* e, const double* Q, int32_t n,
                       uint8_t* free_out, double* clearance_out);
 
-/* Serial pRRTC (Alg. 1 with Alg. 2).  Returns res->status. */
+/* pRRTC (Alg. 1 with Alg. 2): serial, or B workers in lockstep rounds
+ * (p->workers).  Returns res->status. */
 int32_t orc_plan(const orc_robot* r, const orc_env* e, const double* q_start,
                  const double* q_goal, const orc_params* p, orc_result* res);
 
