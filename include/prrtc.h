@@ -121,6 +121,17 @@ typedef struct prrtc_robot prrtc_robot;
 /* ------------------------------------------------------------ parameters */
 #define PRRTC_MODE_ASYNC 0   /* blocks x warps run Alg. 1 iterations concurrently (Sec. III) */
 #define PRRTC_MODE_SERIAL 1  /* one warp runs the iterations in order: the serial Alg. 1   */
+/* B = params.workers concurrent iterations per round on a fixed schedule (the
+ * concurrency of Sec. III made deterministic): in round r, worker b runs
+ * iteration r B + b -- sampling, nearest neighbour, pEXTEND and the greedy
+ * connect -- against both trees as they stood when the round began and holds
+ * its new rows back; at the end of the round every worker's rows are appended
+ * in worker order.  Of the workers whose connect reached its target with all
+ * their rows in the tree, the one that checked the fewest edges in its
+ * iteration (ties: lowest b) wins, as the first connection to finish would in
+ * a concurrent run.  B = 1 is the serial Alg. 1.  The trees equal those of the
+ * FP64 oracle's lockstep form outside the 1e-5 m clearance band. */
+#define PRRTC_MODE_LOCKSTEP 2
 
 typedef struct prrtc_params {
   float range;            /* delta: extension range in configuration space (L2)        */
@@ -151,7 +162,11 @@ typedef struct prrtc_params {
                              by (1 + dd_alpha) after a free extension and shrinks by
                              (1 - dd_alpha), not below dd_min_radius, after a collision */
   float dd_min_radius;
-  int32_t reserved[3];
+  int32_t workers;        /* PRRTC_MODE_LOCKSTEP: concurrent iterations per round, 1..1024
+                             (other modes ignore it); warps_per_block 0 = min(workers, 8)
+                             warps per problem, each running workers / warps iterations
+                             of a round in turn                                       */
+  int32_t reserved[2];
 } prrtc_params;
 
 #define PRRTC_SAMPLER_PHILOX 0

@@ -98,12 +98,17 @@ struct DeviceCtx {
   float* d_packed = nullptr;
   float* h_packed = nullptr;
   size_t packed_cap = 0;
+  float* d_held = nullptr;  // lockstep mode: rows each worker of a round holds back
+  size_t held_cap = 0;
+  int* d_held_meta = nullptr;
+  size_t held_meta_cap = 0;
   float* d_gmm = nullptr;   // [slots][kGmmStride] learned mixtures
   float* h_gmm = nullptr;
   size_t gmm_cap = 0;
   // CUDA graph of the launch sequence, keyed by everything it bakes in
   struct GraphKey {
-    int n, grid, warps, smem, robot_bytes, env_bytes, stage_bytes, max_spheres, max_pairs, max_env, gen, head;
+    int n, grid, warps, smem, robot_bytes, env_bytes, stage_bytes, max_spheres, max_pairs, max_env, gen, head,
+        lockstep;
     bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
   };
   GraphKey gkey{};
@@ -247,7 +252,10 @@ int validate_params(const prrtc_params* p) {
   if (p->tree_capacity < 2) return fail(PRRTC_ERR_INVALID_ARG, "tree_capacity must be >= 2");
   if (p->tree_capacity > (1 << 26)) return fail(PRRTC_ERR_INVALID_ARG, "tree_capacity too large");
   if (p->path_capacity < 2) return fail(PRRTC_ERR_INVALID_ARG, "path_capacity must be >= 2");
-  if (p->mode != PRRTC_MODE_ASYNC && p->mode != PRRTC_MODE_SERIAL) return fail(PRRTC_ERR_INVALID_ARG, "unknown mode");
+  if (p->mode != PRRTC_MODE_ASYNC && p->mode != PRRTC_MODE_SERIAL && p->mode != PRRTC_MODE_LOCKSTEP)
+    return fail(PRRTC_ERR_INVALID_ARG, "unknown mode");
+  if (p->mode == PRRTC_MODE_LOCKSTEP && (p->workers < 1 || p->workers > 1024))
+    return fail(PRRTC_ERR_INVALID_ARG, "lockstep workers must be in 1..1024");
   if (p->blocks < 0 || p->warps_per_block < 0 || p->warps_per_block > 16)
     return fail(PRRTC_ERR_INVALID_ARG, "blocks / warps_per_block out of range");
   if (p->time_limit_s < 0.0) return fail(PRRTC_ERR_INVALID_ARG, "time_limit_s must be >= 0");
@@ -961,6 +969,29 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     }
     c->gmm_cap = (size_t)n;
   }
+  // lockstep mode: each problem's held rows, [workers][held_rows x dpad].  Every
+  // node lies in the box spanned by the joint limits, the start and the goal
+  // (samples lie in the limits, steps are convex combinations), so a connect
+  // takes at most ceil(diagonal / range) steps.
+  std::vector<int> held_rows(n, 0);
+  std::vector<size_t> held_off(n + 1, 0);
+  if (params->mode == PRRTC_MODE_LOCKSTEP) {
+    for (int p = 0; p < n; ++p) {
+      const prrtc_problem& pb = problems[p];
+      const RobotHeader& H = pb.robot->h->h;
+      double diag2 = 0.0;
+      for (int j = 0; j < H.dof; ++j) {
+        const double lo = std::min({(double)H.lo[j], (double)pb.q_start[j], (double)pb.q_goal[j]});
+        const double hi = std::max({(double)H.lo[j] + (double)H.span[j], (double)pb.q_start[j], (double)pb.q_goal[j]});
+        diag2 += (hi - lo) * (hi - lo);
+      }
+      held_rows[p] = 3 + (int)std::ceil(std::sqrt(diag2) / (double)params->range * (1.0 + 1e-5));
+      held_off[p + 1] = held_off[p] + (size_t)params->workers * held_rows[p] * H.dpad;
+    }
+    if (held_off[n] > ((size_t)1 << 28)) return fail(PRRTC_ERR_OOM, "lockstep scratch above 1 GiB");
+    if ((rc = grow_device(&c->d_held, &c->held_cap, held_off[n]))) return rc;
+    if ((rc = grow_device(&c->d_held_meta, &c->held_meta_cap, (size_t)n * params->workers * kHeldMeta))) return rc;
+  }
   int max_spheres = 1, max_pairs = 0, max_env = 0;
   for (int p = 0; p < n; ++p) {
     const prrtc_problem& pb = problems[p];
@@ -988,6 +1019,11 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     D.key_hi = (uint32_t)(pb.seed >> 32);
     D.pid = pb.problem_id;
     D.gmm = (pb.gmm || (proposals && proposals[p])) ? c->d_gmm + (size_t)p * kGmmStride : nullptr;
+    if (params->mode == PRRTC_MODE_LOCKSTEP) {
+      D.held = c->d_held + held_off[p];
+      D.held_meta = c->d_held_meta + (size_t)p * params->workers * kHeldMeta;
+      D.held_rows = held_rows[p];
+    }
     for (int j = 0; j < H.dof; ++j) {
       D.q_start[j] = pb.q_start[j];
       D.q_goal[j] = pb.q_goal[j];
@@ -1013,7 +1049,8 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       warps = it->second.second;
     }
   }
-  const PlanLaunch cfg = plan_launch_config(n, params->mode, blocks, warps, max_spheres, max_pairs, max_env, c->sms);
+  const PlanLaunch cfg =
+      plan_launch_config(n, params->mode, blocks, warps, max_spheres, max_pairs, max_env, c->sms, params->workers);
   if (cfg.smem > 227 * 1024) return fail(PRRTC_ERR_UNSUPPORTED, "robot + environment exceed shared memory");
   const int head_rows = (n == 1) ? std::min(kHeadRows, params->path_capacity) : 0;
 
@@ -1106,7 +1143,8 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     if ((rc = enqueue(false))) return rc;
   } else {
     const DeviceCtx::GraphKey key{n, cfg.grid, cfg.warps, cfg.smem, cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes,
-                                  max_spheres, max_pairs, max_env, c->arena_gen, head_rows * c->h_desc[0].dof};
+                                  max_spheres, max_pairs, max_env, c->arena_gen, head_rows * c->h_desc[0].dof,
+                                  cfg.lockstep ? 1 : 0};
     if (!c->gexec || !(c->gkey == key)) {
       if (c->gexec) cudaGraphExecDestroy(c->gexec);
       c->gexec = nullptr;
@@ -1274,6 +1312,8 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
   if (!problems || n < 1 || !params || trials < 1 || !best) return fail(PRRTC_ERR_INVALID_ARG, "bad autotune arguments");
   int rc = validate_params(params);
   if (rc) return rc;
+  if (params->mode == PRRTC_MODE_LOCKSTEP)
+    return fail(PRRTC_ERR_INVALID_ARG, "lockstep mode runs a fixed schedule: nothing to tune");
   DeviceCtx* c = nullptr;
   if ((rc = current_ctx(&c))) return rc;
   int resident = 0;

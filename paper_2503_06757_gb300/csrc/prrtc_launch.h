@@ -15,11 +15,12 @@ constexpr int kRootParent = -2;    // parent of a tree root
 constexpr int kMixK = 8;           // learned mixture components
 constexpr int kGmmStride = kMixK + 2 * kMixK * kMaxDof;  // logits | means [8][16] | log-sigmas [8][16]
 constexpr int kUnsetParent = -1;   // parent slot not written yet (0xFF fill)
+constexpr int kHeldMeta = 8;       // ints per lockstep worker record
 
 // Launch-wide parameters and bookkeeping (one per planning launch).
 struct PlanGlobals {
   int n_problems;
-  int mode;              // 0 async, 1 serial
+  int mode;              // PRRTC_MODE_*
   int max_iters;
   int n_full;            // ceil(range / resolution): states of a full-length step
   float range;
@@ -40,6 +41,7 @@ struct PlanGlobals {
   float dd_radius;       // dynamic domain: 0 = off
   float dd_alpha;
   float dd_min_radius;
+  int workers;           // lockstep mode: iterations per round (B)
 };
 
 // Check of the sampler and dynamic-domain fields of a parameter block; null
@@ -70,6 +72,7 @@ inline void globals_from_params(PlanGlobals& G, const prrtc_params& p) {
   G.dd_radius = p.dd_radius;
   G.dd_alpha = p.dd_alpha;
   G.dd_min_radius = p.dd_min_radius;
+  G.workers = p.mode == PRRTC_MODE_LOCKSTEP ? p.workers : 1;
 }
 
 // Per-problem inputs (uploaded every call).
@@ -89,6 +92,11 @@ struct ProblemDesc {
   uint32_t key_lo, key_hi;
   uint32_t pid;
   const float* gmm;      // learned mixture (kGmmStride floats, device) or null
+  // lockstep mode: the rows each worker of a round holds back, [workers][held_rows * dpad],
+  // and per worker kHeldMeta ints (see LockstepHeld in prrtc_plan.cu); null otherwise
+  float* held;
+  int* held_meta;
+  int held_rows;         // rows one iteration can add: 1 + the most connect steps
   float q_start[kMaxDof];
   float q_goal[kMaxDof];
 };
@@ -130,14 +138,16 @@ cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, in
 struct PlanLaunch {
   int grid;
   int warps;
+  bool lockstep;         // lockstep_kernel (PRRTC_MODE_LOCKSTEP) instead of plan_kernel
   int smem;
   int robot_bytes;
   int env_bytes;
   int stage_bytes;
 };
 
+// workers: the lockstep round size (PRRTC_MODE_LOCKSTEP), else ignored.
 PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, int max_spheres, int max_pairs,
-                              int max_env_f4, int sm_count);
+                              int max_env_f4, int sm_count, int workers = 1);
 
 cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
                         cudaStream_t stream);

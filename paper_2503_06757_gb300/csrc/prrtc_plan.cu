@@ -17,6 +17,7 @@
 //     all its coordinates are final (each word changes NaN -> value once).
 //   * Serial mode runs one worker per problem; it performs exactly the
 //     iterations of the serial Alg. 1 in order.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <map>
@@ -370,20 +371,45 @@ __device__ __forceinline__ float mixture_draw(const float* __restrict__ gmm, con
   return fminf(fmaxf(fmaf(0.5f * (un + 1.f), span, lo), lo), lo + span);
 }
 
+// Alg. 1 line 4, RANDOM_CONFIG for iteration `it` (element `lane` of the
+// sample): Philox words of counter {pid, it, blk, 0}, lane l holding word l
+// (blocks 0..7).  Word 0 draws the goal bias (the root of T_o, tree `o`),
+// words 1..dof the uniform configuration; with a learned mixture, word 20
+// draws learned-vs-uniform, word 21 the component, words 22.. Box-Muller
+// pairs.  The Halton sampler takes point it + 1 + offset instead of the
+// uniform words (point 0 is the origin of the unit cube).
+__device__ __forceinline__ float random_config(const Ctx& c, int it, int o, bool* goal_sample) {
+  const PlanGlobals* g = c.g;
+  const ProblemDesc* D = c.D;
+  const RobotHeader* R = c.R;
+  const int lane = c.lane, dof = D->dof;
+  const uint2 key = make_uint2(D->key_lo, D->key_hi);
+  const uint4 ph = philox4x32_10(make_uint4(D->pid, (uint32_t)it, (uint32_t)(lane >> 2), 0u), key);
+  const uint32_t w = ((lane & 3) == 0) ? ph.x : ((lane & 3) == 1) ? ph.y : ((lane & 3) == 2) ? ph.z : ph.w;
+  const uint32_t w0 = __shfl_sync(kFull, w, 0);
+  const uint32_t wj = __shfl_sync(kFull, w, (lane + 1) & 31);
+  const uint32_t wl = __shfl_sync(kFull, w, 20);
+  *goal_sample = (w0 >> 8) < g->bias_thr;
+  if (*goal_sample) return row_elem(D->nodes[o], 0, D->dpad, lane);
+  if (D->gmm && (wl >> 8) < g->learned_thr) return mixture_draw(D->gmm, R, D->pid, (uint32_t)it, key, w, lane, dof);
+  if (g->sampler == PRRTC_SAMPLER_HALTON)
+    return (lane < dof) ? fmaf(halton_coord((uint32_t)it + 1u + g->halton_offset, lane), R->span[lane], R->lo[lane])
+                        : 0.f;
+  return (lane < dof) ? fmaf(u24(wj), R->span[lane], R->lo[lane]) : 0.f;
+}
+
 // Alg. 1 iterations of one worker warp on one problem until it is solved,
 // out of budget or out of time.  Lane j holds element j of every vector.
 __device__ void worker(const Ctx& c) {
   const PlanGlobals* g = c.g;
   const ProblemDesc* D = c.D;
   ProblemState* S = c.S;
-  const RobotHeader* R = c.R;
   const int lane = c.lane;
-  const int dof = D->dof, dpad = D->dpad;
+  const int dpad = D->dpad;
   const int cap = D->cap;
   const float range = g->range;
   const float res = g->resolution;
   const int n_full = g->n_full;
-  const uint2 key = make_uint2(D->key_lo, D->key_hi);
   const bool mine = lane < dpad;
   for (;;) {
     int stop = 0, it = 0;
@@ -416,29 +442,9 @@ __device__ void worker(const Ctx& c) {
     const int o = 1 - s;
     const int n_s = s ? nb : na;
 
-    // line 4: RANDOM_CONFIG -- Philox words of counter {pid, it, blk, 0}:
-    // lane l holds word l (blocks 0..7).  Word 0 draws the goal bias, words
-    // 1..dof the uniform configuration; with a learned mixture, word 20 draws
-    // learned-vs-uniform, word 21 the component, words 22.. Box-Muller pairs.
-    const uint4 ph = philox4x32_10(make_uint4(D->pid, (uint32_t)it, (uint32_t)(lane >> 2), 0u), key);
-    const uint32_t w = ((lane & 3) == 0) ? ph.x : ((lane & 3) == 1) ? ph.y : ((lane & 3) == 2) ? ph.z : ph.w;
-    const uint32_t w0 = __shfl_sync(kFull, w, 0);
-    const uint32_t wj = __shfl_sync(kFull, w, (lane + 1) & 31);
-    const uint32_t wl = __shfl_sync(kFull, w, 20);
-    float crand;
-    const bool goal_sample = (w0 >> 8) < g->bias_thr;
-    if (goal_sample) {
-      crand = row_elem(D->nodes[o], 0, dpad, lane);  // goal bias: root of T_o
-    } else if (D->gmm && (wl >> 8) < g->learned_thr) {
-      crand = mixture_draw(D->gmm, R, D->pid, (uint32_t)it, key, w, lane, dof);
-    } else if (g->sampler == PRRTC_SAMPLER_HALTON) {
-      // Halton point it + 1 + offset (point 0 is the origin of the unit cube)
-      crand = (lane < dof)
-                  ? fmaf(halton_coord((uint32_t)it + 1u + g->halton_offset, lane), R->span[lane], R->lo[lane])
-                  : 0.f;
-    } else {
-      crand = (lane < dof) ? fmaf(u24(wj), R->span[lane], R->lo[lane]) : 0.f;
-    }
+    // line 4: RANDOM_CONFIG
+    bool goal_sample;
+    const float crand = random_config(c, it, o, &goal_sample);
     if (mine) c.v.rnd[lane] = crand;
     __syncwarp();
 
@@ -559,11 +565,241 @@ __device__ void worker(const Ctx& c) {
   }
 }
 
+// ------------------------------------------------------------------ lockstep rounds
+// The concurrency of Sec. III on a fixed schedule (PRRTC_MODE_LOCKSTEP): in
+// round r, worker b runs iteration r B + b against the trees as they stood
+// when the round began, holding its new rows back in its slice of D->held;
+// at the end of the round the rows are appended in worker order and the
+// connected worker that checked the fewest edges (ties: lowest b) wins.
+// Virtual worker b runs on warp b % warps of the problem's block.
+
+// One worker's record for a round (kHeldMeta ints of D->held_meta).
+struct LockstepHeld {
+  int n;          // rows held back
+  int nn;         // snapshot row of T_s the first row extends
+  int nno;        // snapshot row of T_o the connect aims at
+  int connected;  // the connect reached c_nno
+  int edges;      // edges this iteration checked
+  int dd_node;    // node whose dynamic-domain radius the extension updates, -1 none
+  int dd_free;    // that edge was free
+  int offset;     // first row of this worker among the round's appended rows
+};
+static_assert(sizeof(LockstepHeld) == kHeldMeta * sizeof(int), "lockstep record layout");
+
+// Alg. 1 lines 4-15 of iteration `it` against T_s = tree s (its first n_s
+// rows) and T_o (its first n_o rows); new rows go to `rows` (held_rows x
+// dpad), the outcome to *h (written by lane 0).
+__device__ void lockstep_iteration(const Ctx& c, int it, int s, int n_s, int n_o, LockstepHeld* h, float* rows) {
+  const PlanGlobals* g = c.g;
+  const ProblemDesc* D = c.D;
+  const int lane = c.lane, dpad = D->dpad, cap = D->cap;
+  const int o = 1 - s;
+  const bool mine = lane < dpad;
+  const float range = g->range, res = g->resolution;
+  const bool dd = g->dd_radius > 0.f;
+  int n = 0, nn = -1, nno = -1, connected = 0, edges = 0, dd_node = -1, dd_free = 0;
+  if (lane == 0) c.cnt->iterations++;
+  do {
+    bool goal_sample;
+    const float crand = random_config(c, it, o, &goal_sample);
+    if (mine) c.v.rnd[lane] = crand;
+    __syncwarp();
+    // line 5: nearest node of T_s as the round found it
+    nn = nearest(D->nodes[s], n_s, dpad, c.v.rnd, lane, &c.cnt->nn_nodes);
+    const float cnn = row_elem(D->nodes[s], nn, dpad, lane);
+    const float diff = crand - cnn;
+    const float d2 = warp_sum(diff * diff);
+    if (!(d2 > 0.f)) break;
+    const float dist = __fsqrt_rn(d2);
+    if (dd && !goal_sample && dist > __ldcg(D->radius[s] + nn)) {  // NaN radius: unbounded
+      if (lane == 0) c.cnt->dd_rejected++;
+      break;
+    }
+    float cnew;
+    int N;
+    if (dist > range) {
+      cnew = fmaf(diff, __fdiv_rn(range, dist), cnn);
+      N = g->n_full;
+    } else {
+      cnew = crand;
+      N = (int)ceilf(__fdiv_rn(dist, res));
+    }
+    if (N < 1) N = 1;
+    if (mine) {
+      c.v.a[lane] = cnn;
+      c.v.b[lane] = cnew;
+    }
+    __syncwarp();
+    // phase 0: the extension (Alg. 2); phase i >= 1: greedy connect step i
+    float ct = 0.f, Dd = 0.f, bval = cnew;
+    int n_ext = 0;
+    for (int phase = 0;; ++phase) {
+      const bool free_edge = edge_free(c, N);
+      ++edges;
+      if (phase == 0 && dd) {
+        dd_node = nn;
+        dd_free = free_edge ? 1 : 0;
+      }
+      if (!free_edge) break;
+      // line 7 / 13, held back; a tree full counting this worker's rows takes no more
+      if (n_s + n >= cap) break;
+      if (n >= D->held_rows) {  // the host sizes held_rows for the longest connect
+        if (lane == 0) atomicExch(&const_cast<PlanGlobals*>(g)->error, PRRTC_ERR_DEVICE_INDEX);
+        break;
+      }
+      if (mine) __stcg(rows + (size_t)n * dpad + lane, bval);
+      ++n;
+      if (phase == 0) {
+        // line 8: nearest node of T_o (as the round found it) to c_new
+        nno = nearest(D->nodes[o], n_o, dpad, c.v.b, lane, &c.cnt->nn_nodes);
+        ct = row_elem(D->nodes[o], nno, dpad, lane);
+        const float dv = ct - cnew;
+        Dd = __fsqrt_rn(warp_sum(dv * dv));
+        n_ext = (Dd > 0.f) ? (int)ceilf(__fdiv_rn(Dd, range)) : 0;
+      }
+      if (phase == n_ext) {
+        connected = 1;
+        break;
+      }
+      const int i = phase + 1;
+      if (i < n_ext) {
+        bval = fmaf(__fdiv_rn((float)i * range, Dd), ct - cnew, cnew);
+        N = g->n_full;
+      } else {
+        bval = ct;
+        const float len = Dd - (float)(n_ext - 1) * range;
+        N = (int)ceilf(__fdiv_rn(len, res));
+        if (N < 1) N = 1;
+      }
+      if (mine) {
+        c.v.a[lane] = c.v.b[lane];
+        c.v.b[lane] = bval;
+      }
+      __syncwarp();
+    }
+  } while (false);
+  __syncwarp();
+  if (lane == 0) {
+    h->n = n;
+    h->nn = nn;
+    h->nno = nno;
+    h->connected = connected;
+    h->edges = edges;
+    h->dd_node = dd_node;
+    h->dd_free = dd_free;
+  }
+  __syncwarp();
+}
+
+// Rounds of one problem by every warp of the block (block-uniform control
+// flow: every thread meets every barrier).
+__device__ void lockstep_problem(const Ctx& c, int warp, int nwarps) {
+  __shared__ int s_it0, s_s, s_ns, s_no, s_stop, s_nb, s_winner, s_total;
+  PlanGlobals* g = const_cast<PlanGlobals*>(c.g);
+  const ProblemDesc* D = c.D;
+  ProblemState* S = c.S;
+  LockstepHeld* meta = reinterpret_cast<LockstepHeld*>(D->held_meta);
+  const int B = g->workers, dpad = D->dpad, cap = D->cap, lane = c.lane;
+  const size_t held_stride = (size_t)D->held_rows * dpad;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int stop = ld_volatile(&S->done) | ld_volatile(&S->solved) | (slice_over(g) ? 1 : 0);
+      const int it0 = S->iter;
+      if (!stop && it0 >= g->max_iters) {
+        atomicExch(&S->done, 1);
+        stop = 1;
+      }
+      if (!stop && g->time_limit_ns && globaltimer_ns() - g->t0 > g->time_limit_ns) {
+        S->timed_out = 1;
+        atomicExch(&S->done, 1);
+        stop = 1;
+      }
+      // line 3 at the start of the round: every worker extends the smaller tree
+      const int na = min(S->count[0], cap), nb = min(S->count[1], cap);
+      s_s = (na <= nb) ? 0 : 1;
+      s_ns = s_s ? nb : na;
+      s_no = s_s ? na : nb;
+      s_it0 = it0;
+      s_nb = min(B, g->max_iters - it0);
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int it0 = s_it0, s = s_s, n_s = s_ns, n_o = s_no, nb = s_nb;
+    for (int b = warp; b < nb; b += nwarps)
+      lockstep_iteration(c, it0 + b, s, n_s, n_o, meta + b, D->held + (size_t)b * held_stride);
+    __syncthreads();
+    // end of the round: radius updates and row offsets in worker order, the winner
+    if (threadIdx.x == 0) {
+      float* rad = D->radius[s];
+      int total = 0, winner = -1;
+      for (int b = 0; b < nb; ++b) {
+        LockstepHeld& h = meta[b];
+        if (h.dd_node >= 0) {
+          const float r = __ldcg(rad + h.dd_node);
+          if (h.dd_free) {
+            if (!isnan(r)) __stcg(rad + h.dd_node, r * (1.f + g->dd_alpha));
+          } else {
+            __stcg(rad + h.dd_node, isnan(r) ? g->dd_radius : fmaxf(r * (1.f - g->dd_alpha), g->dd_min_radius));
+          }
+        }
+        h.offset = total;
+        total += h.n;
+        const bool all_in = n_s + total <= cap;
+        if (h.connected && all_in && (winner < 0 || h.edges < meta[winner].edges)) winner = b;
+      }
+      s_total = total;
+      s_winner = winner;
+      S->iter = it0 + nb;
+    }
+    __syncthreads();
+    // append the held rows: row k of worker b at n_s + offset + k, hanging
+    // from the worker's previous row (k > 0) or its snapshot row nn
+    for (int b = warp; b < nb; b += nwarps) {
+      const LockstepHeld h = meta[b];
+      const float* src = D->held + (size_t)b * held_stride;
+      for (int k = 0; k < h.n; ++k) {
+        const int idx = n_s + h.offset + k;
+        if (idx >= cap) {
+          if (lane == 0) c.cnt->insert_fail++;
+          break;
+        }
+        if (lane == 0) __stcg(D->parent[s] + idx, k == 0 ? h.nn : idx - 1);
+        if (lane < dpad) __stcg(D->nodes[s] + (size_t)idx * dpad + lane, __ldcg(src + (size_t)k * dpad + lane));
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) S->count[s] = min(n_s + s_total, cap);
+    __syncthreads();
+    const int w = s_winner;
+    if (w >= 0) {
+      if (warp == 0) {
+        const LockstepHeld h = meta[w];
+        const int join_s = n_s + h.offset + h.n - 1;
+        if (lane == 0) {
+          S->solved = 1;
+          S->t_solve = globaltimer_ns();
+          S->s_tree = s;
+          S->join_s = join_s;
+          S->join_o = h.nno;
+        }
+        __syncwarp();
+        extract_path(c, s, join_s, h.nno);
+        __threadfence();
+        if (lane == 0) atomicExch(&S->done, 1);
+      }
+      __syncthreads();
+      break;
+    }
+  }
+}
+
 __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
   const int P = g->n_problems;
   if (slice_over(g)) return -1;
   const int t = atomicAdd(&g->cursor, 1);
-  if (g->mode == PRRTC_MODE_SERIAL) return t < P ? (g->active ? g->active[t] : t) : -1;
+  if (g->mode != PRRTC_MODE_ASYNC) return t < P ? (g->active ? g->active[t] : t) : -1;
   for (int k = 0; k < P; ++k) {
     const int i = (t + k) % P;
     const int p = g->active ? g->active[i] : i;
@@ -572,8 +808,13 @@ __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
   return -1;
 }
 
-__global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
-                            ProblemState* __restrict__ states, int robot_bytes, int env_bytes, int warp_floats) {
+// The planner launch: blocks take problems from the work queue, stage each
+// problem's robot and environment in shared memory and run its workers --
+// independent warps (async and serial modes) or the lockstep rounds.
+template <bool kLockstep>
+__device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
+                                          ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
+                                          int warp_floats) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_prob;
@@ -645,7 +886,10 @@ __global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const 
     c.v.b = vecs + 2 * kMaxDof;
     c.stage = vecs + kWarpVecFloats;
     c.lane = lane;
-    worker(c);
+    if constexpr (kLockstep)
+      lockstep_problem(c, warp, blockDim.x >> 5);
+    else
+      worker(c);
     // flush this warp's counters into the problem
     __syncwarp();
     if (lane < 14) {
@@ -660,6 +904,18 @@ __global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const 
     }
     __syncthreads();
   }
+}
+
+__global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
+                                             ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
+                                             int warp_floats) {
+  plan_body<false>(g, descs, states, robot_bytes, env_bytes, warp_floats);
+}
+
+__global__ void __maxnreg__(128) lockstep_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
+                                                 ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
+                                                 int warp_floats) {
+  plan_body<true>(g, descs, states, robot_bytes, env_bytes, warp_floats);
 }
 
 // Reject a start or goal in collision (Alg. 1 lines 1-2): warp 0 checks the
@@ -802,41 +1058,49 @@ cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, in
 
 // Resident planner blocks per SM for a block shape, cached: the occupancy
 // query and the shared-memory attribute cost host time on every call.
-int resident_blocks_per_sm(int warps, int smem) {
+int resident_blocks_per_sm(int warps, int smem, bool lockstep) {
   static std::mutex mu;
   static std::map<std::pair<int, int>, int> cache;
-  static std::map<int, int> attr_smem;  // per device: the attribute value set so far
+  static std::map<int, int> attr_smem;  // per (device, kernel): the attribute value set so far
   int dev = 0;
   cudaGetDevice(&dev);
-  const std::pair<int, int> key{warps + 64 * dev, smem};
+  const int kid = 2 * dev + (lockstep ? 1 : 0);
+  const std::pair<int, int> key{warps + 64 * kid, smem};
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  if (smem > attr_smem[dev]) {
-    cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr_smem[dev] = smem;
+  const void* fn = lockstep ? reinterpret_cast<const void*>(lockstep_kernel) : reinterpret_cast<const void*>(plan_kernel);
+  if (smem > attr_smem[kid]) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr_smem[kid] = smem;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel, warps * 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
   if (per_sm < 1) per_sm = 1;
   cache.emplace(key, per_sm);
   return per_sm;
 }
 
 PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, int max_spheres, int max_pairs,
-                              int max_env_f4, int sm_count) {
+                              int max_env_f4, int sm_count, int workers) {
   PlanLaunch c{};
-  c.warps = (mode == PRRTC_MODE_SERIAL) ? 1 : (warps > 0 ? warps : 4);
+  c.lockstep = mode == PRRTC_MODE_LOCKSTEP;
+  if (mode == PRRTC_MODE_SERIAL)
+    c.warps = 1;
+  else if (c.lockstep)  // no more warps than the round has workers
+    c.warps = std::min(warps > 0 ? warps : 8, std::max(workers, 1));
+  else
+    c.warps = warps > 0 ? warps : 4;
   if (c.warps > 16) c.warps = 16;
   c.robot_bytes = robot_smem_bytes((max_pairs + 3) & ~3);
   c.env_bytes = max_env_f4 * 16;
   c.stage_bytes = (int)sizeof(WarpCount) + kWarpVecFloats * (int)sizeof(float) + stage_bytes(max_spheres);  // per warp
   c.smem = c.robot_bytes + c.env_bytes + c.warps * c.stage_bytes;
-  const int per_sm = resident_blocks_per_sm(c.warps, c.smem);
+  const int per_sm = resident_blocks_per_sm(c.warps, c.smem, c.lockstep);
   int resident = per_sm * sm_count;
   if (blocks > 0) {
     c.grid = blocks;
-  } else if (mode == PRRTC_MODE_SERIAL) {
+  } else if (mode != PRRTC_MODE_ASYNC) {  // one block per problem
     c.grid = n_problems < resident ? n_problems : resident;
   } else if (n_problems == 1) {
     // one problem: 256 concurrent workers (the paper's saturation point, Sec. IV-C)
@@ -851,11 +1115,16 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
 
 cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
                         cudaStream_t stream) {
-  resident_blocks_per_sm(cfg.warps, cfg.smem);  // sets the shared-memory attribute once per size
+  resident_blocks_per_sm(cfg.warps, cfg.smem, cfg.lockstep);  // sets the shared-memory attribute once per size
   cudaError_t e;
-  plan_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
-                                                              cfg.robot_bytes, cfg.env_bytes,
-                                                              cfg.stage_bytes / (int)sizeof(float));
+  if (cfg.lockstep)
+    lockstep_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
+                                                                    cfg.robot_bytes, cfg.env_bytes,
+                                                                    cfg.stage_bytes / (int)sizeof(float));
+  else
+    plan_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
+                                                                cfg.robot_bytes, cfg.env_bytes,
+                                                                cfg.stage_bytes / (int)sizeof(float));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaSuccess;

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libprrtc.so")
 OK = 0
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_INDEX, ERR_NO_DEVICE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 SOLVED, START_IN_COLLISION, GOAL_IN_COLLISION, NO_SOLUTION, PATH_OVERFLOW, TIME_LIMIT = 0, 1, 2, 3, 4, 5
-MODE_ASYNC, MODE_SERIAL = 0, 1
+MODE_ASYNC, MODE_SERIAL, MODE_LOCKSTEP = 0, 1, 2
 OBS_BOX, OBS_CYLINDER, OBS_SPHERE = 0, 1, 2
 
 _f = C.POINTER(C.c_float)
@@ -45,7 +45,8 @@ class prrtc_params(C.Structure):
                 ("mode", C.c_int32), ("blocks", C.c_int32), ("warps_per_block", C.c_int32),
                 ("learned_ratio", C.c_float), ("seed", C.c_uint64), ("time_limit_s", C.c_double),
                 ("sampler", C.c_int32), ("halton_offset", C.c_uint32), ("dd_radius", C.c_float),
-                ("dd_alpha", C.c_float), ("dd_min_radius", C.c_float), ("reserved", C.c_int32 * 3)]
+                ("dd_alpha", C.c_float), ("dd_min_radius", C.c_float), ("workers", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 SAMPLER_PHILOX, SAMPLER_HALTON = 0, 1
