@@ -113,3 +113,36 @@ def bf16_round(x):
     lsb = (bits >> 16) & 1
     bits = (bits + 0x7FFF + lsb) & 0xFFFF0000
     return bits.astype(np.uint32).view(np.float32).reshape(a.shape)
+
+
+def revalidation_counts(items, res):
+    """Re-check paths with the oracle at resolution `res` (4x finer than planning).
+
+    items: (robot, scene, path [k x dof], esdf or None) per path.  Returns
+    (segments, bad segments, lowest clearance seen)."""
+    from oracle import oracle as O
+    segs = bad = 0
+    worst = float("inf")
+    for robot, scene, path, esdf in items:
+        path = np.asarray(path, np.float64)
+        b, mc = O.revalidate(robot, scene, path, res, esdf=esdf)
+        segs += max(0, len(path) - 1)
+        bad += b
+        worst = min(worst, mc)
+    return segs, bad, worst
+
+
+def assert_same_revalidation_rate(gpu, oracle, what=""):
+    """Discrete edge checking can pass a segment that a finer re-check flags, for
+    the oracle's own paths as much as for the GPU's; the hot-path contract is
+    that both flag segments at the same rate.  gpu / oracle: revalidation_counts
+    results on the same problems.  The rates must agree within three standard
+    errors of the pooled rate (floored at one flagged segment in the pool)."""
+    (ng, bg, wg), (no, bo, wo) = gpu, oracle
+    assert ng > 0 and no > 0, (gpu, oracle)
+    pool = (bg + bo) / (ng + no)
+    p = max(pool, 1.0 / (ng + no))
+    tol = 3.0 * np.sqrt(p * (1.0 - p) * (1.0 / ng + 1.0 / no))
+    print(f"revalidation {what}: GPU {bg}/{ng} segments flagged (lowest clearance {wg:.2e}), "
+          f"oracle {bo}/{no} ({wo:.2e})")
+    assert abs(bg / ng - bo / no) <= tol, (what, gpu, oracle, tol)

@@ -8,7 +8,9 @@ the async mode statistically.
   oracle's lockstep form at the same number of concurrent workers: one block
   of 8 warps per problem (8 workers, no other problem's blocks joining) against
   B = 8 rounds, over 200 cubby-shelf problems and 5 Philox keys.  Success rate
-  must agree within 1 percentage point and mean initial-path cost within 2%.
+  must agree within 1 percentage point and mean initial-path cost within 2%,
+  and the oracle's re-check at 4x resolution must flag the GPU's path segments
+  at the rate it flags its own.
 """
 import numpy as np
 import pytest
@@ -128,6 +130,7 @@ def test_async_statistics_match_the_lockstep_oracle(shelf200):
     envs = [P.make_env(pb.scene) for pb in shelf200]
     prm = P.params(mode=P.MODE_ASYNC, blocks=1, warps_per_block=8)
     g_cost, g_ok, o_cost, o_ok, n = [], 0, [], 0, 0
+    g_items, o_items = [], []
     for key in keys:
         for k, pb in enumerate(shelf200):
             r = P.prrtc_plan_batch([(rb, envs[k], pb.q_start.astype(np.float32), pb.q_goal.astype(np.float32),
@@ -136,12 +139,19 @@ def test_async_statistics_match_the_lockstep_oracle(shelf200):
             if r["status"] == P.SOLVED:
                 g_ok += 1
                 g_cost.append(r["cost"])
+                g_items.append((pb.robot, pb.scene, r["path"], None))
         rs = O.plan_batch(shelf200, seed=key, problem_ids=list(range(len(shelf200))), range=RANGE,
                           resolution=RES, goal_bias=BIAS, workers=8)
-        for r in rs:
+        for pb, r in zip(shelf200, rs):
             if r["status"] == 0:
                 o_ok += 1
                 o_cost.append(r["cost"])
+                o_items.append((pb.robot, pb.scene, r["path"], None))
+    # every returned path re-checked by the oracle at 4x resolution: the GPU's
+    # segments are flagged at the rate of the oracle's own paths
+    from tests import helpers as H
+    H.assert_same_revalidation_rate(H.revalidation_counts(g_items, RES / 4), H.revalidation_counts(o_items, RES / 4),
+                                    "shelf-200 x 5 keys")
     g_mean, o_mean = float(np.mean(g_cost)), float(np.mean(o_cost))
     print(f"async W=8: success {g_ok / n:.4f} cost {g_mean:.4f}; oracle B=8: success {o_ok / n:.4f} "
           f"cost {o_mean:.4f} ({100 * (g_mean / o_mean - 1):+.2f}%)")

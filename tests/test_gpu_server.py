@@ -122,14 +122,23 @@ def test_async_burst_paths_revalidate(problems):
             tickets[srv.submit(*hs[k], pb.q_start, pb.q_goal, seed=10 + rep, problem_id=k)] = pb
     res = collect(srv, len(tickets), len(tickets), timeout=120)
     assert len(res) == len(tickets)
+    g_items = []
     for r in res:
         pb = tickets[r["ticket"]]
         assert r["status"] in (P.SOLVED, P.NO_SOLUTION)
         if r["status"] == P.SOLVED:
-            bad, mc = O.revalidate(pb.robot, pb.scene, r["path"].astype(np.float64), F32(1 / 32) / 4)
-            assert bad == 0 or mc > -1e-3
+            g_items.append((pb.robot, pb.scene, r["path"], None))
             np.testing.assert_array_equal(r["path"][0], pb.q_start.astype(np.float32))
             np.testing.assert_array_equal(r["path"][-1], pb.q_goal.astype(np.float32))
+    # re-checked at 4x resolution, flagged at the rate of the oracle's paths for the same queries
+    o_items = []
+    for rep in range(3):
+        orc = O.plan_batch(problems, seed=10 + rep, problem_ids=list(range(len(problems))), range=1.0,
+                           resolution=F32(1 / 32), goal_bias=F32(0.05), max_iters=20000, tree_capacity=1 << 13,
+                           path_capacity=1 << 12)
+        o_items += [(pb.robot, pb.scene, o["path"], None) for pb, o in zip(problems, orc) if o["status"] == 0]
+    H.assert_same_revalidation_rate(H.revalidation_counts(g_items, F32(1 / 32) / 4),
+                                    H.revalidation_counts(o_items, F32(1 / 32) / 4), "server burst")
     assert sum(r["status"] == P.SOLVED for r in res) >= len(res) // 2
     srv.close()
 

@@ -470,3 +470,57 @@ def test_plan_straight_line_state_counts(D):
     assert r["edges_checked"] == edges
     assert r["edge_states"] == states
     assert r["states_checked"] == states
+
+
+# ----------------------------------------------------------------- revalidation
+
+def _point_scene_path(obstacle_spheres=(), boxes=(), z0=0.5):
+    return H.point_robot(z0=z0, radius=0.001), H.scene(boxes=boxes, spheres=obstacle_spheres)
+
+
+def test_revalidate_through_a_box_reports_the_analytic_penetration():
+    """A straight two-waypoint path through the centre of a box: one bad segment,
+    and the deepest state (the box centre, reached at t = 1/2) has clearance
+    -(smallest half extent) - r."""
+    rb, sc = _point_scene_path(boxes=[H.aabb([0.6, 0.6, 0.5], [0.1, 0.15, 0.5])])
+    path = np.array([[0.2, 0.6], [1.0, 0.6]])
+    bad, mc = O.revalidate(rb, sc, path, 0.01)       # 80 states, state 40 at the centre
+    assert bad == 1
+    assert abs(mc - (-0.1 - 0.001)) < 1e-12
+    # two segments, only the second crosses the box
+    path3 = np.array([[0.2, 0.2], [0.2, 0.6], [1.0, 0.6]])
+    bad3, mc3 = O.revalidate(rb, sc, path3, 0.01)
+    assert bad3 == 1 and abs(mc3 - (-0.101)) < 1e-12
+
+
+def test_revalidate_catches_what_the_coarse_resolution_misses():
+    """An obstacle sphere of radius 3 mm centred half way between two states of a
+    1/32 check: free at 1/32 (the nearest states are 1/64 away), caught at 1/128,
+    where a state lands on its centre with clearance -(3 mm + 1 mm)."""
+    x0 = 0.1 + 10.5 / 32
+    rb, sc = _point_scene_path(obstacle_spheres=[[x0, 0.5, 0.5, 0.003]])
+    path = np.array([[0.1, 0.5], [1.1, 0.5]])
+    bad_c, mc_c = O.revalidate(rb, sc, path, 1 / 32)
+    assert bad_c == 0 and abs(mc_c - (1 / 64 - 0.004)) < 1e-9
+    bad_f, mc_f = O.revalidate(rb, sc, path, 1 / 128)
+    assert bad_f == 1 and abs(mc_f - (-0.004)) < 1e-9
+
+
+def test_revalidate_free_path_reports_exact_clearance():
+    """A path parallel to a wall at 5 cm: no bad segment, minimum clearance
+    5 cm - r at every state."""
+    rb, sc = _point_scene_path(boxes=[H.aabb([0.5, 0.8, 0.5], [0.5, 0.05, 0.5])])
+    path = np.array([[0.1, 0.7], [0.5, 0.7], [0.9, 0.7]])
+    bad, mc = O.revalidate(rb, sc, path, 0.01)
+    assert bad == 0
+    assert abs(mc - (0.05 - 0.001)) < 1e-12
+
+
+def test_revalidate_counts_the_first_waypoint_in_the_clearance_only():
+    """The first waypoint enters the minimum clearance but not the segment count
+    (segments test the states after their first waypoint)."""
+    rb, sc = _point_scene_path(obstacle_spheres=[[0.2, 0.5, 0.5, 0.004]])
+    path = np.array([[0.2, 0.5], [0.6, 0.5]])
+    bad, mc = O.revalidate(rb, sc, path, 0.01)   # the next state is 1 cm on: free
+    assert bad == 0
+    assert abs(mc - (-0.005)) < 1e-12

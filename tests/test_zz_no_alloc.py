@@ -12,6 +12,7 @@ import pytest
 from oracle import oracle as O
 from paper_2503_06757_gb300 import prrtc as P
 from paper_2503_06757_gb300 import workload as W
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -48,13 +49,20 @@ def test_noalloc_async_paths_valid_twice(problems):
     pb = problems[0]
     rb, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
     prm = P.params(seed=5, tree_capacity=4096, path_capacity=4096)
+    res = float(np.float32(1 / 32)) / 4
+    o = O.plan(pb.robot, pb.scene, pb.q_start.astype(np.float32).astype(np.float64),
+               pb.q_goal.astype(np.float32).astype(np.float64), seed=5, range=1.0,
+               resolution=float(np.float32(1 / 32)), goal_bias=float(np.float32(0.05)))
+    assert o["status"] == 0
     for _ in range(2):
         r = P.prrtc_plan_noalloc(rb, ev, pb.q_start, pb.q_goal, prm)
         assert r["status"] == P.SOLVED
         np.testing.assert_array_equal(r["path"][0], pb.q_start.astype(np.float32))
         np.testing.assert_array_equal(r["path"][-1], pb.q_goal.astype(np.float32))
-        bad, mc = O.revalidate(pb.robot, pb.scene, r["path"].astype(np.float64), float(np.float32(1 / 32)) / 4)
-        assert bad == 0 or mc > -1e-3
+        # re-checked at 4x resolution, flagged at the rate of the oracle's own path
+        H.assert_same_revalidation_rate(H.revalidation_counts([(pb.robot, pb.scene, r["path"], None)], res),
+                                        H.revalidation_counts([(pb.robot, pb.scene, o["path"], None)], res),
+                                        "allocation-free call")
 
 
 def test_noalloc_rejects_sizes_beyond_scratch(problems):
