@@ -11,13 +11,20 @@ MotionBenchMaker scenes, which are not available here).
 Reported:
   value      edge states checked per second over the device time of the
              setup + planner kernels (CUDA events on the launching stream).
+             A state counts once its collision verdict is established: all
+             states of a free edge, the first colliding state of a colliding
+             one; states an early exit skipped are not counted (they are in
+             edge_states_begun_per_s).
   e2e        the same metric over the wall time of the whole C-ABI call with
              host buffers (descriptor upload and result download included).
   ttfs       time to first solution per problem (device %globaltimer from
              launch start), p50/p95/p99; plus single-problem TTFS through
              prrtc_plan (host wall clock, environment resident).
-  roofline   the planner kernel's counted arithmetic against the issue-rate
-             bound of the SMs (128 lane-instructions / clock / SM).
+  roofline   the planner kernel's executed lane-ops (the multi-stage check as
+             run, counted by the kernel) against the issue-rate bound of the
+             SMs (128 lane-instructions / clock / SM).
+  mixed_600  the 600-problem mixed 7/8/14-DoF batch in one launch.
+  oracle_agreement  serial, lockstep and async statistics against the oracle.
   cpu_baseline  the FP64 oracle on the host cores (bounded sample).
 
 `--impl reference` times the oracle alone on the same workload and metric.
@@ -39,7 +46,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "p50/p95 time-to-first-solution & edge states checked/s; learned vs plain, 1 GB300"
-UNIT = "edge states/s"
+# A state counts once its collision verdict is established: every state of a
+# free edge, and the first colliding state of a colliding edge (the states an
+# early exit skips do not count).
+UNIT = "edge states checked/s"
 WORKLOAD = "shelf-200: 200 cubby-shelf problems, 7-DoF arm (28 spheres), 50 obstacles each, one launch"
 
 # Counted arithmetic per test (lane-level instructions of the test as written:
@@ -68,7 +78,7 @@ def profiled_traffic(problems):
     """DRAM bytes per planner launch from the committed ncu summary, scaled by
     problems, or None when the kernel source changed since the capture."""
     try:
-        text = open(os.path.join(ROOT, "profiles", "plan_kernel_shelf64_full.md")).read()
+        text = open(os.path.join(ROOT, "profiles", "plan_kernel_shelf200_full.md")).read()
         src = text.split("kernel_source:")[1].split()[0]
         per = float(text.split("dram_bytes_per_problem:")[1].split()[0])
     except Exception:
@@ -243,7 +253,7 @@ def oracle_sample(problems, budget_s=12.0, threads=None):
     `threads`, until the time budget is used."""
     from oracle import oracle as O
     threads = threads or os.cpu_count() or 1
-    done, states, wall, solved, costs = 0, 0, 0.0, 0, []
+    done, states, wall, solved, costs, per_problem, serial_states = 0, 0, 0.0, 0, [], [], 0
     while done < len(problems) and wall < budget_s:
         chunk = problems[done:done + threads]
         t = time.perf_counter()
@@ -252,27 +262,84 @@ def oracle_sample(problems, budget_s=12.0, threads=None):
         wall += time.perf_counter() - t
         done += len(chunk)
         for r in rs:
-            states += r["edge_states"]
+            # the oracle checks an edge's states in order and stops at the first
+            # collision: states_checked counts the verdicts it established
+            states += r["states_checked"]
+            serial_states += r["states_checked"]
+            per_problem.append(r["seconds"])
             solved += r["status"] == 0
             if r["status"] == 0:
                 costs.append(r["cost"])
+    pp = np.array(per_problem) if per_problem else np.zeros(1)
     return dict(value=states / wall if wall > 0 else None, unit=UNIT, cores=threads, kind="oracle",
                 sample=f"first {done} of {len(problems)} shelf problems, 1 Philox key, one problem per thread",
                 problems=done, seconds=wall, success_rate=solved / max(done, 1),
-                mean_cost=float(np.mean(costs)) if costs else None)
+                mean_cost=float(np.mean(costs)) if costs else None,
+                single_core=dict(value=serial_states / max(float(pp.sum()), 1e-12), unit=UNIT,
+                                 seconds_per_problem=dict(percentiles(list(pp * 1e3)), unit="ms"),
+                                 note="each problem's own thread time: one core per problem"))
 
 
-def oracle_agreement(P, items, cpu):
-    """Success rate and mean cost of the device planner on the problems the oracle
-    sample solved (same Philox key 1 and problem ids): serial mode (Alg. 1 in order,
-    the oracle's algorithm) and async mode (the parallel workers of the timed step)."""
-    n = cpu["problems"]
-    sub = [it[:4] + (1, k) for k, it in enumerate(items[:n])]
-    out = dict(problems=n, oracle=dict(success_rate=cpu["success_rate"], mean_cost=cpu["mean_cost"]))
-    for name, mode in (("serial", P.MODE_SERIAL), ("async", P.MODE_ASYNC)):
-        res = P.prrtc_plan_batch(sub, P.params(mode=mode))
-        ok = [r for r in res if r["status"] == P.SOLVED]
-        out[name] = dict(success_rate=len(ok) / n, mean_cost=float(np.mean([r["cost"] for r in ok])) if ok else None)
+def oracle_agreement(P, probs, items, keys=(1, 2, 3), workers=8):
+    """Planner statistics against the oracle on the same problems and Philox keys.
+
+    serial:   Alg. 1 in iteration order on one warp against the serial oracle
+              (identical trees wherever no decision is ambiguous).
+    lockstep: `workers` concurrent iterations per round on a fixed schedule,
+              against the oracle's lockstep form (identical trees likewise).
+    async:    the concurrent mode with exactly `workers` warps per problem (one
+              block per problem, no other blocks joining), against the oracle's
+              lockstep form at the same concurrency: the same semantics up to
+              the hardware's interleaving, held to success +-1 pp, cost +-2%.
+    timed:    the timed launch itself (blocks move to unsolved problems, so a
+              problem's concurrency grows as others finish), for reference."""
+    import dataclasses
+    from oracle import oracle as O
+    f32 = lambda x: float(np.float32(x))
+    n = len(items)
+    out = dict(problems=n, keys=list(keys), workers=workers)
+    # the oracle plans from the binary32 start and goal the device receives
+    probs = [dataclasses.replace(pb, q_start=pb.q_start.astype(np.float32).astype(np.float64),
+                                 q_goal=pb.q_goal.astype(np.float32).astype(np.float64)) for pb in probs]
+
+    def stats(rs):
+        ok = [r for r in rs if r["status"] == 0]
+        return dict(success_rate=len(ok) / max(len(rs), 1),
+                    mean_cost=float(np.mean([r["cost"] for r in ok])) if ok else None)
+
+    def oracle_runs(B):
+        rs = []
+        for key in keys:
+            rs += O.plan_batch(probs, seed=key, problem_ids=list(range(n)), range=1.0, resolution=f32(1 / 32),
+                               goal_bias=f32(0.05), workers=B)
+        return rs
+
+    def gpu_runs(prm, single=False):
+        rs = []
+        for key in keys:
+            sub = [it[:4] + (key, k) for k, it in enumerate(items)]
+            if single:
+                for it in sub:
+                    rs += P.prrtc_plan_batch([it], prm)
+            else:
+                rs += P.prrtc_plan_batch(sub, prm)
+        return rs
+
+    o_serial, o_lock = oracle_runs(0), oracle_runs(workers)
+    out["oracle_serial"] = stats(o_serial)
+    out["oracle_lockstep"] = stats(o_lock)
+    for name, prm, single, ref in (
+            ("serial", P.params(mode=P.MODE_SERIAL), False, o_serial),
+            ("lockstep", P.params(mode=P.MODE_LOCKSTEP, workers=workers), False, o_lock),
+            ("async", P.params(mode=P.MODE_ASYNC, blocks=1, warps_per_block=workers), True, o_lock)):
+        g = gpu_runs(prm, single)
+        out[name] = stats(g)
+        same = sum(1 for a, b in zip(g, ref) if a["status"] == b["status"] == 0 and abs(a["cost"] - b["cost"]) <= 1e-4 * b["cost"])
+        out[name]["same_cost_as_oracle"] = same / max(len(g), 1)
+        if out[name]["mean_cost"] and stats(ref)["mean_cost"]:
+            out[name]["cost_vs_oracle"] = out[name]["mean_cost"] / stats(ref)["mean_cost"] - 1.0
+        out[name]["success_vs_oracle_pp"] = 100.0 * (out[name]["success_rate"] - stats(ref)["success_rate"])
+    out["timed"] = stats(gpu_runs(P.params()))
     return out
 
 
@@ -451,7 +518,7 @@ def esdf_section(P, torch, items, prm, flush, F, rb_check, steps=5):
         st = P.prrtc_last_launch_stats()
         dev_ms += st["kernel_ms"] + st["setup_ms"]
         for r in res:
-            states += r["edge_states"]
+            states += r["verdict_states"]
             pre += r["status"] in (P.START_IN_COLLISION, P.GOAL_IN_COLLISION)
             if r["status"] == P.SOLVED:
                 solved += 1
@@ -468,10 +535,74 @@ def esdf_section(P, torch, items, prm, flush, F, rb_check, steps=5):
         ms.append(P.prrtc_last_launch_stats()["kernel_ms"])
     kms = float(np.median(ms))
     return dict(grid=g, environments=len(envs), build_ms_per_env=build_s * 1e3 / len(envs),
-                ms_per_step=dev_ms / steps, edge_states_per_s=states / (dev_ms * 1e-3), ttfs_us=percentiles(ttfs),
+                ms_per_step=dev_ms / steps, states_checked_per_s=states / (dev_ms * 1e-3), ttfs_us=percentiles(ttfs),
                 success_rate=solved / n, endpoint_in_collision_rate=pre / n,
                 check_states_microbench=dict(states=int(len(F)), kernel_ms=kms, states_per_s=len(F) / (kms * 1e-3)),
                 note="start/goal pairs were chosen against the primitives; the voxelised scene can cover some")
+
+
+# ------------------------------------------------------------------ mixed-DoF batch
+
+MIXED_WORKLOAD = ("mixed-600: 200 problems each of the 7-, 8- and 14-DoF arms (28 / 32 / 56 spheres), 10-120 "
+                  "obstacles per scene (cuboid : cylinder : sphere = 3 : 1 : 1), one persistent autotuned launch")
+
+
+def mixed_section(args, P, flush, torch, peak_gops, steps=3):
+    """The largest single-GPU configuration: 600 problems of uneven DoF, obstacle
+    count and tree size in one persistent launch, launch shape from the autotuner."""
+    from paper_2503_06757_gb300 import workload as W
+    t0 = time.perf_counter()
+    probs = W.problem_set("mixed", 600, 2000, gpu_accept_factory(P))
+    gen_s = time.perf_counter() - t0
+    robots, items, counts = {}, [], []
+    for k, pb in enumerate(probs):
+        if pb.robot.name not in robots:
+            robots[pb.robot.name] = P.make_robot(pb.robot)
+        rb = robots[pb.robot.name]
+        ev = P.make_env(pb.scene)
+        info = rb.info()
+        counts.append((ev.info(), pb.robot.dof, info["dpad"], info["n_spheres"], info["n_pairs"]))
+        items.append((rb, ev, pb.q_start, pb.q_goal, 1, k))
+    prm, tuned_ms = P.prrtc_autotune(items, P.params(), trials=1)
+    batch = P.PlanBatch(items)
+    for _ in range(2):
+        batch.run(prm)
+    dev_ms = kms = 0.0
+    states = begun = ops = alg = 0
+    by = {d: dict(ttfs=[], solved=0, n=0, costs=[]) for d in (7, 8, 14)}
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        res = result_rows(batch.run(prm))
+        st = P.prrtc_last_launch_stats()
+        dev_ms += st["kernel_ms"] + st["setup_ms"]
+        kms += st["kernel_ms"]
+        for r, (ec, dof, dpad, nsph, npair) in zip(res, counts):
+            states += r["verdict_states"]
+            begun += r["edge_states"]
+            ops += op_count(r, ec, dof, dpad)
+            alg += algorithmic_ops(r, ec, dof, dpad, nsph, npair)
+            b = by[dof]
+            b["n"] += 1
+            if r["status"] == P.SOLVED:
+                b["solved"] += 1
+                b["ttfs"].append(r["solve_time_us"])
+                b["costs"].append(r["cost"])
+    executed = ops / (kms * 1e-3) * 1e-9
+    one_stage = alg / (kms * 1e-3) * 1e-9
+    all_ttfs = [t for b in by.values() for t in b["ttfs"]]
+    return dict(
+        workload=MIXED_WORKLOAD, problems=len(items), steps=steps, problem_set_seconds=gen_s,
+        launch=dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, autotuned_ms=tuned_ms),
+        ms_per_step=dev_ms / steps, states_checked_per_s=states / (dev_ms * 1e-3),
+        edge_states_begun_per_s=begun / (dev_ms * 1e-3),
+        ttfs_us=dict(percentiles(all_ttfs), note="solved problems, device time from launch start"),
+        success_rate=sum(b["solved"] for b in by.values()) / max(1, sum(b["n"] for b in by.values())),
+        by_dof={str(d): dict(success_rate=b["solved"] / max(b["n"], 1), ttfs_us=percentiles(b["ttfs"]),
+                             mean_cost=float(np.mean(b["costs"])) if b["costs"] else None) for d, b in by.items()},
+        roofline=dict(bound="alu", achieved=executed, peak=peak_gops, unit="Gop/s", frac=executed / peak_gops,
+                      one_stage_equivalent_gops=one_stage, one_stage_equivalent_frac=one_stage / peak_gops,
+                      note="planner kernel over the whole launch, counted as on the main line"))
 
 
 # ------------------------------------------------------------------ sampler / check variants
@@ -500,6 +631,7 @@ def variants_section(args, P, items, prm, counts, flush, torch, steps=5):
         for _ in range(2):
             P.prrtc_plan_batch(items, p)
         dev_ms, kms, states, ops, ttfs, iters, costs, solved, rej = 0.0, 0.0, 0, 0, [], [], [], 0, 0
+        begun = 0
         alg = 0
         for _ in range(steps):
             flush.zero_()
@@ -509,7 +641,8 @@ def variants_section(args, P, items, prm, counts, flush, torch, steps=5):
             dev_ms += st["kernel_ms"] + st["setup_ms"]
             kms += st["kernel_ms"]
             for r, (ec, dof, dpad, nsph, npair) in zip(res, counts):
-                states += r["edge_states"]
+                states += r["verdict_states"]
+                begun += r["edge_states"]
                 ops += op_count(r, ec, dof, dpad)
                 alg += algorithmic_ops(r, ec, dof, dpad, nsph, npair)
                 iters.append(r["iterations"])
@@ -519,11 +652,12 @@ def variants_section(args, P, items, prm, counts, flush, torch, steps=5):
                     ttfs.append(r["solve_time_us"])
                     costs.append(r["cost"])
         n = len(items) * steps
-        out[name] = dict(ms_per_step=dev_ms / steps, edge_states_per_s=states / (dev_ms * 1e-3),
+        out[name] = dict(ms_per_step=dev_ms / steps, states_checked_per_s=states / (dev_ms * 1e-3),
+                         edge_states_begun_per_s=begun / (dev_ms * 1e-3),
                          ttfs_us=percentiles(ttfs), success_rate=solved / n,
                          iterations_mean=float(np.mean(iters)), cost_mean=float(np.mean(costs)) if costs else None,
-                         dd_rejected_per_problem=rej / n, planner_gops=alg / (kms * 1e-3) * 1e-9,
-                         planner_executed_gops=ops / (kms * 1e-3) * 1e-9)
+                         dd_rejected_per_problem=rej / n, planner_executed_gops=ops / (kms * 1e-3) * 1e-9,
+                         planner_one_stage_equivalent_gops=alg / (kms * 1e-3) * 1e-9)
     for rb in robots.values():
         rb.set_two_stage(True)
     return out
@@ -590,9 +724,12 @@ def run_ours(args):
         info = rb.info()
         counts.append((ev.info(), pb.robot.dof, info["dpad"], info["n_spheres"], info["n_pairs"]))
         items.append((rb, ev, pb.q_start, pb.q_goal, 1, rank * args.problems + k))
-    prm = P.params()
+    prm = P.params(tree_capacity=args.tree_capacity)
     tuned = None
-    if not args.no_autotune:
+    if args.blocks or args.warps:
+        # a fixed launch shape (e.g. to profile the shape the autotuner picked)
+        prm.blocks, prm.warps_per_block = args.blocks, args.warps
+    elif not args.no_autotune:
         prm, tuned_ms = P.prrtc_autotune(items, prm, trials=4)
         tuned = dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, mean_ms=tuned_ms)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -609,6 +746,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed")
     dev_ms, wall_s, edge_states, ops, launches, h2d, d2h = 0.0, 0.0, 0, 0, 0, 0, 0
+    verdict_states = 0
     alg_ops = 0
     kernel_ms = 0.0
     ttfs, solved, costs = [], 0, []
@@ -627,6 +765,7 @@ def run_ours(args):
         d2h += st["d2h_bytes"]
         for r, (ec, dof, dpad, nsph, npair) in zip(res, counts):
             edge_states += r["edge_states"]
+            verdict_states += r["verdict_states"]
             ops += op_count(r, ec, dof, dpad)
             alg_ops += algorithmic_ops(r, ec, dof, dpad, nsph, npair)
             if r["status"] == P.SOLVED:
@@ -640,7 +779,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
 
-    device_s, wall_s, total_states = reduce_over_ranks(dist, torch, dev_ms * 1e-3, wall_s, edge_states,
+    device_s, wall_s, total_states = reduce_over_ranks(dist, torch, dev_ms * 1e-3, wall_s, verdict_states,
                                                        "cuda" if torch.cuda.is_available() else "cpu")
     value = total_states / device_s
     peaks = measured_peaks()
@@ -706,11 +845,13 @@ def run_ours(args):
         extra["roofline_cc_microbench"] = dict(micro["two_stage"], one_stage=micro["one_stage"],
                                                workload="1M collision-free 7-DoF states vs one shelf scene "
                                                         "(every test runs)")
+        if not args.no_mixed:
+            extra["mixed_600"] = mixed_section(args, P, flush, torch, peak_gops)
         extra["variants"] = variants_section(args, P, items, prm, counts, flush, torch)
         extra["esdf"] = esdf_section(P, torch, items, prm, flush, F, rb)
         extra["roofline_gemm"] = gemm_section(P, torch, float(peaks.get("bf16_tflops", 1900.0)))
         extra["cpu_baseline"] = oracle_sample(probs, budget_s=args.cpu_budget)
-        extra["oracle_agreement"] = oracle_agreement(P, items, extra["cpu_baseline"])
+        extra["oracle_agreement"] = oracle_agreement(P, probs, items)
         prop = None
         if not args.no_learned:
             extra["learned"], prop = learned_section(args, P)
@@ -728,13 +869,15 @@ def run_ours(args):
                     goal_bias=0.05, max_iters=50000, grid=plan_grid, autotuned=tuned, parallelism=f"problems sharded over {world} GPU(s)"),
         ttfs_us=dict(percentiles(ttfs), note="device time from launch start to each problem's solution"),
         success_rate=solved / (len(items) * args.steps), mean_cost=float(np.mean(costs)) if costs else None,
-        roofline=dict(bound="alu", achieved=achieved_gops, peak=peak_gops, unit="Gop/s",
-                      frac=achieved_gops / peak_gops, traffic=profiled_traffic(args.problems),
-                      executed_gops=executed_gops, executed_frac=executed_gops / peak_gops,
-                      note="planner kernel: algorithmic work = states with an established collision verdict x "
-                           "the one-stage lane-ops of a verdict (FK, every sphere against every primitive, every "
-                           "self pair) + NN row distances, per launch / kernel time; executed_* = the lane-ops "
-                           "the multi-stage check actually ran; peak = SMs x 128 lanes x max SM clock"),
+        edge_states_begun_per_s=edge_states / (dev_ms * 1e-3),
+        roofline=dict(bound="alu", achieved=executed_gops, peak=peak_gops, unit="Gop/s",
+                      frac=executed_gops / peak_gops, traffic=profiled_traffic(args.problems),
+                      one_stage_equivalent_gops=achieved_gops, one_stage_equivalent_frac=achieved_gops / peak_gops,
+                      note="planner kernel: the lane-ops the method ran (FK, the multi-stage sphere hierarchy of "
+                           "Sec. III-A as executed, self pairs, NN row distances; counted by the kernel) per "
+                           "kernel time, against SMs x 128 lanes x max SM clock (of measured sm_max_mhz).  "
+                           "one_stage_equivalent_*: the same verdicts priced as a one-stage check (every sphere "
+                           "against every primitive), which the hierarchy never runs"),
         e2e=dict(value=total_states / wall_s, unit=UNIT, h2d_bytes_per_step=h2d // args.steps,
                  d2h_bytes_per_step=d2h // args.steps),
         gpu_launches=launches, clocks=clk, learned=None, serving=None,
@@ -758,6 +901,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--blocks", type=int, default=0, help="fixed planner grid (skips the autotuner)")
+    ap.add_argument("--warps", type=int, default=0, help="fixed warps per planner block (skips the autotuner)")
+    ap.add_argument("--tree-capacity", type=int, default=1 << 16, help="nodes per tree per problem")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 600-problem mixed-DoF section")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--learned-scenes", type=int, default=1250)
     ap.add_argument("--learned-pairs", type=int, default=40)
