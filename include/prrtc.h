@@ -166,7 +166,13 @@ typedef struct prrtc_params {
                              (other modes ignore it); warps_per_block 0 = min(workers, 8)
                              warps per problem, each running workers / warps iterations
                              of a round in turn                                       */
-  int32_t reserved[2];
+  int32_t debug_wait_polls;  /* test hook for the bounded device waits; 0 = off.  When > 0, the
+                             path extraction of a solved problem first spins, for at most
+                             this many polls, on a device flag that nothing sets; the wait
+                             gives up like a parent walk that found an unwritten row: the
+                             problem reports PRRTC_ERR_TIMEOUT, the call returns
+                             PRRTC_ERR_TIMEOUT, and later calls on the same handles work */
+  int32_t reserved;
 } prrtc_params;
 
 #define PRRTC_SAMPLER_PHILOX 0
@@ -338,6 +344,15 @@ int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const flo
  * (cudaStream_t, 0 = legacy default stream); returns without synchronising. */
 int prrtc_check_states_device(const prrtc_robot* robot, const prrtc_env* env, const float* q_device,
                               int32_t n, uint8_t* valid_device, float* spheres_device, void* stream);
+
+/* The sampler's counter-based generator on the device: Philox4x32-10
+ * (Salmon, Moraes, Dror, Shaw, SC'11), whose words RANDOM_CONFIG (Alg. 1
+ * line 4) draws.  out[4i .. 4i+3] = Philox4x32-10(counter ctr[4i .. 4i+3],
+ * key {low 32 bits of key, high 32 bits}) for i < n.  ctr and out: host
+ * arrays of 4n words owned by the caller; blocks until done.  For tests of
+ * the device generator against an independent implementation.  n = 0 does
+ * nothing; n < 0, or a null buffer with n > 0: PRRTC_ERR_INVALID_ARG. */
+int prrtc_philox(const uint32_t* ctr, int32_t n, uint64_t key, uint32_t* out);
 
 /* Solve one planning problem (Alg. 1) on the device; blocks until done.
  * out_path receives the path (host memory, free with prrtc_path_free). */
@@ -513,9 +528,10 @@ void prrtc_server_destroy(prrtc_server* server);
 /* ------------------------------------------------------------ planning without allocation */
 /* The paper has no counterpart of this entry point; it exists for callers
  * that must not allocate device memory while they plan -- a real-time control
- * thread that cannot block in an allocator, an application whose framework
- * owns all device memory through its own pool or budget, or code running
- * while another component captures the stream into a CUDA graph.
+ * thread that cannot block in an allocator, or an application whose framework
+ * owns all device memory through its own pool or budget.  The call waits for
+ * its stream and reads results back synchronously, so it is not for use
+ * inside another component's stream capture.
  *
  * prrtc_plan_noalloc solves one problem like prrtc_plan but keeps the trees,
  * the planner state and the path in one fixed, file-scope device array of
@@ -535,7 +551,8 @@ void prrtc_server_destroy(prrtc_server* server);
  * tree row unwritten; make that first call before any stream capture.  Every
  * call shares the one array and leaves its contents for the next; calls that
  * overlap on the GPU (other threads or streams) race on it and must be
- * serialised by the caller. */
+ * serialised by the caller.  A device reset (cudaDeviceReset) between calls
+ * is not supported: the first-call set-up is not repeated afterwards. */
 #define PRRTC_NOALLOC_MAX_ROWS 4096
 int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env, const float* q_start,
                        const float* q_goal, const prrtc_params* params, float* path_out,

@@ -221,6 +221,16 @@ def philox(ctr, key):
     return [int(x) for x in out]
 
 
+def philox_blocks(ctr, key64):
+    """Philox4x32-10 of n counters ([n x 4] uint32) under a 64-bit key (low word first)."""
+    c = np.ascontiguousarray(np.asarray(ctr, np.uint32).reshape(-1, 4))
+    out = np.zeros_like(c)
+    key = (C.c_uint32 * 2)(int(key64) & 0xFFFFFFFF, (int(key64) >> 32) & 0xFFFFFFFF)
+    P32 = C.POINTER(C.c_uint32)
+    lib().orc_philox_blocks(c.ctypes.data_as(P32), C.c_int32(c.shape[0]), key, out.ctypes.data_as(P32))
+    return out
+
+
 def sample(robot, seed, problem, it, goal_bias):
     r = make_robot(robot)
     q = np.zeros(robot.dof)

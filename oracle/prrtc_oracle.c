@@ -54,6 +54,10 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[3] = c3;
 }
 
+void orc_philox_blocks(const uint32_t* ctr, int32_t n, const uint32_t key[2], uint32_t* out) {
+  for (int32_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * (size_t)i, key, out + 4 * (size_t)i);
+}
+
 /* Word w of the stream for (problem, it): block w/4 of Philox with counter
  * {problem, it, w/4, 0}. */
 static uint32_t sample_word(uint64_t seed, uint32_t problem, uint32_t it, int w) {

@@ -179,6 +179,8 @@ typedef struct orc_result {
 
 /* Philox4x32-10 block: out = Philox(ctr, key).  Salmon et al. SC'11. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The same for n counters (ctr, out: [4n] words). */
+void orc_philox_blocks(const uint32_t* ctr, int32_t n, const uint32_t key[2], uint32_t* out);
 
 /* Sample of Alg. 1 (RANDOM_CONFIG) for iteration `it`: returns 1 when the
  * goal-bias branch fires (the caller substitutes the opposite root), else 0

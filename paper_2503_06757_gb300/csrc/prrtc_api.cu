@@ -870,6 +870,28 @@ int prrtc_check_states_device(const prrtc_robot* robot, const prrtc_env* env, co
   return PRRTC_OK;
 }
 
+int prrtc_philox(const uint32_t* ctr, int32_t n, uint64_t key, uint32_t* out) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return fail(PRRTC_ERR_INVALID_ARG, "bad philox arguments");
+  if (n == 0) return PRRTC_OK;
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  uint32_t* d = nullptr;
+  const size_t bytes = (size_t)n * 4 * sizeof(uint32_t);
+  if (cudaMalloc(&d, 2 * bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PRRTC_ERR_OOM, "philox buffer allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(d, ctr, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_philox(d, n, key, d + (size_t)n * 4, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + (size_t)n * 4, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail("philox", e);
+  return PRRTC_OK;
+}
+
 int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const float* q, int32_t n, uint8_t* out_valid,
                        float* out_spheres) {
   if (!robot || !env || n < 0 || (n > 0 && (!q || !out_valid)))
@@ -1123,7 +1145,8 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     CK(cudaMemcpyAsync(c->d_desc, c->h_desc, (size_t)n * sizeof(ProblemDesc), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_glob, c->h_glob, sizeof(PlanGlobals), cudaMemcpyHostToDevice, c->stream));
     CK(cudaEventRecordWithFlags(c->ev[0], c->stream, ev_flags));
-    cudaError_t e = launch_setup(c->d_desc, c->d_state, n, max_spheres, max_pairs, max_env, c->stream);
+    cudaError_t e =
+        launch_setup(c->d_desc, c->d_state, n, max_spheres, max_pairs, max_env, c->stream, nullptr, &c->d_glob->error);
     if (e != cudaSuccess) return cuda_fail("setup launch", e);
     CK(cudaEventRecordWithFlags(c->ev[1], c->stream, ev_flags));
     e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, c->stream);

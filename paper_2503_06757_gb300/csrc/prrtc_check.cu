@@ -4,6 +4,8 @@
 // shared memory by TMA bulk copies.  Used for the per-state parity check
 // against the oracle and as the FP32-roofline microbenchmark (collision-free
 // states: every test must run).
+#include <algorithm>
+
 #include "prrtc.h"
 #include "prrtc_launch.h"
 
@@ -44,7 +46,10 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
     }
     if (env_f4) bulk_g2s(senv, env.data, 16u * env_f4, &bar);
     s_ok = mbar_wait(&bar, 0, 1u << 26) ? 1 : 0;
-    if (!s_ok) atomicExch(error, PRRTC_ERR_TIMEOUT);
+    if (!s_ok) {
+      atomicExch(error, PRRTC_ERR_TIMEOUT);
+      mbar_wait(&bar, 0, 1u << 26);  // the block leaves: its copies first (bounded)
+    }
   }
   __syncthreads();
   if (!s_ok) return;  // block-uniform
@@ -84,6 +89,21 @@ __global__ void __launch_bounds__(kCheckWarps * 32) check_states_kernel(const Ro
 }
 
 }  // namespace
+
+// One Philox4x32-10 block per thread (the sampler's generator).
+__global__ void philox_kernel(const uint4* __restrict__ ctr, int n, uint2 key, uint4* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = philox4x32_10(ctr[i], key);
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, int n, uint64_t key, uint32_t* out, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>(((long long)n + 255) / 256, 152LL * 16);
+  philox_kernel<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint4*>(ctr), n,
+                                            make_uint2((uint32_t)(key & 0xffffffffu), (uint32_t)(key >> 32)),
+                                            reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& h, EnvView env, const float* q, int n,
                                 uint8_t* valid, float* spheres, unsigned long long* counters, int* error,

@@ -42,6 +42,7 @@ struct PlanGlobals {
   float dd_alpha;
   float dd_min_radius;
   int workers;           // lockstep mode: iterations per round (B)
+  uint32_t debug_wait_polls;  // test hook: bounded wait on ProblemState::never_set before a path walk
 };
 
 // Check of the sampler and dynamic-domain fields of a parameter block; null
@@ -73,6 +74,7 @@ inline void globals_from_params(PlanGlobals& G, const prrtc_params& p) {
   G.dd_alpha = p.dd_alpha;
   G.dd_min_radius = p.dd_min_radius;
   G.workers = p.mode == PRRTC_MODE_LOCKSTEP ? p.workers : 1;
+  G.debug_wait_polls = p.debug_wait_polls > 0 ? (uint32_t)p.debug_wait_polls : 0u;
 }
 
 // Per-problem inputs (uploaded every call).
@@ -123,7 +125,7 @@ struct ProblemState {
   // arena bookkeeping, preserved across launches
   int used_rows[2];
   int used_dpad;
-  int pad_;
+  int never_set;         // stays 0: the flag the bounded-wait test hook waits on
 };
 
 // Launchers (return cudaError_t of the launch).
@@ -131,9 +133,14 @@ cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& host_h
                                 int n, uint8_t* valid, float* spheres, unsigned long long* counters, int* error,
                                 cudaStream_t stream);
 
+// Philox4x32-10 of n counters (device arrays of 4n words each).
+cudaError_t launch_philox(const uint32_t* ctr, int n, uint64_t key, uint32_t* out, cudaStream_t stream);
+
 // idx (nullable, device): the problems to set up, as indices into desc/state.
+// error (nullable, device): receives PRRTC_ERR_TIMEOUT if a block's staging
+// copies did not complete within the bounded wait.
 cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
-                         int max_env_f4, cudaStream_t stream, const int* idx = nullptr);
+                         int max_env_f4, cudaStream_t stream, const int* idx = nullptr, int* error = nullptr);
 
 struct PlanLaunch {
   int grid;

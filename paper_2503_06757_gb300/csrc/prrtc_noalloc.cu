@@ -1,21 +1,22 @@
 // prrtc_noalloc.cu -- single-problem planning that allocates nothing.
 //
 // Some callers cannot allocate device memory when they plan: a real-time
-// control thread that must not block in the allocator, a host application
+// control thread that must not block in the allocator, or a host application
 // whose framework owns every byte of device memory through its own pool or
-// budget, or code that runs while another component is capturing the stream
-// into a CUDA graph (an allocation there would break or serialise the
-// capture).  prrtc_plan_noalloc serves them: the trees, the per-problem
-// state and the path buffer of the planner kernels live in one file-scope
-// static device array of fixed size, and the caller supplies the stream and
-// the host buffers for the results.
+// budget.  prrtc_plan_noalloc serves them: the trees, the per-problem state
+// and the path buffer of the planner kernels live in one file-scope static
+// device array of fixed size, and the caller supplies the stream and the host
+// buffers for the results.  The call synchronises its stream and copies the
+// results back before it returns.
 //
 // The array is shared by every call on a device and keeps the contents of the
 // last call.  The set-up on the first call per device fills the tree rows
 // with NaN (the planner's "not yet written" marker); each call's setup kernel
 // then clears exactly the rows the previous call wrote and zeroes the state.
 // Calls that overlap on the GPU (two host threads, or two streams) race on
-// the same array and must be serialised by the caller.
+// the same array and must be serialised by the caller.  The per-device
+// set-up flag lives for the process: a device reset between calls is not
+// supported.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -160,7 +161,9 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
 
   cudaError_t e = cudaMemcpyAsync(&S->desc, &D, sizeof(D), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&S->glob, &G, sizeof(G), cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = launch_setup(&S->desc, &S->state, 1, H.n_spheres + H.dof, H.n_pairs, ev.n_float4(), stream);
+  if (e == cudaSuccess)
+    e = launch_setup(&S->desc, &S->state, 1, H.n_spheres + H.dof, H.n_pairs, ev.n_float4(), stream, nullptr,
+                     &S->glob.error);
   if (e == cudaSuccess) e = launch_plan(&S->glob, &S->desc, &S->state, cfg, stream);
   if (e == cudaSuccess) e = launch_record_usage(&S->desc, &S->state, 1, stream);
   ProblemState st;

@@ -235,6 +235,16 @@ __device__ __forceinline__ int parent_of(const int* par, int node, int* err) {
 __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   const ProblemDesc* D = c.D;
   int err = 0;
+  if (c.g->debug_wait_polls) {
+    // test hook: the bounded wait of a parent walk, on a flag nothing sets
+    if (c.lane == 0) {
+      const volatile int* f = &c.S->never_set;
+      for (uint32_t k = 0; *f == 0 && k < c.g->debug_wait_polls; ++k) {
+      }
+      err = (*f == 0) ? 1 : 0;
+    }
+    err = __shfl_sync(kFull, err, 0);
+  }
   // the T_a-side chain (root first) then the T_b-side chain without its join row
   const int a_join = (s == 0) ? js : jo;
   const int b_join = (s == 0) ? jo : js;
@@ -278,7 +288,10 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   const int K = na + nb - 1;
   if (c.lane == 0) c.S->path_n = K;
   if (err || na > D->cap || nb > D->cap) {
-    if (c.lane == 0) c.S->path_status = PRRTC_ERR_TIMEOUT;
+    if (c.lane == 0) {
+      c.S->path_status = PRRTC_ERR_TIMEOUT;
+      atomicExch(&const_cast<PlanGlobals*>(c.g)->error, PRRTC_ERR_TIMEOUT);
+    }
     return;
   }
   if (K > c.g->path_cap) {
@@ -325,6 +338,7 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   if (c.lane == 0) {
     c.S->cost = seg;
     c.S->path_status = err ? PRRTC_ERR_TIMEOUT : PRRTC_SOLVED;
+    if (err) atomicExch(&const_cast<PlanGlobals*>(c.g)->error, PRRTC_ERR_TIMEOUT);
   }
 }
 
@@ -860,7 +874,11 @@ __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const Pro
       }
       if (threadIdx.x == 0) {
         s_ok = mbar_wait(&bar, phase, 1u << 26) ? 1 : 0;
-        if (!s_ok) atomicExch(&g->error, PRRTC_ERR_TIMEOUT);
+        if (!s_ok) {
+          atomicExch(&g->error, PRRTC_ERR_TIMEOUT);
+          // the block leaves: first give its bulk copies (bounded) time to land
+          mbar_wait(&bar, phase, 1u << 26);
+        }
         s_robot = D->robot;
         s_env = D->env.data;
       }
@@ -931,12 +949,15 @@ __device__ bool endpoint_collides(const ProblemDesc* D, int which, const RobotHe
 // NaN / unset parent), insert the roots, reset the counters, check start and
 // goal.  Robot and environment are staged in shared
 // memory (bulk copies, overlapping the clearing) for the endpoint check;
-// should the copy not complete in time the check reads them from global.
+// should the copy not complete in time the check reads them from global, the
+// timeout is recorded in *error (nullable), and the block waits once more
+// (bounded) for its copies before it exits.
 __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState* __restrict__ states,
-                             const int* __restrict__ idx, int robot_bytes, int env_bytes) {
+                             const int* __restrict__ idx, int robot_bytes, int env_bytes, int* error) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_hit[2];
+  __shared__ int s_late;
   const int p = idx ? idx[blockIdx.x] : blockIdx.x;
   const ProblemDesc* D = descs + p;
   ProblemState* S = states + p;
@@ -948,6 +969,7 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
   float* sthr = reinterpret_cast<float*>(spair + np_pad);
   float4* senv = reinterpret_cast<float4*>(smem + robot_bytes);
   if (threadIdx.x == 0) {
+    s_late = 0;
     mbar_init(&bar, 1);
     fence_proxy_async_smem();
     const uint32_t bytes = (uint32_t)sizeof(RobotHeader) + 8u * (uint32_t)np_pad + 16u * (uint32_t)env_f4;
@@ -1004,7 +1026,10 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < 2) {
     int ok = 0;
-    if (lane == 0) ok = mbar_wait(&bar, 0, 1u << 26) ? 1 : 0;
+    if (lane == 0) {
+      ok = mbar_wait(&bar, 0, 1u << 26) ? 1 : 0;
+      if (!ok) s_late = 1;
+    }
     ok = __shfl_sync(kFull, ok, 0);
     // each warp's sphere centres: 3 floats per sphere
     float* stage = reinterpret_cast<float*>(smem + robot_bytes + env_bytes) + warp * 3 * D->n_spheres;
@@ -1017,6 +1042,10 @@ __global__ void setup_kernel(const ProblemDesc* __restrict__ descs, ProblemState
     if (s_hit[0]) S->pre_status = PRRTC_START_IN_COLLISION;
     else if (s_hit[1]) S->pre_status = PRRTC_GOAL_IN_COLLISION;
     if (s_hit[0] | s_hit[1]) S->done = 1;
+    if (s_late) {
+      if (error) atomicExch(error, PRRTC_ERR_TIMEOUT);
+      mbar_wait(&bar, 0, 1u << 26);  // the staged copies, before the block exits
+    }
   }
 }
 
@@ -1045,14 +1074,14 @@ __global__ void gather_paths_kernel(const ProblemDesc* __restrict__ descs, const
 }  // namespace
 
 cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
-                         int max_env_f4, cudaStream_t stream, const int* idx) {
+                         int max_env_f4, cudaStream_t stream, const int* idx, int* error) {
   if (n <= 0) return cudaSuccess;
   const int robot_bytes = robot_smem_bytes((max_pairs + 3) & ~3);
   const int env_bytes = max_env_f4 * 16;
   const int smem = robot_bytes + env_bytes + stage_bytes(max_spheres);
   cudaError_t e = cudaFuncSetAttribute(setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  setup_kernel<<<n, 256, smem, stream>>>(desc, state, idx, robot_bytes, env_bytes);
+  setup_kernel<<<n, 256, smem, stream>>>(desc, state, idx, robot_bytes, env_bytes, error);
   return cudaGetLastError();
 }
 

@@ -46,7 +46,7 @@ class prrtc_params(C.Structure):
                 ("learned_ratio", C.c_float), ("seed", C.c_uint64), ("time_limit_s", C.c_double),
                 ("sampler", C.c_int32), ("halton_offset", C.c_uint32), ("dd_radius", C.c_float),
                 ("dd_alpha", C.c_float), ("dd_min_radius", C.c_float), ("workers", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("debug_wait_polls", C.c_int32), ("reserved", C.c_int32)]
 
 
 SAMPLER_PHILOX, SAMPLER_HALTON = 0, 1
@@ -94,7 +94,7 @@ EXPORTS = [
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
     "prrtc_robot_set_two_stage", "prrtc_robot_bounds", "prrtc_env_create_esdf", "prrtc_env_update_esdf",
     "prrtc_env_esdf_values", "prrtc_voxelize",
-    "prrtc_check_states", "prrtc_check_states_device", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
+    "prrtc_check_states", "prrtc_check_states_device", "prrtc_philox", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
     "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_bf16_splitk", "prrtc_gemm_error",
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
     "prrtc_proposal_forward", "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
@@ -417,6 +417,16 @@ def _path_dict(p: prrtc_path):
     else:
         d["path"] = np.zeros((0, p.dof), np.float32)
     return d
+
+
+def prrtc_philox(ctr, key: int):
+    """Philox4x32-10 blocks on the device: ctr [n x 4] uint32 counters -> [n x 4] words."""
+    c = np.ascontiguousarray(np.asarray(ctr, np.uint32).reshape(-1, 4))
+    out = np.zeros_like(c)
+    P32 = C.POINTER(C.c_uint32)
+    _check(lib().prrtc_philox(c.ctypes.data_as(P32), c.shape[0], C.c_uint64(int(key) & (2 ** 64 - 1)),
+                              out.ctypes.data_as(P32)), "prrtc_philox")
+    return out
 
 
 def prrtc_plan(robot: Robot, env: Env, q_start, q_goal, prm: prrtc_params | None = None):

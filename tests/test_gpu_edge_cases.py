@@ -112,3 +112,30 @@ def test_empty_calls(boxes8):
     with pytest.raises(P.PrrtcError) as e:
         P.prrtc_plan_batch([], P.params())
     assert e.value.code == P.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode", [P.MODE_SERIAL, P.MODE_ASYNC, P.MODE_LOCKSTEP])
+def test_bounded_device_wait_gives_up_and_the_next_call_works(boxes8, mode):
+    """Failure detection without a GPU fault: the test hook makes the path
+    extraction's bounded wait spin on a flag that nothing sets.  The wait must
+    give up after its poll limit, the problem and the call must report
+    PRRTC_ERR_TIMEOUT, and the next call on the same handles must plan as if
+    nothing had happened (serial mode: the same path as a clean call)."""
+    rb, ev = P.make_robot(boxes8.robot), P.make_env(boxes8.scene)
+    kw = dict(seed=4, mode=mode, workers=4, tree_capacity=1 << 14)
+    clean = P.prrtc_plan(rb, ev, boxes8.q_start, boxes8.q_goal, P.params(**kw))
+    assert clean["status"] == P.SOLVED
+    with pytest.raises(P.PrrtcError) as e:
+        P.prrtc_plan(rb, ev, boxes8.q_start, boxes8.q_goal, P.params(debug_wait_polls=2000, **kw))
+    assert e.value.code == P.ERR_TIMEOUT
+    again = P.prrtc_plan(rb, ev, boxes8.q_start, boxes8.q_goal, P.params(**kw))
+    assert again["status"] == P.SOLVED
+    if mode != P.MODE_ASYNC:
+        np.testing.assert_array_equal(again["path"], clean["path"])
+        assert again["iterations"] == clean["iterations"]
+    # a batch: every solved problem reports the timeout, the call fails, the next batch works
+    items = [(rb, ev, boxes8.q_start, boxes8.q_goal, s, 0) for s in (1, 2, 3)]
+    with pytest.raises(P.PrrtcError) as e:
+        P.prrtc_plan_batch(items, P.params(debug_wait_polls=100, **kw))
+    assert e.value.code == P.ERR_TIMEOUT
+    assert all(r["status"] == P.SOLVED for r in P.prrtc_plan_batch(items, P.params(**kw)))

@@ -524,3 +524,11 @@ def test_revalidate_counts_the_first_waypoint_in_the_clearance_only():
     bad, mc = O.revalidate(rb, sc, path, 0.01)   # the next state is 1 cm on: free
     assert bad == 0
     assert abs(mc - (-0.005)) < 1e-12
+
+
+def test_philox_batch_equals_single_blocks():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and not l.startswith("#")]
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox_blocks(np.array([v[0:4]] * 3, np.uint32), v[4] | (v[5] << 32))
+        assert all([int(x) for x in o] == v[6:10] for o in out)

@@ -1,7 +1,9 @@
 """prrtc_plan_noalloc: planning for callers that cannot allocate device memory
-(real-time threads, frameworks that own all device memory, code running under
-someone else's stream capture).  Its results must equal those of prrtc_plan,
-the allocating entry point, on consecutive calls that share its fixed scratch.
+(real-time threads that must not block in an allocator, frameworks that own all
+device memory).  Its results must equal those of prrtc_plan, the allocating
+entry point, on consecutive calls that share its fixed scratch -- also when the
+arm's DoF (row width) and the tree capacity change from one call to the next --
+and the calls must leave the device's free memory unchanged.
 
 Kept in its own file so that it is collected after every other test; it must
 pass both alone in a fresh process and after the rest of the suite.
@@ -83,3 +85,43 @@ def test_noalloc_path_overflow_reported(problems):
     if ref["n"] > 2:
         r = P.prrtc_plan_noalloc(rb, ev, pb.q_start, pb.q_goal, prm, path_rows=2)
         assert r["status"] == P.PATH_OVERFLOW and r["n"] == ref["n"]
+
+
+def _same_outcome(a, b):
+    assert a["status"] == b["status"]
+    assert a["iterations"] == b["iterations"]
+    assert (a["nodes_a"], a["nodes_b"]) == (b["nodes_a"], b["nodes_b"])
+    if b["status"] == P.SOLVED:
+        np.testing.assert_allclose(a["path"], b["path"], atol=TOL)
+
+
+def test_noalloc_row_width_and_capacity_change_between_calls():
+    """14-DoF rows (stride 16) after 7-DoF rows (stride 8) and back, with the tree
+    capacity shrinking and growing: each call's setup must clear exactly the rows
+    the previous call wrote, whatever their stride."""
+    probs = W.problem_set("mixed", 3, 2000, O.accept)   # 7-, 8- and 14-DoF arms in turn
+    by_dof = {pb.robot.dof: pb for pb in probs}
+    seq = [(14, 4096), (7, 512), (14, 2048), (8, 256), (7, 4096), (14, 1024)]
+    for k, (dof, cap) in enumerate(seq):
+        pb = by_dof[dof]
+        rb, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
+        prm = P.params(seed=11 + k, mode=P.MODE_SERIAL, tree_capacity=cap, path_capacity=4096, max_iters=3000)
+        ref = P.prrtc_plan(rb, ev, pb.q_start, pb.q_goal, prm)
+        got = P.prrtc_plan_noalloc(rb, ev, pb.q_start, pb.q_goal, prm)
+        _same_outcome(got, ref)
+
+
+def test_noalloc_calls_leave_device_memory_unchanged(problems):
+    torch = pytest.importorskip("torch")
+    pb = problems[0]
+    rb, ev = P.make_robot(pb.robot), P.make_env(pb.scene)
+    prm = P.params(seed=3, mode=P.MODE_SERIAL, tree_capacity=4096, path_capacity=4096)
+    P.prrtc_plan_noalloc(rb, ev, pb.q_start, pb.q_goal, prm)   # the first call does the set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for seed in range(4, 9):
+        prm.seed = seed
+        P.prrtc_plan_noalloc(rb, ev, pb.q_start, pb.q_goal, prm)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
