@@ -441,6 +441,21 @@ int prrtc_proposal_get_params(const prrtc_proposal* proposal, float* params, flo
  * out host [B * head]. */
 int prrtc_proposal_forward(prrtc_proposal* proposal, const uint8_t* occ, const float* q_start,
                            const float* q_goal, int32_t B, float* out);
+/* The same forward with its intermediate values, for element-wise tests of
+ * each layer: x host [B * 4160] (the BF16 input features: occupancy, then
+ * start and goal normalised to [-1, 1], each zero-padded to 32), h1 / h2 / h3
+ * host [B * 1024], [B * 512], [B * 512] (the BF16 activations after bias and
+ * ReLU), out host [B * head] (FP32 head), BF16 values widened to FP32.  Any
+ * output may be null. */
+int prrtc_proposal_forward_layers(prrtc_proposal* proposal, const uint8_t* occ, const float* q_start,
+                                  const float* q_goal, int32_t B, float* x, float* h1, float* h2, float* h3,
+                                  float* out);
+/* The hidden activations (BF16 widened to FP32, host [B * 1024], [B * 512],
+ * [B * 512]; any may be null) of the first B problems of the last inference
+ * batch of this proposal (prrtc_proposal_mixtures or prrtc_plan_batch_learned),
+ * for element-wise tests of the fused inference kernel.  B larger than that
+ * batch: PRRTC_ERR_INVALID_ARG. */
+int prrtc_proposal_inference_layers(prrtc_proposal* proposal, int32_t B, float* h1, float* h2, float* h3);
 /* Mean mixture negative log-likelihood of target [B * dof] and its gradient
  * (stored in the proposal, read with prrtc_proposal_get_params); no update. */
 int prrtc_proposal_grads(prrtc_proposal* proposal, const uint8_t* occ, const float* q_start,

@@ -61,13 +61,18 @@ def shapes(d: int):
     return [(dims[i + 1], dims[i]) for i in range(4)]
 
 
+def layer(W, b, h, relu):
+    """One layer: W h + b for every row of h, then ReLU on the hidden layers."""
+    z = h @ W.T + b
+    return np.maximum(z, 0.0) if relu else z
+
+
 def forward(params, x):
     """params: list of (W, b); returns out [B, P] and the activations."""
     acts = [x]
     h = x
     for li, (W, b) in enumerate(params):
-        z = h @ W.T + b
-        h = np.maximum(z, 0.0) if li < 3 else z
+        h = layer(W, b, h, li < 3)
         acts.append(h)
     return h, acts
 

@@ -373,6 +373,7 @@ struct prrtc_proposal {
   float* h1o32 = nullptr;  // [envs x kHid0]
   size_t h1o32_cap = 0;
   bf16* atile[3] = {};     // tiled hidden activations, 128-row tiles
+  int last_infer_B = 0;    // problems of the last staged inference batch
   size_t atile_cap[3] = {};
   Pending pend;            // the staged, not yet submitted, inference batch
   bool pend_ok = false;
@@ -694,6 +695,7 @@ int prrtc_internal_proposal_stage(prrtc_proposal* p, const EnvView* envs, const 
   q.B = B;
   q.rows = rows;
   q.U = U;
+  p->last_infer_B = B;
   q.sig = chain_signature(
       {(uint64_t)B, (uint64_t)rows, (uint64_t)U, (uint64_t)(uintptr_t)p->xo16,
        (uint64_t)(uintptr_t)p->h1o32, (uint64_t)(uintptr_t)p->w16t[0], (uint64_t)(uintptr_t)p->atile[0],
@@ -894,6 +896,75 @@ int prrtc_proposal_forward(prrtc_proposal* p, const uint8_t* occ, const float* q
   MCK(cudaMemcpyAsync(out, p->out32, (size_t)B * p->P * 4, cudaMemcpyDeviceToHost, p->stream));
   MCK(cudaStreamSynchronize(p->stream));
   return check_gemm_error();
+}
+
+namespace {
+
+// BF16 device rows [n x width] (row stride `ld` elements) -> FP32 host rows.
+int bf16_rows_to_host(const bf16* d, int n, int width, int ld, float* out, cudaStream_t s) {
+  if (!out) return PRRTC_OK;
+  std::vector<uint16_t> raw((size_t)n * ld);
+  MCK(cudaMemcpyAsync(raw.data(), d, raw.size() * 2, cudaMemcpyDeviceToHost, s));
+  MCK(cudaStreamSynchronize(s));
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < width; ++c) {
+      const uint32_t bits = (uint32_t)raw[(size_t)r * ld + c] << 16;
+      std::memcpy(out + (size_t)r * width + c, &bits, 4);
+    }
+  return PRRTC_OK;
+}
+
+}  // namespace
+
+int prrtc_proposal_forward_layers(prrtc_proposal* p, const uint8_t* occ, const float* q_start, const float* q_goal,
+                                  int32_t B, float* x, float* h1, float* h2, float* h3, float* out) {
+  cudaGetLastError();
+  if (!p || !occ || !q_start || !q_goal || B < 1) return mlp_fail(PRRTC_ERR_INVALID_ARG, "bad arguments");
+  const int rows = (B + 7) & ~7;
+  int rc;
+  if ((rc = ensure_scratch(p, rows))) return rc;
+  if ((rc = upload_samples(p, occ, B, q_start, q_goal, nullptr, B))) return rc;
+  features_kernel<<<rows, 256, 0, p->stream>>>(p->occ, nullptr, nullptr, p->qs, p->qg, p->d_lims, p->d_lims + kMaxDof,
+                                               B, p->dof, p->x16);
+  if ((rc = forward_rows(p, rows))) return rc;
+  if ((rc = check_gemm_error())) return rc;
+  if ((rc = bf16_rows_to_host(p->x16, B, kIn, kIn, x, p->stream))) return rc;
+  float* hs[3] = {h1, h2, h3};
+  for (int l = 0; l < 3; ++l)
+    if ((rc = bf16_rows_to_host(p->h16[l], B, p->out_dim[l], p->out_dim[l], hs[l], p->stream))) return rc;
+  if (out) {
+    MCK(cudaMemcpyAsync(out, p->out32, (size_t)B * p->P * 4, cudaMemcpyDeviceToHost, p->stream));
+    MCK(cudaStreamSynchronize(p->stream));
+  }
+  return PRRTC_OK;
+}
+
+int prrtc_proposal_inference_layers(prrtc_proposal* p, int32_t B, float* h1, float* h2, float* h3) {
+  if (!p || B < 1 || B > p->last_infer_B) return mlp_fail(PRRTC_ERR_INVALID_ARG, "no inference batch of that size");
+  MCK(cudaStreamSynchronize(p->stream));
+  const int width[3] = {kHid0, kHid1, kHid2};
+  float* outs[3] = {h1, h2, h3};
+  const int tiles = (B + 127) / 128;
+  for (int l = 0; l < 3; ++l) {
+    if (!outs[l]) continue;
+    // [row tile][64-column k-block] blocks of 128 rows x 128 bytes, 16-byte
+    // unit u of row i stored at unit u ^ (i % 8)
+    const size_t elems = (size_t)tiles * 128 * width[l];
+    std::vector<uint16_t> raw(elems);
+    MCK(cudaMemcpy(raw.data(), p->atile[l], elems * 2, cudaMemcpyDeviceToHost));
+    const int kbs = width[l] / 64;
+    for (int r = 0; r < B; ++r) {
+      const int mt = r / 128, i = r % 128;
+      for (int c = 0; c < width[l]; ++c) {
+        const int kb = c / 64, cc = c % 64;
+        const size_t byte = ((size_t)mt * kbs + kb) * (128 * 128) + (size_t)i * 128 +
+                            ((size_t)((cc >> 3) ^ (i & 7)) << 4) + ((size_t)(cc & 7) << 1);
+        const uint32_t bits = (uint32_t)raw[byte / 2] << 16;
+        std::memcpy(outs[l] + (size_t)r * width[l] + c, &bits, 4);
+      }
+    }
+  }
+  return PRRTC_OK;
 }
 
 // One step on a batch: gradients into the proposal (readable with

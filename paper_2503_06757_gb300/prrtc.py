@@ -97,7 +97,8 @@ EXPORTS = [
     "prrtc_check_states", "prrtc_check_states_device", "prrtc_philox", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
     "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_bf16_splitk", "prrtc_gemm_error",
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
-    "prrtc_proposal_forward", "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
+    "prrtc_proposal_forward", "prrtc_proposal_forward_layers", "prrtc_proposal_inference_layers",
+    "prrtc_proposal_grads", "prrtc_proposal_train", "prrtc_proposal_save",
     "prrtc_proposal_load", "prrtc_occupancy", "prrtc_proposal_mixtures", "prrtc_plan_batch_learned",
     "prrtc_server_config_default", "prrtc_server_create", "prrtc_server_submit", "prrtc_server_poll",
     "prrtc_server_wait", "prrtc_server_get_stats", "prrtc_server_destroy", "prrtc_autotune",
@@ -158,6 +159,8 @@ def lib():
     L.prrtc_proposal_info.argtypes = [C.c_void_p, _i, _i, C.POINTER(C.c_int64), _i]
     L.prrtc_proposal_get_params.argtypes = [C.c_void_p, _f, _f]
     L.prrtc_proposal_forward.argtypes = [C.c_void_p, _u8, _f, _f, C.c_int32, _f]
+    L.prrtc_proposal_forward_layers.argtypes = [C.c_void_p, _u8, _f, _f, C.c_int32, _f, _f, _f, _f, _f]
+    L.prrtc_proposal_inference_layers.argtypes = [C.c_void_p, C.c_int32, _f, _f, _f]
     L.prrtc_proposal_grads.argtypes = [C.c_void_p, _u8, _f, _f, _f, C.c_int32, _f]
     L.prrtc_proposal_train.argtypes = [C.c_void_p, _u8, C.c_int32, _i, _f, _f, _f, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_float, C.c_uint64, _f]
@@ -671,6 +674,25 @@ class Proposal:
                                               sp, gp, tp, N, int(batch), int(steps), float(lr), int(seed),
                                               losses.ctypes.data_as(_f)), "prrtc_proposal_train")
         return losses[:steps]
+
+    def forward_layers(self, occ, q_start, q_goal):
+        """(x, h1, h2, h3, head) of the training forward, BF16 values widened to FP32."""
+        occ = np.ascontiguousarray(occ, np.uint8).reshape(-1, 4096)
+        B = occ.shape[0]
+        s, sp = _fa(np.asarray(q_start).reshape(B, self.dof))
+        g, gp = _fa(np.asarray(q_goal).reshape(B, self.dof))
+        outs = [np.zeros((B, w), np.float32) for w in (4160, 1024, 512, 512, self.head)]
+        _check(self._lib.prrtc_proposal_forward_layers(self.handle, occ.ctypes.data_as(C.POINTER(C.c_uint8)), sp, gp, B,
+                                                       *[o.ctypes.data_as(_f) for o in outs]),
+               "prrtc_proposal_forward_layers")
+        return tuple(outs)
+
+    def inference_layers(self, B):
+        """Hidden activations (h1, h2, h3) of the first B rows of the last inference batch."""
+        outs = [np.zeros((B, w), np.float32) for w in (1024, 512, 512)]
+        _check(self._lib.prrtc_proposal_inference_layers(self.handle, B, *[o.ctypes.data_as(_f) for o in outs]),
+               "prrtc_proposal_inference_layers")
+        return tuple(outs)
 
     def mixtures(self, envs, q_start, q_goal):
         """Mixtures the learned planner samples from, one row of 8 + 16 dof

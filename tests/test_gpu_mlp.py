@@ -252,3 +252,82 @@ def test_planner_mixtures_match_oracle(distinct, B):
     # the second call is captured, the third replays the capture: identical output
     np.testing.assert_array_equal(prop.mixtures(envs, qs, qg), got)
     np.testing.assert_array_equal(prop.mixtures(envs, qs, qg), got)
+
+
+# ------------------------------------------------------------------ element-wise, layer by layer
+
+def bf16_params(params):
+    """The device's weights: the FP32 masters rounded to BF16 (biases stay FP32)."""
+    return [(H.bf16_round(Wm).astype(np.float64), b.astype(np.float32).astype(np.float64)) for Wm, b in params]
+
+
+def assert_layer(got, a, Wm, b, relu, bf16_out, what):
+    """One layer against the oracle fed the device's own BF16 input rows `a` and
+    BF16 weights, element by element: FP32 accumulation of K products in any
+    order is within 2 K 2^-24 (sum |a||w| + |b|) of the exact value, and a BF16
+    output adds at most half an ulp, 2^-8 of the value."""
+    from oracle import mlp_oracle as M
+    ref = M.layer(Wm, b, a, relu)
+    K = a.shape[1]
+    acc = 2.0 * K * 2.0 ** -24 * (np.abs(a) @ np.abs(Wm).T + np.abs(b))
+    bound = acc * (1 + 2.0 ** -8) + (2.0 ** -8 * np.abs(ref) if bf16_out else 0.0) + 1e-30
+    err = np.abs(got.astype(np.float64) - ref)
+    bad = np.argwhere(err > bound)
+    assert len(bad) == 0, (what, bad[:5].tolist(), float((err / bound).max()))
+    return float((err / bound).max())
+
+
+@pytest.mark.parametrize("name,B", [("arm7", 37), ("dual14", 140)])
+def test_training_forward_layers_elementwise(name, B):
+    rb = W.ROBOTS[name]()
+    params = init(rb.dof, 21)
+    prop = P.Proposal(rb.dof, rb.lower, rb.upper, flat(params))
+    occ, qs, qg, _ = make_batch(rb, B, 7)
+    x, h1, h2, h3, out = prop.forward_layers(occ, qs, qg)
+    # the features: occupancy exactly, normalised start / goal as BF16 (within one BF16 ulp
+    # of the FP64 value; the device rounds its FP32 value)
+    ref_x = oracle_x(rb, occ, qs, qg)
+    np.testing.assert_array_equal(x[:, :4096], ref_x[:, :4096])
+    assert np.all(np.abs(x - ref_x) <= 2.0 ** -7 * np.abs(ref_x) + 1e-30)
+    Wb = bf16_params(params)
+    ins = [x.astype(np.float64), h1.astype(np.float64), h2.astype(np.float64), h3.astype(np.float64)]
+    outs = [h1, h2, h3, out]
+    worst = [assert_layer(outs[l], ins[l], Wb[l][0], Wb[l][1], l < 3, l < 3, f"layer {l + 1}") for l in range(4)]
+    print(f"{name}: worst error / bound per layer {['%.3f' % w for w in worst]}")
+
+
+@pytest.mark.parametrize("distinct,B", [(False, 300), (True, 40)])
+def test_fused_inference_layers_elementwise(distinct, B):
+    """The fused inference kernel layer by layer: its hidden activations read
+    back, each checked against the oracle fed the previous one; the mixture rows
+    against the oracle's head from its third layer (log-sigmas clamped)."""
+    from oracle import mlp_oracle as M
+    rb = W.arm7()
+    d = rb.dof
+    params = init(d, 23)
+    prop = P.Proposal(d, rb.lower, rb.upper, flat(params))
+    n_sc = B if distinct else 3
+    scenes = [W.scene_shelf(1100 + k) for k in range(n_sc)]
+    made = [P.make_env(sc) for sc in scenes]
+    envs = [made[k % n_sc] for k in range(B)]
+    st = W.Stream(24, 3)
+    u = st.uniform(2 * B * d).reshape(2, B, d)
+    qs, qg = ((rb.lower + u[i] * (rb.upper - rb.lower)).astype(np.float32) for i in range(2))
+    mix = prop.mixtures(envs, qs, qg)
+    h1, h2, h3 = prop.inference_layers(B)
+    occ = np.stack([P.prrtc_occupancy(e) for e in envs])
+    x, _, _, _, _ = prop.forward_layers(occ, qs, qg)  # the same BF16 features
+    Wb = bf16_params(params)
+    assert_layer(h1, x.astype(np.float64), Wb[0][0], Wb[0][1], True, True, "layer 1")
+    assert_layer(h2, h1.astype(np.float64), Wb[1][0], Wb[1][1], True, True, "layer 2")
+    assert_layer(h3, h2.astype(np.float64), Wb[2][0], Wb[2][1], True, True, "layer 3")
+    # head -> mixture rows (logits | means | clamped log-sigmas)
+    a = h3.astype(np.float64)
+    ref = M.layer(Wb[3][0], Wb[3][1], a, False)
+    bound = 2.0 * a.shape[1] * 2.0 ** -24 * (np.abs(a) @ np.abs(Wb[3][0]).T + np.abs(Wb[3][1])) + 1e-30
+    logits, mean, raw = M.split_head(ref, d)
+    lb, mb, rbnd = M.split_head(bound, d)
+    want = np.concatenate([logits, mean.reshape(B, -1), np.clip(raw, M.LOGSIG_MIN, M.LOGSIG_MAX).reshape(B, -1)], 1)
+    tol = np.concatenate([lb, mb.reshape(B, -1), rbnd.reshape(B, -1)], 1)
+    bad = np.argwhere(np.abs(mix - want) > tol)
+    assert len(bad) == 0, (bad[:5].tolist(), float((np.abs(mix - want) / tol).max()))
