@@ -563,7 +563,7 @@ def mixed_section(args, P, flush, torch, peak_gops, steps=3):
         info = rb.info()
         counts.append((ev.info(), pb.robot.dof, info["dpad"], info["n_spheres"], info["n_pairs"]))
         items.append((rb, ev, pb.q_start, pb.q_goal, 1, k))
-    prm, tuned_ms = P.prrtc_autotune(items, P.params(), trials=1)
+    prm, tuned_ms = P.prrtc_autotune(items, P.params(), trials=3)
     batch = P.PlanBatch(items)
     for _ in range(2):
         batch.run(prm)
@@ -593,7 +593,8 @@ def mixed_section(args, P, flush, torch, peak_gops, steps=3):
     all_ttfs = [t for b in by.values() for t in b["ttfs"]]
     return dict(
         workload=MIXED_WORKLOAD, problems=len(items), steps=steps, problem_set_seconds=gen_s,
-        launch=dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, autotuned_ms=tuned_ms),
+        launch=dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, obstacle_tile=prm.obstacle_tile,
+                    expansions=prm.expansions, autotuned_mean_ms=tuned_ms, trials=3),
         ms_per_step=dev_ms / steps, states_checked_per_s=states / (dev_ms * 1e-3),
         edge_states_begun_per_s=begun / (dev_ms * 1e-3),
         ttfs_us=dict(percentiles(all_ttfs), note="solved problems, device time from launch start"),
@@ -730,8 +731,9 @@ def run_ours(args):
         # a fixed launch shape (e.g. to profile the shape the autotuner picked)
         prm.blocks, prm.warps_per_block = args.blocks, args.warps
     elif not args.no_autotune:
-        prm, tuned_ms = P.prrtc_autotune(items, prm, trials=4)
-        tuned = dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, mean_ms=tuned_ms)
+        prm, tuned_ms = P.prrtc_autotune(items, prm, trials=16)
+        tuned = dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, obstacle_tile=prm.obstacle_tile,
+                     expansions=prm.expansions, mean_ms=tuned_ms, trials=16)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     batch = P.PlanBatch(items)  # marshalled once; every run uploads its descriptors again

@@ -172,7 +172,15 @@ typedef struct prrtc_params {
                              gives up like a parent walk that found an unwritten row: the
                              problem reports PRRTC_ERR_TIMEOUT, the call returns
                              PRRTC_ERR_TIMEOUT, and later calls on the same handles work */
-  int32_t reserved;
+  int32_t expansions;     /* async mode: Alg. 1 iterations (expansions) a worker takes per claim
+                             of its problem's shared iteration counter, 1..64; 0 = 1.  Fewer
+                             claims mean less contention on the counter when many workers share
+                             a problem.  Every iteration id below max_iters is claimed once; when
+                             the budget runs out, ids claimed but not yet started are dropped */
+  int32_t obstacle_tile;  /* primitives of each type tested per round of the warp-wide first
+                             stage of the collision check (one or two per lane): 32 or 64;
+                             0 = 32.  The verdicts do not depend on it */
+  int32_t reserved[2];
 } prrtc_params;
 
 #define PRRTC_SAMPLER_PHILOX 0
@@ -382,12 +390,20 @@ typedef struct prrtc_problem {
 int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_params* params,
                      prrtc_path* out_paths, int32_t* out_status);
 
-/* Autotuner: plan the given problems `trials` times (seeds varied) under
- * several grid sizes and warps-per-block, keep the fastest (device time of
- * setup + planner kernels) in *best and remember it for this device: later
- * calls whose params leave blocks and warps_per_block at 0 use it for the
- * same row width, obstacle-count bucket (64 float4) and batch-size bucket
- * (power of two).  *best_ms (nullable) receives its mean time. */
+/* Autotuner (the number of concurrent workers is the paper's scaling knob,
+ * Sec. IV-C): plan the given problems `trials` times (the same varied seeds
+ * for every candidate) and score a candidate by the mean device time of
+ * setup + planner kernels.  It picks, one after the other: the launch shape
+ * (grid size x warps per block; shapes within 2% of the fastest count as
+ * equal and the one with the most workers wins), the obstacle tile (32 or
+ * 64) and, in async mode, the expansions per claim (1, 2, 4 or 8); a
+ * non-default tile or expansions must be 3% faster to be chosen, and fields
+ * the caller set (non-zero) are kept.  The choice goes to *best and is remembered for this
+ * device: later calls whose params leave blocks and warps_per_block at 0 use
+ * it (and its tile and expansions where those are 0) for the same row width,
+ * obstacle-count bucket (64 float4) and batch-size bucket (power of two).
+ * *best_ms (nullable) receives the chosen candidate's mean time.  Lockstep
+ * mode has nothing to tune: PRRTC_ERR_INVALID_ARG. */
 int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params* params, int32_t trials,
                    prrtc_params* best, double* best_ms);
 

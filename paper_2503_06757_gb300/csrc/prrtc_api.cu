@@ -116,7 +116,10 @@ struct DeviceCtx {
   int arena_gen = 0;
   float* h_path_head = nullptr;  // first kHeadRows path rows of a single-problem call
   // autotuned (blocks, warps) per (row width, obstacle bucket, batch-size bucket, mode)
-  std::map<uint64_t, std::pair<int, int>> tuned;
+  struct Tuned {
+    int blocks, warps, tile, expansions;
+  };
+  std::map<uint64_t, Tuned> tuned;
   // check_states scratch
   float* d_q = nullptr;
   uint8_t* d_valid = nullptr;
@@ -256,6 +259,9 @@ int validate_params(const prrtc_params* p) {
     return fail(PRRTC_ERR_INVALID_ARG, "unknown mode");
   if (p->mode == PRRTC_MODE_LOCKSTEP && (p->workers < 1 || p->workers > 1024))
     return fail(PRRTC_ERR_INVALID_ARG, "lockstep workers must be in 1..1024");
+  if (p->expansions < 0 || p->expansions > 64) return fail(PRRTC_ERR_INVALID_ARG, "expansions must be in 0..64");
+  if (p->obstacle_tile != 0 && p->obstacle_tile != 32 && p->obstacle_tile != 64)
+    return fail(PRRTC_ERR_INVALID_ARG, "obstacle_tile must be 0, 32 or 64");
   if (p->blocks < 0 || p->warps_per_block < 0 || p->warps_per_block > 16)
     return fail(PRRTC_ERR_INVALID_ARG, "blocks / warps_per_block out of range");
   if (p->time_limit_s < 0.0) return fail(PRRTC_ERR_INVALID_ARG, "time_limit_s must be >= 0");
@@ -1065,10 +1071,13 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
 
   int blocks = params->blocks, warps = params->warps_per_block;
   if (blocks == 0 && warps == 0) {
+    // the autotuner's choice for this workload, for the fields the caller left at 0
     auto it = c->tuned.find(tune_key(c->h_desc[0].dpad, max_env, n, params->mode));
     if (it != c->tuned.end()) {
-      blocks = it->second.first;
-      warps = it->second.second;
+      blocks = it->second.blocks;
+      warps = it->second.warps;
+      if (params->obstacle_tile == 0) G.obstacle_tile = it->second.tile;
+      if (params->expansions == 0 && params->mode == PRRTC_MODE_ASYNC) G.expansions = it->second.expansions;
     }
   }
   const PlanLaunch cfg =
@@ -1288,7 +1297,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       const int dof = c->h_desc[p].dof;
       P.status = status[p];
       P.dof = dof;
-      P.iterations = std::min(S.iter, params->max_iters);
+      P.iterations = reported_iterations(S, *params);
       P.nodes_a = std::min(S.count[0], params->tree_capacity);
       P.nodes_b = std::min(S.count[1], params->tree_capacity);
       P.edges_checked = (int64_t)S.edges;
@@ -1339,15 +1348,34 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
     return fail(PRRTC_ERR_INVALID_ARG, "lockstep mode runs a fixed schedule: nothing to tune");
   DeviceCtx* c = nullptr;
   if ((rc = current_ctx(&c))) return rc;
-  int resident = 0;
+  int resident = 0, max_env = 0;
   {
     // one wave of resident blocks for 4 warps, the default grid of a batch
     const RobotHeader& H = problems[0].robot->h->h;
-    int max_env = 0;
     for (int p = 0; p < n; ++p) max_env = std::max(max_env, problems[p].env->view().n_float4());
     resident = plan_launch_config(n, params->mode, 0, 4, H.n_spheres + H.dof, H.n_pairs, max_env, c->sms).grid;
     if (n == 1) resident = c->sms * 4;
   }
+  std::vector<prrtc_problem> pb(problems, problems + n);
+  // Mean over `trials` runs (the same trial keys for every candidate) of the
+  // device time of setup + planner.  The step is set by the slowest problem,
+  // so single runs are noisy: callers should give enough trials, and the
+  // choices below keep a default unless a candidate beats it clearly.
+  auto measure = [&](const prrtc_params& q, double* out) -> int {
+    double tot = 0.0;
+    for (int k = 0; k < trials; ++k) {
+      for (int p = 0; p < n; ++p) pb[p].seed = problems[p].seed + 7919ull * (uint64_t)(k + 1);
+      const int r = plan_batch_impl(pb.data(), n, &q, nullptr, nullptr, nullptr);
+      if (r) return r;
+      tot += c->last.kernel_ms + c->last.setup_ms;
+    }
+    *out = tot / trials;
+    return PRRTC_OK;
+  };
+  constexpr double kClearly = 0.97;  // a non-default tile or expansions must be 3% faster
+  constexpr double kTie = 1.02;      // launch shapes within 2% count as equal: more workers win
+  // 1. launch shape: blocks x warps per block (Sec. IV-C: the number of
+  //    concurrent workers), obstacle tile and expansions at their defaults
   std::vector<std::pair<int, int>> cands;
   const int warp_opts[5] = {2, 3, 4, 6, 8};
   for (int w : warp_opts) {
@@ -1361,32 +1389,61 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
     }
   }
   if (params->mode == PRRTC_MODE_SERIAL) cands.emplace_back(0, 1);
-  std::vector<prrtc_problem> pb(problems, problems + n);
+  prrtc_params q = *params;
+  q.obstacle_tile = params->obstacle_tile ? params->obstacle_tile : 32;
+  q.expansions = params->expansions ? params->expansions : 1;
+  std::vector<double> times(cands.size());
   double best_t = 1e30;
-  std::pair<int, int> best_c{0, 0};
-  for (auto cand : cands) {
-    prrtc_params q = *params;
-    q.blocks = cand.first;
-    q.warps_per_block = cand.second;
-    double tot = 0.0;
-    for (int t = 0; t < trials; ++t) {
-      for (int p = 0; p < n; ++p) pb[p].seed = problems[p].seed + 7919ull * (uint64_t)(t + 1);
-      if ((rc = plan_batch_impl(pb.data(), n, &q, nullptr, nullptr, nullptr))) return rc;
-      tot += c->last.kernel_ms + c->last.setup_ms;
-    }
-    if (tot / trials < best_t) {
-      best_t = tot / trials;
-      best_c = cand;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    prrtc_params r = q;
+    r.blocks = cands[i].first;
+    r.warps_per_block = cands[i].second;
+    if ((rc = measure(r, &times[i]))) return rc;
+    best_t = std::min(best_t, times[i]);
+  }
+  // among the shapes within kTie of the fastest, the one with the most workers
+  // (it checks the most states in the same time)
+  long long most = -1;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const long long workers = (long long)std::max(cands[i].first, 1) * cands[i].second;
+    if (times[i] <= kTie * best_t && workers > most) {
+      most = workers;
+      q.blocks = cands[i].first;
+      q.warps_per_block = cands[i].second;
+      best_t = std::min(best_t, times[i]);
     }
   }
-  *best = *params;
-  best->blocks = best_c.first;
-  best->warps_per_block = best_c.second;
+  for (size_t i = 0; i < cands.size(); ++i)
+    if (cands[i].first == q.blocks && cands[i].second == q.warps_per_block) best_t = times[i];
+  // 2. obstacle tile: primitives per first-stage round (one or two per lane)
+  if (params->obstacle_tile == 0) {
+    prrtc_params r = q;
+    r.obstacle_tile = 64;
+    double t = 0.0;
+    if ((rc = measure(r, &t))) return rc;
+    if (t < kClearly * best_t) {
+      best_t = t;
+      q.obstacle_tile = 64;
+    }
+  }
+  // 3. expansions per claim of a problem's iteration counter (async mode)
+  if (params->expansions == 0 && params->mode == PRRTC_MODE_ASYNC) {
+    for (int e : {2, 4, 8}) {
+      prrtc_params r = q;
+      r.expansions = e;
+      double t = 0.0;
+      if ((rc = measure(r, &t))) return rc;
+      if (t < kClearly * best_t) {
+        best_t = t;
+        q.expansions = e;
+      }
+    }
+  }
+  *best = q;
   if (best_ms) *best_ms = best_t;
-  int max_env = 0;
-  for (int p = 0; p < n; ++p) max_env = std::max(max_env, problems[p].env->view().n_float4());
   std::lock_guard<std::mutex> lk(c->mu);
-  c->tuned[tune_key(problems[0].robot->h->h.dpad, max_env, n, params->mode)] = best_c;
+  c->tuned[tune_key(problems[0].robot->h->h.dpad, max_env, n, params->mode)] =
+      DeviceCtx::Tuned{q.blocks, q.warps_per_block, q.obstacle_tile, q.expansions};
   return PRRTC_OK;
 }
 

@@ -278,46 +278,6 @@ __device__ __forceinline__ bool frame_two_stage(const float4* __restrict__ prims
   return hit;
 }
 
-// Three-stage test of one frame for a warp whose lanes hold the states of
-// one edge (the planner): first one sphere (ux, uy, uz, ur) around every
-// active lane's bounding sphere against the primitives, one primitive per
-// lane; then each lane's bounding sphere (bx, by, bz, br) against the
-// primitives the enclosing sphere touched; then the fine spheres against
-// the primitives some lane's bounding sphere touched.  Each sphere contains
-// the next with a margin, so the verdict equals the one-stage test.  Adds the
-// lane-level tests of the three stages to *tests.
-template <int K>
-__device__ __forceinline__ bool frame_three_stage(const float4* __restrict__ prims, int n, float ux, float uy,
-                                                  float uz, float ur, float bx, float by, float bz, float br,
-                                                  const float* __restrict__ stage, const float4* __restrict__ sph,
-                                                  int s0, int s1, bool active, int lane, uint32_t& tests) {
-  bool hit = false;
-  for (int base = 0; base < n; base += 32) {
-    const int k = base + lane;
-    const bool near = k < n && Prim<K>::hit(prims + Prim<K>::kStride * k, ux, uy, uz, ur);
-    uint32_t cand = __ballot_sync(kFull, near);
-    tests += 1u + (uint32_t)__popc(cand);
-    uint32_t flags = 0;
-    while (cand) {
-      const int b = __ffs(cand) - 1;
-      cand &= cand - 1;
-      flags |= (uint32_t)Prim<K>::hit(prims + Prim<K>::kStride * (base + b), bx, by, bz, br) << b;
-    }
-    flags = __reduce_or_sync(kFull, active ? flags : 0u);
-    tests += (uint32_t)(s1 - s0) * (uint32_t)__popc(flags);
-    while (flags) {
-      const int b = __ffs(flags) - 1;
-      flags &= flags - 1;
-      const float4* pk = prims + Prim<K>::kStride * (base + b);
-      for (int s = s0; s < s1; ++s) {
-        const float* st = stage + s * 96 + lane;
-        hit |= Prim<K>::hit(pk, st[0], st[32], st[64], sph[s].w);
-      }
-    }
-  }
-  return hit;
-}
-
 // Packs a verdict (bit 63) and four per-type test counts (15 bits each,
 // saturated; AABB lowest).
 __device__ __forceinline__ unsigned long long pack_tests(bool hit, const uint32_t (&t)[4]) {
@@ -350,45 +310,107 @@ static __device__ __noinline__ unsigned long long env_two_stage(const float4* __
   return pack_tests(hit, f);
 }
 
+// Three-stage test of one frame for a warp whose lanes hold the states of
+// one edge (the planner).  Stage A: one sphere (ux, uy, uz, ur) around every
+// active lane's bounding sphere against the primitives, one primitive per
+// lane.  Stage B: each lane's bounding sphere (bx, by, bz, br) against the
+// primitives stage A touched.  Stage C: the fine spheres against the
+// primitives some lane's bounding sphere touched.  Each sphere contains the
+// next with a margin, so the verdict equals the one-stage test.  The
+// lane-level tests of the three stages are added to *tests.
+//
+// Stages B and C of one primitive type for one batch of 32 primitives whose
+// stage-A candidates are `cand`.
+template <int K>
+__device__ __forceinline__ bool frame_stages_bc(const float4* __restrict__ prims, int base, uint32_t cand, float bx,
+                                                float by, float bz, float br, const float* __restrict__ stage,
+                                                const float4* __restrict__ sph, int s0, int s1, bool active, int lane,
+                                                uint32_t& tests) {
+  bool hit = false;
+  tests += 1u + (uint32_t)__popc(cand);
+  uint32_t flags = 0;
+  while (cand) {
+    const int b = __ffs(cand) - 1;
+    cand &= cand - 1;
+    flags |= (uint32_t)Prim<K>::hit(prims + Prim<K>::kStride * (base + b), bx, by, bz, br) << b;
+  }
+  flags = __reduce_or_sync(kFull, active ? flags : 0u);
+  tests += (uint32_t)(s1 - s0) * (uint32_t)__popc(flags);
+  while (flags) {
+    const int b = __ffs(flags) - 1;
+    flags &= flags - 1;
+    const float4* pk = prims + Prim<K>::kStride * (base + b);
+    for (int s = s0; s < s1; ++s) {
+      const float* st = stage + s * 96 + lane;
+      hit |= Prim<K>::hit(pk, st[0], st[32], st[64], sph[s].w);
+    }
+  }
+  return hit;
+}
+
 // The three stages of one frame (warp = one edge), out of line; same return.
+// Stage A of all four primitive types runs first, `tile` primitives of each
+// type per round (one or two per lane), so that a lane's tests of a round are
+// independent; stages B and C then take the round's candidates in order.
 static __device__ __noinline__ unsigned long long env_three_stage(const float4* __restrict__ env, int n_aabb,
                                                            int n_obb, int n_cyl, int n_sph, float ux, float uy,
                                                            float uz, float ur, float bx, float by, float bz, float br,
                                                            const float* __restrict__ stage,
                                                            const float4* __restrict__ sph, int s0, int s1,
-                                                           bool active, int lane) {
+                                                           bool active, int lane, int tile) {
   uint32_t t[4] = {0, 0, 0, 0};
   bool hit = false;
-  const float4* e = env;
-  hit |= frame_three_stage<kAabb>(e, n_aabb, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
-                                  t[kAabb]);
-  e += 2 * n_aabb;
-  hit |= frame_three_stage<kObb>(e, n_obb, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
-                                 t[kObb]);
-  e += 5 * n_obb;
-  hit |= frame_three_stage<kCyl>(e, n_cyl, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
-                                 t[kCyl]);
-  e += 2 * n_cyl;
-  hit |= frame_three_stage<kSph>(e, n_sph, ux, uy, uz, ur, bx, by, bz, br, stage, sph, s0, s1, active, lane,
-                                 t[kSph]);
+  const float4* ea = env;
+  const float4* eo = ea + 2 * n_aabb;
+  const float4* ec = eo + 5 * n_obb;
+  const float4* es = ec + 2 * n_cyl;
+  const int nmax = max(max(n_aabb, n_obb), max(n_cyl, n_sph));
+  const int halves = tile >= 64 ? 2 : 1;
+  for (int base = 0; base < nmax; base += 32 * halves) {
+    bool na[2], no[2], nc[2], ns[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = base + 32 * h + lane;
+      const bool on = h < halves;
+      na[h] = on && k < n_aabb && Prim<kAabb>::hit(ea + 2 * k, ux, uy, uz, ur);
+      no[h] = on && k < n_obb && Prim<kObb>::hit(eo + 5 * k, ux, uy, uz, ur);
+      nc[h] = on && k < n_cyl && Prim<kCyl>::hit(ec + 2 * k, ux, uy, uz, ur);
+      ns[h] = on && k < n_sph && Prim<kSph>::hit(es + k, ux, uy, uz, ur);
+    }
+    for (int h = 0; h < halves; ++h) {
+      const int b0 = base + 32 * h;
+      const uint32_t ca = __ballot_sync(kFull, na[h]), co = __ballot_sync(kFull, no[h]);
+      const uint32_t cc = __ballot_sync(kFull, nc[h]), cs = __ballot_sync(kFull, ns[h]);
+      if (b0 < n_aabb) hit |= frame_stages_bc<kAabb>(ea, b0, ca, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kAabb]);
+      if (b0 < n_obb) hit |= frame_stages_bc<kObb>(eo, b0, co, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kObb]);
+      if (b0 < n_cyl) hit |= frame_stages_bc<kCyl>(ec, b0, cc, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kCyl]);
+      if (b0 < n_sph) hit |= frame_stages_bc<kSph>(es, b0, cs, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kSph]);
+    }
+  }
   return pack_tests(hit, t);
+}
+
+// Order-preserving map of binary32 to uint32 (and back): larger floats give
+// larger keys, so integer warp reductions take exact float minima and maxima.
+__device__ __forceinline__ uint32_t f2key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
 // Sphere around the active lanes' spheres (centre (x, y, z), common radius r):
 // centre of the lanes' bounding box, radius half its diagonal + r, enlarged by
 // 1e-5 m and one part in 10^6 so that FP32 rounding keeps every lane inside.
+// The box comes from six integer min / max warp reductions (exact).
 __device__ __forceinline__ float4 warp_enclosing_sphere(float x, float y, float z, float r, bool active) {
-  float lx = active ? x : INFINITY, ly = active ? y : INFINITY, lz = active ? z : INFINITY;
-  float hx = active ? x : -INFINITY, hy = active ? y : -INFINITY, hz = active ? z : -INFINITY;
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    lx = fminf(lx, __shfl_xor_sync(kFull, lx, off));
-    ly = fminf(ly, __shfl_xor_sync(kFull, ly, off));
-    lz = fminf(lz, __shfl_xor_sync(kFull, lz, off));
-    hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, off));
-    hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, off));
-    hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, off));
-  }
+  const float lx = key2f(__reduce_min_sync(kFull, f2key(active ? x : INFINITY)));
+  const float ly = key2f(__reduce_min_sync(kFull, f2key(active ? y : INFINITY)));
+  const float lz = key2f(__reduce_min_sync(kFull, f2key(active ? z : INFINITY)));
+  const float hx = key2f(__reduce_max_sync(kFull, f2key(active ? x : -INFINITY)));
+  const float hy = key2f(__reduce_max_sync(kFull, f2key(active ? y : -INFINITY)));
+  const float hz = key2f(__reduce_max_sync(kFull, f2key(active ? z : -INFINITY)));
   const float dx = hx - lx, dy = hy - ly, dz = hz - lz;
   const float half = 0.5f * sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
   return make_float4(0.5f * (lx + hx), 0.5f * (ly + hy), 0.5f * (lz + hz), (half + r) * 1.000001f + 1e-5f);
@@ -429,7 +451,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
                                                const float* __restrict__ thr, const float4* __restrict__ env,
                                                int n_aabb, int n_obb, int n_cyl, int n_sph, const EsdfGrid& grid,
                                                float* __restrict__ stage, const QS& qs, bool active, int lane,
-                                               WarpCount* wc) {
+                                               WarpCount* wc, int tile = 32) {
   const bool has_grid = grid.v != nullptr;
   const bool has_prims = (n_aabb | n_obb | n_cyl | n_sph) != 0;
   const int dof = R->dof;
@@ -566,7 +588,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
         const float gx = gst[0], gy = gst[32], gz = gst[64];
         const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
         const unsigned long long r = env_three_stage(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz,
-                                                     cb.w, stage, R->sph, s0, s1, active, lane);
+                                                     cb.w, stage, R->sph, s0, s1, active, lane, tile);
         hit |= (r >> 63) != 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)((r >> (15 * k)) & 0x7fffu);

@@ -43,6 +43,8 @@ struct PlanGlobals {
   float dd_min_radius;
   int workers;           // lockstep mode: iterations per round (B)
   uint32_t debug_wait_polls;  // test hook: bounded wait on ProblemState::never_set before a path walk
+  int expansions;        // async: iterations a worker claims per atomic on the problem's counter
+  int obstacle_tile;     // primitives per type per first-stage round of the edge check (32 or 64)
 };
 
 // Check of the sampler and dynamic-domain fields of a parameter block; null
@@ -75,6 +77,8 @@ inline void globals_from_params(PlanGlobals& G, const prrtc_params& p) {
   G.dd_min_radius = p.dd_min_radius;
   G.workers = p.mode == PRRTC_MODE_LOCKSTEP ? p.workers : 1;
   G.debug_wait_polls = p.debug_wait_polls > 0 ? (uint32_t)p.debug_wait_polls : 0u;
+  G.expansions = (p.mode == PRRTC_MODE_ASYNC && p.expansions > 1) ? p.expansions : 1;
+  G.obstacle_tile = p.obstacle_tile == 64 ? 64 : 32;
 }
 
 // Per-problem inputs (uploaded every call).
@@ -127,6 +131,13 @@ struct ProblemState {
   int used_dpad;
   int never_set;         // stays 0: the flag the bounded-wait test hook waits on
 };
+
+// Alg. 1 iterations a problem ran: the tickets handed out, or with batched
+// claims (expansions > 1) the iteration bodies the workers counted.
+inline int reported_iterations(const ProblemState& S, const prrtc_params& p) {
+  const long long n = (p.mode == PRRTC_MODE_ASYNC && p.expansions > 1) ? (long long)S.iterations : (long long)S.iter;
+  return (int)(n < p.max_iters ? n : p.max_iters);
+}
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& host_header, EnvView env, const float* q,

@@ -188,7 +188,7 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
   info_out->status = status;
   info_out->n = (status == PRRTC_SOLVED || status == PRRTC_PATH_OVERFLOW) ? st.path_n : 0;
   info_out->dof = H.dof;
-  info_out->iterations = std::min(st.iter, params->max_iters);
+  info_out->iterations = reported_iterations(st, *params);
   info_out->q = (status == PRRTC_SOLVED) ? path_out : nullptr;
   info_out->cost = st.cost;
   info_out->nodes_a = std::min(st.count[0], params->tree_capacity);

@@ -177,7 +177,8 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
     const int kk = active ? k : N;
     const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N, &c.S->solved};
     if (state_collides<true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
-                             c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt)) {
+                             c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt,
+                             c.g->obstacle_tile)) {
       __syncwarp();  // lane 0 may have just set the flag
       if (c.cnt->aborted) {
         // the problem was solved meanwhile and the check stopped early: this
@@ -425,13 +426,21 @@ __device__ void worker(const Ctx& c) {
   const float res = g->resolution;
   const int n_full = g->n_full;
   const bool mine = lane < dpad;
+  int claim_next = 0, claim_left = 0;  // iteration ids claimed by lane 0 and not yet run
   for (;;) {
     int stop = 0, it = 0;
     if (lane == 0) {
       // a spent time slice stops the worker before it takes an iteration
       // ticket; the problem resumes in the next launch of a resumable batch
       stop = ld_volatile(&S->done) | ld_volatile(&S->solved) | (slice_over(g) ? 1 : 0);
-      if (!stop) it = atomicAdd(&S->iter, 1);
+      if (!stop) {
+        if (claim_left == 0) {  // `expansions` consecutive ids per claim of the counter
+          claim_next = atomicAdd(&S->iter, g->expansions);
+          claim_left = g->expansions;
+        }
+        it = claim_next++;
+        --claim_left;
+      }
     }
     stop = __shfl_sync(kFull, stop, 0);
     if (stop) break;

@@ -296,7 +296,7 @@ bool server_round(prrtc_server* s) {
     const int dof = s->h_desc[p].dof;
     P.status = status_of(S);
     P.dof = dof;
-    P.iterations = std::min(S.iter, prm.max_iters);
+    P.iterations = reported_iterations(S, prm);
     P.nodes_a = std::min(S.count[0], prm.tree_capacity);
     P.nodes_b = std::min(S.count[1], prm.tree_capacity);
     P.edges_checked = (int64_t)S.edges;

@@ -46,7 +46,8 @@ class prrtc_params(C.Structure):
                 ("learned_ratio", C.c_float), ("seed", C.c_uint64), ("time_limit_s", C.c_double),
                 ("sampler", C.c_int32), ("halton_offset", C.c_uint32), ("dd_radius", C.c_float),
                 ("dd_alpha", C.c_float), ("dd_min_radius", C.c_float), ("workers", C.c_int32),
-                ("debug_wait_polls", C.c_int32), ("reserved", C.c_int32)]
+                ("debug_wait_polls", C.c_int32), ("expansions", C.c_int32), ("obstacle_tile", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 SAMPLER_PHILOX, SAMPLER_HALTON = 0, 1
@@ -845,7 +846,8 @@ class Server:
 
 
 def prrtc_autotune(problems, prm: prrtc_params | None = None, trials: int = 3):
-    """Fastest (blocks, warps_per_block) for these problems; remembered by the library."""
+    """Launch shape, obstacle tile and expansions per claim for these problems (mean device
+    time over `trials` runs); returns (params, mean ms) and is remembered by the library."""
     prm = prm or prrtc_params_default()
     keep = []
     n = len(problems)

@@ -300,10 +300,47 @@ def test_autotune_picks_a_candidate_and_later_calls_use_it(boxes8_problems):
     items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, 1, k) for k, q in enumerate(boxes8_problems)]
     best, ms = P.prrtc_autotune(items, P.params(), trials=2)
     assert best.warps_per_block in (2, 3, 4, 6, 8) and best.blocks >= 1 and ms > 0
+    assert best.obstacle_tile in (32, 64) and best.expansions in (1, 2, 4, 8)
     res = P.prrtc_plan_batch(items, P.params())
     st = P.prrtc_last_launch_stats()
     assert st["grid"] == best.blocks and st["block_threads"] == 32 * best.warps_per_block
     assert all(r["status"] == P.SOLVED for r in res)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_obstacle_tile_does_not_change_serial_plans(seed):
+    """Two primitives per lane in the first stage test the same spheres against
+    the same primitives: serial plans are bitwise those of one per lane, also on
+    scenes with more than 64 primitives of a type."""
+    probs = W.problem_set("mixed", 6, 2000, O.accept, n_obstacles=120)
+    items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, seed, k) for k, q in enumerate(probs)]
+    kw = dict(mode=P.MODE_SERIAL, tree_capacity=1 << 14, max_iters=3000)
+    a = P.prrtc_plan_batch(items, P.params(obstacle_tile=32, **kw))
+    b = P.prrtc_plan_batch(items, P.params(obstacle_tile=64, **kw))
+    for x, y in zip(a, b):
+        for name in ("status", "iterations", "nodes_a", "nodes_b", "edge_states", "verdict_states"):
+            assert x[name] == y[name], name
+        np.testing.assert_array_equal(x["path"], y["path"])
+
+
+def test_expansions_per_claim(boxes8_problems):
+    """Claims of several iteration ids at once: async plans stay valid, the count
+    of iterations run stays within the budget, and serial mode ignores it."""
+    items = [(P.make_robot(q.robot), P.make_env(q.scene), q.q_start, q.q_goal, 3, k) for k, q in enumerate(boxes8_problems)]
+    for e in (1, 4, 16):
+        for r, pb in zip(P.prrtc_plan_batch(items, P.params(expansions=e)), boxes8_problems):
+            assert_path_valid(pb, r)
+    small = P.prrtc_plan_batch(items, P.params(expansions=8, max_iters=5, goal_bias=0.0))
+    assert all(r["iterations"] <= 5 for r in small)
+    s1 = P.prrtc_plan_batch(items, P.params(mode=P.MODE_SERIAL, expansions=1))
+    s8 = P.prrtc_plan_batch(items, P.params(mode=P.MODE_SERIAL, expansions=8))
+    for x, y in zip(s1, s8):
+        assert x["iterations"] == y["iterations"]
+        np.testing.assert_array_equal(x["path"], y["path"])
+    for bad in (dict(expansions=65), dict(expansions=-1), dict(obstacle_tile=48)):
+        with pytest.raises(P.PrrtcError) as e:
+            P.prrtc_plan_batch(items, P.params(**bad))
+        assert e.value.code == P.ERR_INVALID_ARG
 
 
 def test_serial_batch_success_and_mean_cost_match_oracle():
