@@ -367,6 +367,37 @@ def learned_section(args, P):
                      "fused kernel for the rest) that precedes planning"), prop
 
 
+def learned_full_section(P, dofs=(7, 14), paths=50000, steps=20000, eval_scenes=500):
+    """The learned proposal at its stated size: per arm (7-DoF, and the 14-DoF dual
+    arm with the shelf turned to face both arms), at least `paths` plain-planner
+    solution paths on seeded shelf scenes, `steps` Adam steps of 512 samples, then
+    plain vs 50% learned / 50% uniform sampling on `eval_scenes` held-out scenes
+    (one problem each) with the same Philox keys."""
+    from paper_2503_06757_gb300 import learned as L
+    from paper_2503_06757_gb300 import workload as W
+    out = dict(paths_target=paths, steps=steps, eval_scenes=eval_scenes, ratio=0.5)
+    for dof in dofs:
+        rb = W.arm7() if dof == 7 else W.dual14()
+        t0 = time.perf_counter()
+        parts, seed0, got = [], 100000, 0
+        while got < paths:
+            part = L.build_dataset(rb, 500, 40, seed0)
+            parts.append(part)
+            got += part.paths
+            seed0 += 500
+        ds = L.concat_datasets(parts)
+        data_s = time.perf_counter() - t0
+        prop, losses, tt = L.train(rb, ds, steps=steps, batch=512)
+        held = L.build_dataset(rb, 30, 10, 900000)
+        ev = L.evaluate(rb, eval_scenes, 1, 9000, prop, ratio=0.5)
+        out[f"dof{dof}"] = dict(
+            robot=rb.name, train=dict(paths=ds.paths, problems=ds.problems, samples=int(len(ds.target)),
+                                      data_seconds=data_s, train_seconds=tt, loss_first=float(np.mean(losses[:20])),
+                                      loss_last=float(np.mean(losses[-20:])), heldout_nll=L.held_out_nll(prop, held)),
+            eval=ev)
+    return out
+
+
 def door_section(P, door, keys=(1, 2, 3)):
     """The learned proposal where its gain is structural: a point robot in two rooms
     joined by a door in a wall (opening `door` in y).  Train on 256 plain-planner
@@ -418,6 +449,64 @@ def serving_section(args, P, proposals):
         out["slices"] = server.stats()["slices"]
         server.close()
     return out
+
+
+def serving_full_section(args, P, proposals, queries=10000, oracle_sample=96):
+    """The serving loop at its stated size: at least `queries` Poisson arrivals per
+    rate (200 and 1000 queries/s), then the oracle on a seeded sample of the same
+    queries (the scene each one saw at submission, the same seed, budget and tree
+    capacity; serial plain sampling): success rates side by side."""
+    from oracle import oracle as O
+    from paper_2503_06757_gb300 import serving as S
+    scenes = S.build_scenes(30, 12, 3000)
+    prm = P.params(max_iters=20000, tree_capacity=1 << 13, path_capacity=1 << 12, learned_ratio=0.5)
+    server = P.Server(prm, slice_us=300)
+    rates = (200, 1000)
+    mover = S.ObstacleMover(scenes, seconds=sum(queries / r for r in rates) + 30.0)
+    mover.start()
+    out = dict(workload="30 resident scenes (7/8/14-DoF in turn, 40-120 obstacles + 5 spheres moving at "
+                        "0.5 m/s, updated at 30 Hz), Poisson arrivals; learned proposal on the 7-DoF queries",
+               slice_us=300, slots=server.stats()["slots"], queries_per_rate=queries)
+    records = {}
+    try:
+        for rate in rates:
+            rec = []
+            out[f"rate_{rate}"] = S.run_rate(server, scenes, rate, queries / rate, seed=rate, proposals=proposals,
+                                             mover=mover, record=rec)
+            records[rate] = rec
+    finally:
+        mover.stop_flag.set()
+        mover.join()
+        out["obstacle_updates"] = mover.ticks
+        out["slices"] = server.stats()["slices"]
+        server.close()
+    rng = np.random.default_rng(5)
+    for rate, rec in records.items():
+        done = [q for q in rec if "status" in q]
+        pick = [done[i] for i in sorted(rng.choice(len(done), min(oracle_sample, len(done)), replace=False))]
+        probs = []
+        for q in pick:
+            sc = scenes[q["scene"]]
+            qs, qg = sc.queries[q["query"]]
+            probs.append(dataclasses_replace_problem(sc.robot, S.scene_at(sc, q["moving"]), qs, qg, q["seed"]))
+        t = time.perf_counter()
+        orc = O.plan_batch(probs, seeds=[q["seed"] for q in pick], problem_ids=[q["problem_id"] for q in pick],
+                           range=1.0, resolution=float(np.float32(1 / 32)), goal_bias=float(np.float32(0.05)),
+                           max_iters=20000, tree_capacity=1 << 13, path_capacity=1 << 12)
+        secs = time.perf_counter() - t
+        rows = dict(plain_both=[], learned_on_gpu=[])
+        for q, o in zip(pick, orc):
+            rows["learned_on_gpu" if q["learned"] else "plain_both"].append((q["status"] == P.SOLVED, o["status"] == 0))
+        out[f"rate_{rate}"]["oracle_sample"] = dict(
+            queries=len(pick), oracle_seconds=secs,
+            **{k: dict(queries=len(v), gpu_success=float(np.mean([a for a, _ in v])) if v else None,
+                       oracle_success=float(np.mean([b for _, b in v])) if v else None) for k, v in rows.items()})
+    return out
+
+
+def dataclasses_replace_problem(robot, scene, qs, qg, seed):
+    from paper_2503_06757_gb300 import workload as W
+    return W.Problem(robot, scene, np.asarray(qs, np.float64), np.asarray(qg, np.float64), seed)
 
 
 # ------------------------------------------------------------------ tensor-core GEMM
@@ -594,7 +683,7 @@ def mixed_section(args, P, flush, torch, peak_gops, steps=3):
     return dict(
         workload=MIXED_WORKLOAD, problems=len(items), steps=steps, problem_set_seconds=gen_s,
         launch=dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, obstacle_tile=prm.obstacle_tile,
-                    expansions=prm.expansions, autotuned_mean_ms=tuned_ms, trials=3),
+                    expansions=prm.expansions, autotuned_median_ttfs_ms=tuned_ms, trials=3),
         ms_per_step=dev_ms / steps, states_checked_per_s=states / (dev_ms * 1e-3),
         edge_states_begun_per_s=begun / (dev_ms * 1e-3),
         ttfs_us=dict(percentiles(all_ttfs), note="solved problems, device time from launch start"),
@@ -733,7 +822,7 @@ def run_ours(args):
     elif not args.no_autotune:
         prm, tuned_ms = P.prrtc_autotune(items, prm, trials=16)
         tuned = dict(blocks=prm.blocks, warps_per_block=prm.warps_per_block, obstacle_tile=prm.obstacle_tile,
-                     expansions=prm.expansions, mean_ms=tuned_ms, trials=16)
+                     expansions=prm.expansions, median_ttfs_ms=tuned_ms, trials=16)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     batch = P.PlanBatch(items)  # marshalled once; every run uploads its descriptors again
@@ -913,6 +1002,12 @@ def main():
     ap.add_argument("--learned-steps", type=int, default=3000)
     ap.add_argument("--learned-eval-scenes", type=int, default=500)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-full", action="store_true",
+                    help="only the serving loop at its stated size (10^4 queries per rate) with an oracle sample; "
+                         "one JSON line")
+    ap.add_argument("--learned-full", action="store_true",
+                    help="only the learned proposal at its stated size (7- and 14-DoF networks, 50k paths each, "
+                         "500 held-out scenes); one JSON line")
     ap.add_argument("--gemm-only", action="store_true",
                     help="only the tensor-core GEMM microbenchmark (one JSON line; for profiling the GEMM)")
     args = ap.parse_args()
@@ -920,6 +1015,23 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving_full:
+        import torch
+        from paper_2503_06757_gb300 import build as B
+        B.build()
+        from paper_2503_06757_gb300 import prrtc as P
+        torch.cuda.init()
+        _, prop = learned_section(args, P)
+        print(json.dumps(dict(section="serving_full", **serving_full_section(args, P, {"arm7": prop}))))
+        return 0
+    if args.learned_full:
+        import torch
+        from paper_2503_06757_gb300 import build as B
+        B.build()
+        from paper_2503_06757_gb300 import prrtc as P
+        torch.cuda.init()
+        print(json.dumps(dict(section="learned_full", **learned_full_section(P))))
+        return 0
     if args.gemm_only:
         import torch
         from paper_2503_06757_gb300 import build as B

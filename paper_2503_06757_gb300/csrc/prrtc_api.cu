@@ -1357,17 +1357,28 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
     if (n == 1) resident = c->sms * 4;
   }
   std::vector<prrtc_problem> pb(problems, problems + n);
-  // Mean over `trials` runs (the same trial keys for every candidate) of the
-  // device time of setup + planner.  The step is set by the slowest problem,
-  // so single runs are noisy: callers should give enough trials, and the
+  // The score of a candidate: the mean over `trials` runs (the same trial keys
+  // for every candidate) of the batch's median time to first solution -- setup
+  // time plus each problem's device time from launch start to its solution,
+  // an unsolved problem counting the whole launch.  The batch's step time is
+  // the maximum of those times and its mean is led by the few hardest
+  // problems, both noisy; the median follows the typical problem.  The
   // choices below keep a default unless a candidate beats it clearly.
+  std::vector<double> ttfs(n);
   auto measure = [&](const prrtc_params& q, double* out) -> int {
     double tot = 0.0;
     for (int k = 0; k < trials; ++k) {
       for (int p = 0; p < n; ++p) pb[p].seed = problems[p].seed + 7919ull * (uint64_t)(k + 1);
       const int r = plan_batch_impl(pb.data(), n, &q, nullptr, nullptr, nullptr);
       if (r) return r;
-      tot += c->last.kernel_ms + c->last.setup_ms;
+      const unsigned long long t0 = c->h_glob->t0;
+      for (int p = 0; p < n; ++p) {
+        const ProblemState& S = c->h_state[p];
+        const bool solved = S.solved && S.t_solve >= t0;
+        ttfs[p] = solved ? (double)(S.t_solve - t0) * 1e-6 : c->last.kernel_ms;
+      }
+      std::nth_element(ttfs.begin(), ttfs.begin() + n / 2, ttfs.end());
+      tot += c->last.setup_ms + ttfs[n / 2];
     }
     *out = tot / trials;
     return PRRTC_OK;

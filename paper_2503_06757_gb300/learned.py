@@ -90,7 +90,7 @@ def shelf_problem_batch(robot: W.Robot, n_scenes: int, pairs_per_scene: int, see
     rb = P.make_robot(robot)
     scenes, envs, probs = [], [], []
     for k in range(n_scenes):
-        sc = W.scene_shelf(seed0 + k)
+        sc = W.scene_shelf(seed0 + k, W.shelf_facing(robot))
         ev = P.make_env(sc)
         s, g = scene_pairs(robot, sc, rb, ev, pairs_per_scene, seed0 + k)
         scenes.append(sc)
@@ -128,6 +128,20 @@ def build_dataset(robot: W.Robot, n_scenes: int, pairs_per_scene: int, seed0: in
                    q_start=np.asarray(qs, np.float32), q_goal=np.asarray(qg, np.float32),
                    target=np.asarray(tg, np.float32), paths=n_paths, problems=len(probs),
                    seconds=time.perf_counter() - t0)
+
+
+def concat_datasets(parts: list[Dataset]) -> Dataset:
+    """One dataset from several built on disjoint scene ranges (scene indices renumbered)."""
+    occ, scene_of, off = [], [], 0
+    for d in parts:
+        occ.append(d.occ)
+        scene_of.append(d.scene_of + off)
+        off += d.occ.shape[0]
+    cat = lambda name: np.concatenate([getattr(d, name) for d in parts])
+    return Dataset(dof=parts[0].dof, occ=np.concatenate(occ), scene_of=np.concatenate(scene_of).astype(np.int32),
+                   q_start=cat("q_start"), q_goal=cat("q_goal"), target=cat("target"),
+                   paths=sum(d.paths for d in parts), problems=sum(d.problems for d in parts),
+                   seconds=sum(d.seconds for d in parts))
 
 
 def train(robot: W.Robot, data: Dataset, steps: int, batch: int = 512, lr: float = 1e-3, seed: int = 1,

@@ -846,8 +846,9 @@ class Server:
 
 
 def prrtc_autotune(problems, prm: prrtc_params | None = None, trials: int = 3):
-    """Launch shape, obstacle tile and expansions per claim for these problems (mean device
-    time over `trials` runs); returns (params, mean ms) and is remembered by the library."""
+    """Launch shape, obstacle tile and expansions per claim for these problems, scored by the
+    batch's median time to first solution over `trials` runs; returns (params, score in ms) and
+    is remembered by the library."""
     prm = prm or prrtc_params_default()
     keep = []
     n = len(problems)

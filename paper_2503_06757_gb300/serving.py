@@ -62,36 +62,41 @@ def build_scenes(n_scenes: int, pairs: int, seed0: int, n_obs=(40, 120)):
 class ObstacleMover(threading.Thread):
     """Publishes the moving spheres' positions at `rate_hz` until stopped."""
 
-    def __init__(self, scenes, rate_hz: float = 30.0):
+    def __init__(self, scenes, rate_hz: float = 30.0, seconds: float = 30.0):
         super().__init__(daemon=True)
         self.scenes = scenes
         self.period = 1.0 / rate_hz
         self.stop_flag = threading.Event()
         self.ticks = 0
-        self.tracks = []
-        for sc in scenes:
-            # pre-computed positions for up to 30 s of ticks
-            self.tracks.append(sc.moving)
+        self.n_ticks = int(seconds * rate_hz) + 1  # pre-computed positions for `seconds` of ticks
+        self.tracks = [sc.moving for sc in scenes]
+        # the positions last published per scene (read by clients that record what a query saw)
+        self.current = [sc.moving.centres0.copy() for sc in scenes]
 
     def run(self):
         k = 0
-        paths = [mv.positions_track(900) for mv in self.tracks]
+        paths = [mv.positions_track(self.n_ticks) for mv in self.tracks]
         while not self.stop_flag.is_set():
             t0 = time.perf_counter()
             k += 1
-            for sc, tr in zip(self.scenes, paths):
+            for i, (sc, tr) in enumerate(zip(self.scenes, paths)):
                 pos = tr[min(k, len(tr) - 1)]
                 obs = P.obstacles_from_scene(W.Scene(boxes=np.zeros((0, 15)), cylinders=np.zeros((0, 8)),
                                                      spheres=np.concatenate([pos, sc.moving.radii[:, None]], 1)))
                 sc.env.update(sc.moving_ids, obs)
+                self.current[i] = np.array(pos, copy=True)
             self.ticks = k
             dt = self.period - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
 
 
-def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int, proposals=None):
-    """Submit queries with exponential inter-arrival gaps for duration_s, then drain."""
+def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int, proposals=None, mover=None,
+             record=None):
+    """Submit queries with exponential inter-arrival gaps for duration_s, then drain.
+    With `record` (a list) and `mover`, every query is appended as a dict of its
+    scene, query, seed, problem id, the moving spheres' positions published when
+    it was submitted, and (after the drain) its status."""
     rng = np.random.default_rng(seed)
     pool = [(si, qi) for si, sc in enumerate(scenes) for qi in range(len(sc.queries))]
     order = rng.permutation(len(pool))
@@ -117,7 +122,10 @@ def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int
                 break
             skipped += 1
         prop = proposals.get(sc.robot.name) if proposals else None
-        server.submit(sc.rb, sc.env, qs, qg, seed=seed + k, problem_id=k, proposal=prop)
+        ticket = server.submit(sc.rb, sc.env, qs, qg, seed=seed + k, problem_id=k, proposal=prop)
+        if record is not None and mover is not None:
+            record.append(dict(ticket=ticket, scene=si, query=qi, seed=seed + k, problem_id=k,
+                               moving=np.array(mover.current[si], copy=True), learned=prop is not None))
         k += 1
         t_next += rng.exponential(1.0 / rate)
     submitted = k
@@ -129,6 +137,11 @@ def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int
         if not got:
             break
         res += got
+    if record is not None:
+        by_ticket = {r["ticket"]: r for r in res}
+        for q in record:
+            if q["ticket"] in by_ticket and "status" not in q:
+                q["status"] = by_ticket[q["ticket"]]["status"]
     lat = np.array([r["latency_ms"] for r in res])
     que = np.array([r["queue_ms"] for r in res])
     ok = [r for r in res if r["status"] == P.SOLVED]
@@ -140,3 +153,10 @@ def run_rate(server: P.Server, scenes, rate: float, duration_s: float, seed: int
                 queue_ms=dict(p50=pct(que, 50), p99=pct(que, 99)),
                 success_rate=len(ok) / max(len(res), 1), endpoint_in_collision=in_coll,
                 skipped_blocked_endpoints=skipped)
+
+
+def scene_at(sc: ServeScene, moving_positions) -> W.Scene:
+    """The scene with its moving spheres at the given positions (what a query saw)."""
+    sph = sc.scene.spheres.copy()
+    sph[len(sph) - N_MOVING:, :3] = moving_positions
+    return W.Scene(boxes=sc.scene.boxes, cylinders=sc.scene.cylinders, spheres=sph)

@@ -401,14 +401,52 @@ def _shelf_structure():
     return boxes
 
 
-def scene_shelf(seed: int) -> Scene:
+def scene_shelf(seed: int, facing: str = "x") -> Scene:
     """3x3 cubby shelf (9 cuboids) plus clutter inside the cubbies.
 
     Clutter: 21 more cuboids (sides U[0.05,0.3] m), 10 capped cylinders
     (radius U[0.03,0.1] m, length U[0.1,0.5] m, uniform random unit
     quaternion) and 10 spheres (radius U[0.03,0.15] m), each centred at a
     uniform point inside a uniformly chosen cell; objects may protrude.
+    facing "x": the shelf's front is the plane x = 0.45 (the single arm at the
+    origin faces it).  facing "y": the same scene turned 90 degrees about the
+    vertical axis, front plane y = 0.45 -- in front of both arms of the dual
+    arm (bases at x = -0.3 and +0.3), each 0.45 m from it as the single arm is.
     """
+    sc = _scene_shelf_x(seed)
+    return sc if facing == "x" else rotate_scene_z90(sc)
+
+
+def shelf_facing(robot: Robot) -> str:
+    """Shelf placement for a robot: in front of the single arm ("x") or of both
+    arms of the dual arm ("y")."""
+    return "y" if len(robot_bases(robot)) > 1 else "x"
+
+
+def rotate_scene_z90(sc: Scene) -> Scene:
+    """The scene turned +90 degrees about the z axis: (x, y, z) -> (-y, x, z).
+    Axis-aligned boxes stay axis-aligned with their x and y half extents
+    swapped; cylinder axes and sphere centres turn; goal cells are re-sorted."""
+    def rot(p):
+        p = np.asarray(p, np.float64)
+        return np.stack([-p[..., 1], p[..., 0], p[..., 2]], axis=-1)
+    boxes = []
+    for b in sc.boxes:
+        R = b[6:15].reshape(3, 3)
+        Rz = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+        boxes.append(np.concatenate([rot(b[0:3]), b[3:6], (Rz @ R).reshape(9)]))
+        if np.allclose(R, np.eye(3)):   # keep axis-aligned boxes in the identity form
+            boxes[-1] = np.concatenate([rot(b[0:3]), [b[4], b[3], b[5]], np.eye(3).reshape(9)])
+    cyls = [np.concatenate([rot(c[0:3]), rot(c[3:6]), c[6:8]]) for c in sc.cylinders]
+    sphs = [np.concatenate([rot(q[0:3]), q[3:4]]) for q in sc.spheres]
+    cells = []
+    for c in sc.cells:
+        a, b = rot(c[0:3]), rot(c[3:6])
+        cells.append(np.concatenate([np.minimum(a, b), np.maximum(a, b)]))
+    return _finish(boxes, cyls, sphs, cells)
+
+
+def _scene_shelf_x(seed: int) -> Scene:
     st = Stream(seed, 12)
     cells = shelf_cells()
     boxes = _shelf_structure()

@@ -44,3 +44,57 @@ def test_waypoints_are_evenly_spaced_on_the_path():
     np.testing.assert_allclose(full[0], path[0])
     np.testing.assert_allclose(full[-1], path[-1])
     assert len(L.waypoints(path[:1], spacing=0.25)) == 0
+
+
+def test_shelf_facing_both_arms():
+    """The dual arm's shelf is the single arm's scene turned 90 degrees about z:
+    four turns give the scene back, the cells sit behind the plane y = 0.45, and
+    the dual arm has collision-free configurations in it (the oracle's check)."""
+    import numpy as np
+    from oracle import oracle as O
+    sc = W.scene_shelf(1234)
+    r = sc
+    for _ in range(4):
+        r = W.rotate_scene_z90(r)
+    np.testing.assert_allclose(r.boxes, sc.boxes, atol=1e-6)
+    np.testing.assert_allclose(r.cylinders, sc.cylinders, atol=1e-6)
+    np.testing.assert_allclose(r.spheres, sc.spheres, atol=1e-6)
+    y = W.scene_shelf(1234, W.shelf_facing(W.dual14()))
+    assert W.shelf_facing(W.arm7()) == "x" and W.shelf_facing(W.dual14()) == "y"
+    assert np.all(y.cells[:, 1] >= 0.45 - 1e-6)
+    rb = W.dual14()
+    free, _ = O.check_states(rb, y, W.candidates(rb, 1234, 0, 256))
+    assert free.mean() > 0.3
+
+
+def test_concat_datasets_renumbers_scenes():
+    import numpy as np
+    from paper_2503_06757_gb300 import learned as L
+    a = L.Dataset(dof=2, occ=np.zeros((2, 4096), np.uint8), scene_of=np.array([0, 1, 1], np.int32),
+                  q_start=np.zeros((3, 2), np.float32), q_goal=np.zeros((3, 2), np.float32),
+                  target=np.zeros((3, 2), np.float32), paths=2, problems=2)
+    b = L.Dataset(dof=2, occ=np.ones((3, 4096), np.uint8), scene_of=np.array([2, 0], np.int32),
+                  q_start=np.ones((2, 2), np.float32), q_goal=np.ones((2, 2), np.float32),
+                  target=np.ones((2, 2), np.float32), paths=1, problems=3)
+    c = L.concat_datasets([a, b])
+    assert c.occ.shape == (5, 4096) and c.paths == 3 and c.problems == 5
+    np.testing.assert_array_equal(c.scene_of, [0, 1, 1, 4, 2])
+    assert np.all(c.occ[c.scene_of[3:]] == 1)
+
+
+def test_scene_at_places_the_moving_spheres():
+    """The scene a served query saw: the static obstacles as built, the moving
+    spheres at the positions recorded when it was submitted."""
+    import numpy as np
+    from paper_2503_06757_gb300 import serving as S
+    mv = W.moving_spheres(3000, S.N_MOVING)
+    base = W.scene_mixed(3000, 40)
+    sph = np.concatenate([base.spheres, np.concatenate([mv.centres0, mv.radii[:, None]], 1)])
+    sc = S.ServeScene(W.arm7(), None, None, W.Scene(base.boxes, base.cylinders, sph), mv, [], [])
+    pos = mv.positions_track(10)[7]
+    at = S.scene_at(sc, pos)
+    np.testing.assert_array_equal(at.boxes, base.boxes)
+    np.testing.assert_array_equal(at.spheres[:len(base.spheres)], base.spheres)
+    np.testing.assert_array_equal(at.spheres[len(base.spheres):, :3], pos)
+    np.testing.assert_array_equal(at.spheres[len(base.spheres):, 3], mv.radii)
+    assert not np.array_equal(pos, mv.centres0)
