@@ -349,15 +349,17 @@ __device__ __forceinline__ bool frame_stages_bc(const float4* __restrict__ prims
 }
 
 // The three stages of one frame (warp = one edge), out of line; same return.
-// Stage A of all four primitive types runs first, `tile` primitives of each
-// type per round (one or two per lane), so that a lane's tests of a round are
-// independent; stages B and C then take the round's candidates in order.
+// Stage A of all four primitive types runs first, kHalves x 32 primitives of
+// each type per round (one or two per lane), so that a lane's tests of a round
+// are independent; stages B and C then take the round's candidates in order.
+// One instance per tile size, so that the unused one stays out of the hot code.
+template <int kHalves>
 static __device__ __noinline__ unsigned long long env_three_stage(const float4* __restrict__ env, int n_aabb,
                                                            int n_obb, int n_cyl, int n_sph, float ux, float uy,
                                                            float uz, float ur, float bx, float by, float bz, float br,
                                                            const float* __restrict__ stage,
                                                            const float4* __restrict__ sph, int s0, int s1,
-                                                           bool active, int lane, int tile) {
+                                                           bool active, int lane) {
   uint32_t t[4] = {0, 0, 0, 0};
   bool hit = false;
   const float4* ea = env;
@@ -365,19 +367,18 @@ static __device__ __noinline__ unsigned long long env_three_stage(const float4* 
   const float4* ec = eo + 5 * n_obb;
   const float4* es = ec + 2 * n_cyl;
   const int nmax = max(max(n_aabb, n_obb), max(n_cyl, n_sph));
-  const int halves = tile >= 64 ? 2 : 1;
-  for (int base = 0; base < nmax; base += 32 * halves) {
-    bool na[2], no[2], nc[2], ns[2];
+  for (int base = 0; base < nmax; base += 32 * kHalves) {
+    bool na[kHalves], no[kHalves], nc[kHalves], ns[kHalves];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kHalves; ++h) {
       const int k = base + 32 * h + lane;
-      const bool on = h < halves;
-      na[h] = on && k < n_aabb && Prim<kAabb>::hit(ea + 2 * k, ux, uy, uz, ur);
-      no[h] = on && k < n_obb && Prim<kObb>::hit(eo + 5 * k, ux, uy, uz, ur);
-      nc[h] = on && k < n_cyl && Prim<kCyl>::hit(ec + 2 * k, ux, uy, uz, ur);
-      ns[h] = on && k < n_sph && Prim<kSph>::hit(es + k, ux, uy, uz, ur);
+      na[h] = k < n_aabb && Prim<kAabb>::hit(ea + 2 * k, ux, uy, uz, ur);
+      no[h] = k < n_obb && Prim<kObb>::hit(eo + 5 * k, ux, uy, uz, ur);
+      nc[h] = k < n_cyl && Prim<kCyl>::hit(ec + 2 * k, ux, uy, uz, ur);
+      ns[h] = k < n_sph && Prim<kSph>::hit(es + k, ux, uy, uz, ur);
     }
-    for (int h = 0; h < halves; ++h) {
+#pragma unroll
+    for (int h = 0; h < kHalves; ++h) {
       const int b0 = base + 32 * h;
       const uint32_t ca = __ballot_sync(kFull, na[h]), co = __ballot_sync(kFull, no[h]);
       const uint32_t cc = __ballot_sync(kFull, nc[h]), cs = __ballot_sync(kFull, ns[h]);
@@ -587,8 +588,11 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
         const float* gst = stage + (R->n_spheres + i) * 96 + lane;
         const float gx = gst[0], gy = gst[32], gz = gst[64];
         const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
-        const unsigned long long r = env_three_stage(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz,
-                                                     cb.w, stage, R->sph, s0, s1, active, lane, tile);
+        const unsigned long long r =
+            tile >= 64 ? env_three_stage<2>(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz, cb.w,
+                                            stage, R->sph, s0, s1, active, lane)
+                       : env_three_stage<1>(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz, cb.w,
+                                            stage, R->sph, s0, s1, active, lane);
         hit |= (r >> 63) != 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)((r >> (15 * k)) & 0x7fffu);
