@@ -108,7 +108,7 @@ struct DeviceCtx {
   // CUDA graph of the launch sequence, keyed by everything it bakes in
   struct GraphKey {
     int n, grid, warps, smem, robot_bytes, env_bytes, stage_bytes, max_spheres, max_pairs, max_env, gen, head,
-        lockstep;
+        lockstep, tile;
     bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
   };
   GraphKey gkey{};
@@ -1158,7 +1158,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
         launch_setup(c->d_desc, c->d_state, n, max_spheres, max_pairs, max_env, c->stream, nullptr, &c->d_glob->error);
     if (e != cudaSuccess) return cuda_fail("setup launch", e);
     CK(cudaEventRecordWithFlags(c->ev[1], c->stream, ev_flags));
-    e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, c->stream);
+    e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, G.obstacle_tile, c->stream);
     if (e != cudaSuccess) return cuda_fail("plan launch", e);
     CK(cudaEventRecordWithFlags(c->ev[2], c->stream, ev_flags));
     e = launch_record_usage(c->d_desc, c->d_state, n, c->stream);
@@ -1176,7 +1176,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   } else {
     const DeviceCtx::GraphKey key{n, cfg.grid, cfg.warps, cfg.smem, cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes,
                                   max_spheres, max_pairs, max_env, c->arena_gen, head_rows * c->h_desc[0].dof,
-                                  cfg.lockstep ? 1 : 0};
+                                  cfg.lockstep ? 1 : 0, G.obstacle_tile};
     if (!c->gexec || !(c->gkey == key)) {
       if (c->gexec) cudaGraphExecDestroy(c->gexec);
       c->gexec = nullptr;

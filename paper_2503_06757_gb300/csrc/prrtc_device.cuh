@@ -352,7 +352,7 @@ __device__ __forceinline__ bool frame_stages_bc(const float4* __restrict__ prims
 // Stage A of all four primitive types runs first, kHalves x 32 primitives of
 // each type per round (one or two per lane), so that a lane's tests of a round
 // are independent; stages B and C then take the round's candidates in order.
-// One instance per tile size, so that the unused one stays out of the hot code.
+// One instance per tile size: each planner kernel holds only the one it uses.
 template <int kHalves>
 static __device__ __noinline__ unsigned long long env_three_stage(const float4* __restrict__ env, int n_aabb,
                                                            int n_obb, int n_cyl, int n_sph, float ux, float uy,
@@ -447,12 +447,13 @@ struct EdgeQ {
 // from the distal end back (three stages per link) and the whole warp returns
 // true as soon as any active lane collides (the edge verdict).  The joint loop
 // is a runtime loop so that the obstacle loops exist once in the code.
-template <bool kWarpVote, class QS>
+template <bool kWarpVote, int kTile = 32, class QS>
 __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R, const uint32_t* __restrict__ pair,
                                                const float* __restrict__ thr, const float4* __restrict__ env,
                                                int n_aabb, int n_obb, int n_cyl, int n_sph, const EsdfGrid& grid,
                                                float* __restrict__ stage, const QS& qs, bool active, int lane,
-                                               WarpCount* wc, int tile = 32) {
+                                               WarpCount* wc) {
+  static_assert(kTile == 32 || kTile == 64, "obstacle tile is 32 or 64 primitives per type");
   const bool has_grid = grid.v != nullptr;
   const bool has_prims = (n_aabb | n_obb | n_cyl | n_sph) != 0;
   const int dof = R->dof;
@@ -588,11 +589,9 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
         const float* gst = stage + (R->n_spheres + i) * 96 + lane;
         const float gx = gst[0], gy = gst[32], gz = gst[64];
         const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
-        const unsigned long long r =
-            tile >= 64 ? env_three_stage<2>(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz, cb.w,
-                                            stage, R->sph, s0, s1, active, lane)
-                       : env_three_stage<1>(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z, u.w, gx, gy, gz, cb.w,
-                                            stage, R->sph, s0, s1, active, lane);
+        const unsigned long long r = env_three_stage<kTile / 32>(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z,
+                                                                 u.w, gx, gy, gz, cb.w, stage, R->sph, s0, s1,
+                                                                 active, lane);
         hit |= (r >> 63) != 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) fine[k] += (uint32_t)((r >> (15 * k)) & 0x7fffu);

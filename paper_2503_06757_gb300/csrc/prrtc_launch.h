@@ -44,7 +44,7 @@ struct PlanGlobals {
   int workers;           // lockstep mode: iterations per round (B)
   uint32_t debug_wait_polls;  // test hook: bounded wait on ProblemState::never_set before a path walk
   int expansions;        // async: iterations a worker claims per atomic on the problem's counter
-  int obstacle_tile;     // primitives per type per first-stage round of the edge check (32 or 64)
+  int obstacle_tile;     // primitives per type per first-stage round (32 or 64): picks the kernel instance
 };
 
 // Check of the sampler and dynamic-domain fields of a parameter block; null
@@ -167,8 +167,10 @@ struct PlanLaunch {
 PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, int max_spheres, int max_pairs,
                               int max_env_f4, int sm_count, int workers = 1);
 
+// obstacle_tile: 64 launches the 64-obstacle-tile instance of the async/serial
+// kernel, anything else the 32 one (lockstep always uses 32).
 cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
-                        cudaStream_t stream);
+                        int obstacle_tile, cudaStream_t stream);
 
 // Clear-list bookkeeping after a plan: rows each tree used, for the next setup.
 cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, int n, cudaStream_t stream,

@@ -164,7 +164,8 @@ __device__ __noinline__ int nearest(const float* __restrict__ nodes, int n, int 
 
 // Alg. 2 lines 3-5: the N states a + (k/N)(b - a), k = 1..N, of the edge held
 // in c.v.a / c.v.b, one per lane (several passes if N > 32); false at the
-// first colliding state.
+// first colliding state.  kTile: obstacles per type per first-stage round.
+template <int kTile>
 __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
   if (c.lane == 0) {
     c.cnt->edges++;
@@ -176,9 +177,8 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
     const bool active = k <= N;
     const int kk = active ? k : N;
     const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N, &c.S->solved};
-    if (state_collides<true>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
-                             c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt,
-                             c.g->obstacle_tile)) {
+    if (state_collides<true, kTile>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
+                                    c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt)) {
       __syncwarp();  // lane 0 may have just set the flag
       if (c.cnt->aborted) {
         // the problem was solved meanwhile and the check stopped early: this
@@ -415,6 +415,7 @@ __device__ __forceinline__ float random_config(const Ctx& c, int it, int o, bool
 
 // Alg. 1 iterations of one worker warp on one problem until it is solved,
 // out of budget or out of time.  Lane j holds element j of every vector.
+template <int kTile>
 __device__ void worker(const Ctx& c) {
   const PlanGlobals* g = c.g;
   const ProblemDesc* D = c.D;
@@ -520,7 +521,7 @@ __device__ void worker(const Ctx& c) {
         if (lane == 0) solved = ld_volatile(&S->solved);
         if (__shfl_sync(kFull, solved, 0)) break;
       }
-      const bool free_edge = edge_free(c, N);
+      const bool free_edge = edge_free<kTile>(c, N);
       if (phase == 0 && dd && lane == 0) {
         // adaptive radius of the nearest node (Jaillet et al. 2005): a bounded
         // radius grows after a free extension; a collision bounds an unbounded
@@ -657,7 +658,7 @@ __device__ void lockstep_iteration(const Ctx& c, int it, int s, int n_s, int n_o
     float ct = 0.f, Dd = 0.f, bval = cnew;
     int n_ext = 0;
     for (int phase = 0;; ++phase) {
-      const bool free_edge = edge_free(c, N);
+      const bool free_edge = edge_free<32>(c, N);  // lockstep: 32-obstacle tiles
       ++edges;
       if (phase == 0 && dd) {
         dd_node = nn;
@@ -834,7 +835,7 @@ __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
 // The planner launch: blocks take problems from the work queue, stage each
 // problem's robot and environment in shared memory and run its workers --
 // independent warps (async and serial modes) or the lockstep rounds.
-template <bool kLockstep>
+template <bool kLockstep, int kTile>
 __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                           ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
                                           int warp_floats) {
@@ -916,7 +917,7 @@ __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const Pro
     if constexpr (kLockstep)
       lockstep_problem(c, warp, blockDim.x >> 5);
     else
-      worker(c);
+      worker<kTile>(c);
     // flush this warp's counters into the problem
     __syncwarp();
     if (lane < 14) {
@@ -933,16 +934,21 @@ __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const Pro
   }
 }
 
+// One instance per obstacle tile (32 or 64 primitives per type per first-stage
+// round): a tile's check code is all that the launched kernel holds.
+template <int kTile>
 __global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                              ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
                                              int warp_floats) {
-  plan_body<false>(g, descs, states, robot_bytes, env_bytes, warp_floats);
+  plan_body<false, kTile>(g, descs, states, robot_bytes, env_bytes, warp_floats);
 }
+template __global__ void plan_kernel<32>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
+template __global__ void plan_kernel<64>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
 
 __global__ void __maxnreg__(128) lockstep_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                                  ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
                                                  int warp_floats) {
-  plan_body<true>(g, descs, states, robot_bytes, env_bytes, warp_floats);
+  plan_body<true, 32>(g, descs, states, robot_bytes, env_bytes, warp_floats);
 }
 
 // Reject a start or goal in collision (Alg. 1 lines 1-2): warp 0 checks the
@@ -1096,18 +1102,23 @@ cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, in
 
 // Resident planner blocks per SM for a block shape, cached: the occupancy
 // query and the shared-memory attribute cost host time on every call.
-int resident_blocks_per_sm(int warps, int smem, bool lockstep) {
+static const void* plan_kernel_fn(bool lockstep, int tile) {
+  if (lockstep) return reinterpret_cast<const void*>(lockstep_kernel);
+  return tile == 64 ? reinterpret_cast<const void*>(plan_kernel<64>) : reinterpret_cast<const void*>(plan_kernel<32>);
+}
+
+int resident_blocks_per_sm(int warps, int smem, bool lockstep, int tile) {
   static std::mutex mu;
   static std::map<std::pair<int, int>, int> cache;
   static std::map<int, int> attr_smem;  // per (device, kernel): the attribute value set so far
   int dev = 0;
   cudaGetDevice(&dev);
-  const int kid = 2 * dev + (lockstep ? 1 : 0);
+  const int kid = 3 * dev + (lockstep ? 2 : tile == 64 ? 1 : 0);
   const std::pair<int, int> key{warps + 64 * kid, smem};
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  const void* fn = lockstep ? reinterpret_cast<const void*>(lockstep_kernel) : reinterpret_cast<const void*>(plan_kernel);
+  const void* fn = plan_kernel_fn(lockstep, tile);
   if (smem > attr_smem[kid]) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr_smem[kid] = smem;
@@ -1134,7 +1145,8 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
   c.env_bytes = max_env_f4 * 16;
   c.stage_bytes = (int)sizeof(WarpCount) + kWarpVecFloats * (int)sizeof(float) + stage_bytes(max_spheres);  // per warp
   c.smem = c.robot_bytes + c.env_bytes + c.warps * c.stage_bytes;
-  const int per_sm = resident_blocks_per_sm(c.warps, c.smem, c.lockstep);
+  // both tile instances take the same registers (capped) and shared memory
+  const int per_sm = resident_blocks_per_sm(c.warps, c.smem, c.lockstep, 32);
   int resident = per_sm * sm_count;
   if (blocks > 0) {
     c.grid = blocks;
@@ -1152,17 +1164,22 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
 }
 
 cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
-                        cudaStream_t stream) {
-  resident_blocks_per_sm(cfg.warps, cfg.smem, cfg.lockstep);  // sets the shared-memory attribute once per size
+                        int obstacle_tile, cudaStream_t stream) {
+  // sets the shared-memory attribute once per size and kernel
+  resident_blocks_per_sm(cfg.warps, cfg.smem, cfg.lockstep, obstacle_tile);
   cudaError_t e;
   if (cfg.lockstep)
     lockstep_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
                                                                     cfg.robot_bytes, cfg.env_bytes,
                                                                     cfg.stage_bytes / (int)sizeof(float));
+  else if (obstacle_tile == 64)
+    plan_kernel<64><<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
+                                                                    cfg.robot_bytes, cfg.env_bytes,
+                                                                    cfg.stage_bytes / (int)sizeof(float));
   else
-    plan_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
-                                                                cfg.robot_bytes, cfg.env_bytes,
-                                                                cfg.stage_bytes / (int)sizeof(float));
+    plan_kernel<32><<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
+                                                                    cfg.robot_bytes, cfg.env_bytes,
+                                                                    cfg.stage_bytes / (int)sizeof(float));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaSuccess;
