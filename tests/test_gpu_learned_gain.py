@@ -59,9 +59,8 @@ def test_learned_batched_planner_beats_plain_ttfs_through_narrower_door():
     """Through a 5 cm door (1 cm free for the robot's centre) the batched learned
     form reaches its p50 time-to-first-solution before the plain GPU planner does,
     at equal or better success: 200 held-out pairs in one async launch per key,
-    TTFS = device prep (including the on-device inference) + setup + solve time.
-    Timing on a shared GPU is noisy, so the comparison gets a second measurement
-    before it fails."""
+    TTFS = device prep (including the on-device inference) + setup + solve time,
+    over six Philox keys (1200 solves per side, one measurement)."""
     rb = W.point2()
     sc = W.scene_two_rooms(door=(0.865, 0.915))
     h, ev = P.make_robot(rb), P.make_env(sc)
@@ -72,14 +71,12 @@ def test_learned_batched_planner_beats_plain_ttfs_through_narrower_door():
     s2, g2 = pairs(200, 12)
     plain_prm = P.params(**base)
     learned_prm = P.params(learned_ratio=0.5, **base)
-    for attempt in range(2):
-        plain = L.batched_ttfs(h, ev, s2, g2, plain_prm, None)
-        learned = L.batched_ttfs(h, ev, s2, g2, learned_prm, prop)
-        p50_p, p50_l = np.percentile(plain["ttfs_us"], 50), np.percentile(learned["ttfs_us"], 50)
-        print(f"5 cm door: plain {plain['success_rate']:.3f} p50 {p50_p:.1f} us; "
-              f"learned {learned['success_rate']:.3f} p50 {p50_l:.1f} us (inference {learned['infer_us_mean']:.1f} us)")
-        assert learned["success_rate"] >= plain["success_rate"] - 0.01
-        assert learned["iterations_mean"] < 0.5 * plain["iterations_mean"]
-        if p50_l < p50_p:
-            break
+    keys = (1, 2, 3, 4, 5, 6)
+    plain = L.batched_ttfs(h, ev, s2, g2, plain_prm, None, keys=keys)
+    learned = L.batched_ttfs(h, ev, s2, g2, learned_prm, prop, keys=keys)
+    p50_p, p50_l = np.percentile(plain["ttfs_us"], 50), np.percentile(learned["ttfs_us"], 50)
+    print(f"5 cm door: plain {plain['success_rate']:.3f} p50 {p50_p:.1f} us; "
+          f"learned {learned['success_rate']:.3f} p50 {p50_l:.1f} us (inference {learned['infer_us_mean']:.1f} us)")
+    assert learned["success_rate"] >= plain["success_rate"] - 0.01
+    assert learned["iterations_mean"] < 0.5 * plain["iterations_mean"]
     assert p50_l < p50_p, (p50_l, p50_p)
