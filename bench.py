@@ -936,6 +936,11 @@ def run_ours(args):
         extra["roofline_cc_microbench"] = dict(micro["two_stage"], one_stage=micro["one_stage"],
                                                workload="1M collision-free 7-DoF states vs one shelf scene "
                                                         "(every test runs)")
+        # the roofline's denominator checked on the device: an FP32 FMA loop
+        fma_rate, fma_ms = P.prrtc_alu_peak(16384)
+        extra["alu_peak_microbench"] = dict(
+            measured_gops=fma_rate * 1e-9, peak_gops=peak_gops, ratio=fma_rate * 1e-9 / peak_gops,
+            kernel_ms=fma_ms, note="8 independent FMA chains per thread, 64 warps per SM; one FMA = one lane-op")
         if not args.no_mixed:
             extra["mixed_600"] = mixed_section(args, P, flush, torch, peak_gops)
         extra["variants"] = variants_section(args, P, items, prm, counts, flush, torch)

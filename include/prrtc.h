@@ -362,6 +362,15 @@ int prrtc_check_states_device(const prrtc_robot* robot, const prrtc_env* env, co
  * nothing; n < 0, or a null buffer with n > 0: PRRTC_ERR_INVALID_ARG. */
 int prrtc_philox(const uint32_t* ctr, int32_t n, uint64_t key, uint32_t* out);
 
+/* The device's FP32 issue rate, for the denominator of the collision check's
+ * ALU roofline (lane-ops per second = SMs x 128 lanes x SM clock, one FMA per
+ * lane per cycle): times one launch of 8 independent FMA chains per thread,
+ * `iters` steps each, on 8 blocks of 256 threads per SM, after one untimed
+ * launch.  *lane_ops_per_s receives the FMAs per second; *kernel_ms (nullable)
+ * the timed launch.  Blocks until done.  iters < 1 or a null lane_ops_per_s:
+ * PRRTC_ERR_INVALID_ARG. */
+int prrtc_alu_peak(int32_t iters, double* lane_ops_per_s, double* kernel_ms);
+
 /* Solve one planning problem (Alg. 1) on the device; blocks until done.
  * out_path receives the path (host memory, free with prrtc_path_free). */
 int prrtc_plan(const prrtc_robot* robot, const prrtc_env* env, const float* q_start,

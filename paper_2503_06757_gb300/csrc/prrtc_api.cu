@@ -898,6 +898,37 @@ int prrtc_philox(const uint32_t* ctr, int32_t n, uint64_t key, uint32_t* out) {
   return PRRTC_OK;
 }
 
+int prrtc_alu_peak(int32_t iters, double* lane_ops_per_s, double* kernel_ms) {
+  if (iters < 1 || !lane_ops_per_s) return fail(PRRTC_ERR_INVALID_ARG, "bad alu_peak arguments");
+  DeviceCtx* c = nullptr;
+  int rc = current_ctx(&c);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  float* sink = nullptr;
+  if (cudaMalloc(&sink, (size_t)c->sms * 8 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PRRTC_ERR_OOM, "alu_peak buffer allocation failed");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  long long ops = 0;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch_fma_loop(c->sms, iters, sink, c->stream, &ops);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  if (e == cudaSuccess) e = launch_fma_loop(c->sms, iters, sink, c->stream, &ops);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail("alu_peak", e);
+  *lane_ops_per_s = (double)ops / ((double)ms * 1e-3);
+  if (kernel_ms) *kernel_ms = ms;
+  return PRRTC_OK;
+}
+
 int prrtc_check_states(const prrtc_robot* robot, const prrtc_env* env, const float* q, int32_t n, uint8_t* out_valid,
                        float* out_spheres) {
   if (!robot || !env || n < 0 || (n > 0 && (!q || !out_valid)))

@@ -105,6 +105,32 @@ cudaError_t launch_philox(const uint32_t* ctr, int n, uint64_t key, uint32_t* ou
   return cudaGetLastError();
 }
 
+// The FP32 pipe at full rate: kChains independent FMA chains per thread, so
+// that every warp scheduler always has an FMA ready.  One FMA counts one
+// lane-op, the unit of the planner's ALU roofline.  The sum is stored only
+// when it equals a value it never takes, which keeps the chains alive.
+constexpr int kFmaChains = 8;
+__global__ void fma_loop_kernel(int iters, float m, float* __restrict__ sink) {
+  float a[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = fmaf(a[k], m, 1e-7f);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) s += a[k];
+  if (s == -1.f) sink[blockIdx.x] = s;
+}
+
+cudaError_t launch_fma_loop(int sm_count, int iters, float* sink, cudaStream_t stream, long long* lane_ops) {
+  const int blocks = sm_count * 8, threads = 256;  // 64 warps per SM
+  fma_loop_kernel<<<blocks, threads, 0, stream>>>(iters, 0.9999999f, sink);
+  *lane_ops = (long long)blocks * threads * iters * kFmaChains;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& h, EnvView env, const float* q, int n,
                                 uint8_t* valid, float* spheres, unsigned long long* counters, int* error,
                                 cudaStream_t stream) {

@@ -147,6 +147,11 @@ cudaError_t launch_check_states(const RobotDev* robot, const RobotHeader& host_h
 // Philox4x32-10 of n counters (device arrays of 4n words each).
 cudaError_t launch_philox(const uint32_t* ctr, int n, uint64_t key, uint32_t* out, cudaStream_t stream);
 
+// FP32 FMA loop over 8 blocks of 256 threads per SM; *lane_ops receives the
+// FMAs it issues (one lane-op each).  sink: one float per block (never written
+// in practice).
+cudaError_t launch_fma_loop(int sm_count, int iters, float* sink, cudaStream_t stream, long long* lane_ops);
+
 // idx (nullable, device): the problems to set up, as indices into desc/state.
 // error (nullable, device): receives PRRTC_ERR_TIMEOUT if a block's staging
 // copies did not complete within the bounded wait.

@@ -95,7 +95,7 @@ EXPORTS = [
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
     "prrtc_robot_set_two_stage", "prrtc_robot_bounds", "prrtc_env_create_esdf", "prrtc_env_update_esdf",
     "prrtc_env_esdf_values", "prrtc_voxelize",
-    "prrtc_check_states", "prrtc_check_states_device", "prrtc_philox", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
+    "prrtc_check_states", "prrtc_check_states_device", "prrtc_philox", "prrtc_alu_peak", "prrtc_plan", "prrtc_plan_batch", "prrtc_debug_tree",
     "prrtc_plan_noalloc", "prrtc_gemm_bf16", "prrtc_gemm_bf16_splitk", "prrtc_gemm_error",
     "prrtc_proposal_create", "prrtc_proposal_destroy", "prrtc_proposal_info", "prrtc_proposal_get_params",
     "prrtc_proposal_forward", "prrtc_proposal_forward_layers", "prrtc_proposal_inference_layers",
@@ -141,6 +141,7 @@ def lib():
                                  C.POINTER(C.c_uint8)]
     L.prrtc_robot_bounds.argtypes = [C.c_void_p, _f]
     L.prrtc_check_states.argtypes = [C.c_void_p, C.c_void_p, _f, C.c_int32, C.POINTER(C.c_uint8), _f]
+    L.prrtc_alu_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.prrtc_check_states_device.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                                             C.c_void_p, C.c_void_p]
     L.prrtc_plan.argtypes = [C.c_void_p, C.c_void_p, _f, _f, C.POINTER(prrtc_params), C.POINTER(prrtc_path)]
@@ -431,6 +432,14 @@ def prrtc_philox(ctr, key: int):
     _check(lib().prrtc_philox(c.ctypes.data_as(P32), c.shape[0], C.c_uint64(int(key) & (2 ** 64 - 1)),
                               out.ctypes.data_as(P32)), "prrtc_philox")
     return out
+
+
+def prrtc_alu_peak(iters: int = 16384):
+    """FP32 FMA issue rate of the device (lane-ops/s, one FMA = one lane-op) and
+    the timed launch's milliseconds."""
+    rate, ms = C.c_double(), C.c_double()
+    _check(lib().prrtc_alu_peak(int(iters), C.byref(rate), C.byref(ms)), "prrtc_alu_peak")
+    return rate.value, ms.value
 
 
 def prrtc_plan(robot: Robot, env: Env, q_start, q_goal, prm: prrtc_params | None = None):
