@@ -969,6 +969,7 @@ def run_ours(args):
         roofline=dict(bound="alu", achieved=executed_gops, peak=peak_gops, unit="Gop/s",
                       frac=executed_gops / peak_gops, traffic=profiled_traffic(args.problems),
                       one_stage_equivalent_gops=achieved_gops, one_stage_equivalent_frac=achieved_gops / peak_gops,
+                      peak_at_sampled_clock_gops=(sms * 128 * clk["sm_mhz"] * 1e-3) if clk.get("sm_mhz") else None,
                       note="planner kernel: the lane-ops the method ran (FK, the multi-stage sphere hierarchy of "
                            "Sec. III-A as executed, self pairs, NN row distances; counted by the kernel) per "
                            "kernel time, against SMs x 128 lanes x max SM clock (of measured sm_max_mhz).  "
