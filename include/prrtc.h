@@ -218,6 +218,9 @@ typedef struct prrtc_path {
 } prrtc_path;
 
 void prrtc_path_free(prrtc_path* path);
+/* prrtc_path_free on paths[0 .. n-1] (the results of one batch call) in one
+ * call.  A null paths or n <= 0 does nothing. */
+void prrtc_paths_free(prrtc_path* paths, int32_t n);
 
 /* Work counters and timing of the most recent planning launch on the current
  * device (for throughput and roofline accounting). */

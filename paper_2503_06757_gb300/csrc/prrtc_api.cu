@@ -324,6 +324,11 @@ void prrtc_path_free(prrtc_path* path) {
   path->n = 0;
 }
 
+void prrtc_paths_free(prrtc_path* paths, int32_t n) {
+  if (!paths) return;
+  for (int32_t k = 0; k < n; ++k) prrtc_path_free(paths + k);
+}
+
 int prrtc_last_launch_stats(prrtc_launch_stats* out) {
   if (!out) return fail(PRRTC_ERR_INVALID_ARG, "out is null");
   DeviceCtx* c = nullptr;

@@ -90,7 +90,7 @@ class prrtc_problem(C.Structure):
 
 
 EXPORTS = [
-    "prrtc_params_default", "prrtc_path_free", "prrtc_last_launch_stats", "prrtc_status_string",
+    "prrtc_params_default", "prrtc_path_free", "prrtc_paths_free", "prrtc_last_launch_stats", "prrtc_status_string",
     "prrtc_version", "prrtc_last_error", "prrtc_env_create", "prrtc_env_update", "prrtc_env_destroy",
     "prrtc_robot_create", "prrtc_robot_destroy", "prrtc_robot_info", "prrtc_env_info",
     "prrtc_robot_set_two_stage", "prrtc_robot_bounds", "prrtc_env_create_esdf", "prrtc_env_update_esdf",
@@ -148,6 +148,7 @@ def lib():
     L.prrtc_plan_batch.argtypes = [C.POINTER(prrtc_problem), C.c_int32, C.POINTER(prrtc_params),
                                    C.POINTER(prrtc_path), _i]
     L.prrtc_path_free.argtypes = [C.POINTER(prrtc_path)]
+    L.prrtc_paths_free.argtypes = [C.POINTER(prrtc_path), C.c_int32]
     L.prrtc_params_default.argtypes = [C.POINTER(prrtc_params)]
     L.prrtc_last_launch_stats.argtypes = [C.POINTER(prrtc_launch_stats)]
     L.prrtc_debug_tree.argtypes = [C.c_int32, C.c_int32, _f, _i, C.c_int32, _i]
@@ -510,7 +511,6 @@ def _collect(paths, n):
     v = np.frombuffer((C.c_char * (n * C.sizeof(prrtc_path))).from_address(C.addressof(paths)), _PATH_DT, n)
     rows = v[_PATH_FIELDS].tolist()
     out = []
-    free = lib().prrtc_path_free
     for k in range(n):
         d = dict(zip(_PATH_FIELDS, rows[k]))
         d["prim_tests"] = list(d["prim_tests"])
@@ -520,7 +520,7 @@ def _collect(paths, n):
         else:
             d["path"] = np.zeros((0, p.dof), np.float32)
         out.append(d)
-        free(C.byref(p))
+    lib().prrtc_paths_free(paths, n)
     return out
 
 
@@ -575,9 +575,7 @@ class BatchResult:
 
     def __del__(self):
         try:
-            free = lib().prrtc_path_free
-            for k in range(self.n):
-                free(C.byref(self._paths[k]))
+            lib().prrtc_paths_free(self._paths, self.n)
         except Exception:
             pass
 
@@ -829,9 +827,9 @@ class Server:
         out = []
         for k in range(n.value):
             d = _path_dict(paths[k])
-            lib().prrtc_path_free(C.byref(paths[k]))
             d.update(ticket=int(tickets[k]), latency_ms=float(lat[k]), queue_ms=float(que[k]))
             out.append(d)
+        lib().prrtc_paths_free(paths, n.value)
         return out
 
     def wait(self, completed: int, timeout_s: float = 60.0):

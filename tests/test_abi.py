@@ -126,3 +126,19 @@ def test_problem_array_points_at_each_problems_data():
         np.testing.assert_array_equal(np.ctypeslib.as_array(pb.q_start, shape=(d,)), it[2])
         np.testing.assert_array_equal(np.ctypeslib.as_array(pb.q_goal, shape=(d,)), it[3])
         assert bool(pb.gmm) == (len(it) > 6)
+
+
+def test_paths_free_releases_a_batch_in_one_call(lib):
+    """prrtc_paths_free frees library-allocated rows of every path and clears
+    them; a null array or n = 0 does nothing (host-only: no GPU needed)."""
+    n = 3
+    paths = (P.prrtc_path * n)()
+    libc = C.CDLL(None)
+    libc.malloc.restype = C.c_void_p
+    for k in range(n):
+        paths[k].n, paths[k].dof = 2, 7
+        paths[k].q = C.cast(libc.malloc(2 * 7 * 4), C.POINTER(C.c_float))
+    lib.prrtc_paths_free(paths, n)
+    assert all(not paths[k].q and paths[k].n == 0 for k in range(n))
+    lib.prrtc_paths_free(None, 5)
+    lib.prrtc_paths_free(paths, 0)
