@@ -108,13 +108,16 @@ struct DeviceCtx {
   // CUDA graph of the launch sequence, keyed by everything it bakes in
   struct GraphKey {
     int n, grid, warps, smem, robot_bytes, env_bytes, stage_bytes, max_spheres, max_pairs, max_env, gen, head,
-        lockstep, tile;
+        lockstep, tile, batch_head;
     bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
   };
   GraphKey gkey{};
   cudaGraphExec_t gexec = nullptr;
   int arena_gen = 0;
   float* h_path_head = nullptr;  // first kHeadRows path rows of a single-problem call
+  float* d_heads = nullptr;      // first kBatchHeadRows path rows of each problem of a batch
+  float* h_heads = nullptr;
+  size_t heads_cap = 0;
   // autotuned (blocks, warps) per (row width, obstacle bucket, batch-size bucket, mode)
   struct Tuned {
     int blocks, warps, tile, expansions;
@@ -132,6 +135,7 @@ struct DeviceCtx {
 };
 
 constexpr int kHeadRows = 512;
+constexpr int kBatchHeadRows = 32;
 
 DeviceCtx g_ctx[64];
 std::mutex g_init_mu;
@@ -1056,10 +1060,11 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     if ((rc = grow_device(&c->d_held, &c->held_cap, held_off[n]))) return rc;
     if ((rc = grow_device(&c->d_held_meta, &c->held_meta_cap, (size_t)n * params->workers * kHeldMeta))) return rc;
   }
-  int max_spheres = 1, max_pairs = 0, max_env = 0;
+  int max_spheres = 1, max_pairs = 0, max_env = 0, max_dof = 1;
   for (int p = 0; p < n; ++p) {
     const prrtc_problem& pb = problems[p];
     const RobotHeader& H = pb.robot->h->h;
+    max_dof = std::max(max_dof, H.dof);
     ProblemDesc& D = c->h_desc[p];
     std::memset(&D, 0, sizeof(D));
     D.robot = pb.robot->d;
@@ -1120,6 +1125,26 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       plan_launch_config(n, params->mode, blocks, warps, max_spheres, max_pairs, max_env, c->sms, params->workers);
   if (cfg.smem > 227 * 1024) return fail(PRRTC_ERR_UNSUPPORTED, "robot + environment exceed shared memory");
   const int head_rows = (n == 1) ? std::min(kHeadRows, params->path_capacity) : 0;
+  // A batch copies the first rows of every path back with its results; only a
+  // longer path needs the gather after the results are read.
+  const int batch_head = (n > 1) ? std::min(kBatchHeadRows, params->path_capacity) : 0;
+  const int head_stride = batch_head * max_dof;
+  if (batch_head && (size_t)n * head_stride > c->heads_cap) {
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_heads);
+    cudaFreeHost(c->h_heads);
+    c->d_heads = nullptr;
+    c->h_heads = nullptr;
+    c->heads_cap = 0;
+    const size_t want = (size_t)n * head_stride;
+    if (cudaMalloc(&c->d_heads, want * sizeof(float)) != cudaSuccess ||
+        cudaMallocHost(&c->h_heads, want * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PRRTC_ERR_OOM, "path head buffer allocation failed");
+    }
+    c->heads_cap = want;
+    c->arena_gen++;  // the captured launch sequence holds the old buffers
+  }
 
   // Host half of the learned inference (grouping, staging), before the timed
   // device work like the descriptors: one batch per distinct proposal.
@@ -1204,6 +1229,12 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     if (head_rows)
       CK(cudaMemcpyAsync(c->h_path_head, c->paths, (size_t)head_rows * c->h_desc[0].dof * sizeof(float),
                          cudaMemcpyDeviceToHost, c->stream));
+    if (batch_head) {
+      e = launch_gather_heads(c->d_desc, c->d_state, n, batch_head, head_stride, c->d_heads, c->stream);
+      if (e != cudaSuccess) return cuda_fail("path head launch", e);
+      CK(cudaMemcpyAsync(c->h_heads, c->d_heads, (size_t)n * head_stride * sizeof(float), cudaMemcpyDeviceToHost,
+                         c->stream));
+    }
     return PRRTC_OK;
   };
   static const bool no_graph = std::getenv("PRRTC_NO_GRAPH") != nullptr;
@@ -1212,7 +1243,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   } else {
     const DeviceCtx::GraphKey key{n, cfg.grid, cfg.warps, cfg.smem, cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes,
                                   max_spheres, max_pairs, max_env, c->arena_gen, head_rows * c->h_desc[0].dof,
-                                  cfg.lockstep ? 1 : 0, G.obstacle_tile};
+                                  cfg.lockstep ? 1 : 0, G.obstacle_tile, head_stride};
     if (!c->gexec || !(c->gkey == key)) {
       if (c->gexec) cudaGraphExecDestroy(c->gexec);
       c->gexec = nullptr;
@@ -1255,7 +1286,11 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
     c->h_offsets[p + 1] = total;
   }
   const bool from_head = head_rows > 0 && status[0] == PRRTC_SOLVED && c->h_state[0].path_n <= head_rows;
-  if (from_head) {
+  bool from_heads = batch_head > 0;
+  for (int p = 0; p < n && from_heads; ++p)
+    if (status[p] == PRRTC_SOLVED && c->h_state[p].path_n > batch_head) from_heads = false;
+  const bool gathered = !from_head && !from_heads && total > 0;
+  if (from_head || (from_heads && total > 0)) {
     if ((size_t)total > c->packed_cap) {
       cudaFreeHost(c->h_packed);
       cudaFree(c->d_packed);
@@ -1269,8 +1304,15 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
       }
       c->packed_cap = (size_t)std::max(total, 1);
     }
-    std::memcpy(c->h_packed, c->h_path_head, (size_t)total * sizeof(float));
-  } else if (total > 0) {
+    if (from_head) {
+      std::memcpy(c->h_packed, c->h_path_head, (size_t)total * sizeof(float));
+    } else {
+      for (int p = 0; p < n; ++p)
+        if (status[p] == PRRTC_SOLVED)
+          std::memcpy(c->h_packed + c->h_offsets[p], c->h_heads + (size_t)p * head_stride,
+                      (size_t)(c->h_offsets[p + 1] - c->h_offsets[p]) * sizeof(float));
+    }
+  } else if (gathered) {
     if ((size_t)total > c->packed_cap) {
       cudaFree(c->d_packed);
       cudaFreeHost(c->h_packed);
@@ -1306,10 +1348,11 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   L.smem_bytes = cfg.smem;
   L.problems = n;
   L.h2d_bytes = (int64_t)n * (int64_t)sizeof(ProblemDesc) + (int64_t)sizeof(PlanGlobals) +
-                (total > 0 && !from_head ? (int64_t)(n + 1) * (int64_t)sizeof(int) : 0);
+                (gathered ? (int64_t)(n + 1) * (int64_t)sizeof(int) : 0);
   L.d2h_bytes = (int64_t)n * (int64_t)sizeof(ProblemState) + (int64_t)sizeof(PlanGlobals) +
-                (from_head ? (int64_t)head_rows * c->h_desc[0].dof : (int64_t)total) * (int64_t)sizeof(float);
-  L.kernels = 3 + (total > 0 && !from_head ? 1 : 0);
+                ((int64_t)head_rows * c->h_desc[0].dof + (int64_t)n * head_stride + (gathered ? total : 0)) *
+                    (int64_t)sizeof(float);
+  L.kernels = 3 + (batch_head ? 1 : 0) + (gathered ? 1 : 0);
   const unsigned long long t0 = c->h_glob->t0;
   for (int p = 0; p < n; ++p) {
     const ProblemState& S = c->h_state[p];

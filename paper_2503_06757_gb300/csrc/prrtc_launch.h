@@ -185,6 +185,11 @@ cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, in
 // is problem p's float range (n + 1 entries, device memory).
 cudaError_t launch_gather_paths(const ProblemDesc* desc, const int* offsets, int n, float* out, cudaStream_t stream);
 
+// The first `rows` rows of each solved problem's path (dof floats per row)
+// into out + p * stride; stride >= rows * dof.
+cudaError_t launch_gather_heads(const ProblemDesc* desc, const ProblemState* state, int n, int rows, int stride,
+                                float* out, cudaStream_t stream);
+
 // Distance fields (prrtc_esdf.cu): occupancy of voxel centres inside the
 // environment's primitives, and the signed distance transform of an
 // occupancy grid (tmp_a, tmp_b: V int2 each).

@@ -1086,6 +1086,21 @@ __global__ void gather_paths_kernel(const ProblemDesc* __restrict__ descs, const
   for (int k = threadIdx.x; k < count; k += blockDim.x) out[(size_t)begin + k] = src[k];
 }
 
+// The first `rows` path rows of every solved problem into a fixed slot of
+// `stride` floats per problem, so that a batch's paths come back with its
+// results in one copy (no gather sized on the host in between).
+__global__ void gather_heads_kernel(const ProblemDesc* __restrict__ descs, const ProblemState* __restrict__ states,
+                                    int n, int rows, int stride, float* __restrict__ out) {
+  const int p = blockIdx.x;
+  if (p >= n) return;
+  const ProblemState& S = states[p];
+  const int m = (S.solved && S.path_status == PRRTC_SOLVED) ? min(S.path_n, rows) : 0;
+  const int count = m * descs[p].dof;
+  const float* src = descs[p].path;
+  float* dst = out + (size_t)p * stride;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
+}
+
 }  // namespace
 
 cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, int max_spheres, int max_pairs,
@@ -1189,6 +1204,13 @@ cudaError_t launch_record_usage(const ProblemDesc* desc, ProblemState* state, in
                                 const int* idx) {
   if (n <= 0) return cudaSuccess;
   record_usage_kernel<<<(n + 127) / 128, 128, 0, stream>>>(desc, state, n, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_heads(const ProblemDesc* desc, const ProblemState* state, int n, int rows, int stride,
+                                float* out, cudaStream_t stream) {
+  if (n <= 0 || rows <= 0) return cudaSuccess;
+  gather_heads_kernel<<<n, 128, 0, stream>>>(desc, state, n, rows, stride, out);
   return cudaGetLastError();
 }
 

@@ -108,6 +108,28 @@ def test_serial_batch_equals_serial_alone(boxes8_problems):
         assert alone["iterations"] == batch[k]["iterations"]
 
 
+def test_batch_paths_come_back_with_the_results():
+    """A batch copies the first 32 rows of every path back with its results; a
+    longer path takes the gather after the results are read.  Either way each
+    problem's path equals the one it gets alone (serial mode: bitwise)."""
+    robot = H.point_robot()
+    rb, ev = P.make_robot(robot), P.make_env(H.empty_scene())
+    s = np.array([0.1, 0.1], np.float32)
+    prm = P.params(mode=P.MODE_SERIAL, range=F32(0.02), resolution=F32(0.01), goal_bias=1.0, max_iters=200)
+    short = [(rb, ev, s, np.array([0.15, 0.12], np.float32), 1, k) for k in range(3)]
+    long_ = short + [(rb, ev, s, np.array([1.1, 1.1], np.float32), 1, 3)]
+    for items, want_gather in ((short, False), (long_, True)):
+        batch = P.prrtc_plan_batch(items, prm)
+        st = P.prrtc_last_launch_stats()
+        assert st["kernels"] == (5 if want_gather else 4), st["kernels"]
+        rows = [len(r["path"]) for r in batch]
+        assert (max(rows) > 32) == want_gather, rows
+        for k, it in enumerate(items):
+            alone = P.prrtc_plan_batch([it], prm)[0]
+            assert alone["status"] == batch[k]["status"] == P.SOLVED
+            np.testing.assert_array_equal(alone["path"], batch[k]["path"])
+
+
 def test_plan_batch_object_equals_list_call(boxes8_problems):
     """PlanBatch (marshalled once, run many times, results as columns) returns what
     prrtc_plan_batch returns, run after run (serial mode: bitwise)."""
