@@ -259,7 +259,13 @@ __device__ void extract_path(const Ctx& c, int s, int js, int jo) {
   // it was linked; an entry still unset in the copy falls back to the global
   // read.
   const int area = (c.R->n_spheres + c.R->dof) * 96;  // ints
-  const int n0 = min(ld_relaxed(&c.S->count[0]), D->cap), n1 = min(ld_relaxed(&c.S->count[1]), D->cap);
+  int n0 = 0, n1 = 0;
+  if (c.lane == 0) {
+    n0 = min(ld_relaxed(&c.S->count[0]), D->cap);
+    n1 = min(ld_relaxed(&c.S->count[1]), D->cap);
+  }
+  n0 = __shfl_sync(kFull, n0, 0);
+  n1 = __shfl_sync(kFull, n1, 0);
   const bool in_smem = n0 + n1 <= area / 2;
   int* sp = reinterpret_cast<int*>(c.stage);
   if (in_smem) {
@@ -450,7 +456,12 @@ __device__ void worker(const Ctx& c) {
       if (lane == 0) atomicExch(&S->done, 1);
       break;
     }
-    if (g->time_limit_ns && globaltimer_ns() - g->t0 > g->time_limit_ns) {
+    // Every value a warp-wide decision rests on is read by lane 0 and broadcast:
+    // lanes that load a counter or a clock themselves may see different values
+    // (other warps change them, and the lanes need not load in one instruction).
+    int late = 0;
+    if (lane == 0) late = g->time_limit_ns && globaltimer_ns() - g->t0 > g->time_limit_ns;
+    if (__shfl_sync(kFull, late, 0)) {
       if (lane == 0) {
         S->timed_out = 1;
         atomicExch(&S->done, 1);
@@ -460,8 +471,13 @@ __device__ void worker(const Ctx& c) {
     if (lane == 0) c.cnt->iterations++;
 
     // Alg. 1 line 3: extend the smaller tree (ties: T_a).
-    const int na = min(ld_relaxed(&S->count[0]), cap);
-    const int nb = min(ld_relaxed(&S->count[1]), cap);
+    int na = 0, nb = 0;
+    if (lane == 0) {
+      na = min(ld_relaxed(&S->count[0]), cap);
+      nb = min(ld_relaxed(&S->count[1]), cap);
+    }
+    na = __shfl_sync(kFull, na, 0);
+    nb = __shfl_sync(kFull, nb, 0);
     const int s = (na <= nb) ? 0 : 1;
     const int o = 1 - s;
     const int n_s = s ? nb : na;
@@ -486,7 +502,9 @@ __device__ void worker(const Ctx& c) {
     // (every comparison with NaN is false).
     const bool dd = g->dd_radius > 0.f;
     if (dd && !goal_sample) {
-      if (dist > __ldcg(D->radius[s] + nn)) {
+      float rad = 0.f;
+      if (lane == 0) rad = __ldcg(D->radius[s] + nn);  // other warps adapt it
+      if (dist > __shfl_sync(kFull, rad, 0)) {
         if (lane == 0) c.cnt->dd_rejected++;
         continue;
       }
@@ -540,7 +558,9 @@ __device__ void worker(const Ctx& c) {
       prev = added;
       if (phase == 0) {
         // line 8: nearest node of T_o to c_new, and the connect length.
-        const int n_o = min(ld_relaxed(&S->count[o]), cap);
+        int n_o = 0;
+        if (lane == 0) n_o = min(ld_relaxed(&S->count[o]), cap);
+        n_o = __shfl_sync(kFull, n_o, 0);
         nno = nearest(D->nodes[o], n_o, dpad, c.v.b, lane, &c.cnt->nn_nodes);
         ct = row_elem(D->nodes[o], nno, dpad, lane);
         const float dd = ct - cnew;
