@@ -382,10 +382,23 @@ static __device__ __noinline__ unsigned long long env_three_stage(const float4* 
       const int b0 = base + 32 * h;
       const uint32_t ca = __ballot_sync(kFull, na[h]), co = __ballot_sync(kFull, no[h]);
       const uint32_t cc = __ballot_sync(kFull, nc[h]), cs = __ballot_sync(kFull, ns[h]);
-      if (b0 < n_aabb) hit |= frame_stages_bc<kAabb>(ea, b0, ca, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kAabb]);
-      if (b0 < n_obb) hit |= frame_stages_bc<kObb>(eo, b0, co, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kObb]);
-      if (b0 < n_cyl) hit |= frame_stages_bc<kCyl>(ec, b0, cc, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kCyl]);
-      if (b0 < n_sph) hit |= frame_stages_bc<kSph>(es, b0, cs, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kSph]);
+      // a type without stage-A candidates (warp-uniform) needs no stages B and C
+      if (b0 < n_aabb) {
+        if (ca) hit |= frame_stages_bc<kAabb>(ea, b0, ca, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kAabb]);
+        else t[kAabb] += 1u;
+      }
+      if (b0 < n_obb) {
+        if (co) hit |= frame_stages_bc<kObb>(eo, b0, co, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kObb]);
+        else t[kObb] += 1u;
+      }
+      if (b0 < n_cyl) {
+        if (cc) hit |= frame_stages_bc<kCyl>(ec, b0, cc, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kCyl]);
+        else t[kCyl] += 1u;
+      }
+      if (b0 < n_sph) {
+        if (cs) hit |= frame_stages_bc<kSph>(es, b0, cs, bx, by, bz, br, stage, sph, s0, s1, active, lane, t[kSph]);
+        else t[kSph] += 1u;
+      }
     }
   }
   return pack_tests(hit, t);
