@@ -108,7 +108,7 @@ struct DeviceCtx {
   // CUDA graph of the launch sequence, keyed by everything it bakes in
   struct GraphKey {
     int n, grid, warps, smem, robot_bytes, env_bytes, stage_bytes, max_spheres, max_pairs, max_env, gen, head,
-        lockstep, tile, batch_head;
+        lockstep, tile, batch_head, lean;
     bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
   };
   GraphKey gkey{};
@@ -1123,6 +1123,8 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   }
   const PlanLaunch cfg =
       plan_launch_config(n, params->mode, blocks, warps, max_spheres, max_pairs, max_env, c->sms, params->workers);
+  bool lean = params->sampler == PRRTC_SAMPLER_PHILOX && !cfg.lockstep;
+  for (int p = 0; p < n && lean; ++p) lean = problem_is_lean(problems[p].robot->h->h, c->h_desc[p]);
   if (cfg.smem > 227 * 1024) return fail(PRRTC_ERR_UNSUPPORTED, "robot + environment exceed shared memory");
   const int head_rows = (n == 1) ? std::min(kHeadRows, params->path_capacity) : 0;
   // A batch copies the first rows of every path back with its results; only a
@@ -1219,7 +1221,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
         launch_setup(c->d_desc, c->d_state, n, max_spheres, max_pairs, max_env, c->stream, nullptr, &c->d_glob->error);
     if (e != cudaSuccess) return cuda_fail("setup launch", e);
     CK(cudaEventRecordWithFlags(c->ev[1], c->stream, ev_flags));
-    e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, G.obstacle_tile, c->stream);
+    e = launch_plan(c->d_glob, c->d_desc, c->d_state, cfg, G.obstacle_tile, lean, c->stream);
     if (e != cudaSuccess) return cuda_fail("plan launch", e);
     CK(cudaEventRecordWithFlags(c->ev[2], c->stream, ev_flags));
     e = launch_record_usage(c->d_desc, c->d_state, n, c->stream);
@@ -1243,7 +1245,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   } else {
     const DeviceCtx::GraphKey key{n, cfg.grid, cfg.warps, cfg.smem, cfg.robot_bytes, cfg.env_bytes, cfg.stage_bytes,
                                   max_spheres, max_pairs, max_env, c->arena_gen, head_rows * c->h_desc[0].dof,
-                                  cfg.lockstep ? 1 : 0, G.obstacle_tile, head_stride};
+                                  cfg.lockstep ? 1 : 0, G.obstacle_tile, head_stride, lean ? 1 : 0};
     if (!c->gexec || !(c->gkey == key)) {
       if (c->gexec) cudaGraphExecDestroy(c->gexec);
       c->gexec = nullptr;
@@ -1353,6 +1355,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
                 ((int64_t)head_rows * c->h_desc[0].dof + (int64_t)n * head_stride + (gathered ? total : 0)) *
                     (int64_t)sizeof(float);
   L.kernels = 3 + (batch_head ? 1 : 0) + (gathered ? 1 : 0);
+  L.lean_kernel = lean ? 1 : 0;
   const unsigned long long t0 = c->h_glob->t0;
   for (int p = 0; p < n; ++p) {
     const ProblemState& S = c->h_state[p];

@@ -460,14 +460,16 @@ struct EdgeQ {
 // from the distal end back (three stages per link) and the whole warp returns
 // true as soon as any active lane collides (the edge verdict).  The joint loop
 // is a runtime loop so that the obstacle loops exist once in the code.
-template <bool kWarpVote, int kTile = 32, class QS>
+template <bool kWarpVote, int kTile = 32, bool kLean = false, class QS>
 __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R, const uint32_t* __restrict__ pair,
                                                const float* __restrict__ thr, const float4* __restrict__ env,
                                                int n_aabb, int n_obb, int n_cyl, int n_sph, const EsdfGrid& grid,
                                                float* __restrict__ stage, const QS& qs, bool active, int lane,
                                                WarpCount* wc) {
   static_assert(kTile == 32 || kTile == 64, "obstacle tile is 32 or 64 primitives per type");
-  const bool has_grid = grid.v != nullptr;
+  // kLean: an instance for batches without distance fields whose links all have
+  // bounding spheres (the host checks); the other paths are not compiled in.
+  const bool has_grid = !kLean && grid.v != nullptr;
   const bool has_prims = (n_aabb | n_obb | n_cyl | n_sph) != 0;
   const int dof = R->dof;
   // edge warps read the problem's solved flag now and look at it after
@@ -590,7 +592,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       const int s0 = R->sph_begin[i], s1 = R->sph_begin[i + 1];
       if (s0 == s1) continue;
       const float4 cb = R->coarse[i];
-      const bool two = R->two_stage && cb.w > 0.f && has_prims;  // uniform
+      const bool two = kLean || (R->two_stage && cb.w > 0.f && has_prims);  // uniform
       if (two) {
         if (has_grid) {
           for (int s = s0; s < s1; ++s) {

@@ -164,7 +164,7 @@ extern "C" int prrtc_plan_noalloc(const prrtc_robot* robot, const prrtc_env* env
   if (e == cudaSuccess)
     e = launch_setup(&S->desc, &S->state, 1, H.n_spheres + H.dof, H.n_pairs, ev.n_float4(), stream, nullptr,
                      &S->glob.error);
-  if (e == cudaSuccess) e = launch_plan(&S->glob, &S->desc, &S->state, cfg, G.obstacle_tile, stream);
+  if (e == cudaSuccess) e = launch_plan(&S->glob, &S->desc, &S->state, cfg, G.obstacle_tile, false, stream);
   if (e == cudaSuccess) e = launch_record_usage(&S->desc, &S->state, 1, stream);
   ProblemState st;
   PlanGlobals gout;

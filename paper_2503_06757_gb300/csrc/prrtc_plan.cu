@@ -165,7 +165,7 @@ __device__ __noinline__ int nearest(const float* __restrict__ nodes, int n, int 
 // Alg. 2 lines 3-5: the N states a + (k/N)(b - a), k = 1..N, of the edge held
 // in c.v.a / c.v.b, one per lane (several passes if N > 32); false at the
 // first colliding state.  kTile: obstacles per type per first-stage round.
-template <int kTile>
+template <int kTile, bool kLean>
 __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
   if (c.lane == 0) {
     c.cnt->edges++;
@@ -177,7 +177,7 @@ __device__ __forceinline__ bool edge_free(const Ctx& c, int N) {
     const bool active = k <= N;
     const int kk = active ? k : N;
     const EdgeQ qs{c.v.a, c.v.b, __fdiv_rn((float)kk, fN), kk == N, &c.S->solved};
-    if (state_collides<true, kTile>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
+    if (state_collides<true, kTile, kLean>(c.R, c.pair, c.thr, c.env, c.D->env.n_aabb, c.D->env.n_obb, c.D->env.n_cyl,
                                     c.D->env.n_sph, c.D->env.esdf, c.stage, qs, active, c.lane, c.cnt)) {
       __syncwarp();  // lane 0 may have just set the flag
       if (c.cnt->aborted) {
@@ -399,6 +399,7 @@ __device__ __forceinline__ float mixture_draw(const float* __restrict__ gmm, con
 // draws learned-vs-uniform, word 21 the component, words 22.. Box-Muller
 // pairs.  The Halton sampler takes point it + 1 + offset instead of the
 // uniform words (point 0 is the origin of the unit cube).
+template <bool kLean>
 __device__ __forceinline__ float random_config(const Ctx& c, int it, int o, bool* goal_sample) {
   const PlanGlobals* g = c.g;
   const ProblemDesc* D = c.D;
@@ -412,8 +413,9 @@ __device__ __forceinline__ float random_config(const Ctx& c, int it, int o, bool
   const uint32_t wl = __shfl_sync(kFull, w, 20);
   *goal_sample = (w0 >> 8) < g->bias_thr;
   if (*goal_sample) return row_elem(D->nodes[o], 0, D->dpad, lane);
-  if (D->gmm && (wl >> 8) < g->learned_thr) return mixture_draw(D->gmm, R, D->pid, (uint32_t)it, key, w, lane, dof);
-  if (g->sampler == PRRTC_SAMPLER_HALTON)
+  if (!kLean && D->gmm && (wl >> 8) < g->learned_thr)
+    return mixture_draw(D->gmm, R, D->pid, (uint32_t)it, key, w, lane, dof);
+  if (!kLean && g->sampler == PRRTC_SAMPLER_HALTON)
     return (lane < dof) ? fmaf(halton_coord((uint32_t)it + 1u + g->halton_offset, lane), R->span[lane], R->lo[lane])
                         : 0.f;
   return (lane < dof) ? fmaf(u24(wj), R->span[lane], R->lo[lane]) : 0.f;
@@ -421,7 +423,7 @@ __device__ __forceinline__ float random_config(const Ctx& c, int it, int o, bool
 
 // Alg. 1 iterations of one worker warp on one problem until it is solved,
 // out of budget or out of time.  Lane j holds element j of every vector.
-template <int kTile>
+template <int kTile, bool kLean>
 __device__ void worker(const Ctx& c) {
   const PlanGlobals* g = c.g;
   const ProblemDesc* D = c.D;
@@ -484,7 +486,7 @@ __device__ void worker(const Ctx& c) {
 
     // line 4: RANDOM_CONFIG
     bool goal_sample;
-    const float crand = random_config(c, it, o, &goal_sample);
+    const float crand = random_config<kLean>(c, it, o, &goal_sample);
     if (mine) c.v.rnd[lane] = crand;
     __syncwarp();
 
@@ -539,7 +541,7 @@ __device__ void worker(const Ctx& c) {
         if (lane == 0) solved = ld_volatile(&S->solved);
         if (__shfl_sync(kFull, solved, 0)) break;
       }
-      const bool free_edge = edge_free<kTile>(c, N);
+      const bool free_edge = edge_free<kTile, kLean>(c, N);
       if (phase == 0 && dd && lane == 0) {
         // adaptive radius of the nearest node (Jaillet et al. 2005): a bounded
         // radius grows after a free extension; a collision bounds an unbounded
@@ -645,7 +647,7 @@ __device__ void lockstep_iteration(const Ctx& c, int it, int s, int n_s, int n_o
   if (lane == 0) c.cnt->iterations++;
   do {
     bool goal_sample;
-    const float crand = random_config(c, it, o, &goal_sample);
+    const float crand = random_config<false>(c, it, o, &goal_sample);
     if (mine) c.v.rnd[lane] = crand;
     __syncwarp();
     // line 5: nearest node of T_s as the round found it
@@ -678,7 +680,7 @@ __device__ void lockstep_iteration(const Ctx& c, int it, int s, int n_s, int n_o
     float ct = 0.f, Dd = 0.f, bval = cnew;
     int n_ext = 0;
     for (int phase = 0;; ++phase) {
-      const bool free_edge = edge_free<32>(c, N);  // lockstep: 32-obstacle tiles
+      const bool free_edge = edge_free<32, false>(c, N);  // lockstep: 32-obstacle tiles
       ++edges;
       if (phase == 0 && dd) {
         dd_node = nn;
@@ -855,7 +857,7 @@ __device__ int pick_problem(PlanGlobals* g, const ProblemState* states) {
 // The planner launch: blocks take problems from the work queue, stage each
 // problem's robot and environment in shared memory and run its workers --
 // independent warps (async and serial modes) or the lockstep rounds.
-template <bool kLockstep, int kTile>
+template <bool kLockstep, int kTile, bool kLean>
 __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                           ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
                                           int warp_floats) {
@@ -937,7 +939,7 @@ __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const Pro
     if constexpr (kLockstep)
       lockstep_problem(c, warp, blockDim.x >> 5);
     else
-      worker<kTile>(c);
+      worker<kTile, kLean>(c);
     // flush this warp's counters into the problem
     __syncwarp();
     if (lane < 14) {
@@ -955,20 +957,25 @@ __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const Pro
 }
 
 // One instance per obstacle tile (32 or 64 primitives per type per first-stage
-// round): a tile's check code is all that the launched kernel holds.
-template <int kTile>
+// round) and feature set: the launched kernel holds only the check code of its
+// tile, and the lean instances (kLean) leave out the learned mixture draw, the
+// Halton sampler, distance fields and links without a bounding sphere, for
+// batches that use none of them (fewer instructions to fetch on the hot path).
+template <int kTile, bool kLean>
 __global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                              ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
                                              int warp_floats) {
-  plan_body<false, kTile>(g, descs, states, robot_bytes, env_bytes, warp_floats);
+  plan_body<false, kTile, kLean>(g, descs, states, robot_bytes, env_bytes, warp_floats);
 }
-template __global__ void plan_kernel<32>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
-template __global__ void plan_kernel<64>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
+template __global__ void plan_kernel<32, false>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
+template __global__ void plan_kernel<64, false>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
+template __global__ void plan_kernel<32, true>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
+template __global__ void plan_kernel<64, true>(PlanGlobals*, const ProblemDesc*, ProblemState*, int, int, int);
 
 __global__ void __maxnreg__(128) lockstep_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                                  ProblemState* __restrict__ states, int robot_bytes, int env_bytes,
                                                  int warp_floats) {
-  plan_body<true, 32>(g, descs, states, robot_bytes, env_bytes, warp_floats);
+  plan_body<true, 32, false>(g, descs, states, robot_bytes, env_bytes, warp_floats);
 }
 
 // Reject a start or goal in collision (Alg. 1 lines 1-2): warp 0 checks the
@@ -1137,23 +1144,27 @@ cudaError_t launch_setup(const ProblemDesc* desc, ProblemState* state, int n, in
 
 // Resident planner blocks per SM for a block shape, cached: the occupancy
 // query and the shared-memory attribute cost host time on every call.
-static const void* plan_kernel_fn(bool lockstep, int tile) {
+static const void* plan_kernel_fn(bool lockstep, int tile, bool lean) {
   if (lockstep) return reinterpret_cast<const void*>(lockstep_kernel);
-  return tile == 64 ? reinterpret_cast<const void*>(plan_kernel<64>) : reinterpret_cast<const void*>(plan_kernel<32>);
+  if (lean)
+    return tile == 64 ? reinterpret_cast<const void*>(plan_kernel<64, true>)
+                      : reinterpret_cast<const void*>(plan_kernel<32, true>);
+  return tile == 64 ? reinterpret_cast<const void*>(plan_kernel<64, false>)
+                    : reinterpret_cast<const void*>(plan_kernel<32, false>);
 }
 
-int resident_blocks_per_sm(int warps, int smem, bool lockstep, int tile) {
+int resident_blocks_per_sm(int warps, int smem, bool lockstep, int tile, bool lean) {
   static std::mutex mu;
   static std::map<std::pair<int, int>, int> cache;
   static std::map<int, int> attr_smem;  // per (device, kernel): the attribute value set so far
   int dev = 0;
   cudaGetDevice(&dev);
-  const int kid = 3 * dev + (lockstep ? 2 : tile == 64 ? 1 : 0);
+  const int kid = 5 * dev + (lockstep ? 4 : (tile == 64 ? 1 : 0) + (lean ? 2 : 0));
   const std::pair<int, int> key{warps + 64 * kid, smem};
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  const void* fn = plan_kernel_fn(lockstep, tile);
+  const void* fn = plan_kernel_fn(lockstep, tile, lean);
   if (smem > attr_smem[kid]) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr_smem[kid] = smem;
@@ -1181,7 +1192,7 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
   c.stage_bytes = (int)sizeof(WarpCount) + kWarpVecFloats * (int)sizeof(float) + stage_bytes(max_spheres);  // per warp
   c.smem = c.robot_bytes + c.env_bytes + c.warps * c.stage_bytes;
   // both tile instances take the same registers (capped) and shared memory
-  const int per_sm = resident_blocks_per_sm(c.warps, c.smem, c.lockstep, 32);
+  const int per_sm = resident_blocks_per_sm(c.warps, c.smem, c.lockstep, 32, false);
   int resident = per_sm * sm_count;
   if (blocks > 0) {
     c.grid = blocks;
@@ -1199,22 +1210,20 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
 }
 
 cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
-                        int obstacle_tile, cudaStream_t stream) {
+                        int obstacle_tile, bool lean, cudaStream_t stream) {
   // sets the shared-memory attribute once per size and kernel
-  resident_blocks_per_sm(cfg.warps, cfg.smem, cfg.lockstep, obstacle_tile);
+  resident_blocks_per_sm(cfg.warps, cfg.smem, cfg.lockstep, obstacle_tile, lean);
   cudaError_t e;
   if (cfg.lockstep)
     lockstep_kernel<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
                                                                     cfg.robot_bytes, cfg.env_bytes,
                                                                     cfg.stage_bytes / (int)sizeof(float));
-  else if (obstacle_tile == 64)
-    plan_kernel<64><<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
-                                                                    cfg.robot_bytes, cfg.env_bytes,
-                                                                    cfg.stage_bytes / (int)sizeof(float));
-  else
-    plan_kernel<32><<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state,
-                                                                    cfg.robot_bytes, cfg.env_bytes,
-                                                                    cfg.stage_bytes / (int)sizeof(float));
+  else {
+    auto* fn = lean ? (obstacle_tile == 64 ? plan_kernel<64, true> : plan_kernel<32, true>)
+                    : (obstacle_tile == 64 ? plan_kernel<64, false> : plan_kernel<32, false>);
+    fn<<<cfg.grid, cfg.warps * 32, cfg.smem, stream>>>(const_cast<PlanGlobals*>(g), desc, state, cfg.robot_bytes,
+                                                       cfg.env_bytes, cfg.stage_bytes / (int)sizeof(float));
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaSuccess;

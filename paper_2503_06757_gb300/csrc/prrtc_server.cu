@@ -269,7 +269,7 @@ bool server_round(prrtc_server* s) {
   }
   cudaMemcpyAsync(s->d_active, s->h_active, n_active * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(s->d_glob, s->h_glob, sizeof(PlanGlobals), cudaMemcpyHostToDevice, st);
-  launch_plan(s->d_glob, s->d_desc, s->d_state, cfg, G.obstacle_tile, st);
+  launch_plan(s->d_glob, s->d_desc, s->d_state, cfg, G.obstacle_tile, false, st);
   launch_record_usage(s->d_desc, s->d_state, n_active, st, s->d_active);
   cudaMemcpyAsync(s->h_state, s->d_state, (size_t)s->slots * sizeof(ProblemState), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(s->h_glob, s->d_glob, sizeof(PlanGlobals), cudaMemcpyDeviceToHost, st);

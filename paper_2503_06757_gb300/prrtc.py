@@ -68,7 +68,7 @@ class prrtc_launch_stats(C.Structure):
                 ("pair_tests", C.c_int64), ("fk_states", C.c_int64), ("nn_nodes", C.c_int64),
                 ("iterations", C.c_int64), ("grid", C.c_int32), ("block_threads", C.c_int32),
                 ("smem_bytes", C.c_int32), ("problems", C.c_int32), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("reserved_", C.c_int32),
+                ("d2h_bytes", C.c_int64), ("kernels", C.c_int32), ("lean_kernel", C.c_int32),
                 ("prep_ms", C.c_double), ("prim_tests", C.c_int64 * 4), ("dd_rejected", C.c_int64),
                 ("verdict_states", C.c_int64), ("infer_ms", C.c_double)]
 

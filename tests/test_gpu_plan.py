@@ -130,6 +130,40 @@ def test_batch_paths_come_back_with_the_results():
             np.testing.assert_array_equal(alone["path"], batch[k]["path"])
 
 
+def test_lean_planner_instance_serves_only_plain_batches(boxes8_problems):
+    """The lean planner instance (no learned draw, Halton, distance fields or
+    one-stage links in its code) is launched only for batches that need none of
+    them, and plans exactly as the full instance: a zero-ratio mixture puts the
+    same problems on the full instance without changing a sample (serial mode,
+    bitwise)."""
+    pbs = boxes8_problems[:3]
+    rbs = [P.make_robot(pb.robot) for pb in pbs]
+    evs = [P.make_env(pb.scene) for pb in pbs]
+    items = [(rbs[k], evs[k], pb.q_start, pb.q_goal, 3, k) for k, pb in enumerate(pbs)]
+    prm = P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14)
+    lean = P.prrtc_plan_batch(items, prm)
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 1
+    dof = pbs[0].robot.dof
+    zero_mix = np.zeros(8 + 16 * dof, np.float32)
+    full = P.prrtc_plan_batch([it + (zero_mix,) for it in items], prm)
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
+    for a, b in zip(lean, full):
+        assert a["status"] == b["status"] and a["iterations"] == b["iterations"]
+        np.testing.assert_array_equal(a["path"], b["path"])
+    # each feature the lean instance leaves out puts the batch on the full one
+    P.prrtc_plan_batch(items, P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14, sampler=P.SAMPLER_HALTON))
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
+    rbs[0].set_two_stage(False)
+    P.prrtc_plan_batch(items, prm)
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
+    rbs[0].set_two_stage(True)
+    empty = P.make_env(H.empty_scene())
+    P.prrtc_plan_batch([(rbs[0], empty, pbs[0].q_start, pbs[0].q_goal, 3, 0)] + items[1:], prm)
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
+    P.prrtc_plan_batch(items, prm)
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 1
+
+
 def test_plan_batch_object_equals_list_call(boxes8_problems):
     """PlanBatch (marshalled once, run many times, results as columns) returns what
     prrtc_plan_batch returns, run after run (serial mode: bitwise)."""
