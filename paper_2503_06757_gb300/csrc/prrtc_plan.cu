@@ -233,7 +233,9 @@ __device__ __forceinline__ int parent_of(const int* par, int node, int* err) {
 // PATH(T_a, T_b) by the winning warp: root(T_a) .. join .. root(T_b).  The two
 // join rows hold the same configuration; the copy in T_b is dropped when T_a
 // was extended and vice versa, so the path lists each waypoint once.
-__device__ void extract_path(const Ctx& c, int s, int js, int jo) {
+// Out of line: it runs once per solved problem, and kept inline its code (about
+// a fifth of the planner's) would sit inside the hot iteration loop.
+__device__ __noinline__ void extract_path(const Ctx& c, int s, int js, int jo) {
   const ProblemDesc* D = c.D;
   int err = 0;
   if (c.g->debug_wait_polls) {
