@@ -246,7 +246,8 @@ typedef struct prrtc_launch_stats {
   int64_t d2h_bytes;         /* device -> host bytes copied by the call                */
   int32_t kernels;           /* kernels the call launched                              */
   int32_t lean_kernel;       /* 1: the planner instance without the learned draw, Halton,
-                                distance fields and one-stage links (the batch used none) */
+                                distance fields, oriented boxes and one-stage links (the
+                                batch used none)                                          */
   double prep_ms;            /* from the call's first device work to the setup kernel:
                                 learned-mixture inference and descriptor upload         */
   int64_t prim_tests[4];     /* second-stage tests per primitive type (AABB, oriented

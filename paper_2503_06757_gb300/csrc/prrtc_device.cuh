@@ -353,13 +353,16 @@ __device__ __forceinline__ bool frame_stages_bc(const float4* __restrict__ prims
 // each type per round (one or two per lane), so that a lane's tests of a round
 // are independent; stages B and C then take the round's candidates in order.
 // One instance per tile size: each planner kernel holds only the one it uses.
-template <int kHalves>
+// kObb = false: the instance of the lean planner, whose batches hold no
+// oriented boxes (their tests are not compiled in).
+template <int kHalves, bool kObb>
 static __device__ __noinline__ unsigned long long env_three_stage(const float4* __restrict__ env, int n_aabb,
                                                            int n_obb, int n_cyl, int n_sph, float ux, float uy,
                                                            float uz, float ur, float bx, float by, float bz, float br,
                                                            const float* __restrict__ stage,
                                                            const float4* __restrict__ sph, int s0, int s1,
                                                            bool active, int lane) {
+  if (!kObb) n_obb = 0;
   uint32_t t[4] = {0, 0, 0, 0};
   bool hit = false;
   const float4* ea = env;
@@ -604,7 +607,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
         const float* gst = stage + (R->n_spheres + i) * 96 + lane;
         const float gx = gst[0], gy = gst[32], gz = gst[64];
         const float4 u = warp_enclosing_sphere(gx, gy, gz, cb.w, active);
-        const unsigned long long r = env_three_stage<kTile / 32>(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z,
+        const unsigned long long r = env_three_stage<kTile / 32, !kLean>(env, n_aabb, n_obb, n_cyl, n_sph, u.x, u.y, u.z,
                                                                  u.w, gx, gy, gz, cb.w, stage, R->sph, s0, s1,
                                                                  active, lane);
         hit |= (r >> 63) != 0;

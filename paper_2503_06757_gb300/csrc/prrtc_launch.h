@@ -175,17 +175,18 @@ PlanLaunch plan_launch_config(int n_problems, int mode, int blocks, int warps, i
 // obstacle_tile: 64 launches the 64-obstacle-tile instance of the async/serial
 // kernel, anything else the 32 one (lockstep always uses 32).  lean: the
 // instance without the learned mixture draw, the Halton sampler, distance
-// fields and one-stage links; only for batches that use none of them
+// fields, oriented boxes and one-stage links; only for batches that use none of
+// them
 // (problem_is_lean).
 cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemState* state, const PlanLaunch& cfg,
                         int obstacle_tile, bool lean, cudaStream_t stream);
 
 // Whether the lean planner instance serves a problem: no mixture, no distance
-// field, at least one primitive, and a bounding sphere on every robot link that
-// has spheres (with the sphere hierarchy on).  The batch is lean when every
+// field, at least one primitive and no oriented box, and a bounding sphere on
+// every robot link that has spheres (with the sphere hierarchy on).  The batch is lean when every
 // problem is and the sampler is Philox.
 inline bool problem_is_lean(const RobotHeader& H, const ProblemDesc& D) {
-  if (D.gmm || D.env.esdf.v || D.env.n_float4() == 0 || !H.two_stage) return false;
+  if (D.gmm || D.env.esdf.v || D.env.n_float4() == 0 || D.env.n_obb || !H.two_stage) return false;
   for (int f = 0; f < H.dof; ++f)
     if (H.sph_begin[f + 1] > H.sph_begin[f] && !(H.coarse[f].w > 0.f)) return false;
   return true;

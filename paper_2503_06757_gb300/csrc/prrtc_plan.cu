@@ -961,8 +961,9 @@ __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const Pro
 // One instance per obstacle tile (32 or 64 primitives per type per first-stage
 // round) and feature set: the launched kernel holds only the check code of its
 // tile, and the lean instances (kLean) leave out the learned mixture draw, the
-// Halton sampler, distance fields and links without a bounding sphere, for
-// batches that use none of them (fewer instructions to fetch on the hot path).
+// Halton sampler, distance fields, oriented boxes and links without a bounding
+// sphere, for batches that use none of them (fewer instructions to fetch on
+// the hot path).
 template <int kTile, bool kLean>
 __global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                              ProblemState* __restrict__ states, int robot_bytes, int env_bytes,

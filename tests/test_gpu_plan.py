@@ -131,8 +131,8 @@ def test_batch_paths_come_back_with_the_results():
 
 
 def test_lean_planner_instance_serves_only_plain_batches(boxes8_problems):
-    """The lean planner instance (no learned draw, Halton, distance fields or
-    one-stage links in its code) is launched only for batches that need none of
+    """The lean planner instance (no learned draw, Halton, distance fields,
+    oriented boxes or one-stage links in its code) is launched only for batches that need none of
     them, and plans exactly as the full instance: a zero-ratio mixture puts the
     same problems on the full instance without changing a sample (serial mode,
     bitwise)."""
@@ -157,6 +157,10 @@ def test_lean_planner_instance_serves_only_plain_batches(boxes8_problems):
     P.prrtc_plan_batch(items, prm)
     assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
     rbs[0].set_two_stage(True)
+    c, sn = np.cos(0.5), np.sin(0.5)
+    turned = H.scene(boxes=[np.concatenate([[0.5, 0.5, 1.5], [0.05, 0.05, 0.05], [c, -sn, 0, sn, c, 0, 0, 0, 1]])])
+    P.prrtc_plan_batch([(rbs[0], P.make_env(turned), pbs[0].q_start, pbs[0].q_goal, 3, 0)] + items[1:], prm)
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
     empty = P.make_env(H.empty_scene())
     P.prrtc_plan_batch([(rbs[0], empty, pbs[0].q_start, pbs[0].q_goal, 3, 0)] + items[1:], prm)
     assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
