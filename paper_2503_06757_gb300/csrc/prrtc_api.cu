@@ -1123,7 +1123,7 @@ static int plan_batch_impl(const prrtc_problem* problems, int32_t n, const prrtc
   }
   const PlanLaunch cfg =
       plan_launch_config(n, params->mode, blocks, warps, max_spheres, max_pairs, max_env, c->sms, params->workers);
-  bool lean = params->sampler == PRRTC_SAMPLER_PHILOX && !cfg.lockstep;
+  bool lean = params->sampler == PRRTC_SAMPLER_PHILOX && !cfg.lockstep && !(params->dd_radius > 0.f);
   for (int p = 0; p < n && lean; ++p) lean = problem_is_lean(problems[p].robot->h->h, c->h_desc[p]);
   if (cfg.smem > 227 * 1024) return fail(PRRTC_ERR_UNSUPPORTED, "robot + environment exceed shared memory");
   const int head_rows = (n == 1) ? std::min(kHeadRows, params->path_capacity) : 0;

@@ -511,7 +511,7 @@ __device__ __forceinline__ bool state_collides(const RobotHeader* __restrict__ R
       float s, c;
       // the hardware sine/cosine (absolute error about 2^-21 on [-pi, pi]: sphere
       // centres within about 1e-6 m of exact FK); the library routine beyond
-      if (fabsf(qi) <= 3.2f)
+      if (kLean || fabsf(qi) <= 3.2f)  // lean batches keep revolute joints within +-3.2
         __sincosf(qi, &s, &c);
       else
         sincosf(qi, &s, &c);

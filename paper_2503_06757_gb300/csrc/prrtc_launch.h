@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "prrtc.h"
@@ -182,13 +183,22 @@ cudaError_t launch_plan(const PlanGlobals* g, const ProblemDesc* desc, ProblemSt
                         int obstacle_tile, bool lean, cudaStream_t stream);
 
 // Whether the lean planner instance serves a problem: no mixture, no distance
-// field, at least one primitive and no oriented box, and a bounding sphere on
-// every robot link that has spheres (with the sphere hierarchy on).  The batch is lean when every
+// field, at least one primitive and no oriented box, a bounding sphere on every
+// robot link that has spheres (with the sphere hierarchy on), and revolute
+// joints within +-3.2 rad.  The batch also needs Philox sampling and no dynamic
+// domain.  The batch is lean when every
 // problem is and the sampler is Philox.
 inline bool problem_is_lean(const RobotHeader& H, const ProblemDesc& D) {
   if (D.gmm || D.env.esdf.v || D.env.n_float4() == 0 || D.env.n_obb || !H.two_stage) return false;
-  for (int f = 0; f < H.dof; ++f)
+  for (int f = 0; f < H.dof; ++f) {
     if (H.sph_begin[f + 1] > H.sph_begin[f] && !(H.coarse[f].w > 0.f)) return false;
+    // every joint value the planner forms lies between the limits, the start and
+    // the goal: within +-3.2 rad the hardware sine/cosine is the one taken
+    const bool revolute = H.jtype[f] == kRevZ || H.jtype[f] == kRevY || H.jtype[f] == kRevX;
+    const float lo = std::min({H.lo[f], D.q_start[f], D.q_goal[f]});
+    const float hi = std::max({H.lo[f] + H.span[f], D.q_start[f], D.q_goal[f]});
+    if (revolute && !(lo >= -3.2f && hi <= 3.2f)) return false;
+  }
   return true;
 }
 

@@ -504,7 +504,7 @@ __device__ void worker(const Ctx& c) {
     // Dynamic-domain sampling (Yershova et al. 2005): a random sample farther
     // than the nearest node's radius ends the iteration.  NaN = unbounded
     // (every comparison with NaN is false).
-    const bool dd = g->dd_radius > 0.f;
+    const bool dd = !kLean && g->dd_radius > 0.f;  // lean batches have it off
     if (dd && !goal_sample) {
       float rad = 0.f;
       if (lane == 0) rad = __ldcg(D->radius[s] + nn);  // other warps adapt it
@@ -963,7 +963,8 @@ __device__ __forceinline__ void plan_body(PlanGlobals* __restrict__ g, const Pro
 // tile, and the lean instances (kLean) leave out the learned mixture draw, the
 // Halton sampler, distance fields, oriented boxes and links without a bounding
 // sphere, for batches that use none of them (fewer instructions to fetch on
-// the hot path).
+// the hot path), and dynamic-domain sampling and the wide-range sine/cosine
+// (revolute joints beyond +-3.2 rad) as well.
 template <int kTile, bool kLean>
 __global__ void __maxnreg__(128) plan_kernel(PlanGlobals* __restrict__ g, const ProblemDesc* __restrict__ descs,
                                              ProblemState* __restrict__ states, int robot_bytes, int env_bytes,

@@ -131,8 +131,8 @@ def test_batch_paths_come_back_with_the_results():
 
 
 def test_lean_planner_instance_serves_only_plain_batches(boxes8_problems):
-    """The lean planner instance (no learned draw, Halton, distance fields,
-    oriented boxes or one-stage links in its code) is launched only for batches that need none of
+    """The lean planner instance (no learned draw, Halton, dynamic domain, distance
+    fields, oriented boxes or one-stage links in its code) is launched only for batches that need none of
     them, and plans exactly as the full instance: a zero-ratio mixture puts the
     same problems on the full instance without changing a sample (serial mode,
     bitwise)."""
@@ -152,6 +152,8 @@ def test_lean_planner_instance_serves_only_plain_batches(boxes8_problems):
         np.testing.assert_array_equal(a["path"], b["path"])
     # each feature the lean instance leaves out puts the batch on the full one
     P.prrtc_plan_batch(items, P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14, sampler=P.SAMPLER_HALTON))
+    assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
+    P.prrtc_plan_batch(items, P.params(mode=P.MODE_SERIAL, tree_capacity=1 << 14, dd_radius=5.0))
     assert P.prrtc_last_launch_stats()["lean_kernel"] == 0
     rbs[0].set_two_stage(False)
     P.prrtc_plan_batch(items, prm)
