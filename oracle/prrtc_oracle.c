@@ -83,7 +83,7 @@ int orc_sample(const orc_robot* r, uint64_t seed, uint32_t problem, uint32_t it,
   return 0;
 }
 
-/* Learned proposal draw (BASELINE's mixture proposal; not in the paper).
+/* Learned proposal draw (the mixture proposal of the learned sampler; not in the paper).
  * Words 20.. of the iteration's stream (Philox blocks 5-9): word 20 decides
  * learned vs uniform, word 21 picks the component, then Box-Muller pairs
  * (u1 from (w >> 8) + 1, so u1 is in (0, 1]) give standard normals. */
