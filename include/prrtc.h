@@ -406,10 +406,10 @@ int prrtc_plan_batch(const prrtc_problem* problems, int32_t n, const prrtc_param
 
 /* Autotuner (the number of concurrent workers is the paper's scaling knob,
  * Sec. IV-C): plan the given problems `trials` times (the same varied seeds
- * for every candidate) and score a candidate by the batch's median time to
- * first solution (setup time plus each problem's device time from launch
- * start to its solution; an unsolved problem counts the whole launch),
- * averaged over the trials.  It picks, one after the other: the launch shape
+ * for every candidate) and score a candidate by the mean of the batch's median
+ * and 95th-percentile time to first solution (setup time plus each problem's
+ * device time from launch start to its solution; an unsolved problem counts
+ * the whole launch), averaged over the trials.  It picks, one after the other: the launch shape
  * (grid size x warps per block; shapes within 2% of the fastest count as
  * equal and the one with the most workers wins), the obstacle tile (32 or
  * 64) and, in async mode, the expansions per claim (1, 2, 4 or 8); a

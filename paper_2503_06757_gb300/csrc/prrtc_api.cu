@@ -1440,11 +1440,12 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
   }
   std::vector<prrtc_problem> pb(problems, problems + n);
   // The score of a candidate: the mean over `trials` runs (the same trial keys
-  // for every candidate) of the batch's median time to first solution -- setup
-  // time plus each problem's device time from launch start to its solution,
-  // an unsolved problem counting the whole launch.  The batch's step time is
-  // the maximum of those times and its mean is led by the few hardest
-  // problems, both noisy; the median follows the typical problem.  The
+  // for every candidate) of the mean of the batch's median and 95th-percentile
+  // time to first solution -- the two quantiles of the planning-time metric --
+  // with setup time plus each problem's device time from launch start to its
+  // solution, an unsolved problem counting the whole launch.  The batch's step
+  // time (the maximum) and mean are led by the few hardest problems and are
+  // noisy; the two quantiles follow the typical and the hard problems.  The
   // choices below keep a default unless a candidate beats it clearly.
   std::vector<double> ttfs(n);
   auto measure = [&](const prrtc_params& q, double* out) -> int {
@@ -1459,8 +1460,9 @@ int prrtc_autotune(const prrtc_problem* problems, int32_t n, const prrtc_params*
         const bool solved = S.solved && S.t_solve >= t0;
         ttfs[p] = solved ? (double)(S.t_solve - t0) * 1e-6 : c->last.kernel_ms;
       }
-      std::nth_element(ttfs.begin(), ttfs.begin() + n / 2, ttfs.end());
-      tot += c->last.setup_ms + ttfs[n / 2];
+      std::sort(ttfs.begin(), ttfs.end());
+      const double p50 = ttfs[n / 2], p95 = ttfs[std::min(n - 1, (int)std::ceil(0.95 * n) - 1)];
+      tot += c->last.setup_ms + 0.5 * (p50 + p95);
     }
     *out = tot / trials;
     return PRRTC_OK;
